@@ -1,0 +1,247 @@
+"""FP64 CPU oracle for transport-based rendering (TEST INFRASTRUCTURE ONLY).
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg may import this package.  The product path (``paper_2609_08722_b300``) never
+does, and the two share no code: the oracle receives the same seeded input arrays
+and recomputes everything from the paper's definitions in ``tbr_oracle.cpp``.
+
+Functions (all FP64, citing the paper's passages in the C++ source):
+  * ``psi_map`` / ``phi_map``     -- Eq. back / Eq. fwd on a batch of points;
+  * ``map_jacobian``             -- their 2x7 Jacobians by dual numbers;
+  * ``render_hard``              -- Eq. chain + Eq. render with indicator coverage;
+  * ``render_soft``              -- Eq. relax + Eq. state;
+  * ``soft_jvp``                 -- forward-mode derivative of the soft render;
+  * ``soft_vjp``                 -- stored-state adjoint (Eq. adjstep, Eq. adjparam);
+  * ``fd_gradient``              -- central finite differences of a linear
+                                    functional of the soft render.
+
+A program is any object with attributes ``cx, cy, theta, length, half_width``
+([n]), ``logits`` ([n, k]), ``palette`` ([k, 3]), ``background`` ([3]) and
+``color_temp`` (float).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tbr_oracle.cpp")
+_LIB = os.path.join(_HERE, "libtbr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+MODE_CLAMP, MODE_FLOOR, MODE_RAWQ, MODE_FLOOR_RAWQ = 0, 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/libtbr_oracle.so`` (g++ -O2 -fopenmp)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-fPIC", "-shared",
+               "-ffp-contract=off", _SRC, "-o", tmp]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Prog(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32), ("k", ctypes.c_int32),
+        ("cx", ctypes.c_void_p), ("cy", ctypes.c_void_p), ("th", ctypes.c_void_p),
+        ("L", ctypes.c_void_p), ("r", ctypes.c_void_p),
+        ("logits", ctypes.c_void_p), ("palette", ctypes.c_void_p),
+        ("background", ctypes.c_double * 3), ("color_temp", ctypes.c_double),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            lib.orc_map.argtypes = [P, i64, dbl, dbl, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int, P, P]
+            lib.orc_map_jacobian.argtypes = [P, i64, dbl, dbl, dbl, dbl, dbl, ctypes.c_int, ctypes.c_int, P]
+            lib.orc_render_hard.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, P, i64, P, P, P, P]
+            lib.orc_render_soft.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
+                                            P, i64, P, P, P]
+            lib.orc_soft_jvp.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
+                                         P, i64, ctypes.c_int, ctypes.c_int, P]
+            lib.orc_soft_vjp.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
+                                         P, i64, P, P, P, P, P]
+            lib.orc_num_threads.restype = ctypes.c_int
+            for f in ("orc_map", "orc_map_jacobian", "orc_render_hard", "orc_render_soft",
+                      "orc_soft_jvp", "orc_soft_vjp"):
+                getattr(lib, f).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    return _load().orc_num_threads()
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+class _Packed:
+    """Holds FP64 copies of a program's arrays and the ctypes struct pointing at them."""
+
+    def __init__(self, prog):
+        f64 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+        self.cx, self.cy = f64(prog.cx), f64(prog.cy)
+        self.th, self.L, self.r = f64(prog.theta), f64(prog.length), f64(prog.half_width)
+        self.logits, self.palette = f64(prog.logits), f64(prog.palette)
+        n = self.cx.shape[0]
+        k = self.palette.shape[0]
+        if self.logits.shape != (n, k):
+            raise ValueError("logits must be [n, k]")
+        s = _Prog()
+        s.n, s.k = n, k
+        s.cx, s.cy, s.th = _ptr(self.cx), _ptr(self.cy), _ptr(self.th)
+        s.L, s.r = _ptr(self.L), _ptr(self.r)
+        s.logits, s.palette = _ptr(self.logits), _ptr(self.palette)
+        bg = np.asarray(prog.background, dtype=np.float64)
+        s.background = (ctypes.c_double * 3)(*bg.tolist())
+        s.color_temp = float(prog.color_temp)
+        self.struct = s
+        self.n, self.k = n, k
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def _pixels(W, H, pix):
+    if pix is None:
+        return None, W * H
+    pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
+    if pix.size and (pix.min() < 0 or pix.max() >= W * H):
+        raise ValueError("pixel index out of range")
+    return pix, pix.shape[0]
+
+
+def psi_map(pts, stroke, mode=MODE_FLOOR, return_floored=False):
+    """Backward map psi (Eq. back) of one stroke (cx, cy, th, L, r) on points [n,2]."""
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 2))
+    out = np.empty_like(pts)
+    fl = np.empty(pts.shape[0], dtype=np.int32)
+    _load().orc_map(_ptr(pts), pts.shape[0], *map(float, stroke), 0, int(mode), _ptr(out), _ptr(fl))
+    return (out, fl) if return_floored else out
+
+
+def phi_map(pts, stroke, raw_q=False):
+    """Forward map Phi (Eq. fwd) of one stroke on points [n,2]."""
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 2))
+    out = np.empty_like(pts)
+    _load().orc_map(_ptr(pts), pts.shape[0], *map(float, stroke), 1,
+                    MODE_RAWQ if raw_q else MODE_CLAMP, _ptr(out), None)
+    return out
+
+
+def map_jacobian(pts, stroke, direction=0, mode=MODE_FLOOR):
+    """[n, 2, 7] Jacobian d(out)/d(x, y, cx, cy, th, L, r) by dual numbers."""
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 2))
+    jac = np.empty((pts.shape[0], 2, 7), dtype=np.float64)
+    _load().orc_map_jacobian(_ptr(pts), pts.shape[0], *map(float, stroke), int(direction),
+                             int(mode), _ptr(jac))
+    return jac
+
+
+def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with_kappa=False):
+    """Hard render; returns dict rgb [m,3], idx [m], margin [m] (+ kappa [m])."""
+    pk = _Packed(prog)
+    pix, m = _pixels(W, H, pix)
+    rgb = np.empty((m, 3))
+    idx = np.empty(m, dtype=np.int32)
+    margin = np.empty(m)
+    kappa = np.empty(m) if with_kappa else None
+    _load().orc_render_hard(pk.ref, W, H, int(n_prefix), int(bool(snap)), int(bool(inert)),
+                            _ptr(pix), m, _ptr(rgb), _ptr(idx), _ptr(margin), _ptr(kappa))
+    out = {"rgb": rgb, "idx": idx, "margin": margin}
+    if with_kappa:
+        out["kappa"] = kappa
+    return out
+
+
+def render_soft(prog, W, H, tau, tau_min, inert=False, pix=None):
+    """Soft render; returns dict rgb [m,3], T0 [m], nrec [m]."""
+    pk = _Packed(prog)
+    pix, m = _pixels(W, H, pix)
+    rgb = np.empty((m, 3))
+    T0 = np.empty(m)
+    nrec = np.empty(m, dtype=np.int32)
+    _load().orc_render_soft(pk.ref, W, H, float(tau), float(tau_min), int(bool(inert)),
+                            _ptr(pix), m, _ptr(rgb), _ptr(T0), _ptr(nrec))
+    return {"rgb": rgb, "T0": T0, "nrec": nrec}
+
+
+def soft_jvp(prog, W, H, tau, tau_min, stroke, param, inert=False, pix=None):
+    """d rgb / d param of the soft render by forward-mode duals ([m,3])."""
+    pk = _Packed(prog)
+    pix, m = _pixels(W, H, pix)
+    d = np.empty((m, 3))
+    _load().orc_soft_jvp(pk.ref, W, H, float(tau), float(tau_min), int(bool(inert)),
+                         _ptr(pix), m, int(stroke), int(param), _ptr(d))
+    return d
+
+
+def soft_vjp(prog, W, H, tau, tau_min, cot, inert=False, pix=None):
+    """Stored-state adjoint of J = sum cot . R; returns dict of gradients."""
+    pk = _Packed(prog)
+    pix, m = _pixels(W, H, pix)
+    cot = np.ascontiguousarray(np.asarray(cot, dtype=np.float64).reshape(m, 3))
+    g_geo = np.empty((pk.n, 5))
+    g_col = np.empty((pk.n, 3))
+    g_logits = np.empty((pk.n, pk.k))
+    g_pal = np.empty((pk.k, 3))
+    _load().orc_soft_vjp(pk.ref, W, H, float(tau), float(tau_min), int(bool(inert)), _ptr(pix), m,
+                         _ptr(cot), _ptr(g_geo), _ptr(g_col), _ptr(g_logits), _ptr(g_pal))
+    return {"cx": g_geo[:, 0], "cy": g_geo[:, 1], "theta": g_geo[:, 2], "length": g_geo[:, 3],
+            "half_width": g_geo[:, 4], "color": g_col, "logits": g_logits, "palette": g_pal}
+
+
+_FIELD = {0: "cx", 1: "cy", 2: "theta", 3: "length", 4: "half_width"}
+
+
+def fd_gradient(prog, W, H, tau, tau_min, cot, params, h_geo=1e-6, h_logit=1e-5,
+                inert=False, pix=None):
+    """Central differences of J = sum cot . R_soft with respect to the listed
+    parameters, each given as (stroke, param) with param as in ``soft_jvp``
+    (palette entries excluded).  A length at 0 uses the second-order one-sided
+    difference (-3 J(0) + 4 J(h) - J(2h)) / 2h: the map is even in L, so only
+    the one-sided derivative exists there."""
+    import copy
+    cot = np.asarray(cot, dtype=np.float64).reshape(-1, 3)
+
+    def J(pr):
+        return float(np.sum(render_soft(pr, W, H, tau, tau_min, inert, pix)["rgb"] * cot))
+
+    def perturbed(j, q, delta):
+        pr = copy.copy(prog)
+        if q < 5:
+            name = _FIELD[q]
+            arr = np.array(getattr(prog, name), dtype=np.float64)
+            arr[j] += delta
+            setattr(pr, name, arr)
+        else:
+            arr = np.array(prog.logits, dtype=np.float64)
+            arr[j, q - 5] += delta
+            pr.logits = arr
+        return pr
+
+    out = []
+    for (j, q) in params:
+        h = h_geo if q < 5 else h_logit
+        if q == 3 and float(np.asarray(prog.length)[j]) == 0.0:
+            out.append((-3 * J(prog) + 4 * J(perturbed(j, q, h)) - J(perturbed(j, q, 2 * h))) / (2 * h))
+        else:
+            out.append((J(perturbed(j, q, h)) - J(perturbed(j, q, -h))) / (2 * h))
+    return np.array(out)

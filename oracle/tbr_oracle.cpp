@@ -1,0 +1,652 @@
+// TBR oracle: a plain, slow FP64 CPU implementation of transport-based rendering
+// with capsule deposition strokes.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or load
+// this file: only the test suite, the smoke check and the benchmark's CPU-baseline
+// leg use it.  It shares no code, header, table or constant generator with the
+// CUDA path; both sides only receive the same seeded input arrays.
+//
+// What it computes, each function citing the passage it follows:
+//   * the capsule insertion map in its two directions: backward psi (Eq. back)
+//     and forward Phi (Eq. fwd), with the tangential coordinate kept as the
+//     centred arclength v (Eq. phi, Prop. 2 "Centred arclength"), written on
+//     the full stadium (no quadrant folding) from the definitions in Sec. 4;
+//   * the interior extension by clamping C (Sec. 4 "The chain") and the
+//     implemented epsilon-floor of Sec. 5.2;
+//   * the hard and soft renderers (Eq. chain, Eq. render, Eq. relax, Eq. state);
+//   * a stored-state adjoint (Eq. adjstep, Eq. adjparam) whose local Jacobians
+//     come from forward-mode dual numbers, and a forward-mode directional
+//     derivative of the whole soft render used to pin that adjoint.
+//
+// Parity status: every function here is pinned by a "not gpu" test (round trip,
+// drop limit, area, symmetry, commutation, compositing identity, brute force,
+// finite differences).  None is "parity unpinned".
+//
+// Conventions (the readings of the paper used throughout):
+//   * A stroke is (cx, cy, th, L, r): segment centre, direction angle, full
+//     segment length and half-width.  The segment is [m - L e/2, m + L e/2],
+//     e = (cos th, sin th).
+//   * Program index j = 0..N-1 is the paper's stroke i = j+1; rendering visits
+//     j = N-1 down to 0.
+//   * Pixel (row, col) is sampled once at ((col+0.5)/W, (row+0.5)/H).
+//   * Colour c_j = softmax(logits_j / tau_c) . palette, or the palette entry of
+//     the largest logit when snapping.
+//   * Soft coverage alpha = min(sigmoid((r - sigma')/max(tau r, tau_min)), 1 - 1e-7).
+//   * epsilon-floor: C <- (eps r)^2 whenever C < (eps r)^2, eps = 1e-3; each such
+//     sample counts as one side-table record.
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace orc {
+
+static const double kPi = 3.14159265358979323846;
+static const double kEps = 1e-3;            // epsilon of the floor, Sec. 5.2
+static const double kAlphaMax = 1.0 - 1e-7;  // coverage clamp, Sec. 5.2 "Conditioning"
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers (value plus D directional derivatives).
+// ---------------------------------------------------------------------------
+template <int D>
+struct Dual {
+  double v;
+  double d[D];
+  Dual() : v(0.0) { for (int k = 0; k < D; ++k) d[k] = 0.0; }
+  Dual(double x) : v(x) { for (int k = 0; k < D; ++k) d[k] = 0.0; }  // NOLINT
+};
+
+inline double value(double x) { return x; }
+template <int D> inline double value(const Dual<D>& x) { return x.v; }
+
+template <int D> inline Dual<D> operator+(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r; r.v = a.v + b.v; for (int k = 0; k < D; ++k) r.d[k] = a.d[k] + b.d[k]; return r;
+}
+template <int D> inline Dual<D> operator-(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r; r.v = a.v - b.v; for (int k = 0; k < D; ++k) r.d[k] = a.d[k] - b.d[k]; return r;
+}
+template <int D> inline Dual<D> operator-(const Dual<D>& a) {
+  Dual<D> r; r.v = -a.v; for (int k = 0; k < D; ++k) r.d[k] = -a.d[k]; return r;
+}
+template <int D> inline Dual<D> operator*(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r; r.v = a.v * b.v;
+  for (int k = 0; k < D; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+template <int D> inline Dual<D> operator/(const Dual<D>& a, const Dual<D>& b) {
+  Dual<D> r; r.v = a.v / b.v;
+  for (int k = 0; k < D; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) / (b.v * b.v);
+  return r;
+}
+template <int D> inline Dual<D> operator+(const Dual<D>& a, double b) { return a + Dual<D>(b); }
+template <int D> inline Dual<D> operator+(double a, const Dual<D>& b) { return Dual<D>(a) + b; }
+template <int D> inline Dual<D> operator-(const Dual<D>& a, double b) { return a - Dual<D>(b); }
+template <int D> inline Dual<D> operator-(double a, const Dual<D>& b) { return Dual<D>(a) - b; }
+template <int D> inline Dual<D> operator*(const Dual<D>& a, double b) { return a * Dual<D>(b); }
+template <int D> inline Dual<D> operator*(double a, const Dual<D>& b) { return Dual<D>(a) * b; }
+template <int D> inline Dual<D> operator/(const Dual<D>& a, double b) { return a / Dual<D>(b); }
+template <int D> inline Dual<D> operator/(double a, const Dual<D>& b) { return Dual<D>(a) / b; }
+
+// Chain rule helper: f(a) with f'(a) = df.
+template <int D> inline Dual<D> chain(const Dual<D>& a, double f, double df) {
+  Dual<D> r; r.v = f; for (int k = 0; k < D; ++k) r.d[k] = df * a.d[k]; return r;
+}
+template <int D> inline Dual<D> sqrt(const Dual<D>& a) {
+  double s = std::sqrt(a.v); return chain(a, s, 0.5 / s);
+}
+template <int D> inline Dual<D> sin(const Dual<D>& a) { return chain(a, std::sin(a.v), std::cos(a.v)); }
+template <int D> inline Dual<D> cos(const Dual<D>& a) { return chain(a, std::cos(a.v), -std::sin(a.v)); }
+template <int D> inline Dual<D> exp(const Dual<D>& a) { double e = std::exp(a.v); return chain(a, e, e); }
+template <int D> inline Dual<D> log1p(const Dual<D>& a) { return chain(a, std::log1p(a.v), 1.0 / (1.0 + a.v)); }
+template <int D> inline Dual<D> fabs(const Dual<D>& a) { return a.v < 0.0 ? -a : a; }
+template <int D> inline Dual<D> atan2(const Dual<D>& y, const Dual<D>& x) {
+  Dual<D> r; r.v = std::atan2(y.v, x.v);
+  double n = x.v * x.v + y.v * y.v;
+  for (int k = 0; k < D; ++k) r.d[k] = (x.v * y.d[k] - y.v * x.d[k]) / n;
+  return r;
+}
+
+using std::sqrt; using std::sin; using std::cos; using std::exp; using std::log1p;
+using std::fabs; using std::atan2;
+
+template <class T> struct Stroke { T cx, cy, th, L, r; };
+
+// ---------------------------------------------------------------------------
+// Stroke frame.  Sec. 3: the footprint is the capsule about [a, a+d]; with the
+// centre m = a + d/2 and e = d/|d| the segment is {m + t e : |t| <= L/2}.
+// s is the coordinate along e, h the coordinate along e_perp = (-e_y, e_x).
+// ---------------------------------------------------------------------------
+template <class T>
+void to_frame(const T& x, const T& y, const Stroke<T>& g, T& s, T& h) {
+  T ex = cos(g.th), ey = sin(g.th);
+  T dx = x - g.cx, dy = y - g.cy;
+  s = dx * ex + dy * ey;
+  h = dy * ex - dx * ey;
+}
+template <class T>
+void from_frame(const T& s, const T& h, const Stroke<T>& g, T& x, T& y) {
+  T ex = cos(g.th), ey = sin(g.th);
+  x = g.cx + s * ex - h * ey;
+  y = g.cy + s * ey + h * ex;
+}
+
+// sigma(x) = dist(x, segment) (Sec. 3, footprint definition): distance to the
+// nearest point of the segment, which is the clamped projection onto it.
+template <class T>
+T segment_distance(const T& s, const T& h, const T& L) {
+  T hl = 0.5 * L;
+  T t = s;
+  if (value(s) > value(hl)) t = hl;
+  else if (value(s) < -value(hl)) t = -hl;
+  T ds = s - t;
+  if (value(ds) == 0.0) return fabs(h);
+  return sqrt(ds * ds + h * h);
+}
+
+// Arclength along the parallel curve {sigma = const} (a stadium), measured
+// counter-clockwise from the flank corner (-L/2, -sigma): lower flank (length L),
+// right cap (pi sigma), upper flank (L), left cap (pi sigma).  Its perimeter is
+// P_L(sigma) = 2L + 2 pi sigma (Eq. steiner).  q of Sec. 4 is this divided by P.
+template <class T>
+T stadium_arclength(const T& s, const T& h, const T& sig, const T& L) {
+  T hl = 0.5 * L;
+  if (value(s) > value(hl)) {               // right cap, angle from -pi/2 to pi/2
+    T ang = atan2(h, s - hl);
+    return L + sig * (ang + 0.5 * kPi);
+  }
+  if (value(s) < -value(hl)) {              // left cap, angle from 0 to pi
+    T ang = atan2(-(s + hl), h);
+    return 2.0 * L + kPi * sig + sig * ang;
+  }
+  if (value(h) < 0.0) return s + hl;        // lower flank, travelled towards +s
+  return L + kPi * sig + (hl - s);          // upper flank, travelled towards -s
+}
+
+// Inverse of stadium_arclength on the stadium at distance sig.
+template <class T>
+void stadium_point(T a, const T& sig, const T& L, T& s, T& h) {
+  T hl = 0.5 * L;
+  T per = 2.0 * L + 2.0 * kPi * sig;
+  if (value(per) <= 0.0) { s = T(0.0); h = T(0.0); return; }
+  if (value(a) < 0.0) a = a + per;
+  if (value(a) >= value(per)) a = a - per;
+  double av = value(a), Lv = value(L), capv = kPi * value(sig);
+  if (av < Lv) { s = a - hl; h = -sig; return; }
+  if (av < Lv + capv) {
+    T ang = (a - L) / sig - 0.5 * kPi;
+    s = hl + sig * cos(ang); h = sig * sin(ang); return;
+  }
+  if (av < 2.0 * Lv + capv) { s = hl - (a - L - kPi * sig); h = sig; return; }
+  T ang = (a - 2.0 * L - kPi * sig) / sig;
+  s = -hl - sig * sin(ang); h = sig * cos(ang);
+}
+
+enum Mode { kClamp = 0, kFloor = 1, kRawQ = 2, kFloorRawQ = 3 };
+
+// Move a point from the parallel curve at distance sig_from to the one at
+// distance sig_to, keeping the centred arclength fraction
+// v = q - L/(2 P_L(sigma)) (Eq. phi; Prop. 2), or raw q for the negative control
+// of Table "detj" (last row).
+template <class T>
+void keep_tangential(const T& s, const T& h, const T& sig_from, const T& sig_to,
+                     const T& L, bool raw_q, T& s_out, T& h_out) {
+  T a_from = stadium_arclength(s, h, sig_from, L);
+  T p_from = 2.0 * L + 2.0 * kPi * sig_from;
+  T p_to = 2.0 * L + 2.0 * kPi * sig_to;
+  T a_to;
+  if (value(p_from) <= 0.0) {
+    a_to = T(0.0);
+  } else if (raw_q) {
+    a_to = (a_from / p_from) * p_to;
+  } else {
+    T q = a_from / p_from;
+    T v = q - L / (2.0 * p_from);
+    a_to = (v + L / (2.0 * p_to)) * p_to;
+  }
+  stadium_point(a_to, sig_to, L, s_out, h_out);
+}
+
+// Backward material map psi (Eq. back): subtract the inserted area A_L(r) in the
+// area coordinate u = A_L(sigma) = 2 L sigma + pi sigma^2, i.e.
+// C = A_L(sigma') - A_L(r) = (sigma' - r)(2L + pi(sigma' + r)), and take the
+// cancellation-free root sigma = C / (L + sqrt(L^2 + pi C)).
+// Inside the footprint C <= 0: clamped to 0 (ideal extension, Sec. 4 "The
+// chain") or floored at (eps r)^2 (the implemented map, Sec. 5.2).
+// Returns 1 if the floor bound (a side-table record), else 0.
+template <class T>
+int psi(const T& x, const T& y, const Stroke<T>& g, int mode, T& x_out, T& y_out) {
+  T s, h;
+  to_frame(x, y, g, s, h);
+  T sp = segment_distance(s, h, g.L);
+  T C = (sp - g.r) * (2.0 * g.L + kPi * (sp + g.r));
+  int floored = 0;
+  if (mode == kFloor || mode == kFloorRawQ) {
+    T fl = (kEps * g.r) * (kEps * g.r);
+    if (value(C) < value(fl)) { C = fl; floored = 1; }
+  } else if (value(C) < 0.0) {
+    C = T(0.0);
+  }
+  T sig = C / (g.L + sqrt(g.L * g.L + kPi * C));
+  T sn, hn;
+  keep_tangential(s, h, sp, sig, g.L, mode == kRawQ || mode == kFloorRawQ, sn, hn);
+  from_frame(sn, hn, g, x_out, y_out);
+  return floored;
+}
+
+// Forward (regeneration) map Phi (Eq. fwd): add the inserted area,
+// B = A_L(sigma) + A_L(r) = 2L(sigma + r) + pi(sigma^2 + r^2),
+// sigma' = B / (L + sqrt(L^2 + pi B)); same centred arclength.
+template <class T>
+void phi(const T& x, const T& y, const Stroke<T>& g, bool raw_q, T& x_out, T& y_out) {
+  T s, h;
+  to_frame(x, y, g, s, h);
+  T sg = segment_distance(s, h, g.L);
+  T B = 2.0 * g.L * (sg + g.r) + kPi * (sg * sg + g.r * g.r);
+  T sp = B / (g.L + sqrt(g.L * g.L + kPi * B));
+  T sn, hn;
+  keep_tangential(s, h, sg, sp, g.L, raw_q, sn, hn);
+  from_frame(sn, hn, g, x_out, y_out);
+}
+
+// Relaxed coverage (Eq. relax), clamped at 1 - 1e-7 (Sec. 5.2 "Conditioning").
+template <class T>
+T soft_coverage(const T& sp, const T& r, double tau, double tau_min) {
+  T w = tau * r;
+  if (value(w) < tau_min) w = T(tau_min);
+  T z = (r - sp) / w;
+  T a = 1.0 / (1.0 + exp(-z));
+  if (value(a) > kAlphaMax) a = T(kAlphaMax);
+  return a;
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+// Program layout shared with the Python wrapper (ctypes).  All arrays are
+// FP64, program order (index 0 = the paper's g_1).
+typedef struct {
+  int32_t n, k;
+  const double* cx; const double* cy; const double* th; const double* L; const double* r;
+  const double* logits;   // [n][k]
+  const double* palette;  // [k][3]
+  double background[3];   // c_0
+  double color_temp;      // tau_c
+} orc_prog;
+
+}  // extern "C"
+
+namespace {
+
+template <class T>
+Stroke<T> stroke_of(const orc_prog* p, int j) {
+  Stroke<T> g;
+  g.cx = T(p->cx[j]); g.cy = T(p->cy[j]); g.th = T(p->th[j]); g.L = T(p->L[j]); g.r = T(p->r[j]);
+  return g;
+}
+
+// c_j = softmax(logits_j / tau_c) . palette (Sec. 5.1 "Parameterisation");
+// with snap, the palette entry of the largest logit (export snapping).
+void stroke_colours(const orc_prog* p, int snap, std::vector<double>& col, std::vector<double>& prob) {
+  int n = p->n, k = p->k;
+  col.assign((size_t)n * 3, 0.0);
+  prob.assign((size_t)n * k, 0.0);
+  for (int j = 0; j < n; ++j) {
+    const double* z = p->logits + (size_t)j * k;
+    int am = 0;
+    double zmax = z[0];
+    for (int q = 1; q < k; ++q) if (z[q] > zmax) { zmax = z[q]; am = q; }
+    double den = 0.0;
+    for (int q = 0; q < k; ++q) den += std::exp((z[q] - zmax) / p->color_temp);
+    for (int q = 0; q < k; ++q) prob[(size_t)j * k + q] = std::exp((z[q] - zmax) / p->color_temp) / den;
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      if (snap) acc = p->palette[am * 3 + c];
+      else for (int q = 0; q < k; ++q) acc += prob[(size_t)j * k + q] * p->palette[q * 3 + c];
+      col[(size_t)j * 3 + c] = acc;
+    }
+  }
+}
+
+inline void pixel_centre(int64_t pidx, int W, int H, double& x, double& y) {
+  int64_t row = pidx / W, colm = pidx % W;
+  x = ((double)colm + 0.5) / (double)W;
+  y = ((double)row + 0.5) / (double)H;
+}
+
+// Spectral norm of a 2x2 matrix [a b; c d].
+double spectral_norm(double a, double b, double c, double d) {
+  double p = a * a + b * b + c * c + d * d;
+  double q = a * d - b * c;
+  double disc = std::sqrt(std::max(0.0, p * p - 4.0 * q * q));
+  return std::sqrt(0.5 * (p + disc));
+}
+
+}  // namespace
+
+extern "C" {
+
+// Single-map evaluation on a batch of points (for the operator pins).
+// mode: 0 ideal clamp, 1 epsilon floor, 2 raw-q control, 3 floor + raw q.
+// direction: 0 = psi (Eq. back), 1 = Phi (Eq. fwd; mode 2/3 select raw q).
+// floored (nullable): per point 1 if the floor bound.
+int orc_map(const double* pts, int64_t n, double cx, double cy, double th, double L, double r,
+            int direction, int mode, double* out, int32_t* floored) {
+  Stroke<double> g{cx, cy, th, L, r};
+  #pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double xo, yo;
+    int f = 0;
+    if (direction == 0) f = psi(pts[2 * i], pts[2 * i + 1], g, mode, xo, yo);
+    else phi(pts[2 * i], pts[2 * i + 1], g, mode == kRawQ || mode == kFloorRawQ, xo, yo);
+    out[2 * i] = xo; out[2 * i + 1] = yo;
+    if (floored) floored[i] = f;
+  }
+  return 0;
+}
+
+// Jacobian of one map by dual numbers: jac[i] is the 2x7 matrix
+// d(x_out, y_out)/d(x, y, cx, cy, th, L, r), row-major.
+int orc_map_jacobian(const double* pts, int64_t n, double cx, double cy, double th, double L,
+                     double r, int direction, int mode, double* jac) {
+  #pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    typedef Dual<7> D7;
+    D7 x(pts[2 * i]), y(pts[2 * i + 1]);
+    Stroke<D7> g{D7(cx), D7(cy), D7(th), D7(L), D7(r)};
+    x.d[0] = 1; y.d[1] = 1; g.cx.d[2] = 1; g.cy.d[3] = 1; g.th.d[4] = 1; g.L.d[5] = 1; g.r.d[6] = 1;
+    D7 xo, yo;
+    if (direction == 0) psi(x, y, g, mode, xo, yo);
+    else phi(x, y, g, mode == kRawQ || mode == kFloorRawQ, xo, yo);
+    for (int k = 0; k < 7; ++k) { jac[i * 14 + k] = xo.d[k]; jac[i * 14 + 7 + k] = yo.d[k]; }
+  }
+  return 0;
+}
+
+// Hard render (Eq. chain, Eq. render with alpha = indicator of K_i).
+// Pixels: if pix is non-null, only the npix listed flat indices (row*W + col)
+// are rendered and outputs are compact [npix]; otherwise npix must be W*H.
+// For each pixel: rgb[3], idx (terminating program index or -1), margin =
+// min |sigma'_j - r_j| over the visited strokes (terminating one included) and,
+// if kappa is non-null, the product of the spectral norms of Dpsi_j over the
+// strokes passed through (the chain's condition estimate).
+// n_prefix < 0 renders all strokes; otherwise only the first n_prefix.
+// inert != 0 uses psi = id (the inert-mark renderer, Definition 1).
+int orc_render_hard(const orc_prog* p, int W, int H, int n_prefix, int snap, int inert,
+                    const int64_t* pix, int64_t npix, double* rgb, int32_t* idx,
+                    double* margin, double* kappa) {
+  std::vector<double> col, prob;
+  stroke_colours(p, snap, col, prob);
+  int n = (n_prefix < 0 || n_prefix > p->n) ? p->n : n_prefix;
+  #pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < npix; ++q) {
+    int64_t pidx = pix ? pix[q] : q;
+    double x, y;
+    pixel_centre(pidx, W, H, x, y);
+    int hit = -1;
+    double mg = INFINITY, kap = 1.0;
+    for (int j = n - 1; j >= 0; --j) {
+      Stroke<double> g = stroke_of<double>(p, j);
+      double s, h;
+      to_frame(x, y, g, s, h);
+      double sp = segment_distance(s, h, g.L);
+      mg = std::min(mg, std::fabs(sp - g.r));
+      if (sp <= g.r) { hit = j; break; }       // closed footprint: the tie is inside
+      if (inert) continue;
+      if (kappa) {
+        typedef Dual<2> D2;
+        D2 xd(x), yd(y), xo, yo;
+        xd.d[0] = 1; yd.d[1] = 1;
+        Stroke<D2> gd{D2(g.cx), D2(g.cy), D2(g.th), D2(g.L), D2(g.r)};
+        psi(xd, yd, gd, kClamp, xo, yo);
+        kap *= spectral_norm(xo.d[0], xo.d[1], yo.d[0], yo.d[1]);
+        x = xo.v; y = yo.v;
+      } else {
+        double xo, yo;
+        psi(x, y, g, kClamp, xo, yo);
+        x = xo; y = yo;
+      }
+    }
+    for (int c = 0; c < 3; ++c) rgb[q * 3 + c] = hit >= 0 ? col[(size_t)hit * 3 + c] : p->background[c];
+    if (idx) idx[q] = hit;
+    if (margin) margin[q] = mg;
+    if (kappa) kappa[q] = kap;
+  }
+  return 0;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One pixel of the soft render (Eq. state): s_N = (x, 0, 1);
+// C_{i-1} = C_i + T_i alpha_i c_i, T_{i-1} = T_i (1 - alpha_i), x_{i-1} = psi_i(x_i),
+// R = C_0 + T_0 c_0.  Templated so that the same steps run in FP64 and in
+// forward-mode dual numbers (the directional-derivative pin).
+template <class T>
+void soft_pixel(const std::vector<Stroke<T>>& g, const std::vector<T>& col, const T bg[3],
+                double tau, double tau_min, int inert, double px, double py,
+                T out[3], double* T0, int* nrec) {
+  T x(px), y(py);
+  T C[3] = {T(0.0), T(0.0), T(0.0)};
+  T Tr(1.0);
+  int rec = 0;
+  for (int j = (int)g.size() - 1; j >= 0; --j) {
+    T s, h;
+    to_frame(x, y, g[j], s, h);
+    T sp = segment_distance(s, h, g[j].L);
+    T a = soft_coverage(sp, g[j].r, tau, tau_min);
+    for (int c = 0; c < 3; ++c) C[c] = C[c] + Tr * a * col[(size_t)j * 3 + c];
+    Tr = Tr * (1.0 - a);
+    if (!inert) {
+      T xo, yo;
+      rec += psi(x, y, g[j], kFloor, xo, yo);
+      x = xo; y = yo;
+    }
+  }
+  for (int c = 0; c < 3; ++c) out[c] = C[c] + Tr * bg[c];
+  if (T0) *T0 = value(Tr);
+  if (nrec) *nrec = rec;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Soft render (Eq. relax coverage, Eq. state compositing, epsilon-floored psi).
+// Outputs per rendered pixel: rgb[3]; T0 (final transmittance, nullable);
+// nrec (side-table records, i.e. floor binds, nullable).
+int orc_render_soft(const orc_prog* p, int W, int H, double tau, double tau_min, int inert,
+                    const int64_t* pix, int64_t npix, double* rgb, double* T0, int32_t* nrec) {
+  std::vector<double> col, prob;
+  stroke_colours(p, 0, col, prob);
+  std::vector<Stroke<double>> g(p->n);
+  for (int j = 0; j < p->n; ++j) g[j] = stroke_of<double>(p, j);
+  #pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < npix; ++q) {
+    int64_t pidx = pix ? pix[q] : q;
+    double x, y;
+    pixel_centre(pidx, W, H, x, y);
+    double out[3], t0;
+    int nr;
+    soft_pixel<double>(g, col, p->background, tau, tau_min, inert, x, y, out, &t0, &nr);
+    for (int c = 0; c < 3; ++c) rgb[q * 3 + c] = out[c];
+    if (T0) T0[q] = t0;
+    if (nrec) nrec[q] = nr;
+  }
+  return 0;
+}
+
+// Directional derivative of the soft render by forward-mode dual numbers.
+// param in [0,5): geometry (cx, cy, th, L, r) of stroke `stroke`;
+// param in [5, 5+k): logit (param-5) of stroke `stroke`;
+// param in [5+k, 5+k+3k): palette entry (param-5-k)/3, channel (param-5-k)%3.
+int orc_soft_jvp(const orc_prog* p, int W, int H, double tau, double tau_min, int inert,
+                 const int64_t* pix, int64_t npix, int stroke, int param, double* drgb) {
+  typedef Dual<1> D1;
+  int n = p->n, k = p->k;
+  std::vector<Stroke<D1>> g(n);
+  for (int j = 0; j < n; ++j) g[j] = stroke_of<D1>(p, j);
+  if (param < 5) {
+    D1* f[5] = {&g[stroke].cx, &g[stroke].cy, &g[stroke].th, &g[stroke].L, &g[stroke].r};
+    f[param]->d[0] = 1.0;
+  }
+  // colours as duals: softmax(z/tau_c) . palette
+  std::vector<D1> col((size_t)n * 3);
+  for (int j = 0; j < n; ++j) {
+    std::vector<D1> z(k);
+    for (int q = 0; q < k; ++q) {
+      z[q] = D1(p->logits[(size_t)j * k + q]);
+      if (param >= 5 && param < 5 + k && j == stroke && q == param - 5) z[q].d[0] = 1.0;
+    }
+    double zmax = z[0].v;
+    for (int q = 1; q < k; ++q) zmax = std::max(zmax, z[q].v);
+    std::vector<D1> e(k);
+    D1 den(0.0);
+    for (int q = 0; q < k; ++q) { e[q] = exp((z[q] - zmax) / p->color_temp); den = den + e[q]; }
+    for (int c = 0; c < 3; ++c) {
+      D1 acc(0.0);
+      for (int q = 0; q < k; ++q) {
+        D1 pal(p->palette[q * 3 + c]);
+        if (param >= 5 + k && (param - 5 - k) == q * 3 + c) pal.d[0] = 1.0;
+        acc = acc + (e[q] / den) * pal;
+      }
+      col[(size_t)j * 3 + c] = acc;
+    }
+  }
+  D1 bg[3] = {D1(p->background[0]), D1(p->background[1]), D1(p->background[2])};
+  #pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t q = 0; q < npix; ++q) {
+    int64_t pidx = pix ? pix[q] : q;
+    double x, y;
+    pixel_centre(pidx, W, H, x, y);
+    D1 out[3];
+    soft_pixel<D1>(g, col, bg, tau, tau_min, inert, x, y, out, nullptr, nullptr);
+    for (int c = 0; c < 3; ++c) drgb[q * 3 + c] = out[c].d[0];
+  }
+  return 0;
+}
+
+// Stored-state adjoint of the soft render for the linear functional
+// J = sum_pixels cot_p . R(p): runs Eq. state forward keeping every state
+// s_i = (x_i, T_i) of the pixel, then applies Eq. adjstep / Eq. adjparam from
+// i = 1 to N with lambda^C_0 = cot_p, lambda^T_0 = cot_p . c_0, lambda^x_0 = 0.
+// The local derivatives d alpha/d(x, theta), D psi and d psi/d theta come from
+// dual numbers over psi and the coverage; nothing is regenerated.
+// Outputs (summed over the listed pixels): g_geo[n][5] (cx, cy, th, L, r),
+// g_col[n][3] (dJ/dc_i), g_logits[n][k], g_pal[k][3] (nullable each except g_geo).
+int orc_soft_vjp(const orc_prog* p, int W, int H, double tau, double tau_min, int inert,
+                 const int64_t* pix, int64_t npix, const double* cot, double* g_geo,
+                 double* g_col, double* g_logits, double* g_pal) {
+  int n = p->n, k = p->k;
+  std::vector<double> col, prob;
+  stroke_colours(p, 0, col, prob);
+  int nthreads = 1;
+#ifdef _OPENMP
+  nthreads = omp_get_max_threads();
+#endif
+  std::vector<std::vector<double>> acc(nthreads, std::vector<double>((size_t)n * 8, 0.0));
+  #pragma omp parallel
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    std::vector<double>& my = acc[tid];
+    std::vector<double> xs(n), ys(n), Ts(n);
+    #pragma omp for schedule(dynamic, 16)
+    for (int64_t q = 0; q < npix; ++q) {
+      int64_t pidx = pix ? pix[q] : q;
+      double x, y;
+      pixel_centre(pidx, W, H, x, y);
+      // forward, storing s_i (position at which stroke i is evaluated, and T_i)
+      double Tr = 1.0;
+      for (int j = n - 1; j >= 0; --j) {
+        Stroke<double> g = stroke_of<double>(p, j);
+        xs[j] = x; ys[j] = y; Ts[j] = Tr;
+        double s, h;
+        to_frame(x, y, g, s, h);
+        double a = soft_coverage(segment_distance(s, h, g.L), g.r, tau, tau_min);
+        Tr = Tr * (1.0 - a);
+        if (!inert) { double xo, yo; psi(x, y, g, kFloor, xo, yo); x = xo; y = yo; }
+      }
+      // backward, i = 1..N (program index j = 0..n-1)
+      double lC[3] = {cot[q * 3], cot[q * 3 + 1], cot[q * 3 + 2]};
+      double lT = lC[0] * p->background[0] + lC[1] * p->background[1] + lC[2] * p->background[2];
+      double lx[2] = {0.0, 0.0};
+      for (int j = 0; j < n; ++j) {
+        typedef Dual<7> D7;
+        D7 xd(xs[j]), yd(ys[j]);
+        xd.d[0] = 1; yd.d[1] = 1;
+        Stroke<D7> gd = stroke_of<D7>(p, j);
+        gd.cx.d[2] = 1; gd.cy.d[3] = 1; gd.th.d[4] = 1; gd.L.d[5] = 1; gd.r.d[6] = 1;
+        D7 s, h;
+        to_frame(xd, yd, gd, s, h);
+        D7 a = soft_coverage(segment_distance(s, h, gd.L), gd.r, tau, tau_min);
+        double J[2][7];
+        if (inert) {
+          for (int r = 0; r < 2; ++r) for (int c = 0; c < 7; ++c) J[r][c] = (r == c) ? 1.0 : 0.0;
+        } else {
+          D7 xo, yo;
+          psi(xd, yd, gd, kFloor, xo, yo);
+          for (int c = 0; c < 7; ++c) { J[0][c] = xo.d[c]; J[1][c] = yo.d[c]; }
+        }
+        const double* cj = &col[(size_t)j * 3];
+        double lCc = lC[0] * cj[0] + lC[1] * cj[1] + lC[2] * cj[2];
+        double Ti = Ts[j];
+        double mu = Ti * (lCc - lT);
+        double* gj = &my[(size_t)j * 8];
+        for (int t = 0; t < 5; ++t) gj[t] += mu * a.d[2 + t] + lx[0] * J[0][2 + t] + lx[1] * J[1][2 + t];
+        for (int c = 0; c < 3; ++c) gj[5 + c] += lC[c] * Ti * a.v;
+        double lT_new = (1.0 - a.v) * lT + a.v * lCc;
+        double lx0 = J[0][0] * lx[0] + J[1][0] * lx[1] + mu * a.d[0];
+        double lx1 = J[0][1] * lx[0] + J[1][1] * lx[1] + mu * a.d[1];
+        lT = lT_new; lx[0] = lx0; lx[1] = lx1;
+      }
+    }
+  }
+  std::vector<double> tot((size_t)n * 8, 0.0);
+  for (int t = 0; t < nthreads; ++t)
+    for (size_t i = 0; i < tot.size(); ++i) tot[i] += acc[t][i];
+  for (int j = 0; j < n; ++j) {
+    for (int t = 0; t < 5; ++t) g_geo[(size_t)j * 5 + t] = tot[(size_t)j * 8 + t];
+    if (g_col) for (int c = 0; c < 3; ++c) g_col[(size_t)j * 3 + c] = tot[(size_t)j * 8 + 5 + c];
+  }
+  // colour chain rule: c_j = sum_q p_jq Pal_q, p = softmax(z / tau_c):
+  // dc_j/dz_jq = p_jq (Pal_q - c_j) / tau_c.
+  if (g_logits) {
+    for (int j = 0; j < n; ++j)
+      for (int q = 0; q < k; ++q) {
+        double d = 0.0;
+        for (int c = 0; c < 3; ++c)
+          d += (p->palette[q * 3 + c] - col[(size_t)j * 3 + c]) * tot[(size_t)j * 8 + 5 + c];
+        g_logits[(size_t)j * k + q] = prob[(size_t)j * k + q] * d / p->color_temp;
+      }
+  }
+  if (g_pal) {
+    for (int q = 0; q < k; ++q)
+      for (int c = 0; c < 3; ++c) {
+        double d = 0.0;
+        for (int j = 0; j < n; ++j) d += prob[(size_t)j * k + q] * tot[(size_t)j * 8 + 5 + c];
+        g_pal[q * 3 + c] = d;
+      }
+  }
+  return 0;
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

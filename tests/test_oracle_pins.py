@@ -1,0 +1,404 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values the
+paper prints (tests/golden/), closed forms (the drop map), exact invariants
+(round trip, area, symmetry, commutation, compositing), brute force on tiny
+inputs and finite differences.  A plausible slip in the oracle (a dropped term,
+a wrong sign or index, a transposed operand) fails at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_08722_b300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+DETJ = json.load(open(os.path.join(GOLDEN, "table_detj.json")))
+SIDE = json.load(open(os.path.join(GOLDEN, "side_table.json")))
+
+
+def seg_distance(pts, stroke):
+    """Distance to the segment by projection onto [a, b] (independent of the oracle's fold)."""
+    cx, cy, th, L, r = stroke
+    e = np.array([math.cos(th), math.sin(th)])
+    a = np.array([cx, cy]) - 0.5 * L * e
+    if L == 0:
+        return np.hypot(pts[:, 0] - cx, pts[:, 1] - cy)
+    t = np.clip((pts - a) @ e / L, 0.0, 1.0)
+    foot = a[None, :] + (t * L)[:, None] * e[None, :]
+    return np.hypot(*(pts - foot).T)
+
+
+def exterior_sample(stroke, n=200_000, box=0.5, seed=7):
+    cx, cy = stroke[0], stroke[1]
+    u = inputs.uniform(seed, 4 * n).reshape(-1, 2)
+    pts = np.array([cx, cy]) + (2 * u - 1) * box
+    return pts[seg_distance(pts, stroke) > stroke[4]][:n]
+
+
+CAPSULE = (0.0, 0.0, 0.0, DETJ["capsule"]["L"], DETJ["capsule"]["r"])
+ROTATED = (0.31, 0.62, 1.1, 0.13, 0.045)
+
+
+def reflect_bisector(p, stroke):
+    """Mirror across the segment's perpendicular bisector."""
+    cx, cy, th = stroke[:3]
+    e = np.array([math.cos(th), math.sin(th)])
+    d = p - np.array([cx, cy])
+    return p - 2.0 * (d @ e)[:, None] * e[None, :]
+
+
+def reflect_line(p, stroke):
+    """Mirror across the segment's supporting line."""
+    cx, cy, th = stroke[:3]
+    n = np.array([-math.sin(th), math.cos(th)])
+    d = p - np.array([cx, cy])
+    return p - 2.0 * (d @ n)[:, None] * n[None, :]
+
+
+def steiner_area(L, s):
+    return 2 * L * s + math.pi * s * s
+
+
+# --------------------------------------------------------------------------- operator
+
+@pytest.mark.parametrize("stroke", [(0.3, 0.6, 0.7, 0.0, 0.04), (0.5, 0.5, 2.0, 0.0, 0.01)])
+def test_drop_limit_is_the_drop_map(stroke):
+    """At L = 0, Eq. back is the radial drop map sigma = sqrt(sigma'^2 - r^2) and
+    its inverse is x' = c + (x - c) sqrt(1 + r^2/|x - c|^2) (Sec. 4, drop limit)."""
+    cx, cy, _, _, r = stroke
+    pts = exterior_sample(stroke, 20_000)
+    c = np.array([cx, cy])
+    d = pts - c
+    rho = np.hypot(*d.T)
+    back = c + d * (np.sqrt(rho ** 2 - r ** 2) / rho)[:, None]
+    fwd = c + d * np.sqrt(1.0 + r ** 2 / rho ** 2)[:, None]
+    assert np.abs(oracle.psi_map(pts, stroke, oracle.MODE_CLAMP) - back).max() < 1e-14
+    assert np.abs(oracle.phi_map(pts, stroke) - fwd).max() < 1e-14
+
+
+def test_short_capsule_converges_to_drop():
+    """Table detj, row 'drop limit, L = 1e-6' prints 2.9e-6 (FP64) for an
+    unspecified point sample; on the uniform sample the deviation is of that
+    order and shrinks in proportion to L."""
+    r = CAPSULE[4]
+    pts = exterior_sample(CAPSULE)
+    rho = np.hypot(*pts.T)
+    drop = pts * (np.sqrt(rho ** 2 - r ** 2) / rho)[:, None]
+    err = {}
+    for L in (1e-6, 1e-7):
+        got = oracle.psi_map(pts, (0.0, 0.0, 0.0, L, r), oracle.MODE_CLAMP)
+        far = rho > r + 1e-3
+        err[L] = np.abs(got - drop)[far].max()
+    printed = DETJ["float64"]["drop_limit_L_1e-6"]
+    assert printed / 30 < err[1e-6] < printed * 3
+    assert 5.0 < err[1e-6] / err[1e-7] < 20.0
+
+
+@pytest.mark.parametrize("stroke", [CAPSULE, ROTATED])
+def test_round_trip(stroke):
+    """Phi o psi = id on the exterior and psi o Phi = id off the segment
+    (Prop. 1; Table detj prints 5.7e-15 in FP64)."""
+    pts = exterior_sample(stroke)
+    rt = oracle.phi_map(oracle.psi_map(pts, stroke, oracle.MODE_CLAMP), stroke)
+    assert np.abs(rt - pts).max() < 20 * DETJ["float64"]["round_trip"]
+    u = inputs.uniform(3, 2 * 50_000).reshape(-1, 2) - 0.5 + np.array(stroke[:2])
+    rt2 = oracle.psi_map(oracle.phi_map(u, stroke), stroke, oracle.MODE_CLAMP)
+    assert np.abs(rt2 - u).max() < 20 * DETJ["float64"]["round_trip"]
+
+
+@pytest.mark.parametrize("direction", [0, 1])
+def test_area_jacobian(direction):
+    """det D psi = det D Phi = 1 on the exterior (Prop. 1; Table detj prints
+    1.6e-15 for |det J - 1| in FP64)."""
+    pts = exterior_sample(ROTATED, 50_000)
+    J = oracle.map_jacobian(pts, ROTATED, direction=direction, mode=oracle.MODE_CLAMP)
+    det = J[:, 0, 0] * J[:, 1, 1] - J[:, 0, 1] * J[:, 1, 0]
+    assert np.abs(det - 1.0).max() < 1e-12
+
+
+def _richardson_area(curve_fn, n):
+    """Shoelace area of a closed curve sampled at n and 2n points, Richardson-extrapolated."""
+    def shoelace(p):
+        x, y = p[:, 0] - p[:, 0].mean(), p[:, 1] - p[:, 1].mean()
+        return 0.5 * abs(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1)))
+    a1, a2 = shoelace(curve_fn(n)), shoelace(curve_fn(2 * n))
+    return (4 * a2 - a1) / 3
+
+
+def _square(x0, y0, side, n):
+    t = np.arange(n) / n * 4
+    k = np.floor(t).astype(int)
+    f = t - k
+    corners = np.array([[x0, y0], [x0 + side, y0], [x0 + side, y0 + side], [x0, y0 + side], [x0, y0]])
+    return corners[k] + (corners[k + 1] - corners[k]) * f[:, None]
+
+
+def test_polygon_area_preserved():
+    """A fine polygon outside the footprint keeps its area under psi to 1e-9
+    (Prop. 1, measure preservation)."""
+    stroke = ROTATED
+    side, x0, y0 = 0.05, 0.45, 0.78
+    corners = _square(x0, y0, side, 64)
+    assert seg_distance(corners, stroke).min() > stroke[4]
+    area = _richardson_area(lambda n: oracle.psi_map(_square(x0, y0, side, n), stroke, oracle.MODE_CLAMP), 1 << 16)
+    assert abs(area - side * side) / (side * side) < 1e-9
+
+
+def test_deposit_adds_capsule_area():
+    """Phi sends the parallel curve {sigma = s0} to the one enclosing
+    A_L(s0) + A_L(r): the deposit adds 2 L r + pi r^2 (Eq. steiner, Eq. phi)."""
+    cx, cy, th, L, r = ROTATED
+    s0 = 0.02
+
+    def stadium(n):
+        t = np.arange(n) / n * (2 * L + 2 * math.pi * s0)
+        pts = np.empty((n, 2))
+        for i, a in enumerate(t):
+            if a < L:
+                p = (-L / 2 + a, -s0)
+            elif a < L + math.pi * s0:
+                ang = (a - L) / s0 - math.pi / 2
+                p = (L / 2 + s0 * math.cos(ang), s0 * math.sin(ang))
+            elif a < 2 * L + math.pi * s0:
+                p = (L / 2 - (a - L - math.pi * s0), s0)
+            else:
+                ang = (a - 2 * L - math.pi * s0) / s0
+                p = (-L / 2 - s0 * math.sin(ang), s0 * math.cos(ang))
+            pts[i] = p
+        e = np.array([math.cos(th), math.sin(th)])
+        en = np.array([-math.sin(th), math.cos(th)])
+        return np.array([cx, cy]) + pts[:, :1] * e + pts[:, 1:] * en
+
+    area = _richardson_area(lambda n: oracle.phi_map(stadium(n), ROTATED), 1 << 13)
+    want = steiner_area(L, s0) + steiner_area(L, r)
+    assert abs(area - want) / want < 1e-9
+
+
+@pytest.mark.parametrize("stroke", [CAPSULE, ROTATED])
+def test_reflection_symmetry(stroke):
+    """Centred v commutes with both mirror symmetries of the capsule (Prop. 2;
+    Table detj: 5.9e-15); keeping raw q breaks the midplane mirror at ~4.6e-2."""
+    pts = exterior_sample(stroke)
+    for refl in (reflect_bisector, reflect_line):
+        a = oracle.psi_map(refl(pts, stroke), stroke, oracle.MODE_CLAMP)
+        b = refl(oracle.psi_map(pts, stroke, oracle.MODE_CLAMP), stroke)
+        assert np.abs(a - b).max() < 1e-13
+    if stroke is CAPSULE:
+        a = oracle.psi_map(reflect_bisector(pts, stroke), stroke, oracle.MODE_RAWQ)
+        b = reflect_bisector(oracle.psi_map(pts, stroke, oracle.MODE_RAWQ), stroke)
+        printed = DETJ["float64"]["midplane_reflection_raw_q"]
+        assert printed / 1.5 < np.abs(a - b).max() < printed * 1.5
+
+
+def test_same_segment_insertions_commute():
+    """Insertions at the same segment commute and compose to one insertion of
+    the summed area (Sec. 3; Phi is a translation in u)."""
+    cx, cy, th, L, _ = ROTATED
+    r1, r2 = 0.02, 0.035
+    area = steiner_area(L, r1) + steiner_area(L, r2)
+    r3 = (-2 * L + math.sqrt(4 * L * L + 4 * math.pi * area)) / (2 * math.pi)
+    s1, s2, s3 = (cx, cy, th, L, r1), (cx, cy, th, L, r2), (cx, cy, th, L, r3)
+    pts = exterior_sample(s3, 50_000)
+    a = oracle.psi_map(oracle.psi_map(pts, s2, oracle.MODE_CLAMP), s1, oracle.MODE_CLAMP)
+    b = oracle.psi_map(oracle.psi_map(pts, s1, oracle.MODE_CLAMP), s2, oracle.MODE_CLAMP)
+    c = oracle.psi_map(pts, s3, oracle.MODE_CLAMP)
+    assert np.abs(a - b).max() < 1e-13
+    assert np.abs(a - c).max() < 1e-13
+
+
+def test_interior_extension_and_floor():
+    """Inside the footprint the clamped map sends a flank point at signed
+    arclength t and distance sigma' to l t/(l + pi sigma') on the segment (Sec. 4,
+    'The chain'); the epsilon-floor lands within eps r / sqrt(pi) of the segment
+    on the same side and flags the sample (Sec. 5.2)."""
+    cx, cy, th, L, r = ROTATED
+    u = inputs.uniform(11, 2 * 5000).reshape(-1, 2)
+    s = (u[:, 0] - 0.5) * L
+    h = (u[:, 1] - 0.5) * 2 * r * 0.999
+    e = np.array([math.cos(th), math.sin(th)])
+    en = np.array([-math.sin(th), math.cos(th)])
+    pts = np.array([cx, cy]) + s[:, None] * e + h[:, None] * en
+    out = oracle.psi_map(pts, ROTATED, oracle.MODE_CLAMP)
+    d = out - np.array([cx, cy])
+    s_new, h_new = d @ e, d @ en
+    want = s * L / (L + math.pi * np.abs(h))
+    assert np.abs(s_new - want).max() < 1e-14
+    assert np.abs(h_new).max() < 1e-15
+    outf, fl = oracle.psi_map(pts, ROTATED, oracle.MODE_FLOOR, return_floored=True)
+    df = outf - np.array([cx, cy])
+    hf = df @ en
+    assert fl.all()
+    assert (np.abs(hf) <= 1e-3 * r / math.sqrt(math.pi) * (1 + 1e-12)).all()
+    assert (np.sign(hf) == np.sign(h)).all()
+
+
+# --------------------------------------------------------------------------- renderers
+
+def _tiny_program(n, seed, k=4, r_lo=0.05, r_hi=0.2, len_max=0.4):
+    return inputs.make_program(n, seed=seed, palette_seed=seed + 1, k=k, r_lo=r_lo, r_hi=r_hi,
+                               len_max=len_max)
+
+
+def test_compositing_identity():
+    """sum_i T_i alpha_i + T_0 = 1 per pixel (Sec. 6 visible-area identity):
+    white strokes on a white background render exactly white, and white strokes
+    on black render 1 - T_0."""
+    p = _tiny_program(12, 5)
+    p.palette[:] = 1.0
+    got = oracle.render_soft(p, 24, 24, 0.1, 0.01)
+    assert np.abs(got["rgb"] - 1.0).max() < 1e-12
+    p.background[:] = 0.0
+    got = oracle.render_soft(p, 24, 24, 0.1, 0.01)
+    assert np.abs(got["rgb"] - (1.0 - got["T0"])[:, None]).max() < 1e-12
+
+
+def test_inert_soft_render_is_over_compositing():
+    """With psi = id (inert-mark model, Definition 1) Eq. render is ordinary
+    back-to-front 'over' compositing of the coverage of each capsule."""
+    p = _tiny_program(9, 17)
+    W = H = 20
+    tau, tau_min = 0.2, 0.01
+    got = oracle.render_soft(p, W, H, tau, tau_min, inert=True)["rgb"]
+    jj, ii = np.meshgrid(np.arange(W), np.arange(H))
+    pts = np.stack([(jj.ravel() + 0.5) / W, (ii.ravel() + 0.5) / H], 1)
+    z = p.logits.astype(np.float64) / p.color_temp
+    prob = np.exp(z - z.max(1, keepdims=True))
+    prob /= prob.sum(1, keepdims=True)
+    col = prob @ p.palette.astype(np.float64)
+    img = np.tile(p.background.astype(np.float64), (W * H, 1))
+    for j in range(p.n):           # paint in program order, each stroke over the last
+        st = tuple(float(v) for v in (p.cx[j], p.cy[j], p.theta[j], p.length[j], p.half_width[j]))
+        w = max(tau * st[4], tau_min)
+        a = np.minimum(1 / (1 + np.exp(-(st[4] - seg_distance(pts, st)) / w)), 1 - 1e-7)
+        img = a[:, None] * col[j] + (1 - a[:, None]) * img
+    assert np.abs(got - img).max() < 1e-12
+
+
+def test_single_stroke_hard_render_is_the_capsule():
+    st = (0.45, 0.55, 0.6, 0.3, 0.12)
+    p = inputs.Program(cx=np.array([st[0]]), cy=np.array([st[1]]), theta=np.array([st[2]]),
+                       length=np.array([st[3]]), half_width=np.array([st[4]]),
+                       logits=np.zeros((1, 1)), palette=np.array([[0.2, 0.4, 0.6]]),
+                       background=np.ones(3), color_temp=1.0)
+    W = H = 64
+    got = oracle.render_hard(p, W, H)
+    jj, ii = np.meshgrid(np.arange(W), np.arange(H))
+    pts = np.stack([(jj.ravel() + 0.5) / W, (ii.ravel() + 0.5) / H], 1)
+    inside = seg_distance(pts, st) <= st[4]
+    assert np.array_equal(got["idx"] == 0, inside)
+    assert np.allclose(got["rgb"][inside], [0.2, 0.4, 0.6])
+
+
+def test_hard_chain_against_forward_replay():
+    """Brute force on a tiny program: trace each pixel back stroke by stroke
+    (Eq. chain) with the single-map routine and the projection distance, compare
+    the terminating stroke, then carry the in-deposit point forward through the
+    later strokes with Phi and land back on the pixel (Eq. rpos)."""
+    p = _tiny_program(8, 23, r_lo=0.03, r_hi=0.12)
+    W = H = 16
+    got = oracle.render_hard(p, W, H, with_kappa=True)
+    checked = 0
+    for q in range(W * H):
+        x0 = np.array([[(q % W + 0.5) / W, (q // W + 0.5) / H]])
+        x = x0.copy()
+        hit = -1
+        path = []
+        for j in range(p.n - 1, -1, -1):
+            st = tuple(float(v) for v in (p.cx[j], p.cy[j], p.theta[j], p.length[j], p.half_width[j]))
+            if seg_distance(x, st)[0] <= st[4]:
+                hit = j
+                break
+            path.append(st)
+            x = oracle.psi_map(x, st, oracle.MODE_CLAMP)
+        if got["margin"][q] < 1e-9:
+            continue
+        assert hit == got["idx"][q]
+        y = x.copy()
+        for st in reversed(path):
+            y = oracle.phi_map(y, st)
+        assert np.abs(y - x0).max() < 1e-12 * max(1.0, got["kappa"][q])
+        checked += 1
+    assert checked > 0.95 * W * H
+
+
+def test_soft_render_tends_to_hard():
+    """As the relaxation width goes to zero, Eq. relax tends to the indicator
+    and the soft render to the hard render away from deposit boundaries."""
+    p = _tiny_program(10, 31, r_lo=0.03, r_hi=0.1)
+    W = H = 24
+    hard = oracle.render_hard(p, W, H)
+    errs = []
+    for tmin in (1e-3, 1e-4, 1e-5):
+        soft = oracle.render_soft(p, W, H, 0.0, tmin)["rgb"]
+        far = hard["margin"] > 2e-2
+        errs.append(np.abs(soft - hard["rgb"])[far].max())
+    assert errs[-1] < 1e-6
+    assert errs[0] >= errs[1] >= errs[2]
+
+
+# --------------------------------------------------------------------------- adjoint
+
+def _vec(g, p):
+    return np.concatenate([g["cx"], g["cy"], g["theta"], g["length"], g["half_width"], g["logits"].ravel()])
+
+
+@pytest.mark.parametrize("inert", [False, True])
+def test_stored_state_adjoint_matches_finite_differences(inert):
+    """Eq. adjstep / Eq. adjparam (stored-state form) against FP64 central
+    differences of J = sum cot . R (the paper prints 2.5e-9 for its analytic
+    VJP against central differences)."""
+    p = _tiny_program(5, 41, r_lo=0.08, r_hi=0.2)
+    W = H = 10
+    tau, tau_min = 0.3, 0.02
+    cot = inputs.make_cotangent(9, W * H).astype(np.float64)
+    g = oracle.soft_vjp(p, W, H, tau, tau_min, cot, inert=inert)
+    params = [(j, q) for j in range(p.n) for q in list(range(5)) + [5 + t for t in range(p.k)]]
+    fd = oracle.fd_gradient(p, W, H, tau, tau_min, cot, params, h_geo=1e-6, h_logit=1e-6, inert=inert)
+    got = np.array([g[oracle._FIELD[q]][j] if q < 5 else g["logits"][j, q - 5] for (j, q) in params])
+    scale = np.abs(fd).max()
+    assert np.abs(got - fd).max() < 1e-6 * scale
+
+
+def test_stored_state_adjoint_matches_forward_mode():
+    """The reverse recurrence against exact forward-mode differentiation of the
+    whole soft render (the paper prints 5.4e-15 against autograd)."""
+    p = _tiny_program(6, 43, r_lo=0.06, r_hi=0.15)
+    W = H = 8
+    tau, tau_min = 0.25, 0.02
+    cot = inputs.make_cotangent(13, W * H).astype(np.float64)
+    g = oracle.soft_vjp(p, W, H, tau, tau_min, cot)
+    for j in range(p.n):
+        for q in range(5 + p.k):
+            d = oracle.soft_jvp(p, W, H, tau, tau_min, j, q)
+            want = float(np.sum(d * cot))
+            got = g[oracle._FIELD[q]][j] if q < 5 else g["logits"][j, q - 5]
+            assert abs(got - want) <= 1e-12 * (1 + abs(want))
+    for q in range(p.k):
+        for c in range(3):
+            d = oracle.soft_jvp(p, W, H, tau, tau_min, 0, 5 + p.k + 3 * q + c)
+            assert abs(g["palette"][q, c] - float(np.sum(d * cot))) < 1e-12
+
+
+def test_zero_length_angle_gradient_vanishes():
+    """A drop has no direction: d/d theta is zero at L = 0 (reading of the L = 0 kink)."""
+    p = _tiny_program(6, 47)
+    p.length[:] = 0.0
+    cot = inputs.make_cotangent(5, 100).astype(np.float64)
+    g = oracle.soft_vjp(p, 10, 10, 0.3, 0.02, cot)
+    assert np.abs(g["theta"]).max() < 1e-13
+
+
+def test_side_table_size_is_plausible():
+    """Record count per pixel at 2000 strokes, sampled at 1024^2, against the
+    paper's measured 9.9-14 records per pixel (a sanity band, not a bound)."""
+    p = inputs.operating_program()
+    pix = inputs.sample_pixels(3, 1024 * 1024, 1500)
+    got = oracle.render_soft(p, 1024, 1024, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+    mean = got["nrec"].mean()
+    lo, hi = SIDE["records_per_pixel_range"]
+    assert lo / 4 < mean < hi * 4
