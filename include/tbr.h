@@ -1,0 +1,190 @@
+/*
+ * tbr.h -- C ABI of the B300-native transport-based renderer (TBR, capsule
+ * deposition strokes).
+ *
+ * The library renders an ordered program of capsule strokes by pulling each
+ * pixel back through the closed-form inverse exterior transport of every later
+ * stroke (Sec. 3, Eq. chain and Eq. render; Sec. 4, Eq. back), and
+ * differentiates the soft render with the replay adjoint of Sec. 5.2 (Eq. rpos,
+ * Eq. rT, Eq. adjstep, Eq. adjparam): exterior states are regenerated with the
+ * forward map (Eq. fwd) and only the samples the epsilon-floor touched are read
+ * from a side table.
+ *
+ * Conventions shared by every entry point
+ *   - Program order: stroke 0 is executed first (the paper's g_1); rendering
+ *     visits strokes n-1 down to 0.
+ *   - A stroke is (cx, cy, theta, length, half_width): the segment
+ *     [m - L e/2, m + L e/2] with m = (cx, cy), e = (cos theta, sin theta),
+ *     L = length >= 0 (0 is a drop) and r = half_width > 0 (Sec. 3).
+ *   - Colour c_i = softmax(logits_i / color_temp) . palette (Sec. 5.1); the hard
+ *     render can snap to the palette entry of the largest logit.
+ *   - The canvas is [0,1]^2; pixel (row, col) is sampled once at
+ *     ((col + 0.5)/W, (row + 0.5)/H).  Images are row-major [H][W][3] float32
+ *     (RGB interleaved); index maps are [H][W] int32.
+ *   - Unless stated otherwise every pointer is a DEVICE pointer owned by the
+ *     caller; the library never frees it.  Opaque handles (tbr_ctx, tbr_fit,
+ *     tbr_server) are owned by the library and released by their *_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls enqueue
+ *     work and return without synchronising unless their comment says so.
+ *   - Errors: every call returns a tbr_status; tbr_last_error() gives a
+ *     thread-local message for the last failure.  Argument checks that need
+ *     only host data (sizes, NULL pointers) fail synchronously.  Value checks
+ *     that need device data (r <= 0, L < 0, non-finite parameters) run in the
+ *     packing kernel; a program that fails them renders NaN and the failure is
+ *     reported by the next synchronising call (tbr_ctx_status, tbr_fit_step,
+ *     a call given a stats pointer) as TBR_ERR_INVALID_ARG.
+ */
+#ifndef TBR_H_
+#define TBR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TBR_API __attribute__((visibility("default")))
+#else
+#define TBR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TBR_OK = 0,
+  TBR_ERR_INVALID_ARG = 1,  /* bad size, NULL pointer, or bad parameter value */
+  TBR_ERR_OOM = 2,          /* device allocation failed */
+  TBR_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the detail) */
+  TBR_ERR_TIMEOUT = 4,      /* a bounded device wait gave up (status word set) */
+  TBR_ERR_ADMISSION = 5,    /* serving: request refused by the memory cap */
+  TBR_ERR_OVERFLOW = 6,     /* side table overflowed its per-pixel capacity */
+  TBR_ERR_NOT_FOUND = 7     /* serving: unknown program or request id */
+} tbr_status;
+
+/* A stroke program (Sec. 3 problem statement, re-expressed as centre,
+ * direction, length, half-width and palette logits).  Device pointers, fp32,
+ * arrays of length n in program order unless noted. */
+typedef struct {
+  int32_t n;                /* number of strokes N >= 0 */
+  int32_t k;                /* palette size K >= 1 */
+  const float* cx;          /* segment centre x, canvas units */
+  const float* cy;          /* segment centre y */
+  const float* theta;       /* direction angle (radians) */
+  const float* length;      /* full segment length L >= 0 */
+  const float* half_width;  /* r > 0 */
+  const float* logits;      /* [n][k] palette-assignment logits */
+  const float* palette;     /* [k][3] sRGB colours */
+  float background[3];      /* c_0, host value */
+  float color_temp;         /* softmax temperature tau_c > 0, host value */
+} tbr_program;
+
+/* Statistics of one hard render (host struct). */
+typedef struct {
+  int64_t band_steps;       /* pixel-stroke steps whose |sigma' - r| fell in the
+                               FP64 band and were recomputed in FP64 */
+  int64_t background_pixels;/* pixels that left every footprint */
+  int64_t visited_steps;    /* pixel-stroke steps executed (early exit) */
+} tbr_hard_stats;
+
+/* Hard render (Sec. 3, Eq. chain and Eq. render with alpha = 1 on the closed
+ * footprint K_i): each pixel is pulled back through psi_i (Eq. back) of the
+ * strokes from n_prefix-1 down to 0 until it lands inside a footprint
+ * (sigma' <= r, the tie counts as inside) and takes that stroke's colour, else
+ * the background.  Steps with |sigma' - r| < 1e-4 decide membership and apply
+ * psi in FP64 from the FP32 position.
+ *   n_prefix   number of leading strokes to replay (-1 = all; Sec. 7 prefix
+ *              replay)
+ *   snap       0: softmax colour; 1: palette entry of the largest logit
+ *   out_rgb    [H][W][3] output
+ *   out_idx    [H][W] terminating stroke index or -1, or NULL
+ *   stats      host pointer or NULL; when non-NULL the call synchronises the
+ *              stream and reports device-side argument errors.
+ * Scratch: the packed strokes (128 B per stroke) and counters are allocated
+ * stream-ordered from the device's default memory pool and freed on return. */
+TBR_API tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
+                           int32_t snap, float* out_rgb, int32_t* out_idx,
+                           tbr_hard_stats* stats, void* stream);
+
+/* Options of the soft render / replay record. */
+typedef struct {
+  float tau;                /* relaxation width factor tau of Eq. relax */
+  float tau_min;            /* floor tau_min of Eq. relax */
+  int32_t checkpoint_every; /* k: store (x, log T) every k strokes (Sec. 5.2
+                               conditioning); 0 = library default (32) */
+  int32_t record_capacity;  /* side-table records per pixel; 0 = default (64) */
+  int32_t inert;            /* 1: psi = id (inert-mark model, Definition 1) */
+} tbr_soft_opts;
+
+typedef struct tbr_ctx tbr_ctx;
+
+/* Soft render (Eq. relax coverage with alpha clamped at 1 - 1e-7, Eq. state
+ * compositing, psi with the epsilon-floor C >= (1e-3 r)^2 of Sec. 5.2).
+ *   out_rgb  [H][W][3]
+ *   ctx      NULL: forward only.  Otherwise *ctx receives a new handle that
+ *            holds what the replay adjoint needs (Sec. 5.2): per pixel s_0 =
+ *            (x_0, log T_0), position checkpoints every k strokes, and the side
+ *            table of (i, x_i) for every sample the floor touched.  The program
+ *            arrays are packed into the handle, so the caller may change them
+ *            after this call returns on the stream.
+ * Memory: 16 B/pixel (s_0) + 16 B/pixel per checkpoint + 16 B/pixel per record
+ * slot, allocated stream-ordered. */
+TBR_API tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H,
+                           const tbr_soft_opts* opts, float* out_rgb, tbr_ctx** ctx,
+                           void* stream);
+
+/* Replay adjoint (Sec. 5.2): for i = 1..N regenerate x_i = Phi_i(x_{i-1})
+ * (Eq. rpos), or pop it from the side table, or reset it from a checkpoint;
+ * regenerate log T_i (Eq. rT); take the adjoint step (Eq. adjstep) and
+ * accumulate the parameter gradients (Eq. adjparam) of
+ * J = sum_pixels dL_drgb . R.
+ *   dL_drgb   [H][W][3] cotangent of the rendered image
+ *   g_*       [n] gradients w.r.t. cx, cy, theta, length, half_width (written)
+ *   g_logits  [n][k] (written)
+ *   g_palette [k][3] or NULL (written)
+ * The sums over pixels are reduced per CTA in fixed order and then across CTAs
+ * in fixed order, so results are bitwise reproducible for a given size. */
+TBR_API tbr_status tbr_render_backward(tbr_ctx* ctx, const float* dL_drgb, float* g_cx, float* g_cy,
+                               float* g_theta, float* g_length, float* g_half_width,
+                               float* g_logits, float* g_palette, void* stream);
+
+/* Counters of a context (host struct). */
+typedef struct {
+  int64_t records;          /* side-table records written */
+  int64_t max_records;      /* largest per-pixel record count */
+  int64_t overflow_pixels;  /* pixels whose records exceeded the capacity */
+  int64_t drift_resets;     /* checkpoint resets where the regenerated position
+                               differed from the stored one by more than 1e-5 */
+  int64_t timeouts;         /* bounded waits that gave up */
+  int64_t invalid_params;   /* strokes that failed the value checks */
+} tbr_ctx_stats;
+
+/* Synchronises the context's last stream and reads its counters.  Returns
+ * TBR_ERR_OVERFLOW, TBR_ERR_TIMEOUT or TBR_ERR_INVALID_ARG if the matching
+ * counter is non-zero (the gradients of such a context are NaN). */
+TBR_API tbr_status tbr_ctx_status(tbr_ctx* ctx, tbr_ctx_stats* stats);
+
+/* Device bytes held by a context. */
+TBR_API size_t tbr_ctx_bytes(const tbr_ctx* ctx);
+
+/* Releases a context (stream-ordered on the stream it was created on). */
+TBR_API void tbr_ctx_destroy(tbr_ctx* ctx);
+
+/* Pixel mean-squared error on sRGB values (Sec. 5.1 "Objective and
+ * metrics"): loss = mean over the 3*H*W values of (rgb - target)^2, written to
+ * loss_out[0] (device, fp32; the sum is carried in fp64), and
+ * dL_drgb = 2 (rgb - target) / (3 H W) (device, may be NULL).  Scratch: one
+ * fp64 partial per block, stream-ordered. */
+TBR_API tbr_status tbr_loss_mse(const float* rgb, const float* target, int64_t n_pixels,
+                        float* loss_out, float* dL_drgb, void* stream);
+
+/* Thread-local description of the last error (never NULL). */
+TBR_API const char* tbr_last_error(void);
+
+/* Library version string. */
+TBR_API const char* tbr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif  /* TBR_H_ */

@@ -1,0 +1,447 @@
+// Internal header of the TBR CUDA library (sm_103a): packed stroke layout,
+// PTX wrappers for 1-D bulk TMA staging with mbarriers, and the per-step device
+// math of the capsule transport (Sec. 4) and the replay adjoint (Sec. 5.2).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tbr.h"
+
+namespace tbr {
+
+// ---------------------------------------------------------------------------
+// Packed stroke record: 32 floats (128 B) per stroke, built once per call by
+// k_pack (tbr_pack.cu) and staged into shared memory chunk by chunk.
+// ---------------------------------------------------------------------------
+constexpr int kRec = 32;
+enum : int {
+  F_MX = 0, F_MY = 1, F_EX = 2, F_EY = 3,    // centre m, direction e
+  F_HL = 4, F_L = 5, F_R = 6, F_R2 = 7,      // L/2, L, r, r^2
+  F_L2 = 8, F_KA = 9, F_AR = 10, F_FL2 = 11, // L^2, 2L + pi r, A_L(r) = 2Lr + pi r^2, (eps r)^2
+  F_CR = 12, F_CG = 13, F_CB = 14, F_IW = 15,// colour c_i, 1 / max(tau r, tau_min)
+  F_DLW = 16, F_TH = 17, F_BAD = 18, F_2L = 19, // (dw/dr)/w, theta, invalid flag, 2L
+  F_D64 = 20                                 // 6 doubles: mx, my, ex, ey, L/2, r (FP64 band)
+};
+
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr double kPiD = 3.14159265358979323846;
+constexpr float kEpsFloor = 1e-3f;           // epsilon of the floor (Sec. 5.2)
+constexpr float kZMax = 16.11809565095832f;  // ln(1e7 - 1): alpha <= 1 - 1e-7
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kBand = 1e-4f;               // FP64 band half-width on |sigma' - r|
+constexpr float kDriftTol = 1e-5f;           // checkpoint drift threshold
+
+// Device status words (unsigned long long[ST_COUNT]).
+enum : int {
+  ST_TIMEOUT = 0, ST_OVERFLOW = 1, ST_DRIFT = 2, ST_BAND = 3, ST_INVALID = 4,
+  ST_RECORDS = 5, ST_MAXREC = 6, ST_BG = 7, ST_VISITED = 8, ST_COUNT = 16
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers: mbarrier + cp.async.bulk (1-D bulk TMA, global -> shared).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait on an mbarrier phase: gives up after ~2 s of device time, sets
+// the timeout status word and returns false.  Never traps.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  unsigned long long* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && global_timer_ns() - t0 > 2000000000ull) break;
+  }
+  atomicAdd(status + ST_TIMEOUT, 1ull);
+  return false;
+}
+
+// Two-deep ring of stroke chunks in shared memory.  Iteration q of a kernel's
+// chunk loop consumes buffer q & 1; thread 0 refills it with the chunk of
+// iteration q + 2 once every thread has passed the end-of-chunk barrier.
+template <int CH>
+struct ChunkRing {
+  float* buf;         // [2][CH * kRec]
+  uint64_t* bar;      // [2]
+  uint32_t phase;     // bit b = expected parity of buffer b
+  uint32_t pending;   // bit b = a copy into buffer b is in flight
+
+  __device__ __forceinline__ void init(float* b, uint64_t* br) {
+    buf = b; bar = br; phase = 0; pending = 0;
+    if (threadIdx.x == 0) {
+      mbar_init(&bar[0], 1);
+      mbar_init(&bar[1], 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  // Thread 0 only: copy `count` packed strokes starting at `src` into buffer b.
+  __device__ __forceinline__ void issue(int b, const float* src, int count) {
+    const uint32_t bytes = static_cast<uint32_t>(count) * kRec * 4u;
+    mbar_expect_tx(&bar[b], bytes);
+    bulk_copy_g2s(buf + b * CH * kRec, src, bytes, &bar[b]);
+  }
+  // All threads: wait for buffer b; false on timeout.
+  __device__ __forceinline__ bool wait(int b, unsigned long long* status) {
+    const bool ok = mbar_wait_bounded(&bar[b], (phase >> b) & 1u, status);
+    phase ^= (1u << b);
+    return ok;
+  }
+  __device__ __forceinline__ const float* data(int b) const { return buf + b * CH * kRec; }
+};
+
+// ---------------------------------------------------------------------------
+// Stroke fields read from shared memory as broadcasts.
+// ---------------------------------------------------------------------------
+struct StrokeF {
+  float mx, my, ex, ey, hl, L, r, r2, L2, kA, Ar, fl2, iw, dlw, twoL;
+};
+__device__ __forceinline__ StrokeF load_stroke(const float* __restrict__ S) {
+  const float4 a = *reinterpret_cast<const float4*>(S);
+  const float4 b = *reinterpret_cast<const float4*>(S + 4);
+  const float4 c = *reinterpret_cast<const float4*>(S + 8);
+  const float4 d = *reinterpret_cast<const float4*>(S + 12);
+  const float4 e = *reinterpret_cast<const float4*>(S + 16);
+  StrokeF g;
+  g.mx = a.x; g.my = a.y; g.ex = a.z; g.ey = a.w;
+  g.hl = b.x; g.L = b.y; g.r = b.z; g.r2 = b.w;
+  g.L2 = c.x; g.kA = c.y; g.Ar = c.z; g.fl2 = c.w;
+  g.iw = d.w; g.dlw = e.x; g.twoL = e.w;
+  return g;
+}
+
+// ---------------------------------------------------------------------------
+// Per-step quantities of one application of psi_i at x_i (to x_{i-1}) in the
+// stroke frame, with the quadrant fold: s along e, h along e_perp, folded to
+// |s|, |h|; t is the arclength from the flank midpoint along the parallel curve
+// (the centred coordinate v of Eq. phi times the perimeter).
+// ---------------------------------------------------------------------------
+struct Geo {
+  float sgs, sgh;     // fold signs (psi keeps the quadrant)
+  float si, hi;       // signed frame coordinates of x_i
+  float so, ho;       // signed frame coordinates of x_{i-1}
+  float sp, sig;      // sigma' = dist(x_i), sigma = dist(x_{i-1})
+  float t, tn;        // folded arclength coordinates of x_i and x_{i-1}
+  float ud, uh;       // at x_i: cap ? ((|s|-L/2)/sigma', |h|/sigma') : (0, 1)
+  float phi;          // at x_i on a cap: angle from the flank normal
+  float sb, cb, beta; // at x_{i-1} on a cap: angle and its sine / cosine
+  bool cap_i, cap_o, floored;
+};
+
+__device__ __forceinline__ float sgn1(float v) { return copysignf(1.0f, v); }
+
+// psi evaluated explicitly at x_i with the epsilon-floor (Eq. back; Sec. 5.2),
+// keeping every intermediate the adjoint needs.  Returns x_{i-1}.
+__device__ __forceinline__ void psi_explicit(float x, float y, const StrokeF& g, Geo& q,
+                                             float& xo, float& yo) {
+  const float dx = x - g.mx, dy = y - g.my;
+  const float s = fmaf(dx, g.ex, dy * g.ey);
+  const float h = fmaf(dy, g.ex, -dx * g.ey);
+  q.sgs = sgn1(s); q.sgh = sgn1(h); q.si = s; q.hi = h;
+  const float as = fabsf(s), ah = fabsf(h);
+  const float d = as - g.hl;
+  q.cap_i = d > 0.0f;
+  if (q.cap_i) {
+    q.sp = sqrtf(fmaf(d, d, ah * ah));
+    const float inv = 1.0f / q.sp;
+    q.ud = d * inv; q.uh = ah * inv;
+    q.phi = atan2f(d, ah);
+    q.t = fmaf(q.sp, q.phi, g.hl);
+  } else {
+    q.sp = ah; q.ud = 0.0f; q.uh = 1.0f; q.phi = 0.0f; q.t = as;
+  }
+  float C = (q.sp - g.r) * fmaf(kPiF, q.sp, g.kA);
+  q.floored = C < g.fl2;
+  C = q.floored ? g.fl2 : C;
+  q.sig = C / (g.L + sqrtf(fmaf(kPiF, C, g.L2)));
+  const float Qp = fmaf(kPiF, q.sp, g.L), Q = fmaf(kPiF, q.sig, g.L);
+  q.tn = Qp > 0.0f ? q.t * (Q / Qp) : 0.0f;
+  float sn, hn;
+  if (q.tn <= g.hl) {
+    q.cap_o = false; q.beta = 0.0f; q.sb = 0.0f; q.cb = 1.0f;
+    sn = q.tn; hn = q.sig;
+  } else {
+    q.cap_o = true;
+    q.beta = (q.tn - g.hl) / q.sig;
+    sincosf(q.beta, &q.sb, &q.cb);
+    sn = fmaf(q.sig, q.sb, g.hl); hn = q.sig * q.cb;
+  }
+  q.so = copysignf(sn, s); q.ho = copysignf(hn, h);
+  xo = g.mx + fmaf(q.so, g.ex, -q.ho * g.ey);
+  yo = g.my + fmaf(q.so, g.ey, q.ho * g.ex);
+}
+
+// Regeneration x_i = Phi_i(x_{i-1}) (Eq. fwd, Eq. rpos), recording the same
+// intermediates as psi_explicit (the two maps share them exactly on the
+// exterior).  Input x_{i-1} = (x, y); returns x_i.
+__device__ __forceinline__ void phi_regen(float x, float y, const StrokeF& g, Geo& q,
+                                          float& xi, float& yi) {
+  const float dx = x - g.mx, dy = y - g.my;
+  const float s = fmaf(dx, g.ex, dy * g.ey);
+  const float h = fmaf(dy, g.ex, -dx * g.ey);
+  q.sgs = sgn1(s); q.sgh = sgn1(h); q.so = s; q.ho = h;
+  const float as = fabsf(s), ah = fabsf(h);
+  const float d = as - g.hl;
+  q.cap_o = d > 0.0f;
+  if (q.cap_o) {
+    q.sig = sqrtf(fmaf(d, d, ah * ah));
+    const float inv = 1.0f / q.sig;
+    q.sb = d * inv; q.cb = ah * inv;
+    q.beta = atan2f(d, ah);
+    q.tn = fmaf(q.sig, q.beta, g.hl);
+  } else {
+    q.sig = ah; q.sb = 0.0f; q.cb = 1.0f; q.beta = 0.0f; q.tn = as;
+  }
+  const float B = fmaf(q.sig, fmaf(kPiF, q.sig, g.twoL), g.Ar);
+  q.sp = B / (g.L + sqrtf(fmaf(kPiF, B, g.L2)));
+  const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
+  q.t = Q > 0.0f ? q.tn * (Qp / Q) : 0.0f;
+  float sn, hn;
+  if (q.t <= g.hl) {
+    q.cap_i = false; q.phi = 0.0f; q.ud = 0.0f; q.uh = 1.0f;
+    sn = q.t; hn = q.sp;
+  } else {
+    q.cap_i = true;
+    q.phi = (q.t - g.hl) / q.sp;
+    sincosf(q.phi, &q.ud, &q.uh);
+    sn = fmaf(q.sp, q.ud, g.hl); hn = q.sp * q.uh;
+  }
+  q.floored = false;
+  q.si = copysignf(sn, s); q.hi = copysignf(hn, h);
+  xi = g.mx + fmaf(q.si, g.ex, -q.hi * g.ey);
+  yi = g.my + fmaf(q.si, g.ey, q.hi * g.ex);
+}
+
+// Vector-Jacobian product of one step (Eq. adjstep, Eq. adjparam), written out
+// by reverse-mode differentiation of psi_explicit in the stroke frame.
+//   lam     lambda^x_{i-1} (world), replaced by lambda^x_i
+//   mua     mu_i * d alpha / d z (0 where the clamp binds)
+//   z       the (clamped) coverage logit (r - sigma') / w
+// Outputs: gradient of lambda^x_{i-1} . psi_i + mu_i alpha_i with respect to
+// (cx, cy, theta, L, r).
+__device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& lamx, float& lamy,
+                                         float mua, float z, float& gcx, float& gcy, float& gth,
+                                         float& gL, float& gr) {
+  const float ls = fmaf(lamx, g.ex, lamy * g.ey);   // lambda . e
+  const float lh = fmaf(lamy, g.ex, -lamx * g.ey);  // lambda . e_perp
+  const float gsn = q.sgs * ls, ghn = q.sgh * lh;
+  float g_tn, g_sig, g_hl = 0.0f, g_L = 0.0f, g_r = 0.0f, g_sp = 0.0f;
+  if (!q.cap_o) {
+    g_tn = gsn; g_sig = ghn;
+  } else {
+    g_sig = fmaf(gsn, q.sb, ghn * q.cb);
+    const float g_beta = q.sig * fmaf(gsn, q.cb, -ghn * q.sb);
+    g_hl = gsn;
+    g_tn = g_beta / q.sig;
+    g_hl -= g_tn;
+    g_sig -= g_tn * q.beta;
+  }
+  // tn = t * Q / Qp
+  const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
+  float g_t = 0.0f;
+  if (Qp > 0.0f) {
+    const float iQp = 1.0f / Qp;
+    g_t = g_tn * Q * iQp;
+    const float g_Q = g_tn * q.t * iQp;
+    const float g_Qp = -g_tn * q.tn * iQp;
+    g_L += g_Q + g_Qp;
+    g_sig = fmaf(kPiF, g_Q, g_sig);
+    g_sp = fmaf(kPiF, g_Qp, g_sp);
+  }
+  // sigma solves A_L(sigma) = C: d sigma/dC = 1/(2Q), d sigma/dL = -sigma/Q
+  float g_C = 0.0f;
+  if (Q > 0.0f) {
+    const float iQ = 1.0f / Q;
+    g_C = 0.5f * g_sig * iQ;
+    g_L -= g_sig * q.sig * iQ;
+  }
+  if (q.floored) {
+    g_r = fmaf(g_C * 2.0f * kEpsFloor * kEpsFloor, g.r, g_r);
+  } else {
+    g_sp = fmaf(2.0f * g_C, Qp, g_sp);                 // dC/dsigma' = P_L(sigma')
+    g_r -= 2.0f * g_C * fmaf(kPiF, g.r, g.L);          // dC/dr = -P_L(r)
+    g_L = fmaf(2.0f * g_C, q.sp - g.r, g_L);           // dC/dL = 2(sigma' - r)
+  }
+  // coverage alpha(z), z = (r - sigma') / w(r)
+  g_sp = fmaf(-mua, g.iw, g_sp);
+  g_r = fmaf(mua, fmaf(-z, g.dlw, g.iw), g_r);
+  // t and sigma' from (|s|, |h|): cap: t = L/2 + sigma' phi, sigma' = |(d, |h|)|
+  float g_as, g_ah;
+  if (q.cap_i) {
+    g_hl += g_t;
+    g_sp = fmaf(g_t, q.phi, g_sp);
+    const float g_d = fmaf(g_sp, q.ud, g_t * q.uh);
+    g_ah = fmaf(g_sp, q.uh, -g_t * q.ud);
+    g_as = g_d;
+    g_hl -= g_d;
+  } else {
+    g_as = g_t;
+    g_ah = g_sp;
+  }
+  g_L = fmaf(0.5f, g_hl, g_L);
+  const float GS = q.sgs * g_as, GH = q.sgh * g_ah;
+  const float nlx = fmaf(GS, g.ex, -GH * g.ey);
+  const float nly = fmaf(GS, g.ey, GH * g.ex);
+  gcx = lamx - nlx;
+  gcy = lamy - nly;
+  gth = fmaf(q.so, lh, -q.ho * ls) + fmaf(GS, q.hi, -GH * q.si);
+  gL = g_L;
+  gr = g_r;
+  lamx = nlx;
+  lamy = nly;
+}
+
+// Relaxed coverage (Eq. relax) in the logit form used by both soft kernels.
+struct Cover {
+  float z;      // clamped logit
+  float alpha;  // sigmoid(z)
+  float oma;    // 1 - alpha (computed without cancellation)
+  float dadz;   // alpha (1 - alpha), 0 where the clamp binds
+  float sp2;    // -log2(1 - alpha) = softplus(z) / ln 2
+};
+__device__ __forceinline__ Cover coverage(float sp, const StrokeF& g) {
+  Cover c;
+  const float zr = (g.r - sp) * g.iw;
+  const bool clamped = zr > kZMax;
+  c.z = clamped ? kZMax : zr;
+  const float e = exp2f(-fabsf(c.z) * kLog2e);
+  const float opl = 1.0f + e;
+  const float inv = 1.0f / opl;
+  const bool pos = c.z >= 0.0f;
+  c.alpha = pos ? inv : e * inv;
+  c.oma = pos ? e * inv : inv;
+  c.dadz = clamped ? 0.0f : e * inv * inv;
+  c.sp2 = fmaf(fmaxf(c.z, 0.0f), kLog2e, log2f(opl));
+  return c;
+}
+
+// Warp reduce-scatter of 8 values: afterwards every lane holds the warp total
+// of value (lane >> 2) & 7.
+__device__ __forceinline__ float warp_reduce8(const float (&v)[8]) {
+  const unsigned lane = threadIdx.x & 31u;
+  const bool b4 = lane & 16u, b3 = lane & 8u, b2 = lane & 4u;
+  float w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float send = b4 ? v[j] : v[j + 4];
+    const float keep = b4 ? v[j + 4] : v[j];
+    w[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float u[2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float send = b3 ? w[j] : w[j + 2];
+    const float keep = b3 ? w[j + 2] : w[j];
+    u[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const float send = b2 ? u[0] : u[1];
+  float r = (b2 ? u[1] : u[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers (defined in the .cu files of this directory).
+// ---------------------------------------------------------------------------
+struct PackArgs {
+  const tbr_program* prog;   // host struct with device pointers
+  int n;                     // strokes to pack (prefix)
+  float tau, tau_min;
+  int snap;
+  float* packed;             // [n][kRec]
+  float* probs;              // [n][k] softmax probabilities or NULL
+  unsigned long long* status;
+};
+cudaError_t launch_pack(const PackArgs& a, cudaStream_t st);
+
+cudaError_t launch_hard(const float* packed, int n, int W, int H, const float bg[3], float* out_rgb,
+                        int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st);
+
+struct SoftArgs {
+  const float* packed;
+  int n, W, H;
+  float bg[3];
+  int inert;
+  int ck_every;              // checkpoint interval k (>= 1)
+  int cap;                   // side-table capacity per pixel
+  float* out_rgb;
+  float4* s0;                // [P] or NULL (forward only)
+  float4* ckpt;              // [(n-1)/k][P] or NULL
+  float4* rec;               // [cap][P] or NULL
+  unsigned long long* status;
+};
+cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st);
+
+struct BwdArgs {
+  const float* packed;
+  int n, W, H;
+  float bg[3];
+  int inert;
+  int ck_every;
+  int cap;                   // side-table capacity per pixel
+  const float4* s0;
+  const float4* ckpt;
+  const float4* rec;
+  const float* dLdR;
+  float* partial;            // [grid][n][8]
+  int grid;
+  unsigned long long* status;
+};
+int backward_grid(int W, int H);
+cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st);
+
+struct EpilogueArgs {
+  const float* partial;
+  int grid, n, k;
+  const float* packed;
+  const float* probs;
+  const float* palette;
+  float inv_color_temp;
+  float* grad8;              // [n][8] scratch
+  float *g_cx, *g_cy, *g_th, *g_len, *g_r, *g_logits, *g_pal;
+  const unsigned long long* status;
+};
+cudaError_t launch_backward_epilogue(const EpilogueArgs& a, cudaStream_t st);
+
+cudaError_t launch_loss(const float* rgb, const float* target, int64_t npix, double* partial,
+                        int nblocks, float* loss_out, float* dLdR, cudaStream_t st);
+int loss_blocks(int64_t npix);
+
+}  // namespace tbr

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (see the design doc for the derivation):
+  * hard render: terminating stroke index bit-exact except pixels whose oracle
+    margin min_j |sigma'_j - r_j| < 1e-5 (counted); a mismatch outside that band
+    is accepted only where the oracle's chain condition kappa makes an FP32
+    trajectory uncertain beyond 1e-5 (kappa * 6e-8 > 1e-5), and is reported;
+  * soft render: |R_gpu - R_oracle| <= 1e-4 per channel;
+  * gradients: per parameter group ||g_gpu - g_oracle|| / ||g_oracle|| <= 1e-3.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_08722_b300 import inputs, tbr
+
+pytestmark = pytest.mark.gpu
+
+SOFT_TOL = 1e-4
+GRAD_TOL = 1e-3
+BAND = 1e-5
+GROUPS = ["cx", "cy", "theta", "length", "half_width", "logits", "palette"]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def hard_agreement(idx_gpu, o):
+    mism = idx_gpu != o["idx"]
+    band = o["margin"] < BAND
+    outside = mism & ~band
+    cond = o["kappa"] * 6e-8 > BAND
+    return mism, band, outside, cond
+
+
+@pytest.fixture(scope="module")
+def small():
+    p = inputs.small_program()
+    return p, tbr.DeviceProgram.from_host(p)
+
+
+def test_hard_small_program(small):
+    p, dp = small
+    W = H = 128
+    rgb, idx, st = tbr.render_hard(dp, W, H, stats=True)
+    o = oracle.render_hard(p, W, H, with_kappa=True)
+    mism, band, outside, cond = hard_agreement(idx.cpu().numpy().ravel(), o)
+    print(f"band pixels {band.sum()}, mismatches {mism.sum()} (outside band {outside.sum()}), stats {st}")
+    assert not (outside & ~cond).any()
+    ok = ~mism
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3)[ok] - o["rgb"][ok]).max() < 1e-6
+
+
+@pytest.mark.parametrize("W,H,n", [(77, 45, 50), (33, 9, 1), (40, 40, 0), (1, 1, 50)])
+def test_hard_ragged_sizes(small, W, H, n):
+    p, _ = small
+    q = p.prefix(n)
+    if n == 0:
+        q = p.prefix(0)
+    dq = tbr.DeviceProgram.from_host(q)
+    rgb, idx, _ = tbr.render_hard(dq, W, H)
+    o = oracle.render_hard(q, W, H, with_kappa=True)
+    mism, band, outside, cond = hard_agreement(idx.cpu().numpy().ravel(), o)
+    assert not (outside & ~cond).any()
+    if n == 0:
+        assert (idx.cpu().numpy() == -1).all()
+        assert np.allclose(rgb.cpu().numpy(), 1.0)
+
+
+def test_hard_prefix_and_snap(small):
+    p, dp = small
+    W = H = 64
+    for m in (0, 1, 17, 50):
+        _, idx, _ = tbr.render_hard(dp, W, H, n_prefix=m)
+        o = oracle.render_hard(p, W, H, n_prefix=m, with_kappa=True)
+        mism, band, outside, cond = hard_agreement(idx.cpu().numpy().ravel(), o)
+        assert not (outside & ~cond).any()
+        assert idx.max().item() < max(m, 0) or m == 0
+    rgb, idx, _ = tbr.render_hard(dp, W, H, snap=True)
+    o = oracle.render_hard(p, W, H, snap=True)
+    ok = idx.cpu().numpy().ravel() == o["idx"]
+    assert np.array_equal(rgb.cpu().numpy().reshape(-1, 3)[ok], o["rgb"][ok].astype(np.float32))
+
+
+def test_recolour_edit_keeps_the_index_map(small):
+    """Transport ignores pigment, so a recolour edit changes no terminating index (Sec. 7 edits)."""
+    p, dp = small
+    _, idx0, _ = tbr.render_hard(dp, 96, 96)
+    q = p.copy()
+    q.logits = np.ascontiguousarray(q.logits[:, ::-1])
+    _, idx1, _ = tbr.render_hard(tbr.DeviceProgram.from_host(q), 96, 96)
+    assert torch.equal(idx0, idx1)
+
+
+@pytest.mark.parametrize("res", [512, 1024, 2048, 4096])
+def test_hard_resolution_replay(res):
+    """One 2000-stroke program replayed at 512^2 .. 4096^2; sampled pixels vs the oracle."""
+    p = inputs.resolution_program()
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, idx, st = tbr.render_hard(dp, res, res, stats=True)
+    pix = inputs.sample_pixels(res, res * res, 4000)
+    o = oracle.render_hard(p, res, res, pix=pix, with_kappa=True)
+    mism, band, outside, cond = hard_agreement(idx.cpu().numpy().ravel()[pix], o)
+    print(f"{res}^2: band {band.sum()}, mismatches {mism.sum()}, outside band {outside.sum()} "
+          f"(ill-conditioned {(outside & cond).sum()}), fp64 steps {st['band_steps']}")
+    assert not (outside & ~cond).any()
+    assert mism.mean() < 0.01
+
+
+@pytest.mark.parametrize("tau,tau_min", [(0.0, 1 / 200), (0.3, 0.01)])
+def test_soft_small_program(small, tau, tau_min):
+    p, dp = small
+    W = H = 128
+    rgb, _ = tbr.render_soft(dp, W, H, tau, tau_min)
+    o = oracle.render_soft(p, W, H, tau, tau_min)
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"])
+    print(f"soft max {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= SOFT_TOL
+
+
+@pytest.mark.parametrize("W,H", [(77, 45), (1, 1), (33, 9)])
+def test_soft_ragged(small, W, H):
+    p, dp = small
+    rgb, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    cot = inputs.make_cotangent(21, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    for k in GROUPS:
+        assert rel(g[k].cpu().numpy().ravel(), og[k].ravel()) <= GRAD_TOL, k
+
+
+@pytest.mark.parametrize("tau,tau_min,inert", [(0.0, 1 / 200, False), (0.3, 0.01, False),
+                                               (0.3, 0.01, True)])
+def test_backward_small_program(small, tau, tau_min, inert):
+    p, dp = small
+    W = H = 128
+    rgb, ctx = tbr.render_soft(dp, W, H, tau, tau_min, record=True, inert=inert)
+    cot = inputs.make_cotangent(5, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    st = ctx.status()
+    og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64), inert=inert)
+    for k in GROUPS:
+        e = rel(g[k].cpu().numpy().ravel(), og[k].ravel())
+        print(f"{k}: {e:.3e}")
+        assert e <= GRAD_TOL, k
+    assert st["overflow_pixels"] == 0
+
+
+def test_backward_is_reproducible(small):
+    p, dp = small
+    _, ctx = tbr.render_soft(dp, 96, 96, 0.0, 1 / 200, record=True)
+    cot = torch.from_numpy(inputs.make_cotangent(7, 96 * 96)).reshape(96, 96, 3).cuda()
+    a = ctx.backward(cot)
+    b = ctx.backward(cot)
+    for k in GROUPS:
+        assert torch.equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("k", [8, 32, 1000])
+def test_checkpoint_interval_does_not_change_gradients(small, k):
+    p, dp = small
+    W = H = 64
+    cot = inputs.make_cotangent(8, W * H)
+    _, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=k)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    for name in GROUPS:
+        assert rel(g[name].cpu().numpy().ravel(), og[name].ravel()) <= GRAD_TOL
+
+
+@pytest.fixture(scope="module")
+def operating():
+    p = inputs.operating_program()
+    return p, tbr.DeviceProgram.from_host(p)
+
+
+def test_soft_operating_point_sampled(operating):
+    """2000 strokes at 1024^2 in the launch configuration the benchmark times."""
+    p, dp = operating
+    W = H = 1024
+    rgb, ctx = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, record=True)
+    pix = inputs.sample_pixels(31, W * H, 3000)
+    o = oracle.render_soft(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3)[pix] - o["rgb"])
+    print(f"soft op max {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= SOFT_TOL
+    st = ctx.status()
+    recs = o["nrec"].mean()
+    print(f"records/px gpu {st['records'] / (W * H):.2f} oracle(sampled) {recs:.2f}, max {st['max_records']}")
+    assert abs(st["records"] / (W * H) - recs) < 0.25 * recs + 0.5
+
+
+def test_backward_operating_point_sampled(operating):
+    """Full-size replay adjoint with the cotangent supported on sampled pixels,
+    against the oracle's stored-state adjoint on those pixels."""
+    p, dp = operating
+    W = H = 1024
+    _, ctx = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, record=True)
+    pix = inputs.sample_pixels(41, W * H, 2048)
+    cot = inputs.make_cotangent(42, pix.size)
+    full = torch.zeros((H * W, 3), device="cuda")
+    full[torch.from_numpy(pix).cuda()] = torch.from_numpy(cot).cuda()
+    g = ctx.backward(full.view(H, W, 3))
+    og = oracle.soft_vjp(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), pix=pix)
+    for k in GROUPS:
+        e = rel(g[k].cpu().numpy().ravel(), og[k].ravel())
+        print(f"{k}: {e:.3e}")
+        assert e <= GRAD_TOL, k
+
+
+def test_loss_mse_matches_numpy():
+    rng = np.random.default_rng(0)
+    a = rng.random((37, 53, 3), dtype=np.float32)
+    b = rng.random((37, 53, 3), dtype=np.float32)
+    loss, d = tbr.loss_mse(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+    want = np.mean((a.astype(np.float64) - b) ** 2)
+    assert abs(loss.item() - want) < 1e-6 * want
+    assert np.allclose(d.cpu().numpy(), 2 * (a - b) / a.size, rtol=1e-6, atol=1e-12)
+
+
+def test_invalid_stroke_values_are_reported(small):
+    p, _ = small
+    q = p.copy()
+    q.half_width[3] = -0.01
+    dq = tbr.DeviceProgram.from_host(q)
+    with pytest.raises(tbr.TbrError) as ei:
+        tbr.render_hard(dq, 32, 32, stats=True)
+    assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
+    rgb, ctx = tbr.render_soft(dq, 32, 32, 0.0, 1 / 200, record=True)
+    assert torch.isnan(rgb).all()
+    with pytest.raises(tbr.TbrError):
+        ctx.status()
+
+
+def test_side_table_overflow_is_reported(operating):
+    p, dp = operating
+    _, ctx = tbr.render_soft(dp, 256, 256, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, record=True,
+                             record_capacity=2)
+    g = ctx.backward(torch.ones((256, 256, 3), device="cuda"))
+    st = ctx.status(raise_on_error=False)
+    assert st["status"] == tbr.TBR_ERR_OVERFLOW and st["overflow_pixels"] > 0
+    assert torch.isnan(g["cx"]).all()
