@@ -1,0 +1,429 @@
+#!/usr/bin/env python3
+"""Benchmark of the TBR hot path: soft forward + replay adjoint of a
+2000-stroke capsule program at 1024^2 (FP32), the paper's operating point.
+
+One step = stroke packing, soft forward with the replay record (side table +
+position checkpoints), pixel-MSE loss and adjoint seed against a hard-rendered
+target, replay adjoint and gradient reduction: every kernel of the path, through
+the C ABI.  ``value`` = pixel-stroke evaluations per second
+(P * N per step / device time per step).  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Under torchrun (N > 1) every rank runs its own independent program (weak
+scaling; no collective on the data path), and the step time is the max over
+ranks.  ``--impl reference`` times the FP64 CPU oracle on a bounded pixel sample
+of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_STROKES, RES, PALETTE = 2000, 1024, 16
+CHECKPOINT_EVERY = 32
+
+# Algorithmic FP32 work per pixel-stroke (FP32 arithmetic instructions: add, mul
+# and fused multiply-add each count 1; transcendental / reciprocal operations are
+# counted separately), counted from the step formulas of the kernels at this
+# workload's measured branch mix (95% of steps on a capsule cap).  Derivation
+# table in DESIGN.md ("Roofline").
+OPS_FWD = 40.6
+OPS_BWD = 120.8
+XU_FWD = 11.8
+XU_BWD = 15.7
+# FP32 lane peak: 148 SMs x 128 FP32 lanes x 2032 MHz (one op per lane per cycle).
+SMS, LANES, SM_MAX_MHZ = 148, 128, 2032.0
+PEAK_GOPS = SMS * LANES * SM_MAX_MHZ * 1e-3
+
+METRIC = "pixel·stroke evals/s fwd+adjoint @2000 strokes 1024²"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fit-steps", type=int, default=5)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (torchrun) -- timing only, no collective on the data path
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world, backend):
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle (soft forward + stored-state adjoint)
+# ---------------------------------------------------------------------------
+def oracle_rate(prog, seconds, max_pixels=65536):
+    """evals/s of the oracle's soft forward + stored-state adjoint on a pixel
+    sample of the operating-point workload sized to ~``seconds`` of CPU time."""
+    import numpy as np
+
+    import oracle
+    from paper_2609_08722_b300 import inputs
+    total_pix = RES * RES
+
+    def run(m):
+        pix = inputs.sample_pixels(77, total_pix, m)
+        cot = inputs.make_cotangent(78, m).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.render_soft(prog, RES, RES, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+        oracle.soft_vjp(prog, RES, RES, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot, pix=pix)
+        return time.perf_counter() - t0
+
+    m = 64
+    dt = run(m)
+    m2 = int(min(max_pixels, max(64, m * seconds / max(dt, 1e-3))))
+    dt2 = run(m2)
+    rate = m2 * prog.n / dt2
+    return rate, {"pixels": m2, "seconds": dt2, "threads": oracle.num_threads()}
+
+
+def run_reference(args):
+    """--impl reference: the oracle as the reference arm (rank 0 only)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2609_08722_b300 import inputs
+    prog = inputs.operating_program()
+    per_step = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    rate0, info = oracle_rate(prog, per_step)
+    import numpy as np
+
+    import oracle
+    m = info["pixels"]
+    times = []
+    for s in range(args.warmup + args.steps):
+        pix = inputs.sample_pixels(100 + s, RES * RES, m)
+        cot = inputs.make_cotangent(200 + s, m).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.render_soft(prog, RES, RES, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+        oracle.soft_vjp(prog, RES, RES, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot, pix=pix)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    value = m * prog.n / step_s
+    sample = (f"{m} sampled pixels x {prog.n} strokes per step (of {RES}x{RES}): FP64 soft forward + "
+              f"stored-state adjoint")
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded program, no dataset)",
+        "impl": "reference",
+        "config": {"workload": "soft forward + replay adjoint, 2000 capsule strokes at 1024x1024 "
+                               "(CPU oracle on a pixel sample)",
+                   "strokes": prog.n, "resolution": [RES, RES], "palette": PALETTE},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": info["threads"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from paper_2609_08722_b300 import inputs, tbr
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    init_dist(world, "nccl")
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
+
+    # per-rank independent program (weak scaling); target = hard render of another program
+    prog_h = inputs.operating_program(seed=102 + 1000 * rank)
+    targ_h = inputs.operating_program(seed=103 + 1000 * rank)
+    prog = tbr.DeviceProgram.from_host(prog_h, device)
+    targ = tbr.DeviceProgram.from_host(targ_h, device)
+    W = H = RES
+    P = W * H
+    target, _, _ = tbr.render_hard(targ, W, H, with_idx=False)
+    tau, tau_min = inputs.SHARP_TAU, inputs.SHARP_TAU_MIN
+
+    rgb = torch.empty((H, W, 3), device=device)
+    _, ctx = tbr.render_soft(prog, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
+                             out_rgb=rgb)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=device)  # 256 MB > L2
+
+    def step():
+        tbr.render_soft(prog, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
+                        out_rgb=rgb, reuse=ctx)
+        loss, dL = tbr.loss_mse(rgb, target)
+        g = ctx.backward(dL)
+        return loss, g
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st = ctx.status()
+
+    tbr.profile_reset()
+    tbr.profile_enable(True)
+    clocks = ClockSampler(gpu_index)
+    time.sleep(0.3)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        starts[i].record()
+        step()
+        ends[i].record()
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    tbr.profile_enable(False)
+    step_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends)) / args.steps
+    kernel_ms = {}
+    for name in ("pack", "soft", "backward", "epilogue", "loss"):
+        launches, total = tbr.profile_read(name)
+        kernel_ms[name] = (launches, total)
+    st = ctx.status()
+
+    step_ms_max = max_over_ranks(step_ms, world, device)
+    units = float(P) * prog.n
+    value = sum_over_ranks(units, world, device) / (step_ms_max * 1e-3)
+
+    # roofline of the dominant kernel (replay adjoint), timed with events on its stream
+    bl, bt = kernel_ms["backward"]
+    bwd_ms = bt / max(bl, 1)
+    achieved = OPS_BWD * units / (bwd_ms * 1e-3) * 1e-9
+    sl, stt = kernel_ms["soft"]
+    soft_ms = stt / max(sl, 1)
+    traffic = None
+    prof_path = os.path.join(ROOT, "profiles", "traffic_backward_1024_2000.json")
+    if os.path.exists(prof_path):
+        try:
+            tr = json.load(open(prof_path))
+            if tr.get("source_sha") == _kernel_source_sha():
+                traffic = tr.get("bytes_per_launch")
+        except (OSError, ValueError):
+            traffic = None
+
+    # e2e through the public API with host buffers: upload program + target from
+    # pinned memory, fwd + loss + adjoint, read back gradients and loss
+    e2e = None
+    if True:
+        host_arrays = {name: torch.from_numpy(np.ascontiguousarray(getattr(prog_h, name), dtype=np.float32)).pin_memory()
+                       for name in ("cx", "cy", "theta", "length", "half_width", "logits", "palette")}
+        host_target = target.cpu().pin_memory()
+        dev_prog = tbr.DeviceProgram(**{k: torch.empty_like(v, device=device) for k, v in host_arrays.items()},
+                                     background=prog.background, color_temp=prog.color_temp)
+        dev_target = torch.empty_like(target)
+        out_names = ("cx", "cy", "theta", "length", "half_width", "logits", "palette")
+        host_out = {k: torch.empty(tuple(getattr(prog, k).shape), dtype=torch.float32).pin_memory()
+                    for k in out_names}
+        host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        h2d = sum(v.numel() * 4 for v in host_arrays.values()) + host_target.numel() * 4
+        d2h = sum(v.numel() * 4 for v in host_out.values()) + 4
+
+        def e2e_step():
+            for k, v in host_arrays.items():
+                getattr(dev_prog, k).copy_(v, non_blocking=True)
+            dev_target.copy_(host_target, non_blocking=True)
+            tbr.render_soft(dev_prog, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
+                            out_rgb=rgb, reuse=ctx)
+            loss, dL = tbr.loss_mse(rgb, dev_target)
+            g = ctx.backward(dL)
+            for k in out_names:
+                host_out[k].copy_(g[k], non_blocking=True)
+            host_loss.copy_(loss, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        es.record()
+        for _ in range(args.steps):
+            e2e_step()
+        ee.record()
+        torch.cuda.synchronize()
+        e2e_ms = max_over_ranks(es.elapsed_time(ee) / args.steps, world, device)
+        e2e = {"value": sum_over_ranks(units, world, device) / (e2e_ms * 1e-3), "unit": "evals/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    # fit step (A11): forward + loss + adjoint + Adam, schedules of Table hyper
+    fit_ms = None
+    if args.fit_steps > 0:
+        fit = tbr.Fit(prog, target, tbr.default_fit_config(iterations=200))
+        fit.step()
+        torch.cuda.synchronize()
+        fs, fe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fs.record()
+        for _ in range(args.fit_steps):
+            fit.step()
+        fe.record()
+        torch.cuda.synchronize()
+        fit_ms = fs.elapsed_time(fe) / args.fit_steps
+        fit.destroy()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, info = oracle_rate(prog_h, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "evals/s", "cores": info["threads"], "kind": "oracle",
+               "sample": f"{info['pixels']} sampled pixels x {prog_h.n} strokes of the {RES}x{RES} workload "
+                         f"(FP64 soft forward + stored-state adjoint, {info['seconds']:.1f} s)"}
+
+    launches_per_step = 5  # pack, soft, backward, grad-sum + colour epilogue (3), loss (2)
+    kernels_per_step = 1 + 1 + 1 + 3 + 2
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded programs, no dataset)",
+            "config": {"workload": "soft forward + replay adjoint, 2000 capsule strokes at 1024x1024",
+                       "strokes": prog.n, "resolution": [W, H], "palette": PALETTE, "tau": tau,
+                       "tau_min": tau_min, "checkpoint_every": CHECKPOINT_EVERY,
+                       "target": "hard render of a second seeded 2000-stroke program",
+                       "l2": "flushed between timed steps (256 MB write); step working set > L2",
+                       "parallelism": f"independent program per GPU x{world}"},
+            "roofline": {"bound": "alu", "kernel": "k_backward (replay adjoint)", "achieved": achieved,
+                         "peak": PEAK_GOPS, "unit": "Gop/s", "frac": achieved / PEAK_GOPS,
+                         "traffic": traffic, "ops_per_unit": OPS_BWD,
+                         "peak_basis": "148 SMs x 128 FP32 lanes x 2032 MHz (recipe unit counts and clock)"},
+            "kernel_ms": {"backward": bwd_ms, "soft_forward": soft_ms,
+                          "other": step_ms - bwd_ms - soft_ms},
+            "fit_step_ms": fit_ms,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": kernels_per_step * args.steps,
+            "records_per_pixel": st["records"] / P, "max_records": st["max_records"],
+            "drift_resets": st["drift_resets"], "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def _kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_08722_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

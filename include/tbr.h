@@ -120,12 +120,14 @@ typedef struct tbr_ctx tbr_ctx;
 /* Soft render (Eq. relax coverage with alpha clamped at 1 - 1e-7, Eq. state
  * compositing, psi with the epsilon-floor C >= (1e-3 r)^2 of Sec. 5.2).
  *   out_rgb  [H][W][3]
- *   ctx      NULL: forward only.  Otherwise *ctx receives a new handle that
- *            holds what the replay adjoint needs (Sec. 5.2): per pixel s_0 =
- *            (x_0, log T_0), position checkpoints every k strokes, and the side
- *            table of (i, x_i) for every sample the floor touched.  The program
- *            arrays are packed into the handle, so the caller may change them
- *            after this call returns on the stream.
+ *   ctx      NULL: forward only.  Otherwise, if *ctx is NULL it receives a
+ *            new handle that holds what the replay adjoint needs (Sec. 5.2):
+ *            per pixel s_0 = (x_0, log T_0), position checkpoints every k
+ *            strokes, and the side table of (i, x_i) for every sample the floor
+ *            touched.  If *ctx is an existing handle of the same n, k, W, H,
+ *            interval, capacity and inert flag, it is overwritten in place
+ *            (no allocation).  The program arrays are packed into the handle,
+ *            so the caller may change them once this call's work has run.
  * Memory: 16 B/pixel (s_0) + 16 B/pixel per checkpoint + 16 B/pixel per record
  * slot, allocated stream-ordered. */
 TBR_API tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H,
@@ -176,6 +178,83 @@ TBR_API void tbr_ctx_destroy(tbr_ctx* ctx);
  * fp64 partial per block, stream-ordered. */
 TBR_API tbr_status tbr_loss_mse(const float* rgb, const float* target, int64_t n_pixels,
                         float* loss_out, float* dL_drgb, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Fit (Sec. 5.1 "Parameterisation and relaxation", Eq. inverse, Table hyper):
+ * Adam on (cx, cy, theta, length, half_width, logits [, palette]) against a
+ * target image, loss = pixel MSE (Sec. 5.1 "Objective and metrics") +
+ * length_weight * sum_i L_i.  Each step renders the soft image at the
+ * annealed relaxation tau_t (geometric tau_start -> tau_end) and colour
+ * temperature (geometric color_temp_start -> color_temp_end), runs the replay
+ * adjoint, and applies Adam with cosine-decayed step sizes, then projects:
+ * centres into [0,1]^2, 0 <= L <= length_max, r into [width_lo r0, width_hi r0]
+ * with r0 the initial half-width of each stroke, palette into [0,1].
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t iterations;                   /* schedule length T (Table hyper: 240) */
+  float tau_start, tau_end;             /* relaxation schedule (0.35 -> 0.02) */
+  float tau_min;                        /* 0 = 0.7 / max(W, H) (Table hyper) */
+  float color_temp_start, color_temp_end;  /* 1.0 -> 0.05 */
+  float lr_center, lr_angle, lr_length, lr_width, lr_logits, lr_palette;
+  float beta1, beta2, adam_eps;         /* Adam (0.9, 0.999, 1e-8) */
+  float length_max;                     /* L_max (Table hyper: 0.30) */
+  float width_lo, width_hi;             /* half-width window factors (0.6, 1.7) */
+  float length_weight;                  /* lambda of the length regulariser (3e-4) */
+  int32_t train_palette;                /* 1: the palette is optimised too */
+  int32_t checkpoint_every;             /* replay checkpoint interval (0 = 32) */
+  int32_t record_capacity;              /* initial side-table capacity (0 = 64);
+                                           doubled and the step redone on overflow */
+} tbr_fit_config;
+
+typedef struct tbr_fit tbr_fit;
+
+/* Fills the defaults listed above. */
+TBR_API void tbr_fit_default_config(tbr_fit_config* cfg);
+
+/* Creates a fit: copies the initial program and the [H][W][3] target into
+ * library-owned device memory (stream-ordered).  cfg may be NULL (defaults). */
+TBR_API tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t W, int32_t H,
+                                  const tbr_fit_config* cfg, tbr_fit** fit, void* stream);
+
+/* One optimisation step (forward, loss, replay adjoint, update).  Synchronises
+ * the stream once to read the loss and the context status; loss_out (host,
+ * nullable) receives the loss of the parameters before the update. */
+TBR_API tbr_status tbr_fit_step(tbr_fit* fit, float* loss_out, void* stream);
+
+/* A view of the current program (device pointers into the fit; valid until the
+ * next step or destroy).  color_temp is the current schedule value. */
+TBR_API tbr_status tbr_fit_get_program(const tbr_fit* fit, tbr_program* view);
+
+/* Number of completed steps. */
+TBR_API int32_t tbr_fit_iteration(const tbr_fit* fit);
+
+/* Releases the fit. */
+TBR_API void tbr_fit_destroy(tbr_fit* fit);
+
+/* ------------------------------------------------------------------------
+ * Per-kernel timing without a profiler: while enabled, each launch of the
+ * library's kernels is bracketed by CUDA events on its launch stream.
+ * tbr_profile_read synchronises the pending events and returns the launch
+ * count and summed device time of one kernel since the last reset.
+ * ------------------------------------------------------------------------ */
+enum {
+  TBR_K_PACK = 0,        /* stroke packing */
+  TBR_K_HARD = 1,        /* hard render */
+  TBR_K_SOFT = 2,        /* soft forward (+ replay record) */
+  TBR_K_BACKWARD = 3,    /* replay adjoint */
+  TBR_K_EPILOGUE = 4,    /* gradient sums and colour chain rule */
+  TBR_K_LOSS = 5,        /* MSE and adjoint seed */
+  TBR_K_UPDATE = 6,      /* Adam update */
+  TBR_K_SERVE = 7,       /* persistent serving kernel */
+  TBR_K_COUNT = 8
+};
+typedef struct {
+  int64_t launches;
+  double total_ms;
+} tbr_kernel_time;
+TBR_API tbr_status tbr_profile_enable(int32_t on);
+TBR_API tbr_status tbr_profile_read(int32_t kernel, tbr_kernel_time* out);
+TBR_API void tbr_profile_reset(void);
 
 /* Thread-local description of the last error (never NULL). */
 TBR_API const char* tbr_last_error(void);

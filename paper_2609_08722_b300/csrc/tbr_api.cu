@@ -6,13 +6,13 @@
 #include <cstring>
 #include <string>
 
-#include "tbr_internal.cuh"
+#include "tbr_host.h"
 
-using namespace tbr;
+namespace tbr {
 
 namespace {
-
 thread_local std::string g_last_error = "no error";
+}  // namespace
 
 tbr_status fail(tbr_status code, const char* fmt, ...) {
   char buf[512];
@@ -24,28 +24,11 @@ tbr_status fail(tbr_status code, const char* fmt, ...) {
   return code;
 }
 
+const char* last_error_text() { return g_last_error.c_str(); }
+
 tbr_status cuda_fail(cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation)
-    return fail(TBR_ERR_OOM, "%s: out of device memory", what);
+  if (e == cudaErrorMemoryAllocation) return fail(TBR_ERR_OOM, "%s: out of device memory", what);
   return fail(TBR_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-#define TBR_CUDA(call, what)                       \
-  do {                                             \
-    cudaError_t e_ = (call);                       \
-    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-  } while (0)
-
-template <class T>
-cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
-  *p = nullptr;
-  if (count == 0) return cudaSuccess;
-  return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
-}
-template <class T>
-void dfree(T*& p, cudaStream_t st) {
-  if (p) cudaFreeAsync(p, st);
-  p = nullptr;
 }
 
 tbr_status check_program(const tbr_program* p, int n_used) {
@@ -69,40 +52,99 @@ tbr_status check_size(int32_t W, int32_t H) {
   return TBR_OK;
 }
 
-}  // namespace
+cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert,
+                         cudaStream_t st) {
+  const size_t P = static_cast<size_t>(W) * H;
+  c->n = n; c->k = k; c->W = W; c->H = H;
+  c->ck = ck; c->cap = cap; c->inert = inert;
+  c->grid = backward_grid(W, H);
+  c->last_stream = st;
+  const size_t nck = n > 1 ? static_cast<size_t>((n - 1) / ck) : 0;
+  cudaError_t e = dalloc(&c->packed, static_cast<size_t>(n) * kRec, st);
+  if (e == cudaSuccess) e = dalloc(&c->status, ST_COUNT, st);
+  if (e == cudaSuccess) e = dalloc(&c->probs, static_cast<size_t>(n) * k, st);
+  if (e == cudaSuccess) e = dalloc(&c->palette, static_cast<size_t>(k) * 3, st);
+  if (e == cudaSuccess) e = dalloc(&c->s0, P, st);
+  if (e == cudaSuccess) e = dalloc(&c->ckpt, nck * P, st);
+  if (e == cudaSuccess && !inert) e = dalloc(&c->rec, static_cast<size_t>(cap) * P, st);
+  if (e == cudaSuccess) e = dalloc(&c->partial, static_cast<size_t>(c->grid) * n * 8, st);
+  if (e == cudaSuccess) e = dalloc(&c->grad8, static_cast<size_t>(n) * 8, st);
+  c->bytes = static_cast<size_t>(n) * kRec * 4 + ST_COUNT * 8 + static_cast<size_t>(n) * k * 4 +
+             static_cast<size_t>(k) * 12 + P * 16 + nck * P * 16 +
+             (inert ? 0 : static_cast<size_t>(cap) * P * 16) + static_cast<size_t>(c->grid) * n * 32 +
+             static_cast<size_t>(n) * 32;
+  return e;
+}
 
-struct tbr_ctx {
-  int n = 0, k = 0, W = 0, H = 0, ck = 32, cap = 64, inert = 0, grid = 0;
-  float bg[3] = {0, 0, 0};
-  float inv_tc = 1.0f;
-  float* packed = nullptr;
-  float* probs = nullptr;
-  float* palette = nullptr;
-  float4* s0 = nullptr;
-  float4* ckpt = nullptr;
-  float4* rec = nullptr;
-  unsigned long long* status = nullptr;
-  float* partial = nullptr;
-  float* grad8 = nullptr;
-  cudaStream_t create_stream = nullptr;
-  cudaStream_t last_stream = nullptr;
-  size_t bytes = 0;
-};
-
-namespace {
-
-void ctx_free(tbr_ctx* c) {
+void ctx_release(tbr_ctx* c) {
   cudaStream_t st = c->last_stream;
   dfree(c->packed, st); dfree(c->probs, st); dfree(c->palette, st);
   dfree(c->s0, st); dfree(c->ckpt, st); dfree(c->rec, st);
   dfree(c->status, st); dfree(c->partial, st); dfree(c->grad8, st);
 }
 
-}  // namespace
+cudaError_t ctx_forward(tbr_ctx* c, const tbr_program* prog, float tau, float tau_min, float* out_rgb,
+                        cudaStream_t st) {
+  c->last_stream = st;
+  for (int i = 0; i < 3; ++i) c->bg[i] = prog->background[i];
+  c->inv_tc = 1.0f / prog->color_temp;
+  cudaError_t e = cudaMemsetAsync(c->status, 0, ST_COUNT * sizeof(unsigned long long), st);
+  if (e == cudaSuccess && c->k > 0)
+    e = cudaMemcpyAsync(c->palette, prog->palette, static_cast<size_t>(c->k) * 12, cudaMemcpyDeviceToDevice, st);
+  PackArgs pa{prog, c->n, tau, tau_min, 0, c->packed, c->probs, c->status};
+  if (e == cudaSuccess) e = launch_pack(pa, st);
+  SoftArgs sa;
+  sa.packed = c->packed; sa.n = c->n; sa.W = c->W; sa.H = c->H;
+  for (int i = 0; i < 3; ++i) sa.bg[i] = c->bg[i];
+  sa.inert = c->inert; sa.ck_every = c->ck; sa.cap = c->cap;
+  sa.out_rgb = out_rgb; sa.s0 = c->s0; sa.ckpt = c->ckpt; sa.rec = c->rec; sa.status = c->status;
+  if (e == cudaSuccess) e = launch_soft(sa, st);
+  return e;
+}
+
+cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy, float* g_th,
+                         float* g_len, float* g_r, float* g_logits, float* g_pal, cudaStream_t st) {
+  c->last_stream = st;
+  if (c->n == 0) {
+    if (g_pal) return cudaMemsetAsync(g_pal, 0, static_cast<size_t>(c->k) * 12, st);
+    return cudaSuccess;
+  }
+  BwdArgs ba;
+  ba.packed = c->packed; ba.n = c->n; ba.W = c->W; ba.H = c->H;
+  for (int i = 0; i < 3; ++i) ba.bg[i] = c->bg[i];
+  ba.inert = c->inert; ba.ck_every = c->ck; ba.cap = c->cap;
+  ba.s0 = c->s0; ba.ckpt = c->ckpt; ba.rec = c->rec; ba.dLdR = dLdR;
+  ba.partial = c->partial; ba.grid = c->grid; ba.status = c->status;
+  cudaError_t e = launch_backward(ba, st);
+  if (e != cudaSuccess) return e;
+  EpilogueArgs ea;
+  ea.partial = c->partial; ea.grid = c->grid; ea.n = c->n; ea.k = c->k;
+  ea.packed = c->packed; ea.probs = c->probs; ea.palette = c->palette; ea.inv_color_temp = c->inv_tc;
+  ea.grad8 = c->grad8;
+  ea.g_cx = g_cx; ea.g_cy = g_cy; ea.g_th = g_th; ea.g_len = g_len; ea.g_r = g_r;
+  ea.g_logits = g_logits; ea.g_pal = g_pal; ea.status = c->status;
+  return launch_backward_epilogue(ea, st);
+}
+
+tbr_status ctx_read_status(tbr_ctx* c, unsigned long long host[ST_COUNT]) {
+  TBR_CUDA(cudaMemcpyAsync(host, c->status, ST_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                           c->last_stream),
+           "reading context status");
+  TBR_CUDA(cudaStreamSynchronize(c->last_stream), "synchronising context stream");
+  if (host[ST_INVALID]) return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);
+  if (host[ST_OVERFLOW])
+    return fail(TBR_ERR_OVERFLOW, "%llu pixels exceeded the side-table capacity %d", host[ST_OVERFLOW], c->cap);
+  if (host[ST_TIMEOUT]) return fail(TBR_ERR_TIMEOUT, "a bounded device wait gave up");
+  return TBR_OK;
+}
+
+}  // namespace tbr
+
+using namespace tbr;
 
 extern "C" {
 
-const char* tbr_last_error(void) { return g_last_error.c_str(); }
+const char* tbr_last_error(void) { return last_error_text(); }
 
 const char* tbr_version(void) { return "tbr-b300 0.1 (sm_103a)"; }
 
@@ -120,12 +162,15 @@ tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H, int32_
   unsigned long long* status = nullptr;
   TBR_CUDA(dalloc(&packed, static_cast<size_t>(n) * kRec, st), "allocating packed strokes");
   cudaError_t e = dalloc(&status, ST_COUNT, st);
-  if (e != cudaSuccess) { dfree(packed, st); return cuda_fail(e, "allocating status"); }
+  if (e != cudaSuccess) {
+    dfree(packed, st);
+    return cuda_fail(e, "allocating status");
+  }
   e = cudaMemsetAsync(status, 0, ST_COUNT * sizeof(unsigned long long), st);
   PackArgs pa{prog, n, 0.0f, 1.0f, snap ? 1 : 0, packed, nullptr, status};
   if (e == cudaSuccess) e = launch_pack(pa, st);
-  if (e == cudaSuccess) e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status,
-                                        stats != nullptr, st);
+  if (e == cudaSuccess)
+    e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status, stats != nullptr, st);
   unsigned long long host[ST_COUNT] = {0};
   if (e == cudaSuccess && stats) {
     e = cudaMemcpyAsync(host, status, sizeof(host), cudaMemcpyDeviceToHost, st);
@@ -138,7 +183,8 @@ tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H, int32_
     stats->band_steps = static_cast<int64_t>(host[ST_BAND]);
     stats->background_pixels = static_cast<int64_t>(host[ST_BG]);
     stats->visited_steps = static_cast<int64_t>(host[ST_VISITED]);
-    if (host[ST_INVALID]) return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);
+    if (host[ST_INVALID])
+      return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);
     if (host[ST_TIMEOUT]) return fail(TBR_ERR_TIMEOUT, "a bounded device wait gave up");
   }
   return TBR_OK;
@@ -156,54 +202,46 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return fail(TBR_ERR_INVALID_ARG, "need tau >= 0 and tau_min > 0");
   if (opts->checkpoint_every < 0 || opts->record_capacity < 0)
     return fail(TBR_ERR_INVALID_ARG, "negative checkpoint interval or record capacity");
-  if (ctx) *ctx = nullptr;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int n = prog->n, k = prog->k;
-  const size_t P = static_cast<size_t>(W) * H;
-  tbr_ctx* c = new tbr_ctx();
-  c->n = n; c->k = k; c->W = W; c->H = H;
-  c->ck = opts->checkpoint_every > 0 ? opts->checkpoint_every : 32;
-  c->cap = opts->record_capacity > 0 ? opts->record_capacity : 64;
-  c->inert = opts->inert ? 1 : 0;
-  for (int i = 0; i < 3; ++i) c->bg[i] = prog->background[i];
-  c->inv_tc = 1.0f / prog->color_temp;
-  c->create_stream = st;
-  c->last_stream = st;
-  const bool record = ctx != nullptr;
-  const size_t nck = (record && n > 1) ? static_cast<size_t>((n - 1) / c->ck) : 0;
-  cudaError_t e = dalloc(&c->packed, static_cast<size_t>(n) * kRec, st);
-  if (e == cudaSuccess) e = dalloc(&c->status, ST_COUNT, st);
-  if (record) {
-    c->grid = backward_grid(W, H);
-    if (e == cudaSuccess) e = dalloc(&c->probs, static_cast<size_t>(n) * k, st);
-    if (e == cudaSuccess) e = dalloc(&c->palette, static_cast<size_t>(k) * 3, st);
-    if (e == cudaSuccess) e = dalloc(&c->s0, P, st);
-    if (e == cudaSuccess) e = dalloc(&c->ckpt, nck * P, st);
-    if (e == cudaSuccess && !c->inert) e = dalloc(&c->rec, static_cast<size_t>(c->cap) * P, st);
-    if (e == cudaSuccess) e = dalloc(&c->partial, static_cast<size_t>(c->grid) * n * 8, st);
-    if (e == cudaSuccess) e = dalloc(&c->grad8, static_cast<size_t>(n) * 8, st);
-  }
-  c->bytes = static_cast<size_t>(n) * kRec * 4 + ST_COUNT * 8;
-  if (record)
-    c->bytes += static_cast<size_t>(n) * k * 4 + k * 12 + P * 16 + nck * P * 16 +
-                (c->inert ? 0 : static_cast<size_t>(c->cap) * P * 16) +
-                static_cast<size_t>(c->grid) * n * 32 + static_cast<size_t>(n) * 32;
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->status, 0, ST_COUNT * sizeof(unsigned long long), st);
-  if (e == cudaSuccess && record)
-    e = cudaMemcpyAsync(c->palette, prog->palette, static_cast<size_t>(k) * 12, cudaMemcpyDeviceToDevice, st);
-  PackArgs pa{prog, n, opts->tau, opts->tau_min, 0, c->packed, c->probs, c->status};
-  if (e == cudaSuccess) e = launch_pack(pa, st);
-  SoftArgs sa;
-  sa.packed = c->packed; sa.n = n; sa.W = W; sa.H = H;
-  for (int i = 0; i < 3; ++i) sa.bg[i] = prog->background[i];
-  sa.inert = c->inert; sa.ck_every = c->ck; sa.cap = c->cap;
-  sa.out_rgb = out_rgb; sa.s0 = c->s0; sa.ckpt = c->ckpt; sa.rec = c->rec; sa.status = c->status;
-  if (e == cudaSuccess) e = launch_soft(sa, st);
-  if (e != cudaSuccess || !record) {
-    ctx_free(c);
-    delete c;
+  const int ck = opts->checkpoint_every > 0 ? opts->checkpoint_every : 32;
+  const int cap = opts->record_capacity > 0 ? opts->record_capacity : 64;
+  if (!ctx) {
+    // forward only: the packed strokes and the status words are the only scratch
+    float* packed = nullptr;
+    unsigned long long* status = nullptr;
+    TBR_CUDA(dalloc(&packed, static_cast<size_t>(prog->n) * kRec, st), "allocating packed strokes");
+    cudaError_t e = dalloc(&status, ST_COUNT, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, ST_COUNT * sizeof(unsigned long long), st);
+    PackArgs pa{prog, prog->n, opts->tau, opts->tau_min, 0, packed, nullptr, status};
+    if (e == cudaSuccess) e = launch_pack(pa, st);
+    SoftArgs sa;
+    sa.packed = packed; sa.n = prog->n; sa.W = W; sa.H = H;
+    for (int i = 0; i < 3; ++i) sa.bg[i] = prog->background[i];
+    sa.inert = opts->inert ? 1 : 0; sa.ck_every = ck; sa.cap = cap;
+    sa.out_rgb = out_rgb; sa.s0 = nullptr; sa.ckpt = nullptr; sa.rec = nullptr; sa.status = status;
+    if (e == cudaSuccess) e = launch_soft(sa, st);
+    dfree(packed, st);
+    dfree(status, st);
     if (e != cudaSuccess) return cuda_fail(e, "tbr_render_soft");
     return TBR_OK;
+  }
+  const int inert = opts->inert ? 1 : 0;
+  tbr_ctx* c = *ctx;
+  if (c) {
+    // reuse an existing context of the same shape: no allocation
+    if (c->n != prog->n || c->k != prog->k || c->W != W || c->H != H || c->ck != ck || c->cap != cap ||
+        c->inert != inert)
+      return fail(TBR_ERR_INVALID_ARG, "context shape differs from this call (n, k, W, H, k_ckpt, capacity, inert)");
+    TBR_CUDA(ctx_forward(c, prog, opts->tau, opts->tau_min, out_rgb, st), "tbr_render_soft");
+    return TBR_OK;
+  }
+  c = new tbr_ctx();
+  cudaError_t e = ctx_allocate(c, prog->n, prog->k, W, H, ck, cap, inert, st);
+  if (e == cudaSuccess) e = ctx_forward(c, prog, opts->tau, opts->tau_min, out_rgb, st);
+  if (e != cudaSuccess) {
+    ctx_release(c);
+    delete c;
+    return cuda_fail(e, "tbr_render_soft");
   }
   *ctx = c;
   return TBR_OK;
@@ -216,35 +254,16 @@ tbr_status tbr_render_backward(tbr_ctx* c, const float* dL_drgb, float* g_cx, fl
   if (!dL_drgb) return fail(TBR_ERR_INVALID_ARG, "dL_drgb is NULL");
   if (c->n > 0 && (!g_cx || !g_cy || !g_theta || !g_length || !g_half_width || !g_logits))
     return fail(TBR_ERR_INVALID_ARG, "NULL gradient output");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  c->last_stream = st;
-  if (c->n == 0) {
-    if (g_palette) TBR_CUDA(cudaMemsetAsync(g_palette, 0, static_cast<size_t>(c->k) * 12, st), "memset");
-    return TBR_OK;
-  }
-  BwdArgs ba;
-  ba.packed = c->packed; ba.n = c->n; ba.W = c->W; ba.H = c->H;
-  for (int i = 0; i < 3; ++i) ba.bg[i] = c->bg[i];
-  ba.inert = c->inert; ba.ck_every = c->ck; ba.cap = c->cap;
-  ba.s0 = c->s0; ba.ckpt = c->ckpt; ba.rec = c->rec; ba.dLdR = dL_drgb;
-  ba.partial = c->partial; ba.grid = c->grid; ba.status = c->status;
-  TBR_CUDA(launch_backward(ba, st), "launching the replay adjoint");
-  EpilogueArgs ea;
-  ea.partial = c->partial; ea.grid = c->grid; ea.n = c->n; ea.k = c->k;
-  ea.packed = c->packed; ea.probs = c->probs; ea.palette = c->palette; ea.inv_color_temp = c->inv_tc;
-  ea.grad8 = c->grad8;
-  ea.g_cx = g_cx; ea.g_cy = g_cy; ea.g_th = g_theta; ea.g_len = g_length; ea.g_r = g_half_width;
-  ea.g_logits = g_logits; ea.g_pal = g_palette; ea.status = c->status;
-  TBR_CUDA(launch_backward_epilogue(ea, st), "launching the gradient epilogue");
+  TBR_CUDA(ctx_backward(c, dL_drgb, g_cx, g_cy, g_theta, g_length, g_half_width, g_logits, g_palette,
+                        static_cast<cudaStream_t>(stream)),
+           "tbr_render_backward");
   return TBR_OK;
 }
 
 tbr_status tbr_ctx_status(tbr_ctx* c, tbr_ctx_stats* stats) {
   if (!c) return fail(TBR_ERR_INVALID_ARG, "ctx is NULL");
   unsigned long long host[ST_COUNT] = {0};
-  TBR_CUDA(cudaMemcpyAsync(host, c->status, sizeof(host), cudaMemcpyDeviceToHost, c->last_stream),
-           "reading context status");
-  TBR_CUDA(cudaStreamSynchronize(c->last_stream), "synchronising context stream");
+  const tbr_status s = ctx_read_status(c, host);
   if (stats) {
     stats->records = static_cast<int64_t>(host[ST_RECORDS]);
     stats->max_records = static_cast<int64_t>(host[ST_MAXREC]);
@@ -253,18 +272,14 @@ tbr_status tbr_ctx_status(tbr_ctx* c, tbr_ctx_stats* stats) {
     stats->timeouts = static_cast<int64_t>(host[ST_TIMEOUT]);
     stats->invalid_params = static_cast<int64_t>(host[ST_INVALID]);
   }
-  if (host[ST_INVALID]) return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);
-  if (host[ST_OVERFLOW])
-    return fail(TBR_ERR_OVERFLOW, "%llu pixels exceeded the side-table capacity %d", host[ST_OVERFLOW], c->cap);
-  if (host[ST_TIMEOUT]) return fail(TBR_ERR_TIMEOUT, "a bounded device wait gave up");
-  return TBR_OK;
+  return s;
 }
 
 size_t tbr_ctx_bytes(const tbr_ctx* c) { return c ? c->bytes : 0; }
 
 void tbr_ctx_destroy(tbr_ctx* c) {
   if (!c) return;
-  ctx_free(c);
+  ctx_release(c);
   delete c;
 }
 

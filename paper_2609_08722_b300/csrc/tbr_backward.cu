@@ -282,6 +282,7 @@ int backward_grid(int W, int H) {
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
+  KernelTimer kt(TBR_K_BACKWARD, st);
   if (a.inert) k_backward<kBwdCH, true><<<a.grid, kBwdThreads, 0, st>>>(a);
   else k_backward<kBwdCH, false><<<a.grid, kBwdThreads, 0, st>>>(a);
   return cudaGetLastError();
@@ -292,6 +293,7 @@ cudaError_t launch_backward_epilogue(const EpilogueArgs& a, cudaStream_t st) {
     return cudaSuccess;
   }
   const int n8 = a.n * 8;
+  KernelTimer kt(TBR_K_EPILOGUE, st);
   k_grad_sum<<<(n8 + 255) / 256, 256, 0, st>>>(a.partial, a.grid, n8, a.grad8);
   k_grad_out<<<(a.n + 127) / 128, 128, 0, st>>>(a);
   if (a.g_pal) k_grad_palette<<<a.k * 3, 256, 0, st>>>(a);

@@ -175,6 +175,7 @@ __global__ void __launch_bounds__(256) k_hard(const float* __restrict__ packed, 
 cudaError_t launch_hard(const float* packed, int n, int W, int H, const float bg[3], float* out_rgb,
                         int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st) {
   const int tiles = ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+  KernelTimer kt(TBR_K_HARD, st);
   k_hard<kHardCH><<<tiles, 256, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb, out_idx,
                                          status, want_stats);
   return cudaGetLastError();

@@ -1,0 +1,70 @@
+// Host-side internals shared by the C ABI translation units: error reporting,
+// argument checks, stream-ordered allocation and the replay context.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "tbr.h"
+#include "tbr_internal.cuh"
+
+// Replay context (opaque in tbr.h): what one soft forward leaves for the
+// replay adjoint of Sec. 5.2, plus the backward's reduction scratch.
+struct tbr_ctx {
+  int n = 0, k = 0, W = 0, H = 0, ck = 32, cap = 64, inert = 0, grid = 0;
+  float bg[3] = {0, 0, 0};
+  float inv_tc = 1.0f;
+  float* packed = nullptr;            // [n][kRec]
+  float* probs = nullptr;             // [n][k] softmax probabilities
+  float* palette = nullptr;           // [k][3] copy
+  float4* s0 = nullptr;               // [P] (x_0, y_0, log2 T_0, record count)
+  float4* ckpt = nullptr;             // [(n-1)/ck][P] (x_i, y_i, log2 T_i, -)
+  float4* rec = nullptr;              // [cap][P] side table (x_i, y_i, i, -)
+  unsigned long long* status = nullptr;  // [ST_COUNT]
+  float* partial = nullptr;           // [grid][n][8] per-CTA gradient partials
+  float* grad8 = nullptr;             // [n][8]
+  cudaStream_t last_stream = nullptr;
+  size_t bytes = 0;
+};
+
+namespace tbr {
+
+tbr_status fail(tbr_status code, const char* fmt, ...);
+const char* last_error_text();
+tbr_status cuda_fail(cudaError_t e, const char* what);
+tbr_status check_program(const tbr_program* p, int n_used);
+tbr_status check_size(int32_t W, int32_t H);
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
+  *p = nullptr;
+  if (count == 0) return cudaSuccess;
+  return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
+}
+template <class T>
+void dfree(T*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+}
+
+// Allocates every buffer of a context for n strokes, palette k, W x H pixels.
+cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert,
+                         cudaStream_t st);
+void ctx_release(tbr_ctx* c);
+// Soft forward into an allocated context (resets its status words).
+cudaError_t ctx_forward(tbr_ctx* c, const tbr_program* prog, float tau, float tau_min,
+                        float* out_rgb, cudaStream_t st);
+// Replay adjoint of the context's last forward.
+cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy, float* g_th,
+                         float* g_len, float* g_r, float* g_logits, float* g_pal, cudaStream_t st);
+// Reads the status words (synchronising) and maps them to a tbr_status.
+tbr_status ctx_read_status(tbr_ctx* c, unsigned long long host[ST_COUNT]);
+
+}  // namespace tbr
+
+#define TBR_CUDA(call, what)                                 \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return ::tbr::cuda_fail(e_, what); \
+  } while (0)

@@ -380,6 +380,22 @@ __device__ __forceinline__ float warp_reduce8(const float (&v)[8]) {
 // ---------------------------------------------------------------------------
 // Host launchers (defined in the .cu files of this directory).
 // ---------------------------------------------------------------------------
+// RAII: records CUDA events around one kernel launch when profiling is on
+// (tbr_profile_enable); tbr_profile.cu.
+class KernelTimer {
+ public:
+  KernelTimer(int kernel, cudaStream_t st);
+  ~KernelTimer();
+  KernelTimer(const KernelTimer&) = delete;
+  KernelTimer& operator=(const KernelTimer&) = delete;
+
+ private:
+  int kernel_;
+  cudaStream_t st_;
+  cudaEvent_t start_ = nullptr, stop_ = nullptr;
+  bool active_ = false;
+};
+
 struct PackArgs {
   const tbr_program* prog;   // host struct with device pointers
   int n;                     // strokes to pack (prefix)

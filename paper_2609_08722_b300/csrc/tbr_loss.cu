@@ -57,6 +57,7 @@ int loss_blocks(int64_t npix) {
 cudaError_t launch_loss(const float* rgb, const float* target, int64_t npix, double* partial, int nblocks,
                         float* loss_out, float* dLdR, cudaStream_t st) {
   const int64_t nval = 3 * npix;
+  KernelTimer kt(TBR_K_LOSS, st);
   k_loss_partial<<<nblocks, kLossThreads, 0, st>>>(rgb, target, nval, partial, dLdR);
   k_loss_final<<<1, kLossThreads, 0, st>>>(partial, nblocks, nval, loss_out);
   return cudaGetLastError();

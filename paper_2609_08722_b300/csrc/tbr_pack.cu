@@ -74,6 +74,7 @@ cudaError_t launch_pack(const PackArgs& a, cudaStream_t st) {
   const tbr_program* p = a.prog;
   const int threads = 128;
   const int blocks = (a.n + threads - 1) / threads;
+  KernelTimer kt(TBR_K_PACK, st);
   k_pack<<<blocks, threads, 0, st>>>(p->cx, p->cy, p->theta, p->length, p->half_width, p->logits,
                                      p->palette, a.n, p->k, 1.0f / p->color_temp, a.tau, a.tau_min,
                                      a.snap, a.packed, a.probs, a.status);

@@ -141,6 +141,7 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
 cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
   const int tiles = ((a.W + kTileW - 1) / kTileW) * ((a.H + kTileH - 1) / kTileH);
   const bool rec = a.s0 != nullptr;
+  KernelTimer kt(TBR_K_SOFT, st);
   if (rec && a.inert) k_soft<kSoftCH, true, true><<<tiles, 256, 0, st>>>(a);
   else if (rec) k_soft<kSoftCH, true, false><<<tiles, 256, 0, st>>>(a);
   else if (a.inert) k_soft<kSoftCH, false, true><<<tiles, 256, 0, st>>>(a);

@@ -27,7 +27,10 @@ _STATUS_NAMES = {0: "TBR_OK", 1: "TBR_ERR_INVALID_ARG", 2: "TBR_ERR_OOM", 3: "TB
 
 # Every entry point include/tbr.h declares (checked by the ABI test).
 EXPORTED = ["tbr_render_hard", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
-            "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_last_error", "tbr_version"]
+            "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_fit_default_config",
+            "tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_fit_iteration",
+            "tbr_fit_destroy", "tbr_profile_enable", "tbr_profile_read", "tbr_profile_reset",
+            "tbr_last_error", "tbr_version"]
 
 
 class TbrError(RuntimeError):
@@ -232,16 +235,20 @@ class SoftContext:
 
 def render_soft(prog: DeviceProgram, W: int, H: int, tau: float, tau_min: float, record: bool = False,
                 checkpoint_every: int = 0, record_capacity: int = 0, inert: bool = False,
-                out_rgb=None, stream=None):
-    """tbr_render_soft; returns (rgb [H,W,3], SoftContext or None)."""
+                out_rgb=None, stream=None, reuse: Optional["SoftContext"] = None):
+    """tbr_render_soft; returns (rgb [H,W,3], SoftContext or None).  ``reuse``
+    overwrites an existing context of the same shape instead of allocating."""
     dev = prog.cx.device
     rgb = out_rgb if out_rgb is not None else torch.empty((H, W, 3), device=dev, dtype=torch.float32)
     opts = TbrSoftOpts(float(tau), float(tau_min), int(checkpoint_every), int(record_capacity),
                        int(bool(inert)))
-    handle = ctypes.c_void_p()
+    handle = ctypes.c_void_p(reuse.handle if reuse is not None else None)
     s = prog.struct()
     check(lib().tbr_render_soft(ctypes.byref(s), W, H, ctypes.byref(opts), _ptr(rgb),
-                                ctypes.byref(handle) if record else None, _stream(stream)))
+                                ctypes.byref(handle) if (record or reuse is not None) else None,
+                                _stream(stream)))
+    if reuse is not None:
+        return rgb, reuse
     ctx = SoftContext(handle.value, prog, W, H) if record else None
     return rgb, ctx
 
@@ -261,3 +268,177 @@ def loss_mse(rgb: torch.Tensor, target: torch.Tensor, want_grad: bool = True, st
 
 def version() -> str:
     return lib().tbr_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# Fit (tbr_fit_*) and per-kernel timing (tbr_profile_*)
+# ---------------------------------------------------------------------------
+class TbrFitConfig(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("tau_start", ctypes.c_float),
+                ("tau_end", ctypes.c_float), ("tau_min", ctypes.c_float),
+                ("color_temp_start", ctypes.c_float), ("color_temp_end", ctypes.c_float),
+                ("lr_center", ctypes.c_float), ("lr_angle", ctypes.c_float),
+                ("lr_length", ctypes.c_float), ("lr_width", ctypes.c_float),
+                ("lr_logits", ctypes.c_float), ("lr_palette", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+                ("length_max", ctypes.c_float), ("width_lo", ctypes.c_float),
+                ("width_hi", ctypes.c_float), ("length_weight", ctypes.c_float),
+                ("train_palette", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("record_capacity", ctypes.c_int32)]
+
+
+class TbrKernelTime(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+KERNELS = {"pack": 0, "hard": 1, "soft": 2, "backward": 3, "epilogue": 4, "loss": 5, "update": 6,
+           "serve": 7}
+
+
+def _fit_lib():
+    L = lib()
+    if not getattr(L, "_fit_typed", False):
+        P = ctypes.c_void_p
+        L.tbr_fit_default_config.argtypes = [ctypes.POINTER(TbrFitConfig)]
+        L.tbr_fit_default_config.restype = None
+        L.tbr_fit_create.argtypes = [ctypes.POINTER(TbrProgram), P, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(TbrFitConfig), ctypes.POINTER(P), P]
+        L.tbr_fit_step.argtypes = [P, ctypes.POINTER(ctypes.c_float), P]
+        L.tbr_fit_get_program.argtypes = [P, ctypes.POINTER(TbrProgram)]
+        L.tbr_fit_iteration.argtypes = [P]
+        L.tbr_fit_iteration.restype = ctypes.c_int32
+        L.tbr_fit_destroy.argtypes = [P]
+        L.tbr_fit_destroy.restype = None
+        for f in ("tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_profile_enable",
+                  "tbr_profile_read"):
+            getattr(L, f).restype = ctypes.c_int
+        L.tbr_profile_enable.argtypes = [ctypes.c_int32]
+        L.tbr_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(TbrKernelTime)]
+        L.tbr_profile_reset.argtypes = []
+        L.tbr_profile_reset.restype = None
+        L._fit_typed = True
+    return L
+
+
+def default_fit_config(**overrides) -> TbrFitConfig:
+    c = TbrFitConfig()
+    _fit_lib().tbr_fit_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+class _DeviceArray:
+    """Exposes a library-owned float32 device buffer to torch (no copy)."""
+
+    def __init__(self, ptr: int, count: int):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": "<f4", "data": (ptr, False),
+                                         "version": 2, "strides": None}
+
+
+class Fit:
+    """tbr_fit_*: Adam on a stroke program against a target image."""
+
+    def __init__(self, init: DeviceProgram, target: torch.Tensor, config: Optional[TbrFitConfig] = None,
+                 stream=None):
+        L = _fit_lib()
+        t = target.contiguous()
+        H, W = int(t.shape[0]), int(t.shape[1])
+        if t.shape != (H, W, 3) or t.dtype != torch.float32 or not t.is_cuda:
+            raise ValueError("target must be a [H, W, 3] float32 CUDA tensor")
+        self.W, self.H, self.n, self.k = W, H, init.n, init.k
+        self.device = init.cx.device
+        self.config = config if config is not None else default_fit_config()
+        h = ctypes.c_void_p()
+        s = init.struct()
+        check(L.tbr_fit_create(ctypes.byref(s), _ptr(t), W, H, ctypes.byref(self.config), ctypes.byref(h),
+                               _stream(stream)))
+        self.handle = h.value
+
+    def step(self, stream=None) -> float:
+        loss = ctypes.c_float()
+        check(_fit_lib().tbr_fit_step(ctypes.c_void_p(self.handle), ctypes.byref(loss), _stream(stream)))
+        return float(loss.value)
+
+    @property
+    def iteration(self) -> int:
+        return int(_fit_lib().tbr_fit_iteration(ctypes.c_void_p(self.handle)))
+
+    def program(self) -> DeviceProgram:
+        """A copy of the current program as torch tensors."""
+        v = TbrProgram()
+        check(_fit_lib().tbr_fit_get_program(ctypes.c_void_p(self.handle), ctypes.byref(v)))
+        n, k = self.n, self.k
+        # the view's arrays are consecutive slices of one device buffer of 5n + nk + 3k floats
+        total = 5 * n + n * k + 3 * k
+        buf = torch.as_tensor(_DeviceArray(v.cx, total), device=self.device)
+        sl = lambda a, b: buf[a:b].clone()
+        return DeviceProgram(cx=sl(0, n), cy=sl(n, 2 * n), theta=sl(2 * n, 3 * n), length=sl(3 * n, 4 * n),
+                             half_width=sl(4 * n, 5 * n), logits=sl(5 * n, 5 * n + n * k).view(n, k),
+                             palette=sl(5 * n + n * k, total).view(k, 3),
+                             background=tuple(v.background), color_temp=float(v.color_temp))
+
+    def destroy(self):
+        if self.handle is not None:
+            _fit_lib().tbr_fit_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def profile_enable(on: bool = True) -> None:
+    check(_fit_lib().tbr_profile_enable(int(bool(on))))
+
+
+def profile_reset() -> None:
+    _fit_lib().tbr_profile_reset()
+
+
+def profile_read(kernel: str) -> tuple[int, float]:
+    """(launches, total device ms) of one kernel since the last reset."""
+    t = TbrKernelTime()
+    check(_fit_lib().tbr_profile_read(KERNELS[kernel], ctypes.byref(t)))
+    return int(t.launches), float(t.total_ms)
+
+
+# ---------------------------------------------------------------------------
+# torch.autograd wrapper: soft render forward, replay adjoint backward
+# ---------------------------------------------------------------------------
+class SoftRender(torch.autograd.Function):
+    """R = soft render of (cx, cy, theta, length, half_width, logits, palette);
+    backward runs the replay adjoint (tbr_render_backward)."""
+
+    @staticmethod
+    def forward(fctx, cx, cy, theta, length, half_width, logits, palette, W, H, tau, tau_min,
+                background, color_temp, checkpoint_every, record_capacity):
+        dp = DeviceProgram(cx.detach().contiguous(), cy.detach().contiguous(), theta.detach().contiguous(),
+                           length.detach().contiguous(), half_width.detach().contiguous(),
+                           logits.detach().contiguous(), palette.detach().contiguous(),
+                           tuple(float(b) for b in background), float(color_temp))
+        rgb, sctx = render_soft(dp, W, H, tau, tau_min, record=True, checkpoint_every=checkpoint_every,
+                                record_capacity=record_capacity)
+        fctx.sctx = sctx
+        return rgb
+
+    @staticmethod
+    def backward(fctx, grad_rgb):
+        sctx = fctx.sctx
+        g = sctx.backward(grad_rgb.contiguous().float())
+        sctx.status()
+        sctx.destroy()
+        fctx.sctx = None
+        return (g["cx"], g["cy"], g["theta"], g["length"], g["half_width"], g["logits"], g["palette"],
+                None, None, None, None, None, None, None, None)
+
+
+def soft_render(cx, cy, theta, length, half_width, logits, palette, W, H, tau, tau_min,
+                background=(1.0, 1.0, 1.0), color_temp=1.0, checkpoint_every=0, record_capacity=0):
+    """Differentiable soft render (the replay adjoint provides the gradients)."""
+    return SoftRender.apply(cx, cy, theta, length, half_width, logits, palette, W, H, tau, tau_min,
+                            background, color_temp, checkpoint_every, record_capacity)
