@@ -57,6 +57,9 @@ def parse_args():
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-steps", type=int, default=5)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--res", type=int, default=RES, help="square resolution (profiling cases only)")
+    ap.add_argument("--strokes", type=int, default=N_STROKES, help="stroke count (profiling cases only)")
     return ap.parse_args()
 
 
@@ -239,9 +242,11 @@ def run_native(args):
     # per-rank independent program (weak scaling); target = hard render of another program
     prog_h = inputs.operating_program(seed=102 + 1000 * rank)
     targ_h = inputs.operating_program(seed=103 + 1000 * rank)
+    if args.strokes != N_STROKES:
+        prog_h, targ_h = prog_h.prefix(args.strokes), targ_h.prefix(args.strokes)
     prog = tbr.DeviceProgram.from_host(prog_h, device)
     targ = tbr.DeviceProgram.from_host(targ_h, device)
-    W = H = RES
+    W = H = args.res
     P = W * H
     target, _, _ = tbr.render_hard(targ, W, H, with_idx=False)
     tau, tau_min = inputs.SHARP_TAU, inputs.SHARP_TAU_MIN
@@ -312,7 +317,7 @@ def run_native(args):
     # e2e through the public API with host buffers: upload program + target from
     # pinned memory, fwd + loss + adjoint, read back gradients and loss
     e2e = None
-    if True:
+    if not args.no_e2e:
         host_arrays = {name: torch.from_numpy(np.ascontiguousarray(getattr(prog_h, name), dtype=np.float32)).pin_memory()
                        for name in ("cx", "cy", "theta", "length", "half_width", "logits", "palette")}
         host_target = target.cpu().pin_memory()
@@ -355,7 +360,7 @@ def run_native(args):
     # fit step (A11): forward + loss + adjoint + Adam, schedules of Table hyper
     fit_ms = None
     if args.fit_steps > 0:
-        fit = tbr.Fit(prog, target, tbr.default_fit_config(iterations=200))
+        fit = tbr.Fit(prog, target, tbr.default_fit_config(iterations=200, checkpoint_every=CHECKPOINT_EVERY))
         fit.step()
         torch.cuda.synchronize()
         fs, fe = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -368,7 +373,7 @@ def run_native(args):
         fit.destroy()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.res == RES and args.strokes == N_STROKES:
         rate, info = oracle_rate(prog_h, args.cpu_seconds)
         cpu = {"value": rate, "unit": "evals/s", "cores": info["threads"], "kind": "oracle",
                "sample": f"{info['pixels']} sampled pixels x {prog_h.n} strokes of the {RES}x{RES} workload "
@@ -381,7 +386,7 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded programs, no dataset)",
-            "config": {"workload": "soft forward + replay adjoint, 2000 capsule strokes at 1024x1024",
+            "config": {"workload": f"soft forward + replay adjoint, {prog.n} capsule strokes at {W}x{H}",
                        "strokes": prog.n, "resolution": [W, H], "palette": PALETTE, "tau": tau,
                        "tau_min": tau_min, "checkpoint_every": CHECKPOINT_EVERY,
                        "target": "hard render of a second seeded 2000-stroke program",

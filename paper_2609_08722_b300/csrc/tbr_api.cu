@@ -65,13 +65,16 @@ cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap
   if (e == cudaSuccess) e = dalloc(&c->probs, static_cast<size_t>(n) * k, st);
   if (e == cudaSuccess) e = dalloc(&c->palette, static_cast<size_t>(k) * 3, st);
   if (e == cudaSuccess) e = dalloc(&c->s0, P, st);
+  if (e == cudaSuccess) e = dalloc(&c->s0b, P, st);
   if (e == cudaSuccess) e = dalloc(&c->ckpt, nck * P, st);
+  if (e == cudaSuccess) e = dalloc(&c->ck_lt, nck * P, st);
   if (e == cudaSuccess && !inert) e = dalloc(&c->rec, static_cast<size_t>(cap) * P, st);
+  if (e == cudaSuccess && !inert) e = dalloc(&c->rec_i, static_cast<size_t>(cap) * P, st);
   if (e == cudaSuccess) e = dalloc(&c->partial, static_cast<size_t>(c->grid) * n * 8, st);
   if (e == cudaSuccess) e = dalloc(&c->grad8, static_cast<size_t>(n) * 8, st);
   c->bytes = static_cast<size_t>(n) * kRec * 4 + ST_COUNT * 8 + static_cast<size_t>(n) * k * 4 +
-             static_cast<size_t>(k) * 12 + P * 16 + nck * P * 16 +
-             (inert ? 0 : static_cast<size_t>(cap) * P * 16) + static_cast<size_t>(c->grid) * n * 32 +
+             static_cast<size_t>(k) * 12 + P * 24 + nck * P * 20 +
+             (inert ? 0 : static_cast<size_t>(cap) * P * 20) + static_cast<size_t>(c->grid) * n * 32 +
              static_cast<size_t>(n) * 32;
   return e;
 }
@@ -79,7 +82,8 @@ cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap
 void ctx_release(tbr_ctx* c) {
   cudaStream_t st = c->last_stream;
   dfree(c->packed, st); dfree(c->probs, st); dfree(c->palette, st);
-  dfree(c->s0, st); dfree(c->ckpt, st); dfree(c->rec, st);
+  dfree(c->s0, st); dfree(c->s0b, st); dfree(c->ckpt, st); dfree(c->ck_lt, st);
+  dfree(c->rec, st); dfree(c->rec_i, st);
   dfree(c->status, st); dfree(c->partial, st); dfree(c->grad8, st);
 }
 
@@ -97,7 +101,8 @@ cudaError_t ctx_forward(tbr_ctx* c, const tbr_program* prog, float tau, float ta
   sa.packed = c->packed; sa.n = c->n; sa.W = c->W; sa.H = c->H;
   for (int i = 0; i < 3; ++i) sa.bg[i] = c->bg[i];
   sa.inert = c->inert; sa.ck_every = c->ck; sa.cap = c->cap;
-  sa.out_rgb = out_rgb; sa.s0 = c->s0; sa.ckpt = c->ckpt; sa.rec = c->rec; sa.status = c->status;
+  sa.out_rgb = out_rgb; sa.s0 = c->s0; sa.s0b = c->s0b; sa.ckpt = c->ckpt; sa.ck_lt = c->ck_lt;
+  sa.rec = c->rec; sa.rec_i = c->rec_i; sa.status = c->status;
   if (e == cudaSuccess) e = launch_soft(sa, st);
   return e;
 }
@@ -113,7 +118,8 @@ cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy
   ba.packed = c->packed; ba.n = c->n; ba.W = c->W; ba.H = c->H;
   for (int i = 0; i < 3; ++i) ba.bg[i] = c->bg[i];
   ba.inert = c->inert; ba.ck_every = c->ck; ba.cap = c->cap;
-  ba.s0 = c->s0; ba.ckpt = c->ckpt; ba.rec = c->rec; ba.dLdR = dLdR;
+  ba.s0 = c->s0; ba.s0b = c->s0b; ba.ckpt = c->ckpt; ba.ck_lt = c->ck_lt;
+  ba.rec = c->rec; ba.rec_i = c->rec_i; ba.dLdR = dLdR;
   ba.partial = c->partial; ba.grid = c->grid; ba.status = c->status;
   cudaError_t e = launch_backward(ba, st);
   if (e != cudaSuccess) return e;
@@ -218,7 +224,8 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     sa.packed = packed; sa.n = prog->n; sa.W = W; sa.H = H;
     for (int i = 0; i < 3; ++i) sa.bg[i] = prog->background[i];
     sa.inert = opts->inert ? 1 : 0; sa.ck_every = ck; sa.cap = cap;
-    sa.out_rgb = out_rgb; sa.s0 = nullptr; sa.ckpt = nullptr; sa.rec = nullptr; sa.status = status;
+    sa.out_rgb = out_rgb; sa.s0 = nullptr; sa.s0b = nullptr; sa.ckpt = nullptr; sa.ck_lt = nullptr;
+    sa.rec = nullptr; sa.rec_i = nullptr; sa.status = status;
     if (e == cudaSuccess) e = launch_soft(sa, st);
     dfree(packed, st);
     dfree(status, st);

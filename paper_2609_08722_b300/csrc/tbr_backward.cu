@@ -26,12 +26,9 @@ constexpr int kBwdThreads = 256;
 
 // d alpha path only (psi = id, inert-mark model): cotangent of sigma' pushed
 // back to (x, theta, L, r).
-__device__ __forceinline__ void inert_vjp(float x, float y, const StrokeF& g, float& sp_out,
-                                          float& lamx, float& lamy, float mua, float z, bool want,
-                                          float& gcx, float& gcy, float& gth, float& gL, float& gr) {
-  const float dx = x - g.mx, dy = y - g.my;
-  const float s = fmaf(dx, g.ex, dy * g.ey);
-  const float h = fmaf(dy, g.ex, -dx * g.ey);
+__device__ __forceinline__ void inert_vjp(float s, float h, const StrokeF& g, float& sp_out, float& lamx,
+                                          float& lamy, float mua, float z, bool want, float& gcx, float& gcy,
+                                          float& gth, float& gL, float& gr) {
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
   const bool cap = d > 0.0f;
@@ -86,13 +83,13 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_backward(BwdArgs a) {
     if (total > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
   }
 
-  // per-pixel state
+  // per-pixel state (positions are hi/lo pairs)
   bool valid = false;
   size_t p = 0;
-  float x = 0.0f, y = 0.0f, lt = 0.0f;
+  float xh = 0.0f, yh = 0.0f, xl = 0.0f, yl = 0.0f, lt = 0.0f;
   float lC0 = 0.0f, lC1 = 0.0f, lC2 = 0.0f, lT = 0.0f, lx = 0.0f, ly = 0.0f;
   int rc = 0, nri = -1, next_ck = 0;
-  float rx = 0.0f, ry = 0.0f;
+  float4 rpos = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   unsigned drift = 0;
 
   bool aborted = false;
@@ -107,15 +104,17 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_backward(BwdArgs a) {
       p = valid ? static_cast<size_t>(py) * W + px : 0;
       if (valid) {
         const float4 s0 = a.s0[p];
-        x = s0.x; y = s0.y; lt = s0.z;
-        rc = min(__float_as_int(s0.w), a.cap);
+        const float2 s0b = a.s0b[p];
+        xh = s0.x; yh = s0.y; xl = s0.z; yl = s0.w; lt = s0b.x;
+        rc = min(__float_as_int(s0b.y), a.cap);
         lC0 = a.dLdR[3 * p + 0]; lC1 = a.dLdR[3 * p + 1]; lC2 = a.dLdR[3 * p + 2];
         lT = fmaf(lC0, a.bg[0], fmaf(lC1, a.bg[1], lC2 * a.bg[2]));
         lx = 0.0f; ly = 0.0f;
         nri = -1;
         if (rc > 0) {
-          const float4 r = a.rec[static_cast<size_t>(rc - 1) * P + p];
-          rx = r.x; ry = r.y; nri = __float_as_int(r.z);
+          const size_t o = static_cast<size_t>(rc - 1) * P + p;
+          rpos = a.rec[o];
+          nri = a.rec_i[o];
         }
         next_ck = (ck < n) ? ck : 0;
       }
@@ -136,52 +135,59 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_backward(BwdArgs a) {
         const StrokeF g = load_stroke(S);
         const float cR = S[F_CR], cG = S[F_CG], cB = S[F_CB];
         const bool at_ck = (i1 == next_ck);
-        float4 ckv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        size_t cko = 0;
         if (at_ck) {
           next_ck = (next_ck + ck < n) ? next_ck + ck : 0;
-          ckv = a.ckpt[static_cast<size_t>(i1 / ck - 1) * P + p];
+          cko = static_cast<size_t>(i1 / ck - 1) * P + p;
         }
+        const float lCc = fmaf(lC0, cR, fmaf(lC1, cG, lC2 * cB));
         if (INERT) {
-          float sp;
+          float s, h, sp;
+          to_frame(xh, yh, xl, yl, g, s, h);
           float d0, d1, d2, d3, d4;
-          inert_vjp(x, y, g, sp, lx, ly, 0.0f, 0.0f, false, d0, d1, d2, d3, d4);
+          inert_vjp(s, h, g, sp, lx, ly, 0.0f, 0.0f, false, d0, d1, d2, d3, d4);
           const Cover cv = coverage(sp, g);
-          if (at_ck) lt = ckv.z; else lt += cv.sp2;
+          if (at_ck) lt = a.ck_lt[cko]; else lt += cv.sp2;
           const float T = exp2f(lt);
-          const float lCc = fmaf(lC0, cR, fmaf(lC1, cG, lC2 * cB));
           const float mu = T * (lCc - lT);
           const float Ta = T * cv.alpha;
           v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;
-          inert_vjp(x, y, g, sp, lx, ly, mu * cv.dadz, cv.z, true, v[0], v[1], v[2], v[3], v[4]);
+          inert_vjp(s, h, g, sp, lx, ly, mu * cv.dadz, cv.z, true, v[0], v[1], v[2], v[3], v[4]);
           lT = fmaf(cv.oma, lT, cv.alpha * lCc);
         } else {
           Geo gq;
+          float s, h, ds, dh;
           if (i1 == nri) {
-            x = rx; y = ry;
-            float xo, yo;
-            psi_explicit(x, y, g, gq, xo, yo);
+            // x_i was inside the floor's reach: read it back (Lemma "Support of the replay record")
+            xh = rpos.x; yh = rpos.y; xl = rpos.z; yl = rpos.w;
+            to_frame(xh, yh, xl, yl, g, s, h);
+            psi_local<true>(s, h, g, gq, ds, dh);
             --rc;
             nri = -1;
             if (rc > 0) {
-              const float4 r = a.rec[static_cast<size_t>(rc - 1) * P + p];
-              rx = r.x; ry = r.y; nri = __float_as_int(r.z);
+              const size_t o = static_cast<size_t>(rc - 1) * P + p;
+              rpos = a.rec[o];
+              nri = a.rec_i[o];
             }
           } else if (at_ck) {
-            float xr, yr;
-            phi_regen(x, y, g, gq, xr, yr);
-            if (fabsf(xr - ckv.x) > kDriftTol || fabsf(yr - ckv.y) > kDriftTol) ++drift;
-            x = ckv.x; y = ckv.y;
-            float xo, yo;
-            psi_explicit(x, y, g, gq, xo, yo);
+            // regenerate, measure the drift against the stored position, then reset to it
+            to_frame(xh, yh, xl, yl, g, s, h);
+            phi_local(s, h, g, gq, ds, dh);
+            add_frame_disp(xh, yh, xl, yl, g, ds, dh);
+            const float4 c = a.ckpt[cko];
+            if (fabsf((xh - c.x) + (xl - c.z)) > kDriftTol || fabsf((yh - c.y) + (yl - c.w)) > kDriftTol) ++drift;
+            xh = c.x; yh = c.y; xl = c.z; yl = c.w;
+            to_frame(xh, yh, xl, yl, g, s, h);
+            psi_local<true>(s, h, g, gq, ds, dh);
           } else {
-            float xr, yr;
-            phi_regen(x, y, g, gq, xr, yr);
-            x = xr; y = yr;
+            // x_i = Phi_i(x_{i-1}) (Eq. rpos)
+            to_frame(xh, yh, xl, yl, g, s, h);
+            phi_local(s, h, g, gq, ds, dh);
+            add_frame_disp(xh, yh, xl, yl, g, ds, dh);
           }
           const Cover cv = coverage(gq.sp, g);
-          if (at_ck) lt = ckv.z; else lt += cv.sp2;
+          if (at_ck) lt = a.ck_lt[cko]; else lt += cv.sp2;
           const float T = exp2f(lt);
-          const float lCc = fmaf(lC0, cR, fmaf(lC1, cG, lC2 * cB));
           const float mu = T * (lCc - lT);
           const float Ta = T * cv.alpha;
           v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;

@@ -15,13 +15,16 @@ namespace {
 constexpr int kHardCH = 64;
 constexpr int kTileW = 32, kTileH = 8;
 
-// Membership test and psi (Eq. back) recomputed in FP64 from the FP32 position,
-// used where |sigma' - r| < kBand.  Returns true if the point is inside.
-__device__ __noinline__ bool hard_step_f64(float& x, float& y, const float* __restrict__ S) {
+// Membership test and psi (Eq. back) recomputed in FP64 from the hi/lo
+// position, used where |sigma' - r| < kBand.  Returns true if the point is inside.
+__device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& xl, float& yl,
+                                           const float* __restrict__ S) {
   const double* D = reinterpret_cast<const double*>(S + F_D64);
   const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
   const double L = 2.0 * hl;
-  const double dx = static_cast<double>(x) - mx, dy = static_cast<double>(y) - my;
+  const double x = static_cast<double>(xh) + static_cast<double>(xl);
+  const double y = static_cast<double>(yh) + static_cast<double>(yl);
+  const double dx = x - mx, dy = y - my;
   const double s = dx * ex + dy * ey, h = dy * ex - dx * ey;
   const double as = fabs(s), ah = fabs(h), d = as - hl;
   const bool cap = d > 0.0;
@@ -41,47 +44,32 @@ __device__ __noinline__ bool hard_step_f64(float& x, float& y, const float* __re
     sn = hl + sig * sb; hn = sig * cb;
   }
   sn = copysign(sn, s); hn = copysign(hn, h);
-  x = static_cast<float>(mx + sn * ex - hn * ey);
-  y = static_cast<float>(my + sn * ey + hn * ex);
+  const double xo = mx + sn * ex - hn * ey, yo = my + sn * ey + hn * ex;
+  xh = static_cast<float>(xo); xl = static_cast<float>(xo - static_cast<double>(xh));
+  yh = static_cast<float>(yo); yl = static_cast<float>(yo - static_cast<double>(yh));
   return false;
 }
 
 // One stroke of the hard chain in FP32.  Returns true if x lies in K_i;
-// otherwise replaces x by psi_i(x).
-__device__ __forceinline__ bool hard_step(float& x, float& y, const float* __restrict__ S,
-                                          unsigned& band) {
-  const float4 a = *reinterpret_cast<const float4*>(S);      // mx my ex ey
-  const float4 b = *reinterpret_cast<const float4*>(S + 4);  // hl L r r2
-  const float4 c = *reinterpret_cast<const float4*>(S + 8);  // L2 kA Ar fl2
-  const float dx = x - a.x, dy = y - a.y;
-  const float s = fmaf(dx, a.z, dy * a.w);
-  const float h = fmaf(dy, a.z, -dx * a.w);
+// otherwise moves x to psi_i(x) (displacement form, hi/lo position).
+__device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float& yl,
+                                          const float* __restrict__ S, unsigned& band) {
+  const StrokeF g = load_stroke(S);
+  float s, h;
+  to_frame(xh, yh, xl, yl, g, s, h);
   const float as = fabsf(s), ah = fabsf(h);
-  const float d = as - b.x;
-  const bool cap = d > 0.0f;
-  const float sp = cap ? sqrtf(fmaf(d, d, ah * ah)) : ah;
-  const float diff = sp - b.z;
+  const float d = as - g.hl;
+  const float sp = d > 0.0f ? sqrtf(fmaf(d, d, ah * ah)) : ah;
+  const float diff = sp - g.r;
   if (fabsf(diff) < kBand) {
     ++band;
-    return hard_step_f64(x, y, S);
+    return hard_step_f64(xh, yh, xl, yl, S);
   }
   if (diff <= 0.0f) return true;
-  const float C = diff * fmaf(kPiF, sp, c.y);
-  const float sig = C / (b.y + sqrtf(fmaf(kPiF, C, c.x)));
-  const float Qp = fmaf(kPiF, sp, b.y), Q = fmaf(kPiF, sig, b.y);
-  const float t = cap ? fmaf(sp, atan2f(d, ah), b.x) : as;
-  const float tn = t * (Q / Qp);
-  float sn, hn;
-  if (tn <= b.x) {
-    sn = tn; hn = sig;
-  } else {
-    float sb, cb;
-    sincosf((tn - b.x) / sig, &sb, &cb);
-    sn = fmaf(sig, sb, b.x); hn = sig * cb;
-  }
-  sn = copysignf(sn, s); hn = copysignf(hn, h);
-  x = a.x + fmaf(sn, a.z, -hn * a.w);
-  y = a.y + fmaf(sn, a.w, hn * a.z);
+  Geo q;
+  float ds, dh;
+  psi_local<false>(s, h, g, q, ds, dh);
+  add_frame_disp(xh, yh, xl, yl, g, ds, dh);
   return false;
 }
 
@@ -99,8 +87,9 @@ __global__ void __launch_bounds__(256) k_hard(const float* __restrict__ packed, 
   const bool valid = px < W && py < H;
   const bool invalid_prog = status[ST_INVALID] != 0ull;
   bool alive = valid && !invalid_prog;
-  float x = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
-  float y = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
+  float xh = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
+  float yh = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
+  float xl = 0.0f, yl = 0.0f;
   int hit = -1;
   unsigned band = 0, visited = 0;
 
@@ -129,7 +118,7 @@ __global__ void __launch_bounds__(256) k_hard(const float* __restrict__ packed, 
     if (alive) {
       for (int j = cnt - 1; j >= 0; --j) {
         ++visited;
-        if (hard_step(x, y, S0 + j * kRec, band)) {
+        if (hard_step(xh, yh, xl, yl, S0 + j * kRec, band)) {
           hit = base + j;
           alive = false;
           break;

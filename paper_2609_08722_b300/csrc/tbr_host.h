@@ -18,9 +18,12 @@ struct tbr_ctx {
   float* packed = nullptr;            // [n][kRec]
   float* probs = nullptr;             // [n][k] softmax probabilities
   float* palette = nullptr;           // [k][3] copy
-  float4* s0 = nullptr;               // [P] (x_0, y_0, log2 T_0, record count)
-  float4* ckpt = nullptr;             // [(n-1)/ck][P] (x_i, y_i, log2 T_i, -)
-  float4* rec = nullptr;              // [cap][P] side table (x_i, y_i, i, -)
+  float4* s0 = nullptr;               // [P] x_0 as (x_hi, y_hi, x_lo, y_lo)
+  float2* s0b = nullptr;              // [P] (log2 T_0, record count)
+  float4* ckpt = nullptr;             // [(n-1)/ck][P] x_i checkpoints (hi/lo)
+  float* ck_lt = nullptr;             // [(n-1)/ck][P] log2 T_i at the checkpoints
+  float4* rec = nullptr;              // [cap][P] side table positions (hi/lo)
+  int* rec_i = nullptr;               // [cap][P] side table stroke indices
   unsigned long long* status = nullptr;  // [ST_COUNT]
   float* partial = nullptr;           // [grid][n][8] per-CTA gradient partials
   float* grad8 = nullptr;             // [n][8]

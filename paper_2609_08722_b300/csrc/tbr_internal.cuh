@@ -147,10 +147,23 @@ __device__ __forceinline__ StrokeF load_stroke(const float* __restrict__ S) {
 }
 
 // ---------------------------------------------------------------------------
+// Positions are carried as unevaluated float pairs x = hi + lo: the local
+// frame coordinate is formed as (hi - m) + lo, and each stroke adds its
+// displacement with a two-sum, so the FP32 rounding of a step is of the order
+// of the (small) displacement rather than of the coordinate itself.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pos_add(float& hi, float& lo, float d) {
+  const float s = hi + d;
+  lo += d - (s - hi);  // exact error of hi + d when |hi| >= |d|
+  hi = s;
+}
+
+// ---------------------------------------------------------------------------
 // Per-step quantities of one application of psi_i at x_i (to x_{i-1}) in the
 // stroke frame, with the quadrant fold: s along e, h along e_perp, folded to
 // |s|, |h|; t is the arclength from the flank midpoint along the parallel curve
-// (the centred coordinate v of Eq. phi times the perimeter).
+// (the centred coordinate v of Eq. phi times the quarter perimeter fraction).
+// On a cap the point is at angle phi from the flank normal, so t = L/2 + sigma phi.
 // ---------------------------------------------------------------------------
 struct Geo {
   float sgs, sgh;     // fold signs (psi keeps the quadrant)
@@ -158,7 +171,7 @@ struct Geo {
   float so, ho;       // signed frame coordinates of x_{i-1}
   float sp, sig;      // sigma' = dist(x_i), sigma = dist(x_{i-1})
   float t, tn;        // folded arclength coordinates of x_i and x_{i-1}
-  float ud, uh;       // at x_i: cap ? ((|s|-L/2)/sigma', |h|/sigma') : (0, 1)
+  float ud, uh;       // at x_i: cap ? (sin phi, cos phi) : (0, 1)
   float phi;          // at x_i on a cap: angle from the flank normal
   float sb, cb, beta; // at x_{i-1} on a cap: angle and its sine / cosine
   bool cap_i, cap_o, floored;
@@ -166,13 +179,16 @@ struct Geo {
 
 __device__ __forceinline__ float sgn1(float v) { return copysignf(1.0f, v); }
 
-// psi evaluated explicitly at x_i with the epsilon-floor (Eq. back; Sec. 5.2),
-// keeping every intermediate the adjoint needs.  Returns x_{i-1}.
-__device__ __forceinline__ void psi_explicit(float x, float y, const StrokeF& g, Geo& q,
-                                             float& xo, float& yo) {
-  const float dx = x - g.mx, dy = y - g.my;
-  const float s = fmaf(dx, g.ex, dy * g.ey);
-  const float h = fmaf(dy, g.ex, -dx * g.ey);
+// psi_i in displacement form at the frame point (s, h) of x_i (Eq. back with the
+// centred arclength of Eq. phi).  The normal step uses
+//   sigma - sigma' = -A_L(r) / (2L + pi (sigma' + sigma))  (exterior),
+// the cap-to-cap tangential step rotates by
+//   Delta = beta - phi = (sigma' - sigma) L (phi - pi/2) / (Q' sigma),
+// both free of cancellation, so (ds, dh) keeps full relative precision even
+// when the stroke is far.  FLOOR selects the epsilon-floor of Sec. 5.2 (soft
+// render); without it the caller guarantees sigma' > r (hard render).
+template <bool FLOOR>
+__device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh) {
   q.sgs = sgn1(s); q.sgh = sgn1(h); q.si = s; q.hi = h;
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
@@ -187,34 +203,53 @@ __device__ __forceinline__ void psi_explicit(float x, float y, const StrokeF& g,
     q.sp = ah; q.ud = 0.0f; q.uh = 1.0f; q.phi = 0.0f; q.t = as;
   }
   float C = (q.sp - g.r) * fmaf(kPiF, q.sp, g.kA);
-  q.floored = C < g.fl2;
-  C = q.floored ? g.fl2 : C;
+  q.floored = FLOOR && C < g.fl2;
+  if (q.floored) C = g.fl2;
   q.sig = C / (g.L + sqrtf(fmaf(kPiF, C, g.L2)));
   const float Qp = fmaf(kPiF, q.sp, g.L), Q = fmaf(kPiF, q.sig, g.L);
+  const float dsig = q.floored ? q.sig - q.sp : -g.Ar / fmaf(kPiF, q.sp + q.sig, g.twoL);
   q.tn = Qp > 0.0f ? q.t * (Q / Qp) : 0.0f;
-  float sn, hn;
-  if (q.tn <= g.hl) {
-    q.cap_o = false; q.beta = 0.0f; q.sb = 0.0f; q.cb = 1.0f;
-    sn = q.tn; hn = q.sig;
-  } else {
-    q.cap_o = true;
-    q.beta = (q.tn - g.hl) / q.sig;
-    sincosf(q.beta, &q.sb, &q.cb);
-    sn = fmaf(q.sig, q.sb, g.hl); hn = q.sig * q.cb;
+  q.cap_o = q.tn > g.hl;
+  float dS, dH;
+  if (!q.floored && q.cap_i && q.cap_o) {
+    float delta = -dsig * g.L * (q.phi - 0.5f * kPiF) / (Qp * q.sig);
+    delta = fminf(fmaxf(delta, -q.phi), 0.0f);
+    const float sD = sinf(delta), s2 = sinf(0.5f * delta);
+    const float omc = 2.0f * s2 * s2;  // 1 - cos(delta)
+    dS = fmaf(dsig, q.ud, q.sig * fmaf(q.uh, sD, -q.ud * omc));
+    dH = fmaf(dsig, q.uh, -q.sig * fmaf(q.ud, sD, q.uh * omc));
+    const float cD = 1.0f - omc;
+    q.beta = q.phi + delta;
+    q.sb = fmaf(q.ud, cD, q.uh * sD);
+    q.cb = fmaf(q.uh, cD, -q.ud * sD);
+  } else if (!q.floored && !q.cap_i) {  // flank to flank (tn <= t <= L/2)
+    dS = as * kPiF * dsig / Qp;
+    dH = dsig;
+    q.beta = 0.0f; q.sb = 0.0f; q.cb = 1.0f;
+  } else {                             // floored, or cap to flank: direct form
+    float sn, hn;
+    if (q.cap_o) {
+      q.beta = (q.tn - g.hl) / q.sig;
+      sincosf(q.beta, &q.sb, &q.cb);
+      sn = fmaf(q.sig, q.sb, g.hl); hn = q.sig * q.cb;
+    } else {
+      q.beta = 0.0f; q.sb = 0.0f; q.cb = 1.0f;
+      sn = q.tn; hn = q.sig;
+    }
+    dS = sn - as; dH = hn - ah;
   }
-  q.so = copysignf(sn, s); q.ho = copysignf(hn, h);
-  xo = g.mx + fmaf(q.so, g.ex, -q.ho * g.ey);
-  yo = g.my + fmaf(q.so, g.ey, q.ho * g.ex);
+  ds = q.sgs * dS;
+  dh = q.sgh * dH;
+  q.so = s + ds;
+  q.ho = h + dh;
 }
 
-// Regeneration x_i = Phi_i(x_{i-1}) (Eq. fwd, Eq. rpos), recording the same
-// intermediates as psi_explicit (the two maps share them exactly on the
-// exterior).  Input x_{i-1} = (x, y); returns x_i.
-__device__ __forceinline__ void phi_regen(float x, float y, const StrokeF& g, Geo& q,
-                                          float& xi, float& yi) {
-  const float dx = x - g.mx, dy = y - g.my;
-  const float s = fmaf(dx, g.ex, dy * g.ey);
-  const float h = fmaf(dy, g.ex, -dx * g.ey);
+// Phi_i (Eq. fwd, Eq. rpos) in displacement form at the frame point (s, h) of
+// x_{i-1}, recording the same intermediates as psi_local (the two maps share
+// them exactly on the exterior):
+//   sigma' - sigma = A_L(r) / (2L + pi (sigma + sigma')),
+//   cap to cap: phi - beta = (sigma' - sigma) L (pi/2 - beta) / (Q sigma').
+__device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh) {
   q.sgs = sgn1(s); q.sgh = sgn1(h); q.so = s; q.ho = h;
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
@@ -230,26 +265,57 @@ __device__ __forceinline__ void phi_regen(float x, float y, const StrokeF& g, Ge
   }
   const float B = fmaf(q.sig, fmaf(kPiF, q.sig, g.twoL), g.Ar);
   q.sp = B / (g.L + sqrtf(fmaf(kPiF, B, g.L2)));
+  const float dsp = g.Ar / fmaf(kPiF, q.sig + q.sp, g.twoL);
   const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
   q.t = Q > 0.0f ? q.tn * (Qp / Q) : 0.0f;
-  float sn, hn;
-  if (q.t <= g.hl) {
-    q.cap_i = false; q.phi = 0.0f; q.ud = 0.0f; q.uh = 1.0f;
-    sn = q.t; hn = q.sp;
-  } else {
+  q.cap_i = q.t > g.hl;
+  float dS, dH;
+  if (q.cap_o) {                       // cap to cap (t >= tn > L/2)
+    float delta = dsp * g.L * (0.5f * kPiF - q.beta) / (Q * q.sp);
+    delta = fminf(fmaxf(delta, 0.0f), 0.5f * kPiF - q.beta);
+    const float sD = sinf(delta), s2 = sinf(0.5f * delta);
+    const float omc = 2.0f * s2 * s2;
+    dS = fmaf(dsp, q.sb, q.sp * fmaf(q.cb, sD, -q.sb * omc));
+    dH = fmaf(dsp, q.cb, -q.sp * fmaf(q.sb, sD, q.cb * omc));
+    const float cD = 1.0f - omc;
+    q.phi = q.beta + delta;
+    q.ud = fmaf(q.sb, cD, q.cb * sD);
+    q.uh = fmaf(q.cb, cD, -q.sb * sD);
     q.cap_i = true;
+  } else if (!q.cap_i) {               // flank to flank
+    dS = q.tn * kPiF * dsp / Q;
+    dH = dsp;
+    q.phi = 0.0f; q.ud = 0.0f; q.uh = 1.0f;
+  } else {                             // flank to cap: direct form
     q.phi = (q.t - g.hl) / q.sp;
     sincosf(q.phi, &q.ud, &q.uh);
-    sn = fmaf(q.sp, q.ud, g.hl); hn = q.sp * q.uh;
+    dS = fmaf(q.sp, q.ud, g.hl) - as;
+    dH = fmaf(q.sp, q.uh, -ah);
   }
   q.floored = false;
-  q.si = copysignf(sn, s); q.hi = copysignf(hn, h);
-  xi = g.mx + fmaf(q.si, g.ex, -q.hi * g.ey);
-  yi = g.my + fmaf(q.si, g.ey, q.hi * g.ex);
+  ds = q.sgs * dS;
+  dh = q.sgh * dH;
+  q.si = s + ds;
+  q.hi = h + dh;
+}
+
+// Frame coordinates of a hi/lo position.
+__device__ __forceinline__ void to_frame(float xh, float yh, float xl, float yl, const StrokeF& g, float& s,
+                                         float& h) {
+  const float dx = (xh - g.mx) + xl, dy = (yh - g.my) + yl;
+  s = fmaf(dx, g.ex, dy * g.ey);
+  h = fmaf(dy, g.ex, -dx * g.ey);
+}
+
+// Adds a frame displacement (ds, dh) to a hi/lo position.
+__device__ __forceinline__ void add_frame_disp(float& xh, float& yh, float& xl, float& yl, const StrokeF& g,
+                                               float ds, float dh) {
+  pos_add(xh, xl, fmaf(ds, g.ex, -dh * g.ey));
+  pos_add(yh, yl, fmaf(ds, g.ey, dh * g.ex));
 }
 
 // Vector-Jacobian product of one step (Eq. adjstep, Eq. adjparam), written out
-// by reverse-mode differentiation of psi_explicit in the stroke frame.
+// by reverse-mode differentiation of psi_local in the stroke frame.
 //   lam     lambda^x_{i-1} (world), replaced by lambda^x_i
 //   mua     mu_i * d alpha / d z (0 where the clamp binds)
 //   z       the (clamped) coverage logit (r - sigma') / w
@@ -418,9 +484,13 @@ struct SoftArgs {
   int ck_every;              // checkpoint interval k (>= 1)
   int cap;                   // side-table capacity per pixel
   float* out_rgb;
-  float4* s0;                // [P] or NULL (forward only)
-  float4* ckpt;              // [(n-1)/k][P] or NULL
-  float4* rec;               // [cap][P] or NULL
+  // replay record (all NULL for a forward-only render); positions are hi/lo pairs
+  float4* s0;                // [P] (x_hi, y_hi, x_lo, y_lo) of x_0
+  float2* s0b;               // [P] (log2 T_0, record count as int bits)
+  float4* ckpt;              // [(n-1)/k][P] x_i at i = k, 2k, ...
+  float* ck_lt;              // [(n-1)/k][P] log2 T_i
+  float4* rec;               // [cap][P] x_i of floored samples (LIFO per pixel)
+  int* rec_i;                // [cap][P] their 1-based stroke index i
   unsigned long long* status;
 };
 cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st);
@@ -433,8 +503,11 @@ struct BwdArgs {
   int ck_every;
   int cap;                   // side-table capacity per pixel
   const float4* s0;
+  const float2* s0b;
   const float4* ckpt;
+  const float* ck_lt;
   const float4* rec;
+  const int* rec_i;
   const float* dLdR;
   float* partial;            // [grid][n][8]
   int grid;

@@ -31,8 +31,9 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
   const size_t p = valid ? static_cast<size_t>(py) * W + px : 0;
   unsigned long long* status = a.status;
   const bool invalid_prog = status[ST_INVALID] != 0ull;
-  float x = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
-  float y = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
+  float xh = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
+  float yh = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
+  float xl = 0.0f, yl = 0.0f;  // positions are hi/lo pairs
   float lt = 0.0f;  // log2 T
   float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
   int cnt = 0;
@@ -63,50 +64,44 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
       for (int j = cntc - 1; j >= 0; --j) {
         const int i1 = base + j + 1;  // the paper's 1-based stroke index
         if (RECORD && i1 == next_ck) {
-          a.ckpt[static_cast<size_t>(i1 / ck - 1) * P + p] = make_float4(x, y, lt, 0.0f);
+          const size_t o = static_cast<size_t>(i1 / ck - 1) * P + p;
+          a.ckpt[o] = make_float4(xh, yh, xl, yl);
+          a.ck_lt[o] = lt;
           next_ck -= ck;
         }
-        const StrokeF g = load_stroke(S0 + j * kRec);
-        const float dx = x - g.mx, dy = y - g.my;
-        const float s = fmaf(dx, g.ex, dy * g.ey);
-        const float h = fmaf(dy, g.ex, -dx * g.ey);
-        const float as = fabsf(s), ah = fabsf(h);
-        const float d = as - g.hl;
-        const bool cap = d > 0.0f;
-        const float sp = cap ? sqrtf(fmaf(d, d, ah * ah)) : ah;
-        const Cover cv = coverage(sp, g);
-        const float w = exp2f(lt) * cv.alpha;
         const float* S = S0 + j * kRec;
-        C0 = fmaf(w, S[F_CR], C0);
-        C1 = fmaf(w, S[F_CG], C1);
-        C2 = fmaf(w, S[F_CB], C2);
-        lt -= cv.sp2;
-        if (!INERT) {
-          float C = (sp - g.r) * fmaf(kPiF, sp, g.kA);
-          const bool fl = C < g.fl2;
-          if (fl) {
-            C = g.fl2;
-            if (RECORD) {
-              if (cnt < a.cap)
-                a.rec[static_cast<size_t>(cnt) * P + p] = make_float4(x, y, __int_as_float(i1), 0.0f);
-              ++cnt;
+        const StrokeF g = load_stroke(S);
+        float s, h;
+        to_frame(xh, yh, xl, yl, g, s, h);
+        if (INERT) {
+          const float as = fabsf(s), ah = fabsf(h);
+          const float d = as - g.hl;
+          const float sp = d > 0.0f ? sqrtf(fmaf(d, d, ah * ah)) : ah;
+          const Cover cv = coverage(sp, g);
+          const float w = exp2f(lt) * cv.alpha;
+          C0 = fmaf(w, S[F_CR], C0);
+          C1 = fmaf(w, S[F_CG], C1);
+          C2 = fmaf(w, S[F_CB], C2);
+          lt -= cv.sp2;
+        } else {
+          Geo q;
+          float ds, dh;
+          psi_local<true>(s, h, g, q, ds, dh);
+          const Cover cv = coverage(q.sp, g);
+          const float w = exp2f(lt) * cv.alpha;
+          C0 = fmaf(w, S[F_CR], C0);
+          C1 = fmaf(w, S[F_CG], C1);
+          C2 = fmaf(w, S[F_CB], C2);
+          lt -= cv.sp2;
+          if (RECORD && q.floored) {
+            if (cnt < a.cap) {
+              const size_t o = static_cast<size_t>(cnt) * P + p;
+              a.rec[o] = make_float4(xh, yh, xl, yl);
+              a.rec_i[o] = i1;
             }
+            ++cnt;
           }
-          const float sig = C / (g.L + sqrtf(fmaf(kPiF, C, g.L2)));
-          const float Qp = fmaf(kPiF, sp, g.L), Q = fmaf(kPiF, sig, g.L);
-          const float t = cap ? fmaf(sp, atan2f(d, ah), g.hl) : as;
-          const float tn = Qp > 0.0f ? t * (Q / Qp) : 0.0f;
-          float sn, hn;
-          if (tn <= g.hl) {
-            sn = tn; hn = sig;
-          } else {
-            float sb, cb;
-            sincosf((tn - g.hl) / sig, &sb, &cb);
-            sn = fmaf(sig, sb, g.hl); hn = sig * cb;
-          }
-          sn = copysignf(sn, s); hn = copysignf(hn, h);
-          x = g.mx + fmaf(sn, g.ex, -hn * g.ey);
-          y = g.my + fmaf(sn, g.ey, hn * g.ex);
+          add_frame_disp(xh, yh, xl, yl, g, ds, dh);
         }
       }
     }
@@ -121,7 +116,10 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
     a.out_rgb[3 * p + 0] = o0;
     a.out_rgb[3 * p + 1] = o1;
     a.out_rgb[3 * p + 2] = o2;
-    if (RECORD) a.s0[p] = make_float4(x, y, lt, __int_as_float(cnt));
+    if (RECORD) {
+      a.s0[p] = make_float4(xh, yh, xl, yl);
+      a.s0b[p] = make_float2(lt, __int_as_float(cnt));
+    }
   }
   if (RECORD) {
     const unsigned c = valid ? static_cast<unsigned>(cnt) : 0u;
