@@ -29,7 +29,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_STROKES, RES, PALETTE = 2000, 1024, 16
-CHECKPOINT_EVERY = 32
+CHECKPOINT_EVERY = 64
 
 # Algorithmic FP32 work per pixel-stroke (FP32 arithmetic instructions: add, mul
 # and fused multiply-add each count 1; transcendental / reciprocal operations are

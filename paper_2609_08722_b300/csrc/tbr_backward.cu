@@ -32,14 +32,14 @@ __device__ __forceinline__ void inert_vjp(float s, float h, const StrokeF& g, fl
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
   const bool cap = d > 0.0f;
-  const float sp = cap ? sqrtf(fmaf(d, d, ah * ah)) : ah;
+  const float sp = cap ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
   sp_out = sp;
   if (!want) return;
   const float g_sp = -mua * g.iw;
   gr = mua * fmaf(-z, g.dlw, g.iw);
   float g_as = 0.0f, g_ah = g_sp, g_hl = 0.0f;
   if (cap && sp > 0.0f) {
-    const float inv = 1.0f / sp;
+    const float inv = rcp_a(sp);
     g_as = g_sp * d * inv;
     g_ah = g_sp * ah * inv;
     g_hl = -g_as;
@@ -56,7 +56,7 @@ __device__ __forceinline__ void inert_vjp(float s, float h, const StrokeF& g, fl
 }
 
 template <int CH, bool INERT>
-__global__ void __launch_bounds__(kBwdThreads, 2) k_backward(BwdArgs a) {
+__global__ void __launch_bounds__(kBwdThreads, 4) k_backward(BwdArgs a) {
   static_assert(CH * 8 == kBwdThreads, "one partial per thread per chunk");
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_backward(BwdArgs a) {
           inert_vjp(s, h, g, sp, lx, ly, 0.0f, 0.0f, false, d0, d1, d2, d3, d4);
           const Cover cv = coverage(sp, g);
           if (at_ck) lt = a.ck_lt[cko]; else lt += cv.sp2;
-          const float T = exp2f(lt);
+          const float T = ex2_a(lt);
           const float mu = T * (lCc - lT);
           const float Ta = T * cv.alpha;
           v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;
@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_backward(BwdArgs a) {
           }
           const Cover cv = coverage(gq.sp, g);
           if (at_ck) lt = a.ck_lt[cko]; else lt += cv.sp2;
-          const float T = exp2f(lt);
+          const float T = ex2_a(lt);
           const float mu = T * (lCc - lT);
           const float Ta = T * cv.alpha;
           v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;

@@ -59,7 +59,7 @@ __device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float
   to_frame(xh, yh, xl, yl, g, s, h);
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
-  const float sp = d > 0.0f ? sqrtf(fmaf(d, d, ah * ah)) : ah;
+  const float sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
   const float diff = sp - g.r;
   if (fabsf(diff) < kBand) {
     ++band;

@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include "tbr.h"
+#include "tbr_poly.h"
 
 namespace tbr {
 
@@ -127,6 +128,56 @@ struct ChunkRing {
 };
 
 // ---------------------------------------------------------------------------
+// Fast arithmetic: single-instruction PTX approximations (reciprocal and square
+// root within 1-2 ulp, base-2 exponential / logarithm within ~2^-22) and
+// polynomial atan / sin / 1-cos on the folded ranges the maps need
+// (tbr_poly.h, generated by gen_poly.py), so that the hot loops avoid the
+// multi-instruction IEEE division, square-root and range-reduction sequences.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_a(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_a(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_a(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_a(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float div_a(float a, float b) { return a * rcp_a(b); }
+
+template <int N>
+__device__ __forceinline__ float horner(const float (&c)[N], float u) {
+  float acc = c[N - 1];
+#pragma unroll
+  for (int k = N - 2; k >= 0; --k) acc = fmaf(acc, u, c[k]);
+  return acc;
+}
+// atan2(y, x) for y, x >= 0 (result in [0, pi/2]).
+__device__ __forceinline__ float atan2_pos(float y, float x) {
+  const float mx = fmaxf(y, x), mn = fminf(y, x);
+  const float z = mx > 0.0f ? mn * rcp_a(mx) : 0.0f;
+  const float a = z * horner(kAtan, z * z);
+  return y > x ? 0.5f * kPiF - a : a;
+}
+// sin(d) and 1 - cos(d) for |d| <= pi/2, both with full relative precision at small d.
+__device__ __forceinline__ float sin_pi2(float d) { return d * horner(kSin, d * d); }
+__device__ __forceinline__ float omc_pi2(float d) {
+  const float u = d * d;
+  return u * horner(kOmc, u);
+}
+
+// ---------------------------------------------------------------------------
 // Stroke fields read from shared memory as broadcasts.
 // ---------------------------------------------------------------------------
 struct StrokeF {
@@ -194,10 +245,10 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
   const float d = as - g.hl;
   q.cap_i = d > 0.0f;
   if (q.cap_i) {
-    q.sp = sqrtf(fmaf(d, d, ah * ah));
-    const float inv = 1.0f / q.sp;
+    q.sp = sqrt_a(fmaf(d, d, ah * ah));
+    const float inv = rcp_a(q.sp);
     q.ud = d * inv; q.uh = ah * inv;
-    q.phi = atan2f(d, ah);
+    q.phi = atan2_pos(d, ah);
     q.t = fmaf(q.sp, q.phi, g.hl);
   } else {
     q.sp = ah; q.ud = 0.0f; q.uh = 1.0f; q.phi = 0.0f; q.t = as;
@@ -205,17 +256,17 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
   float C = (q.sp - g.r) * fmaf(kPiF, q.sp, g.kA);
   q.floored = FLOOR && C < g.fl2;
   if (q.floored) C = g.fl2;
-  q.sig = C / (g.L + sqrtf(fmaf(kPiF, C, g.L2)));
+  q.sig = div_a(C, g.L + sqrt_a(fmaf(kPiF, C, g.L2)));
   const float Qp = fmaf(kPiF, q.sp, g.L), Q = fmaf(kPiF, q.sig, g.L);
-  const float dsig = q.floored ? q.sig - q.sp : -g.Ar / fmaf(kPiF, q.sp + q.sig, g.twoL);
-  q.tn = Qp > 0.0f ? q.t * (Q / Qp) : 0.0f;
+  const float iQp = Qp > 0.0f ? rcp_a(Qp) : 0.0f;
+  const float dsig = q.floored ? q.sig - q.sp : -div_a(g.Ar, fmaf(kPiF, q.sp + q.sig, g.twoL));
+  q.tn = q.t * (Q * iQp);
   q.cap_o = q.tn > g.hl;
   float dS, dH;
   if (!q.floored && q.cap_i && q.cap_o) {
-    float delta = -dsig * g.L * (q.phi - 0.5f * kPiF) / (Qp * q.sig);
+    float delta = -dsig * g.L * (q.phi - 0.5f * kPiF) * iQp * rcp_a(q.sig);
     delta = fminf(fmaxf(delta, -q.phi), 0.0f);
-    const float sD = sinf(delta), s2 = sinf(0.5f * delta);
-    const float omc = 2.0f * s2 * s2;  // 1 - cos(delta)
+    const float sD = sin_pi2(delta), omc = omc_pi2(delta);
     dS = fmaf(dsig, q.ud, q.sig * fmaf(q.uh, sD, -q.ud * omc));
     dH = fmaf(dsig, q.uh, -q.sig * fmaf(q.ud, sD, q.uh * omc));
     const float cD = 1.0f - omc;
@@ -223,14 +274,15 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
     q.sb = fmaf(q.ud, cD, q.uh * sD);
     q.cb = fmaf(q.uh, cD, -q.ud * sD);
   } else if (!q.floored && !q.cap_i) {  // flank to flank (tn <= t <= L/2)
-    dS = as * kPiF * dsig / Qp;
+    dS = as * kPiF * dsig * iQp;
     dH = dsig;
     q.beta = 0.0f; q.sb = 0.0f; q.cb = 1.0f;
   } else {                             // floored, or cap to flank: direct form
     float sn, hn;
     if (q.cap_o) {
-      q.beta = (q.tn - g.hl) / q.sig;
-      sincosf(q.beta, &q.sb, &q.cb);
+      q.beta = fminf((q.tn - g.hl) * rcp_a(q.sig), 0.5f * kPiF);
+      q.sb = sin_pi2(q.beta);
+      q.cb = 1.0f - omc_pi2(q.beta);
       sn = fmaf(q.sig, q.sb, g.hl); hn = q.sig * q.cb;
     } else {
       q.beta = 0.0f; q.sb = 0.0f; q.cb = 1.0f;
@@ -255,26 +307,26 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
   const float d = as - g.hl;
   q.cap_o = d > 0.0f;
   if (q.cap_o) {
-    q.sig = sqrtf(fmaf(d, d, ah * ah));
-    const float inv = 1.0f / q.sig;
+    q.sig = sqrt_a(fmaf(d, d, ah * ah));
+    const float inv = rcp_a(q.sig);
     q.sb = d * inv; q.cb = ah * inv;
-    q.beta = atan2f(d, ah);
+    q.beta = atan2_pos(d, ah);
     q.tn = fmaf(q.sig, q.beta, g.hl);
   } else {
     q.sig = ah; q.sb = 0.0f; q.cb = 1.0f; q.beta = 0.0f; q.tn = as;
   }
   const float B = fmaf(q.sig, fmaf(kPiF, q.sig, g.twoL), g.Ar);
-  q.sp = B / (g.L + sqrtf(fmaf(kPiF, B, g.L2)));
-  const float dsp = g.Ar / fmaf(kPiF, q.sig + q.sp, g.twoL);
+  q.sp = div_a(B, g.L + sqrt_a(fmaf(kPiF, B, g.L2)));
+  const float dsp = div_a(g.Ar, fmaf(kPiF, q.sig + q.sp, g.twoL));
   const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
-  q.t = Q > 0.0f ? q.tn * (Qp / Q) : 0.0f;
+  const float iQ = Q > 0.0f ? rcp_a(Q) : 0.0f;
+  q.t = q.tn * (Qp * iQ);
   q.cap_i = q.t > g.hl;
   float dS, dH;
   if (q.cap_o) {                       // cap to cap (t >= tn > L/2)
-    float delta = dsp * g.L * (0.5f * kPiF - q.beta) / (Q * q.sp);
+    float delta = dsp * g.L * (0.5f * kPiF - q.beta) * iQ * rcp_a(q.sp);
     delta = fminf(fmaxf(delta, 0.0f), 0.5f * kPiF - q.beta);
-    const float sD = sinf(delta), s2 = sinf(0.5f * delta);
-    const float omc = 2.0f * s2 * s2;
+    const float sD = sin_pi2(delta), omc = omc_pi2(delta);
     dS = fmaf(dsp, q.sb, q.sp * fmaf(q.cb, sD, -q.sb * omc));
     dH = fmaf(dsp, q.cb, -q.sp * fmaf(q.sb, sD, q.cb * omc));
     const float cD = 1.0f - omc;
@@ -283,12 +335,13 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
     q.uh = fmaf(q.cb, cD, -q.sb * sD);
     q.cap_i = true;
   } else if (!q.cap_i) {               // flank to flank
-    dS = q.tn * kPiF * dsp / Q;
+    dS = q.tn * kPiF * dsp * iQ;
     dH = dsp;
     q.phi = 0.0f; q.ud = 0.0f; q.uh = 1.0f;
   } else {                             // flank to cap: direct form
-    q.phi = (q.t - g.hl) / q.sp;
-    sincosf(q.phi, &q.ud, &q.uh);
+    q.phi = fminf((q.t - g.hl) * rcp_a(q.sp), 0.5f * kPiF);
+    q.ud = sin_pi2(q.phi);
+    q.uh = 1.0f - omc_pi2(q.phi);
     dS = fmaf(q.sp, q.ud, g.hl) - as;
     dH = fmaf(q.sp, q.uh, -ah);
   }
@@ -334,7 +387,7 @@ __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& 
     g_sig = fmaf(gsn, q.sb, ghn * q.cb);
     const float g_beta = q.sig * fmaf(gsn, q.cb, -ghn * q.sb);
     g_hl = gsn;
-    g_tn = g_beta / q.sig;
+    g_tn = g_beta * rcp_a(q.sig);
     g_hl -= g_tn;
     g_sig -= g_tn * q.beta;
   }
@@ -342,7 +395,7 @@ __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& 
   const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
   float g_t = 0.0f;
   if (Qp > 0.0f) {
-    const float iQp = 1.0f / Qp;
+    const float iQp = rcp_a(Qp);
     g_t = g_tn * Q * iQp;
     const float g_Q = g_tn * q.t * iQp;
     const float g_Qp = -g_tn * q.tn * iQp;
@@ -353,7 +406,7 @@ __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& 
   // sigma solves A_L(sigma) = C: d sigma/dC = 1/(2Q), d sigma/dL = -sigma/Q
   float g_C = 0.0f;
   if (Q > 0.0f) {
-    const float iQ = 1.0f / Q;
+    const float iQ = rcp_a(Q);
     g_C = 0.5f * g_sig * iQ;
     g_L -= g_sig * q.sig * iQ;
   }
@@ -406,14 +459,14 @@ __device__ __forceinline__ Cover coverage(float sp, const StrokeF& g) {
   const float zr = (g.r - sp) * g.iw;
   const bool clamped = zr > kZMax;
   c.z = clamped ? kZMax : zr;
-  const float e = exp2f(-fabsf(c.z) * kLog2e);
+  const float e = ex2_a(-fabsf(c.z) * kLog2e);
   const float opl = 1.0f + e;
-  const float inv = 1.0f / opl;
+  const float inv = rcp_a(opl);
   const bool pos = c.z >= 0.0f;
   c.alpha = pos ? inv : e * inv;
   c.oma = pos ? e * inv : inv;
   c.dadz = clamped ? 0.0f : e * inv * inv;
-  c.sp2 = fmaf(fmaxf(c.z, 0.0f), kLog2e, log2f(opl));
+  c.sp2 = fmaf(fmaxf(c.z, 0.0f), kLog2e, lg2_a(opl));
   return c;
 }
 

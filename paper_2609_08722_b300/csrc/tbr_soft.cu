@@ -76,9 +76,9 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
         if (INERT) {
           const float as = fabsf(s), ah = fabsf(h);
           const float d = as - g.hl;
-          const float sp = d > 0.0f ? sqrtf(fmaf(d, d, ah * ah)) : ah;
+          const float sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
           const Cover cv = coverage(sp, g);
-          const float w = exp2f(lt) * cv.alpha;
+          const float w = ex2_a(lt) * cv.alpha;
           C0 = fmaf(w, S[F_CR], C0);
           C1 = fmaf(w, S[F_CG], C1);
           C2 = fmaf(w, S[F_CB], C2);
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
           float ds, dh;
           psi_local<true>(s, h, g, q, ds, dh);
           const Cover cv = coverage(q.sp, g);
-          const float w = exp2f(lt) * cv.alpha;
+          const float w = ex2_a(lt) * cv.alpha;
           C0 = fmaf(w, S[F_CR], C0);
           C1 = fmaf(w, S[F_CG], C1);
           C2 = fmaf(w, S[F_CB], C2);
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(256) k_soft(SoftArgs a) {
   }
 
   if (valid) {
-    const float T0 = exp2f(lt);
+    const float T0 = ex2_a(lt);
     float o0 = fmaf(T0, a.bg[0], C0), o1 = fmaf(T0, a.bg[1], C1), o2 = fmaf(T0, a.bg[2], C2);
     if (invalid_prog || aborted) o0 = o1 = o2 = __int_as_float(0x7fc00000);
     a.out_rgb[3 * p + 0] = o0;
