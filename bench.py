@@ -357,6 +357,25 @@ def run_native(args):
         e2e = {"value": sum_over_ranks(units, world, device) / (e2e_ms * 1e-3), "unit": "evals/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
 
+    # loss-fused forward + adjoint (tbr_render_soft_adjoint_mse): same work, record kept in L2
+    fused = None
+    if not args.no_e2e:
+        for _ in range(2):
+            tbr.soft_adjoint_mse(prog, target, tau, tau_min, checkpoint_every=CHECKPOINT_EVERY)
+        torch.cuda.synchronize()
+        fz = []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            tbr.soft_adjoint_mse(prog, target, tau, tau_min, checkpoint_every=CHECKPOINT_EVERY)
+            a1.record()
+            fz.append((a0, a1))
+        torch.cuda.synchronize()
+        fms = sum(x.elapsed_time(y) for x, y in fz) / args.steps
+        fused = {"ms_per_step": fms, "value": units / (fms * 1e-3), "unit": "evals/s",
+                 "api": "tbr_render_soft_adjoint_mse"}
+
     # fit step (A11): forward + loss + adjoint + Adam, schedules of Table hyper
     fit_ms = None
     if args.fit_steps > 0:
@@ -399,6 +418,7 @@ def run_native(args):
             "kernel_ms": {"backward": bwd_ms, "soft_forward": soft_ms,
                           "other": step_ms - bwd_ms - soft_ms},
             "fit_step_ms": fit_ms,
+            "fused_path": fused,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,

@@ -150,7 +150,7 @@ TBR_API tbr_status tbr_render_backward(tbr_ctx* ctx, const float* dL_drgb, float
                                float* g_logits, float* g_palette, void* stream);
 
 /* Counters of a context (host struct). */
-typedef struct {
+struct tbr_ctx_stats {
   int64_t records;          /* side-table records written */
   int64_t max_records;      /* largest per-pixel record count */
   int64_t overflow_pixels;  /* pixels whose records exceeded the capacity */
@@ -158,7 +158,8 @@ typedef struct {
                                differed from the stored one by more than 1e-5 */
   int64_t timeouts;         /* bounded waits that gave up */
   int64_t invalid_params;   /* strokes that failed the value checks */
-} tbr_ctx_stats;
+};
+typedef struct tbr_ctx_stats tbr_ctx_stats;
 
 /* Synchronises the context's last stream and reads its counters.  Returns
  * TBR_ERR_OVERFLOW, TBR_ERR_TIMEOUT or TBR_ERR_INVALID_ARG if the matching
@@ -178,6 +179,26 @@ TBR_API void tbr_ctx_destroy(tbr_ctx* ctx);
  * fp64 partial per block, stream-ordered. */
 TBR_API tbr_status tbr_loss_mse(const float* rgb, const float* target, int64_t n_pixels,
                         float* loss_out, float* dL_drgb, void* stream);
+
+/* Loss-fused soft forward + replay adjoint for the pixel MSE (Sec. 5.1
+ * objective; Sec. 5.2 adjoint): the seed lambda^C_0 = 2 (R - target) / (3HW) is
+ * pixel-local, so each 32x8 tile runs its soft forward with the replay record
+ * in per-CTA scratch (L2-resident), seeds, and runs the replay adjoint at once;
+ * no full-image side table or checkpoint array is written.  Same gradients as
+ * tbr_render_soft + tbr_loss_mse + tbr_render_backward (to rounding).
+ *   target    [H][W][3]
+ *   out_rgb   [H][W][3] soft render, or NULL
+ *   loss_out  device scalar (MSE, FP64 sums) or NULL
+ *   g_*       as tbr_render_backward (written)
+ *   stats     host, or NULL; when non-NULL the call synchronises and reports
+ *             overflow / invalid values / timeouts as errors.
+ * opts->inert must be 0.  Scratch (packed strokes, per-CTA record, gradient
+ * slices) is allocated stream-ordered and released on return. */
+TBR_API tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32_t H,
+                                               const tbr_soft_opts* opts, const float* target, float* out_rgb,
+                                               float* loss_out, float* g_cx, float* g_cy, float* g_theta,
+                                               float* g_length, float* g_half_width, float* g_logits,
+                                               float* g_palette, tbr_ctx_stats* stats, void* stream);
 
 /* ------------------------------------------------------------------------
  * Fit (Sec. 5.1 "Parameterisation and relaxation", Eq. inverse, Table hyper):
@@ -246,7 +267,8 @@ enum {
   TBR_K_LOSS = 5,        /* MSE and adjoint seed */
   TBR_K_UPDATE = 6,      /* Adam update */
   TBR_K_SERVE = 7,       /* persistent serving kernel */
-  TBR_K_COUNT = 8
+  TBR_K_FUSED = 8,       /* loss-fused soft forward + replay adjoint */
+  TBR_K_COUNT = 9
 };
 typedef struct {
   int64_t launches;

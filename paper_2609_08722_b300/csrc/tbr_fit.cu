@@ -24,13 +24,10 @@ struct tbr_fit {
   float* rlo = nullptr;      // [n]
   float* rhi = nullptr;      // [n]
   float* target = nullptr;   // [P][3]
-  float* rgb = nullptr;      // [P][3]
-  float* dLdR = nullptr;     // [P][3]
   float* scal = nullptr;     // [2]: MSE, sum of lengths
-  double* loss_partial = nullptr;
-  int loss_nb = 0;
   float* host = nullptr;     // pinned [2]
-  tbr_ctx ctx;
+  tbr::FusedWork work;       // loss-fused forward + replay adjoint buffers
+  cudaStream_t last_stream = nullptr;
 };
 
 namespace tbr {
@@ -110,10 +107,9 @@ float geometric(float a, float b, int t, int T) {
 }
 
 void fit_free(tbr_fit* f, cudaStream_t st) {
-  ctx_release(&f->ctx);
+  f->work.release(st);
   dfree(f->params, st); dfree(f->grads, st); dfree(f->m, st); dfree(f->v, st);
-  dfree(f->rlo, st); dfree(f->rhi, st); dfree(f->target, st); dfree(f->rgb, st);
-  dfree(f->dLdR, st); dfree(f->scal, st); dfree(f->loss_partial, st);
+  dfree(f->rlo, st); dfree(f->rhi, st); dfree(f->target, st); dfree(f->scal, st);
   if (f->host) cudaFreeHost(f->host);
   f->host = nullptr;
 }
@@ -138,7 +134,7 @@ void tbr_fit_default_config(tbr_fit_config* c) {
   c->width_lo = 0.6f; c->width_hi = 1.7f;
   c->length_weight = 3e-4f;
   c->train_palette = 0;
-  c->checkpoint_every = 32;
+  c->checkpoint_every = 64;
   c->record_capacity = 64;
 }
 
@@ -156,7 +152,7 @@ tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t 
       !(c.color_temp_end > 0) || !(c.length_max > 0) || !(c.width_lo > 0) || !(c.width_hi >= c.width_lo) ||
       c.checkpoint_every < 0 || c.record_capacity < 0)
     return fail(TBR_ERR_INVALID_ARG, "invalid fit configuration");
-  if (c.checkpoint_every == 0) c.checkpoint_every = 32;
+  if (c.checkpoint_every == 0) c.checkpoint_every = 64;
   if (c.record_capacity == 0) c.record_capacity = 64;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   tbr_fit* f = new tbr_fit();
@@ -166,7 +162,7 @@ tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t 
   f->tau_min = c.tau_min > 0 ? c.tau_min : 0.7f / static_cast<float>(W > H ? W : H);
   const size_t n = f->n, k = f->k, P = static_cast<size_t>(W) * H;
   f->nparam = 5 * n + n * k + 3 * k;
-  f->loss_nb = loss_blocks(static_cast<int64_t>(P));
+  f->last_stream = st;
   cudaError_t e = dalloc(&f->params, f->nparam, st);
   if (e == cudaSuccess) e = dalloc(&f->grads, f->nparam, st);
   if (e == cudaSuccess) e = dalloc(&f->m, f->nparam, st);
@@ -174,13 +170,9 @@ tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t 
   if (e == cudaSuccess) e = dalloc(&f->rlo, n, st);
   if (e == cudaSuccess) e = dalloc(&f->rhi, n, st);
   if (e == cudaSuccess) e = dalloc(&f->target, 3 * P, st);
-  if (e == cudaSuccess) e = dalloc(&f->rgb, 3 * P, st);
-  if (e == cudaSuccess) e = dalloc(&f->dLdR, 3 * P, st);
   if (e == cudaSuccess) e = dalloc(&f->scal, 2, st);
-  if (e == cudaSuccess) e = dalloc(&f->loss_partial, static_cast<size_t>(f->loss_nb), st);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&f->host), 2 * sizeof(float));
-  if (e == cudaSuccess)
-    e = ctx_allocate(&f->ctx, f->n, f->k, W, H, c.checkpoint_every, c.record_capacity, 0, st);
+  if (e == cudaSuccess) e = f->work.allocate(f->n, f->k, W, H, c.checkpoint_every, c.record_capacity, st);
   const float* src[5] = {init->cx, init->cy, init->theta, init->length, init->half_width};
   for (int g = 0; g < 5 && e == cudaSuccess && n > 0; ++g)
     e = cudaMemcpyAsync(f->params + g * n, src[g], n * 4, cudaMemcpyDeviceToDevice, st);
@@ -214,17 +206,14 @@ tbr_status tbr_fit_step(tbr_fit* f, float* loss_out, void* stream) {
   const float tau = geometric(c.tau_start, c.tau_end, t, T);
   const float tc = geometric(c.color_temp_start, c.color_temp_end, t, T);
   const float cosine = 0.5f * (1.0f + std::cos(3.14159265358979f * static_cast<float>(t) / static_cast<float>(T)));
-  const size_t n = f->n, k = f->k, P = static_cast<size_t>(f->W) * f->H;
+  const size_t n = f->n, k = f->k;
+  f->last_stream = st;
   for (int attempt = 0; attempt < 4; ++attempt) {
     const tbr_program view = view_of(f, tc);
-    TBR_CUDA(ctx_forward(&f->ctx, &view, tau, f->tau_min, f->rgb, st), "fit: soft forward");
-    TBR_CUDA(launch_loss(f->rgb, f->target, static_cast<int64_t>(P), f->loss_partial, f->loss_nb, f->scal,
-                         f->dLdR, st),
-             "fit: loss");
     float* g = f->grads;
-    TBR_CUDA(ctx_backward(&f->ctx, f->dLdR, g, g + n, g + 2 * n, g + 3 * n, g + 4 * n, g + 5 * n,
-                          c.train_palette ? g + 5 * n + n * k : nullptr, st),
-             "fit: replay adjoint");
+    TBR_CUDA(f->work.run(&view, tau, f->tau_min, f->target, nullptr, f->scal, g, g + n, g + 2 * n, g + 3 * n,
+                         g + 4 * n, g + 5 * n, c.train_palette ? g + 5 * n + n * k : nullptr, st),
+             "fit: loss-fused forward + replay adjoint");
     if (n > 0) k_length_sum<<<1, 256, 0, st>>>(f->params + 3 * n, f->n, f->scal + 1);
     AdamStep as;
     const float lr[7] = {c.lr_center, c.lr_center, c.lr_angle, c.lr_length, c.lr_width, c.lr_logits,
@@ -236,23 +225,26 @@ tbr_status tbr_fit_step(tbr_fit* f, float* loss_out, void* stream) {
     as.lambda_len = c.length_weight; as.len_max = c.length_max;
     as.n = f->n; as.k = f->k; as.train_palette = c.train_palette;
     const size_t total = 5 * n + n * k + (c.train_palette ? 3 * k : 0);
-    KernelTimer kt(TBR_K_UPDATE, st);
-    if (total > 0)
-      k_adam<<<static_cast<unsigned>((total + kAdamThreads - 1) / kAdamThreads), kAdamThreads, 0, st>>>(
-          f->params, f->grads, f->m, f->v, f->rlo, f->rhi, as, f->ctx.status);
+    {
+      KernelTimer kt(TBR_K_UPDATE, st);
+      if (total > 0)
+        k_adam<<<static_cast<unsigned>((total + kAdamThreads - 1) / kAdamThreads), kAdamThreads, 0, st>>>(
+            f->params, f->grads, f->m, f->v, f->rlo, f->rhi, as, f->work.status);
+    }
     TBR_CUDA(cudaGetLastError(), "fit: update");
-    TBR_CUDA(cudaMemcpyAsync(f->host, f->scal, 2 * sizeof(float), cudaMemcpyDeviceToHost, st), "fit: loss copy");
     unsigned long long host[ST_COUNT];
-    const tbr_status s = ctx_read_status(&f->ctx, host);
-    if (s == TBR_ERR_OVERFLOW) {
+    TBR_CUDA(cudaMemcpyAsync(f->host, f->scal, 2 * sizeof(float), cudaMemcpyDeviceToHost, st), "fit: loss copy");
+    TBR_CUDA(cudaMemcpyAsync(host, f->work.status, sizeof(host), cudaMemcpyDeviceToHost, st), "fit: status copy");
+    TBR_CUDA(cudaStreamSynchronize(st), "fit: synchronise");
+    if (host[ST_OVERFLOW]) {
       // the update was skipped on the device; grow the side table and redo the step
-      const int cap = f->ctx.cap * 2;
-      ctx_release(&f->ctx);
-      TBR_CUDA(ctx_allocate(&f->ctx, f->n, f->k, f->W, f->H, c.checkpoint_every, cap, 0, st),
-               "fit: growing the side table");
+      const int cap = f->work.cap * 2;
+      f->work.release(st);
+      TBR_CUDA(f->work.allocate(f->n, f->k, f->W, f->H, c.checkpoint_every, cap, st), "fit: growing the side table");
       continue;
     }
-    if (s != TBR_OK) return s;
+    if (host[ST_INVALID]) return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);
+    if (host[ST_TIMEOUT]) return fail(TBR_ERR_TIMEOUT, "a bounded device wait gave up");
     if (loss_out) *loss_out = f->host[0] + c.length_weight * (n > 0 ? f->host[1] : 0.0f);
     ++f->iter;
     return TBR_OK;
@@ -272,7 +264,7 @@ int32_t tbr_fit_iteration(const tbr_fit* f) { return f ? f->iter : -1; }
 
 void tbr_fit_destroy(tbr_fit* f) {
   if (!f) return;
-  fit_free(f, f->ctx.last_stream);
+  fit_free(f, f->last_stream);
   delete f;
 }
 

@@ -584,6 +584,28 @@ cudaError_t launch_backward_epilogue(const EpilogueArgs& a, cudaStream_t st);
 
 cudaError_t launch_loss(const float* rgb, const float* target, int64_t npix, double* partial,
                         int nblocks, float* loss_out, float* dLdR, cudaStream_t st);
+// loss_out[0] = (sum of the nparts FP64 partials, in order) / nval.
+cudaError_t launch_loss_final(const double* partial, int nparts, int64_t nval, float* loss_out, cudaStream_t st);
+
+struct FusedArgs {
+  const float* packed;
+  int n, W, H;
+  float bg[3];
+  int ck, cap;
+  const float* target;       // [P][3]
+  float* out_rgb;            // [P][3] or NULL
+  float4* rec;               // per-CTA scratch [grid][cap][256]
+  int* rec_i;
+  float4* ckpt;              // per-CTA scratch [grid][(n-1)/ck][256]
+  float* ck_lt;
+  float* partial;            // [grid][n][8]
+  double* loss_part;         // [grid]
+  int grid;
+  float seed_scale;          // 2 / (3P)
+  unsigned long long* status;
+};
+int fused_grid(int W, int H);
+cudaError_t launch_fused(const FusedArgs& a, cudaStream_t st);
 int loss_blocks(int64_t npix);
 
 }  // namespace tbr

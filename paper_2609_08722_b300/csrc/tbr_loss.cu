@@ -63,4 +63,10 @@ cudaError_t launch_loss(const float* rgb, const float* target, int64_t npix, dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_loss_final(const double* partial, int nparts, int64_t nval, float* loss_out, cudaStream_t st) {
+  KernelTimer kt(TBR_K_LOSS, st);
+  k_loss_final<<<1, kLossThreads, 0, st>>>(partial, nparts, nval, loss_out);
+  return cudaGetLastError();
+}
+
 }  // namespace tbr

@@ -1,0 +1,412 @@
+// Per-tile device routines shared by the soft forward, the replay adjoint, the
+// loss-fused forward+adjoint kernel and the serving kernel.  A tile is 32x8
+// pixels, one pixel per thread (a warp = 32 consecutive pixels of one row);
+// strokes stream through the CTA's two-deep shared-memory ring (ChunkRing).
+#pragma once
+
+#include "tbr_internal.cuh"
+
+namespace tbr {
+
+constexpr int kTileW = 32, kTileH = 8, kTileThreads = 256;
+
+// Where one pixel's replay record lives: element (slot, pixel) of each array is
+// at slot * stride + off.  The plain kernels use [slot][P] with off = pixel;
+// the fused kernels use a per-CTA scratch [slot][256] with off = threadIdx.x.
+struct RecordView {
+  float4* rec;     // side table positions (hi/lo), `cap` slots
+  int* rec_i;      // side table stroke indices (1-based)
+  float4* ckpt;    // checkpoints at i = ck, 2ck, ... (< n)
+  float* ck_lt;    // log2 T at the checkpoints
+  size_t stride;
+  size_t off;
+  int cap, ck;
+};
+
+// State of one pixel after the soft forward (s_0 of Eq. state plus the colour).
+struct PixelState {
+  float xh, yh, xl, yl;  // x_0 as a hi/lo pair
+  float lt;              // log2 T_0
+  int cnt;               // side-table records written (may exceed cap)
+  float C0, C1, C2;      // accumulated colour C_0
+};
+
+__device__ __forceinline__ void tile_pixel(int tile, int W, int& px, int& py) {
+  const int tiles_x = (W + kTileW - 1) / kTileW;
+  px = (tile % tiles_x) * kTileW + (threadIdx.x & 31);
+  py = (tile / tiles_x) * kTileH + (threadIdx.x >> 5);
+}
+
+// Soft forward (Eq. relax, Eq. state, floored psi) of one pixel per thread over
+// strokes n-1 .. 0.  With RECORD, pushes (x_i, i) for floored samples and
+// stores (x_i, log2 T_i) every ck strokes.  All threads of the CTA must call it.
+// Returns false if a bounded wait gave up (the status word is set).
+template <int CH, bool RECORD, bool INERT>
+__device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, bool valid,
+                                  float x0, float y0, const RecordView& rv, PixelState& st,
+                                  unsigned long long* status) {
+  st.xh = x0; st.yh = y0; st.xl = 0.0f; st.yl = 0.0f;
+  st.lt = 0.0f; st.cnt = 0;
+  st.C0 = st.C1 = st.C2 = 0.0f;
+  const int ck = rv.ck;
+  int next_ck = (RECORD && n > 1) ? ((n - 1) / ck) * ck : 0;  // largest checkpoint index < n
+  const int nch = (n + CH - 1) / CH;
+  auto chunk_src = [&](int q) { return packed + static_cast<size_t>(nch - 1 - q) * CH * kRec; };
+  auto chunk_cnt = [&](int q) { return min(CH, n - (nch - 1 - q) * CH); };
+  if (threadIdx.x == 0) {
+    if (nch > 0) ring.issue(0, chunk_src(0), chunk_cnt(0));
+    if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
+  }
+  bool ok = true;
+  for (int q = 0; q < nch; ++q) {
+    const int b = q & 1;
+    const bool got = ring.wait(b, status);
+    if (__syncthreads_or(!got)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);
+      ok = false;
+      break;
+    }
+    const int base = (nch - 1 - q) * CH;
+    const int cntc = chunk_cnt(q);
+    const float* S0 = ring.data(b);
+    if (valid) {
+      for (int j = cntc - 1; j >= 0; --j) {
+        const int i1 = base + j + 1;  // the paper's 1-based stroke index
+        if (RECORD && i1 == next_ck) {
+          const size_t o = static_cast<size_t>(i1 / ck - 1) * rv.stride + rv.off;
+          rv.ckpt[o] = make_float4(st.xh, st.yh, st.xl, st.yl);
+          rv.ck_lt[o] = st.lt;
+          next_ck -= ck;
+        }
+        const float* S = S0 + j * kRec;
+        const StrokeF g = load_stroke(S);
+        float s, h;
+        to_frame(st.xh, st.yh, st.xl, st.yl, g, s, h);
+        float sp, ds = 0.0f, dh = 0.0f;
+        bool floored = false;
+        if (INERT) {
+          const float as = fabsf(s), ah = fabsf(h);
+          const float d = as - g.hl;
+          sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
+        } else {
+          Geo q;
+          psi_local<true>(s, h, g, q, ds, dh);
+          sp = q.sp;
+          floored = q.floored;
+        }
+        const Cover cv = coverage(sp, g);
+        const float w = ex2_a(st.lt) * cv.alpha;
+        st.C0 = fmaf(w, S[F_CR], st.C0);
+        st.C1 = fmaf(w, S[F_CG], st.C1);
+        st.C2 = fmaf(w, S[F_CB], st.C2);
+        st.lt -= cv.sp2;
+        if (!INERT) {
+          if (RECORD && floored) {
+            if (st.cnt < rv.cap) {
+              const size_t o = static_cast<size_t>(st.cnt) * rv.stride + rv.off;
+              rv.rec[o] = make_float4(st.xh, st.yh, st.xl, st.yl);
+              rv.rec_i[o] = i1;
+            }
+            ++st.cnt;
+          }
+          add_frame_disp(st.xh, st.yh, st.xl, st.yl, g, ds, dh);
+        }
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
+  }
+  return ok;
+}
+
+// Membership test and psi (Eq. back) recomputed in FP64 from the hi/lo
+// position, used where |sigma' - r| < kBand.  Returns true if the point is inside.
+static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& xl, float& yl,
+                                           const float* __restrict__ S) {
+  const double* D = reinterpret_cast<const double*>(S + F_D64);
+  const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
+  const double L = 2.0 * hl;
+  const double x = static_cast<double>(xh) + static_cast<double>(xl);
+  const double y = static_cast<double>(yh) + static_cast<double>(yl);
+  const double dx = x - mx, dy = y - my;
+  const double s = dx * ex + dy * ey, h = dy * ex - dx * ey;
+  const double as = fabs(s), ah = fabs(h), d = as - hl;
+  const bool cap = d > 0.0;
+  const double sp = cap ? sqrt(d * d + ah * ah) : ah;
+  if (sp <= r) return true;
+  const double C = (sp - r) * (2.0 * L + kPiD * (sp + r));
+  const double sig = C / (L + sqrt(L * L + kPiD * C));
+  const double Qp = L + kPiD * sp, Q = L + kPiD * sig;
+  const double t = cap ? hl + sp * atan2(d, ah) : as;
+  const double tn = t * (Q / Qp);
+  double sn, hn;
+  if (tn <= hl) {
+    sn = tn; hn = sig;
+  } else {
+    double sb, cb;
+    sincos((tn - hl) / sig, &sb, &cb);
+    sn = hl + sig * sb; hn = sig * cb;
+  }
+  sn = copysign(sn, s); hn = copysign(hn, h);
+  const double xo = mx + sn * ex - hn * ey, yo = my + sn * ey + hn * ex;
+  xh = static_cast<float>(xo); xl = static_cast<float>(xo - static_cast<double>(xh));
+  yh = static_cast<float>(yo); yl = static_cast<float>(yo - static_cast<double>(yh));
+  return false;
+}
+
+// One stroke of the hard chain in FP32.  Returns true if x lies in K_i;
+// otherwise moves x to psi_i(x) (displacement form, hi/lo position).
+__device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float& yl,
+                                          const float* __restrict__ S, unsigned& band) {
+  const StrokeF g = load_stroke(S);
+  float s, h;
+  to_frame(xh, yh, xl, yl, g, s, h);
+  const float as = fabsf(s), ah = fabsf(h);
+  const float d = as - g.hl;
+  const float sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
+  const float diff = sp - g.r;
+  if (fabsf(diff) < kBand) {
+    ++band;
+    return hard_step_f64(xh, yh, xl, yl, S);
+  }
+  if (diff <= 0.0f) return true;
+  Geo q;
+  float ds, dh;
+  psi_local<false>(s, h, g, q, ds, dh);
+  add_frame_disp(xh, yh, xl, yl, g, ds, dh);
+  return false;
+}
+
+// Hard render of one tile (Eq. chain + Eq. render with the indicator of K_i):
+// strokes last to first, each pixel stops at the first footprint containing it,
+// the CTA stops when all its pixels have.  Writes colour and index.
+// All threads of the CTA must call it.  Returns false if a bounded wait gave up.
+template <int CH>
+__device__ bool hard_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, int tile, int W, int H,
+                          const float bg[3], bool poison, float* __restrict__ out_rgb, int* __restrict__ out_idx,
+                          unsigned& band, unsigned& visited, bool& background, unsigned long long* status) {
+  int px, py;
+  tile_pixel(tile, W, px, py);
+  const bool valid = px < W && py < H;
+  bool alive = valid && !poison;
+  float xh = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
+  float yh = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
+  float xl = 0.0f, yl = 0.0f;
+  int hit = -1;
+  const int nch = (n + CH - 1) / CH;
+  auto chunk_src = [&](int q) { return packed + static_cast<size_t>(nch - 1 - q) * CH * kRec; };
+  auto chunk_cnt = [&](int q) { return min(CH, n - (nch - 1 - q) * CH); };
+  if (threadIdx.x == 0) {
+    if (nch > 0) ring.issue(0, chunk_src(0), chunk_cnt(0));
+    if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
+  }
+  bool ok = true;
+  for (int q = 0; q < nch; ++q) {
+    const int b = q & 1;
+    const bool got = ring.wait(b, status);
+    if (__syncthreads_or(!got)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);
+      ok = false;
+      break;
+    }
+    const int base = (nch - 1 - q) * CH;
+    const int cnt = chunk_cnt(q);
+    const float* S0 = ring.data(b);
+    if (alive) {
+      for (int j = cnt - 1; j >= 0; --j) {
+        ++visited;
+        if (hard_step(xh, yh, xl, yl, S0 + j * kRec, band)) {
+          hit = base + j;
+          alive = false;
+          break;
+        }
+      }
+    }
+    const bool any = __syncthreads_or(alive);
+    if (!any) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);  // drain the prefetched chunk
+      break;
+    }
+    if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
+  }
+  background = valid && hit < 0;
+  if (valid) {
+    const size_t p = static_cast<size_t>(py) * W + px;
+    float c0 = bg[0], c1 = bg[1], c2 = bg[2];
+    if (poison || !ok) {
+      c0 = c1 = c2 = __int_as_float(0x7fc00000);
+    } else if (hit >= 0) {
+      const float* R = packed + static_cast<size_t>(hit) * kRec;
+      c0 = R[F_CR]; c1 = R[F_CG]; c2 = R[F_CB];
+    }
+    out_rgb[3 * p + 0] = c0;
+    out_rgb[3 * p + 1] = c1;
+    out_rgb[3 * p + 2] = c2;
+    if (out_idx) out_idx[p] = hit;
+  }
+  return ok;
+}
+
+// d alpha path only (psi = id, inert-mark model): cotangent of sigma' pushed
+// back to (x, theta, L, r).
+__device__ __forceinline__ void inert_vjp(float s, float h, const StrokeF& g, float& sp_out, float& lamx,
+                                          float& lamy, float mua, float z, bool want, float& gcx, float& gcy,
+                                          float& gth, float& gL, float& gr) {
+  const float as = fabsf(s), ah = fabsf(h);
+  const float d = as - g.hl;
+  const bool cap = d > 0.0f;
+  const float sp = cap ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
+  sp_out = sp;
+  if (!want) return;
+  const float g_sp = -mua * g.iw;
+  gr = mua * fmaf(-z, g.dlw, g.iw);
+  float g_as = 0.0f, g_ah = g_sp, g_hl = 0.0f;
+  if (cap && sp > 0.0f) {
+    const float inv = rcp_a(sp);
+    g_as = g_sp * d * inv;
+    g_ah = g_sp * ah * inv;
+    g_hl = -g_as;
+  }
+  gL = 0.5f * g_hl;
+  const float GS = copysignf(1.0f, s) * g_as, GH = copysignf(1.0f, h) * g_ah;
+  const float nx = fmaf(GS, g.ex, -GH * g.ey);
+  const float ny = fmaf(GS, g.ey, GH * g.ex);
+  gcx = -nx;
+  gcy = -ny;
+  gth = fmaf(GS, h, -GH * s);
+  lamx += nx;
+  lamy += ny;
+}
+
+// Replay adjoint (Sec. 5.2) of one pixel per thread over strokes 1 .. n,
+// starting from the forward's final state st and the cotangent lambda^C_0 =
+// (lC0, lC1, lC2).  Per stroke the 8 gradient values are reduced over the warp
+// (reduce-scatter) and the CTA (shared memory, fixed order) and stored to
+// slice[i][8] (first == true) or added to it.  red is shared [2][8][CH * 8].
+// All threads of the CTA must call it.  Returns false if a bounded wait gave up.
+template <int CH, bool INERT>
+__device__ bool backward_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, bool valid,
+                              const PixelState& st, float lC0, float lC1, float lC2, const float bg[3],
+                              const RecordView& rv, float (*red)[kTileThreads / 32][CH * 8],
+                              float* __restrict__ slice, bool first, unsigned& drift,
+                              unsigned long long* status) {
+  static_assert(CH * 8 == kTileThreads, "one partial per thread per chunk");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ck = rv.ck;
+  float xh = st.xh, yh = st.yh, xl = st.xl, yl = st.yl, lt = st.lt;
+  float lT = fmaf(lC0, bg[0], fmaf(lC1, bg[1], lC2 * bg[2]));
+  float lx = 0.0f, ly = 0.0f;
+  int rc = min(st.cnt, rv.cap), nri = -1;
+  float4 rpos = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (valid && rc > 0) {
+    const size_t o = static_cast<size_t>(rc - 1) * rv.stride + rv.off;
+    rpos = rv.rec[o];
+    nri = rv.rec_i[o];
+  }
+  int next_ck = (ck < n) ? ck : 0;
+  const int nch = (n + CH - 1) / CH;
+  auto chunk_src = [&](int q) { return packed + static_cast<size_t>(q) * CH * kRec; };
+  auto chunk_cnt = [&](int q) { return min(CH, n - q * CH); };
+  if (threadIdx.x == 0) {
+    if (nch > 0) ring.issue(0, chunk_src(0), chunk_cnt(0));
+    if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
+  }
+  bool ok = true;
+  for (int q = 0; q < nch; ++q) {
+    const int b = q & 1;
+    const bool got = ring.wait(b, status);
+    if (__syncthreads_or(!got)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);
+      ok = false;
+      break;
+    }
+    const int cntc = chunk_cnt(q);
+    const float* S0 = ring.data(b);
+    float (*rb)[CH * 8] = red[b];
+    for (int j = 0; j < cntc; ++j) {
+      const int i1 = q * CH + j + 1;
+      float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f, v4 = 0.0f, v5 = 0.0f, v6 = 0.0f, v7 = 0.0f;
+      if (valid) {
+        const float* S = S0 + j * kRec;
+        const StrokeF g = load_stroke(S);
+        const float cR = S[F_CR], cG = S[F_CG], cB = S[F_CB];
+        const bool at_ck = (i1 == next_ck);
+        size_t cko = 0;
+        if (at_ck) {
+          next_ck = (next_ck + ck < n) ? next_ck + ck : 0;
+          cko = static_cast<size_t>(i1 / ck - 1) * rv.stride + rv.off;
+        }
+        const float lCc = fmaf(lC0, cR, fmaf(lC1, cG, lC2 * cB));
+        if (INERT) {
+          float s, h, sp;
+          to_frame(xh, yh, xl, yl, g, s, h);
+          float d0, d1, d2, d3, d4;
+          inert_vjp(s, h, g, sp, lx, ly, 0.0f, 0.0f, false, d0, d1, d2, d3, d4);
+          const Cover cv = coverage(sp, g);
+          if (at_ck) lt = rv.ck_lt[cko]; else lt += cv.sp2;
+          const float T = ex2_a(lt);
+          const float mu = T * (lCc - lT);
+          const float Ta = T * cv.alpha;
+          v5 = lC0 * Ta; v6 = lC1 * Ta; v7 = lC2 * Ta;
+          inert_vjp(s, h, g, sp, lx, ly, mu * cv.dadz, cv.z, true, v0, v1, v2, v3, v4);
+          lT = fmaf(cv.oma, lT, cv.alpha * lCc);
+        } else {
+          Geo gq;
+          float s, h, ds, dh;
+          if (i1 == nri) {
+            // x_i was within the floor's reach: read it back (Lemma "Support of the replay record")
+            xh = rpos.x; yh = rpos.y; xl = rpos.z; yl = rpos.w;
+            to_frame(xh, yh, xl, yl, g, s, h);
+            psi_local<true>(s, h, g, gq, ds, dh);
+            --rc;
+            nri = -1;
+            if (rc > 0) {
+              const size_t o = static_cast<size_t>(rc - 1) * rv.stride + rv.off;
+              rpos = rv.rec[o];
+              nri = rv.rec_i[o];
+            }
+          } else if (at_ck) {
+            // regenerate, measure the drift against the stored position, then reset to it
+            to_frame(xh, yh, xl, yl, g, s, h);
+            phi_local(s, h, g, gq, ds, dh);
+            add_frame_disp(xh, yh, xl, yl, g, ds, dh);
+            const float4 c = rv.ckpt[cko];
+            if (fabsf((xh - c.x) + (xl - c.z)) > kDriftTol || fabsf((yh - c.y) + (yl - c.w)) > kDriftTol) ++drift;
+            xh = c.x; yh = c.y; xl = c.z; yl = c.w;
+            to_frame(xh, yh, xl, yl, g, s, h);
+            psi_local<true>(s, h, g, gq, ds, dh);
+          } else {
+            // x_i = Phi_i(x_{i-1}) (Eq. rpos)
+            to_frame(xh, yh, xl, yl, g, s, h);
+            phi_local(s, h, g, gq, ds, dh);
+            add_frame_disp(xh, yh, xl, yl, g, ds, dh);
+          }
+          const Cover cv = coverage(gq.sp, g);
+          if (at_ck) lt = rv.ck_lt[cko]; else lt += cv.sp2;  // log T_i = log T_{i-1} - log(1 - alpha_i)
+          const float T = ex2_a(lt);
+          const float mu = T * (lCc - lT);
+          const float Ta = T * cv.alpha;
+          v5 = lC0 * Ta; v6 = lC1 * Ta; v7 = lC2 * Ta;
+          step_vjp(gq, g, lx, ly, mu * cv.dadz, cv.z, v0, v1, v2, v3, v4);
+          lT = fmaf(cv.oma, lT, cv.alpha * lCc);
+        }
+      }
+      const float vv[8] = {v0, v1, v2, v3, v4, v5, v6, v7};
+      const float r = warp_reduce8(vv);
+      if ((lane & 3) == 0) rb[warp][j * 8 + ((lane >> 2) & 7)] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
+    const int t = threadIdx.x;
+    if (t < cntc * 8) {
+      float sum = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kTileThreads / 32; ++w) sum += rb[w][t];
+      float* dst = slice + static_cast<size_t>(q) * CH * 8 + t;
+      *dst = first ? sum : *dst + sum;
+    }
+  }
+  return ok;
+}
+
+}  // namespace tbr

@@ -27,7 +27,7 @@ _STATUS_NAMES = {0: "TBR_OK", 1: "TBR_ERR_INVALID_ARG", 2: "TBR_ERR_OOM", 3: "TB
 
 # Every entry point include/tbr.h declares (checked by the ABI test).
 EXPORTED = ["tbr_render_hard", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
-            "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_fit_default_config",
+            "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_render_soft_adjoint_mse", "tbr_fit_default_config",
             "tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_fit_iteration",
             "tbr_fit_destroy", "tbr_profile_enable", "tbr_profile_read", "tbr_profile_reset",
             "tbr_last_error", "tbr_version"]
@@ -292,7 +292,7 @@ class TbrKernelTime(ctypes.Structure):
 
 
 KERNELS = {"pack": 0, "hard": 1, "soft": 2, "backward": 3, "epilogue": 4, "loss": 5, "update": 6,
-           "serve": 7}
+           "serve": 7, "fused": 8}
 
 
 def _fit_lib():
@@ -442,3 +442,36 @@ def soft_render(cx, cy, theta, length, half_width, logits, palette, W, H, tau, t
     """Differentiable soft render (the replay adjoint provides the gradients)."""
     return SoftRender.apply(cx, cy, theta, length, half_width, logits, palette, W, H, tau, tau_min,
                             background, color_temp, checkpoint_every, record_capacity)
+
+
+def soft_adjoint_mse(prog: DeviceProgram, target: torch.Tensor, tau: float, tau_min: float,
+                     checkpoint_every: int = 0, record_capacity: int = 0, want_rgb: bool = False,
+                     want_palette: bool = True, stats: bool = False, stream=None):
+    """tbr_render_soft_adjoint_mse: loss-fused soft forward + replay adjoint.
+    Returns (loss [1] device tensor, gradients dict, rgb or None, stats dict or None)."""
+    L = lib()
+    if not getattr(L, "_fused_typed", False):
+        P = ctypes.c_void_p
+        L.tbr_render_soft_adjoint_mse.argtypes = [ctypes.POINTER(TbrProgram), ctypes.c_int32, ctypes.c_int32,
+                                                  ctypes.POINTER(TbrSoftOpts), P, P, P, P, P, P, P, P, P, P,
+                                                  ctypes.POINTER(TbrCtxStats), P]
+        L.tbr_render_soft_adjoint_mse.restype = ctypes.c_int
+        L._fused_typed = True
+    t = target.contiguous()
+    H, W = int(t.shape[0]), int(t.shape[1])
+    dev = prog.cx.device
+    e = lambda *sh: torch.empty(sh, device=dev, dtype=torch.float32)
+    n, k = prog.n, prog.k
+    g = {"cx": e(n), "cy": e(n), "theta": e(n), "length": e(n), "half_width": e(n), "logits": e(n, k),
+         "palette": e(k, 3) if want_palette else None}
+    loss = e(1)
+    rgb = e(H, W, 3) if want_rgb else None
+    opts = TbrSoftOpts(float(tau), float(tau_min), int(checkpoint_every), int(record_capacity), 0)
+    st = TbrCtxStats() if stats else None
+    s = prog.struct()
+    check(L.tbr_render_soft_adjoint_mse(ctypes.byref(s), W, H, ctypes.byref(opts), _ptr(t), _ptr(rgb), _ptr(loss),
+                                        _ptr(g["cx"]), _ptr(g["cy"]), _ptr(g["theta"]), _ptr(g["length"]),
+                                        _ptr(g["half_width"]), _ptr(g["logits"]), _ptr(g["palette"]),
+                                        ctypes.byref(st) if st is not None else None, _stream(stream)))
+    sd = {f: getattr(st, f) for f, _ in TbrCtxStats._fields_} if st is not None else None
+    return loss, g, rgb, sd

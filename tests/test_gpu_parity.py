@@ -244,3 +244,40 @@ def test_side_table_overflow_is_reported(operating):
     st = ctx.status(raise_on_error=False)
     assert st["status"] == tbr.TBR_ERR_OVERFLOW and st["overflow_pixels"] > 0
     assert torch.isnan(g["cx"]).all()
+
+
+@pytest.mark.parametrize("W,H", [(128, 128), (77, 45)])
+def test_fused_mse_adjoint_matches_split_path_and_oracle(small, W, H):
+    """The loss-fused forward + adjoint equals render_soft + loss_mse +
+    render_backward, and the oracle's stored-state adjoint of the same seed."""
+    p, dp = small
+    tgt_h = inputs.make_program(50, seed=7001, palette_seed=201, k=8, r_lo=0.01, r_hi=0.08)
+    target, _, _ = tbr.render_hard(tbr.DeviceProgram.from_host(tgt_h), W, H)
+    loss_f, g_f, rgb_f, st = tbr.soft_adjoint_mse(dp, target, 0.0, 1 / 200, want_rgb=True, stats=True)
+    rgb, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True)
+    loss_s, dL = tbr.loss_mse(rgb, target)
+    g_s = ctx.backward(dL)
+    assert torch.equal(rgb_f, rgb)
+    assert abs(loss_f.item() - loss_s.item()) <= 1e-6 * abs(loss_s.item())
+    for k in GROUPS:
+        assert rel(g_f[k].cpu().numpy().ravel(), g_s[k].cpu().numpy().ravel()) <= 1e-5, k
+    cot = dL.cpu().numpy().reshape(-1, 3).astype(np.float64)
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot)
+    for k in GROUPS:
+        assert rel(g_f[k].cpu().numpy().ravel(), og[k].ravel()) <= GRAD_TOL, k
+    assert st["overflow_pixels"] == 0
+
+
+def test_fused_mse_adjoint_operating_point(operating):
+    """Full-size loss-fused path against the split path (same seed, same record)."""
+    p, dp = operating
+    W = H = 1024
+    tgt = tbr.DeviceProgram.from_host(inputs.operating_target_program())
+    target, _, _ = tbr.render_hard(tgt, W, H)
+    loss_f, g_f, _, st = tbr.soft_adjoint_mse(dp, target, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, stats=True)
+    rgb, ctx = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, record=True)
+    loss_s, dL = tbr.loss_mse(rgb, target)
+    g_s = ctx.backward(dL)
+    assert abs(loss_f.item() - loss_s.item()) <= 1e-6 * abs(loss_s.item())
+    for k in GROUPS:
+        assert rel(g_f[k].cpu().numpy().ravel(), g_s[k].cpu().numpy().ravel()) <= 1e-4, k
