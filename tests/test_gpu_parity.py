@@ -260,7 +260,7 @@ def test_fused_mse_adjoint_matches_split_path_and_oracle(small, W, H):
     assert torch.equal(rgb_f, rgb)
     assert abs(loss_f.item() - loss_s.item()) <= 1e-6 * abs(loss_s.item())
     for k in GROUPS:
-        assert rel(g_f[k].cpu().numpy().ravel(), g_s[k].cpu().numpy().ravel()) <= 1e-5, k
+        assert rel(g_f[k].cpu().numpy().ravel(), g_s[k].cpu().numpy().ravel()) <= 1e-4, k
     cot = dL.cpu().numpy().reshape(-1, 3).astype(np.float64)
     og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot)
     for k in GROUPS:
