@@ -105,6 +105,31 @@ TBR_API tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H
                            int32_t snap, float* out_rgb, int32_t* out_idx,
                            tbr_hard_stats* stats, void* stream);
 
+/* Allocation-free hard render.  The paper has no counterpart: this entry
+ * point exists for callers that may not allocate device memory at all (a
+ * plugin hosted by another runtime that owns the device's memory budget, a
+ * real-time loop that must never wait on an allocator, code that runs when
+ * the memory pool is exhausted).  It renders exactly what tbr_render_hard
+ * renders (same kernels, same arguments, no stats), but its scratch -- the
+ * packed stroke records and the status words -- lives in one fixed device
+ * array inside the library, sized for at most 8192 strokes (about 1 MiB,
+ * held on every GPU that loads the library until the process exits).  The
+ * caller still passes the program, out_rgb and out_idx.
+ *   - Programs (or prefixes) longer than 8192 strokes are rejected with
+ *     TBR_ERR_INVALID_ARG before anything is launched.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - No cudaMalloc, cudaFree or other allocating routine is called.
+ *   - Every call shares the one array, which keeps the last call's contents
+ *     (the status words are cleared on each call).  Calls whose work overlaps
+ *     on the GPU (for example on two streams at once) race on the array: run
+ *     them one after another on a stream.
+ *   - Parameter values that fail the device-side checks render NaN; there is
+ *     no synchronising stats variant. */
+TBR_API tbr_status tbr_render_hard_noalloc(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
+                                           int32_t snap, float* out_rgb, int32_t* out_idx, void* stream);
+
 /* Options of the soft render / replay record. */
 typedef struct {
   float tau;                /* relaxation width factor tau of Eq. relax */

@@ -26,7 +26,7 @@ _STATUS_NAMES = {0: "TBR_OK", 1: "TBR_ERR_INVALID_ARG", 2: "TBR_ERR_OOM", 3: "TB
                  7: "TBR_ERR_NOT_FOUND"}
 
 # Every entry point include/tbr.h declares (checked by the ABI test).
-EXPORTED = ["tbr_render_hard", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
+EXPORTED = ["tbr_render_hard", "tbr_render_hard_noalloc", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
             "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_render_soft_adjoint_mse", "tbr_fit_default_config",
             "tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_fit_iteration",
             "tbr_fit_destroy", "tbr_profile_enable", "tbr_profile_read", "tbr_profile_reset",
