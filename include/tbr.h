@@ -278,6 +278,86 @@ TBR_API int32_t tbr_fit_iteration(const tbr_fit* fit);
 TBR_API void tbr_fit_destroy(tbr_fit* fit);
 
 /* ------------------------------------------------------------------------
+ * Serving (continuous batching).  Programs are loaded once and stay resident
+ * on the device.  Requests -- hard re-renders, soft render + adjoint against a
+ * target, and edit re-renders (recolour, reorder, stroke insert; Sec. 7
+ * "program edits", prefix replay via n_prefix) -- are admitted in arrival order
+ * as request slots and the memory cap allow, and their work (32x8 hard tiles,
+ * or groups of soft tiles fused with the MSE seed and the replay adjoint) is
+ * claimed item by item by one persistent kernel, so requests that arrive while
+ * others run are batched into the same launch.  Each result is bitwise the same
+ * whether the request runs alone or in a mix (per-tile / per-group reductions
+ * in a fixed order).  A library worker thread does admission and completion;
+ * the persistent kernel exits after idle_exit_us without work and is relaunched
+ * when work arrives.  Output buffers are caller-owned device memory and must
+ * stay valid until the request is done.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  size_t memory_cap_bytes;   /* admission cap on request working memory (80 GiB) */
+  int32_t max_inflight;      /* admitted requests at a time (64, at most 1024) */
+  int32_t max_strokes;       /* largest program + 1 (8192); sizes the per-CTA record */
+  int32_t checkpoint_every;  /* soft requests: checkpoint interval (64) */
+  int32_t record_capacity;   /* soft requests: side-table records per pixel (64) */
+  int32_t idle_exit_us;      /* persistent kernel idle exit (2000 us) */
+} tbr_serve_config;
+
+enum {
+  TBR_REQ_HARD = 0,          /* hard render (n_prefix, snap apply) */
+  TBR_REQ_SOFT_ADJOINT = 1,  /* soft render + MSE vs target + replay adjoint */
+  TBR_REQ_RECOLOUR = 2,      /* swap palette entries edit_a, edit_b for strokes >= edit_start, hard render */
+  TBR_REQ_REORDER = 3,       /* reverse strokes [edit_start, edit_start + edit_b), hard render */
+  TBR_REQ_INSERT = 4         /* insert insert_stroke before index edit_start, hard render */
+};
+
+typedef struct {
+  int32_t kind;              /* TBR_REQ_* */
+  uint64_t program;          /* id from tbr_serve_load_program */
+  int32_t W, H;
+  int32_t n_prefix;          /* reserved (use -1) */
+  int32_t snap;              /* hard kinds: palette snapping */
+  float tau, tau_min;        /* soft: relaxation (Eq. relax) */
+  const float* target;       /* soft: [H][W][3] */
+  float* out_rgb;            /* [H][W][3] (soft: optional) */
+  int32_t* out_idx;          /* hard kinds: [H][W] or NULL */
+  float* out_loss;           /* soft: device scalar (MSE) or NULL */
+  float* out_grad;           /* soft: [5n + n k]: cx, cy, theta, length, half_width (n each), logits */
+  int32_t edit_a, edit_b;    /* recolour: palette entries; reorder: edit_b = window length */
+  int32_t edit_start;        /* first stroke affected / insertion index */
+  int32_t insert_palette;    /* insert: palette entry of the new stroke (logits 6 * onehot) */
+  float insert_stroke[5];    /* insert: cx, cy, theta, length, half_width */
+} tbr_request;
+
+typedef struct {
+  int64_t admitted, completed, refused, queued, inflight, kernel_launches;
+  int64_t bytes_in_use;      /* request working memory in use */
+  int64_t fixed_bytes;       /* per-CTA replay scratch held by the server */
+  int32_t persistent_ctas;
+} tbr_serve_counters;
+
+typedef struct tbr_server tbr_server;
+
+TBR_API void tbr_serve_default_config(tbr_serve_config* cfg);
+/* Creates a server on the current device (cfg may be NULL for the defaults). */
+TBR_API tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** server);
+/* Copies a program into server memory (synchronous); *id names it in requests. */
+TBR_API tbr_status tbr_serve_load_program(tbr_server* server, const tbr_program* prog, uint64_t* id);
+/* Queues a request; returns at once.  TBR_ERR_ADMISSION if it could never fit the cap. */
+TBR_API tbr_status tbr_serve_submit(tbr_server* server, const tbr_request* req, uint64_t* req_id);
+/* *done = 1 once the request's outputs are written; *result is its status. */
+TBR_API tbr_status tbr_serve_poll(tbr_server* server, uint64_t req_id, int32_t* done, tbr_status* result);
+/* Blocks until the request is done (timeout_ms < 0: no limit). */
+TBR_API tbr_status tbr_serve_wait(tbr_server* server, uint64_t req_id, int32_t timeout_ms, tbr_status* result);
+/* Host-clock times of a finished request: queueing (submit to admission) and
+ * latency (submit to completion), in milliseconds. */
+TBR_API tbr_status tbr_serve_request_times(tbr_server* server, uint64_t req_id, double* queue_ms,
+                                           double* latency_ms);
+/* Forgets a finished request. */
+TBR_API tbr_status tbr_serve_release(tbr_server* server, uint64_t req_id);
+TBR_API tbr_status tbr_serve_stats(tbr_server* server, tbr_serve_counters* stats);
+/* Stops the worker and the persistent kernel and frees everything. */
+TBR_API void tbr_serve_destroy(tbr_server* server);
+
+/* ------------------------------------------------------------------------
  * Per-kernel timing without a profiler: while enabled, each launch of the
  * library's kernels is bracketed by CUDA events on its launch stream.
  * tbr_profile_read synchronises the pending events and returns the launch

@@ -1,0 +1,232 @@
+// Persistent serving kernel (continuous batching of hard renders, edits and
+// soft render + adjoint requests).  The host publishes request descriptors into
+// a ring in mapped pinned memory and advances a published-item counter; each
+// CTA claims the next item with a compare-and-swap on a device counter, runs it
+// (a 32x8 hard tile, or a group of soft tiles fused with the MSE seed and the
+// replay adjoint), and the CTA that finishes a request's last item finalises
+// it (gradient sums in a fixed order) and signals completion through mapped
+// memory.  Every wait is bounded; the kernel exits after idle_ns without work
+// and the host relaunches it when new work is published.
+#include "tbr_serve.h"
+#include "tbr_tile.cuh"
+
+namespace tbr {
+
+namespace {
+
+constexpr int kServeCH = 32;
+
+__device__ __forceinline__ long long ld_volatile_ll(const volatile long long* p) { return *p; }
+
+// dL/dPal and the colour chain rule, written by one CTA (Sec. 5.1 colour parameterisation).
+__device__ void finalize_soft(const ServeDesc& d) {
+  const int n = d.n, k = d.k, G = d.n_items;
+  const bool bad = d.status[ST_INVALID] != 0ull || d.status[ST_OVERFLOW] != 0ull ||
+                   d.status[ST_TIMEOUT] != 0ull;
+  const float nan = __int_as_float(0x7fc00000);
+  // fixed-order FP64 sum over the group slices
+  for (int t = threadIdx.x; t < n * 8; t += blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += static_cast<double>(d.partial[static_cast<size_t>(g) * n * 8 + t]);
+    d.grad8[t] = static_cast<float>(s);
+  }
+  __syncthreads();
+  __threadfence_block();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const float* g8 = d.grad8 + static_cast<size_t>(i) * 8;
+    for (int c = 0; c < 5; ++c) d.out_grad[static_cast<size_t>(c) * n + i] = bad ? nan : g8[c];
+    const float* R = d.packed + static_cast<size_t>(i) * kRec;
+    const float c0 = R[F_CR], c1 = R[F_CG], c2 = R[F_CB];
+    for (int q = 0; q < k; ++q) {
+      const float* pal = d.palette + 3 * q;
+      const float dd = fmaf(pal[0] - c0, g8[5], fmaf(pal[1] - c1, g8[6], (pal[2] - c2) * g8[7]));
+      d.out_grad[5 * static_cast<size_t>(n) + static_cast<size_t>(i) * k + q] =
+          bad ? nan : d.probs[static_cast<size_t>(i) * k + q] * dd * d.inv_tc;
+    }
+  }
+  if (threadIdx.x == 0 && d.out_loss) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += d.loss_part[g];
+    *d.out_loss = bad ? nan : static_cast<float>(s / (3.0 * static_cast<double>(d.W) * d.H));
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
+  __shared__ __align__(128) float sbuf[2 * kServeCH * kRec];
+  __shared__ __align__(8) uint64_t sbar[2];
+  __shared__ float red[2][kTileThreads / 32][kServeCH * 8];
+  __shared__ double lsum[kTileThreads / 32];
+  __shared__ ServeDesc sd;
+  __shared__ long long s_item;
+  __shared__ long long s_cursor;
+  __shared__ int s_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  ChunkRing<kServeCH> ring;
+  ring.init(sbuf, sbar);
+  if (threadIdx.x == 0) s_cursor = a.first_seq;
+  const size_t cta = blockIdx.x;
+  while (true) {
+    // ---- claim the next published item (thread 0), bounded by the idle timeout
+    if (threadIdx.x == 0) {
+      long long got = -1;
+      uint64_t idle0 = global_timer_ns();
+      for (uint32_t it = 0;; ++it) {
+        if (a.ctl->stop) break;
+        const long long pub = ld_volatile_ll(&a.ctl->published);
+        const long long cur = atomicAdd(reinterpret_cast<unsigned long long*>(a.next_item), 0ull);
+        if (cur < pub) {
+          if (static_cast<long long>(atomicCAS(reinterpret_cast<unsigned long long*>(a.next_item),
+                                               static_cast<unsigned long long>(cur),
+                                               static_cast<unsigned long long>(cur + 1))) == cur) {
+            got = cur;
+            break;
+          }
+          continue;
+        }
+        if ((it & 63u) == 63u && global_timer_ns() - idle0 > a.idle_ns) break;
+        __nanosleep(2000);
+      }
+      s_item = got;
+      if (got >= 0) {
+        // locate the request: items are published contiguously in request order;
+        // an entry whose seq differs from the cursor was recycled (its request is done)
+        long long c = s_cursor;
+        for (int guard = 0; guard < 4 * kServeRing; ++guard) {
+          const volatile ServeDesc* vd = &a.ring[c % kServeRing];
+          const long long s1 = vd->seq;
+          const long long base = vd->item_base;
+          const int cnt = vd->n_items;
+          __threadfence_system();
+          const long long s2 = vd->seq;
+          if (s1 == c && s2 == c && got < base + cnt) break;
+          ++c;
+        }
+        s_cursor = c;
+        const volatile unsigned int* src = reinterpret_cast<const volatile unsigned int*>(&a.ring[c % kServeRing]);
+        unsigned int* dst = reinterpret_cast<unsigned int*>(&sd);
+        for (size_t w = 0; w < sizeof(ServeDesc) / 4; ++w) dst[w] = src[w];
+        __threadfence();
+      }
+    }
+    __syncthreads();
+    const long long item = s_item;
+    if (item < 0) break;
+    const ServeDesc& d = sd;
+    const long long local = item - d.item_base;
+    bool ok = true;
+    if (d.kind == kServeHard) {
+      const bool poison = d.status[ST_INVALID] != 0ull;
+      unsigned band = 0, visited = 0;
+      bool background = false;
+      ok = hard_tile<kServeCH>(ring, d.packed, d.n, static_cast<int>(local), d.W, d.H, d.bg, poison, d.out_rgb,
+                               d.out_idx, band, visited, background, d.status);
+    } else {
+      // soft render + MSE seed + replay adjoint over tiles local, local + G, ...
+      const int ntiles = ((d.W + kTileW - 1) / kTileW) * ((d.H + kTileH - 1) / kTileH);
+      const size_t nck = d.n > 1 ? static_cast<size_t>((d.n - 1) / d.ck) : 0;
+      RecordView rv{a.rec + cta * a.cap * kTileThreads, a.rec_i + cta * a.cap * kTileThreads,
+                    a.ckpt + cta * a.nck_max * kTileThreads, a.ck_lt + cta * a.nck_max * kTileThreads,
+                    static_cast<size_t>(kTileThreads), static_cast<size_t>(threadIdx.x), d.cap, d.ck};
+      (void)nck;
+      float* slice = d.partial + static_cast<size_t>(local) * d.n * 8;
+      const bool skip = d.status[ST_INVALID] != 0ull;
+      double lacc = 0.0;
+      unsigned drift = 0, ovf = 0;
+      bool first = true;
+      for (int tile = static_cast<int>(local); tile < ntiles; tile += d.n_items) {
+        int px, py;
+        tile_pixel(tile, d.W, px, py);
+        const bool valid = px < d.W && py < d.H && !skip;
+        const size_t p = valid ? static_cast<size_t>(py) * d.W + px : 0;
+        PixelState st;
+        if (!soft_forward_tile<kServeCH, true, false>(ring, d.packed, d.n, valid,
+                                                      (static_cast<float>(px) + 0.5f) / static_cast<float>(d.W),
+                                                      (static_cast<float>(py) + 0.5f) / static_cast<float>(d.H),
+                                                      rv, st, d.status)) {
+          ok = false;
+          break;
+        }
+        float lC0 = 0.0f, lC1 = 0.0f, lC2 = 0.0f;
+        if (valid) {
+          const float T0 = ex2_a(st.lt);
+          const float R0 = fmaf(T0, d.bg[0], st.C0), R1 = fmaf(T0, d.bg[1], st.C1),
+                      R2 = fmaf(T0, d.bg[2], st.C2);
+          if (d.out_rgb) {
+            d.out_rgb[3 * p + 0] = R0;
+            d.out_rgb[3 * p + 1] = R1;
+            d.out_rgb[3 * p + 2] = R2;
+          }
+          const float e0 = R0 - d.target[3 * p + 0], e1 = R1 - d.target[3 * p + 1], e2 = R2 - d.target[3 * p + 2];
+          lacc += static_cast<double>(e0) * e0 + static_cast<double>(e1) * e1 + static_cast<double>(e2) * e2;
+          lC0 = d.seed_scale * e0; lC1 = d.seed_scale * e1; lC2 = d.seed_scale * e2;
+          if (st.cnt > d.cap) ++ovf;
+        }
+        if (!backward_tile<kServeCH, false>(ring, d.packed, d.n, valid, st, lC0, lC1, lC2, d.bg, rv, red, slice,
+                                            first, drift, d.status)) {
+          ok = false;
+          break;
+        }
+        first = false;
+      }
+      if (first && ok) {  // a group with no tile (cannot happen: n_items <= ntiles) keeps a zero slice
+        for (int t = threadIdx.x; t < d.n * 8; t += blockDim.x) slice[t] = 0.0f;
+      }
+      for (int o = 16; o > 0; o >>= 1) lacc += __shfl_xor_sync(0xffffffffu, lacc, o);
+      if (lane == 0) lsum[warp] = lacc;
+      const unsigned osum = __reduce_add_sync(0xffffffffu, ovf);
+      if (lane == 0 && osum) atomicAdd(d.status + ST_OVERFLOW, static_cast<unsigned long long>(osum));
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kTileThreads / 32; ++w) s += lsum[w];
+        d.loss_part[local] = s;
+      }
+    }
+    (void)ok;  // a failing bounded wait has already set the request's timeout word
+    // ---- completion
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const int done = atomicAdd(a.items_done + d.slot, 1) + 1;
+      s_last = (done == d.n_items) ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      if (d.kind == kServeSoft) finalize_soft(d);
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        a.items_done[d.slot] = 0;  // the slot is reused by a later request
+        __threadfence_system();
+        a.ctl->done[d.slot] = d.seq;
+        __threadfence_system();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int serve_grid() {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, kTileThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    // leave one CTA per SM free so packing and edit kernels of new requests can run alongside
+    if (per_sm > 1) per_sm -= 1;
+  }
+  return per_sm * sms;
+}
+
+cudaError_t launch_serve(const ServeArgs& a, cudaStream_t st) {
+  KernelTimer kt(TBR_K_SERVE, st);
+  k_serve<<<a.grid, kTileThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tbr

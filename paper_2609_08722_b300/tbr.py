@@ -29,7 +29,9 @@ _STATUS_NAMES = {0: "TBR_OK", 1: "TBR_ERR_INVALID_ARG", 2: "TBR_ERR_OOM", 3: "TB
 EXPORTED = ["tbr_render_hard", "tbr_render_hard_noalloc", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
             "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_render_soft_adjoint_mse", "tbr_fit_default_config",
             "tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_fit_iteration",
-            "tbr_fit_destroy", "tbr_profile_enable", "tbr_profile_read", "tbr_profile_reset",
+            "tbr_fit_destroy", "tbr_serve_default_config", "tbr_serve_create", "tbr_serve_load_program",
+            "tbr_serve_submit", "tbr_serve_poll", "tbr_serve_wait", "tbr_serve_request_times",
+            "tbr_serve_release", "tbr_serve_stats", "tbr_serve_destroy", "tbr_profile_enable", "tbr_profile_read", "tbr_profile_reset",
             "tbr_last_error", "tbr_version"]
 
 
@@ -475,3 +477,137 @@ def soft_adjoint_mse(prog: DeviceProgram, target: torch.Tensor, tau: float, tau_
                                         ctypes.byref(st) if st is not None else None, _stream(stream)))
     sd = {f: getattr(st, f) for f, _ in TbrCtxStats._fields_} if st is not None else None
     return loss, g, rgb, sd
+
+
+# ---------------------------------------------------------------------------
+# Serving (tbr_serve_*)
+# ---------------------------------------------------------------------------
+REQ_HARD, REQ_SOFT_ADJOINT, REQ_RECOLOUR, REQ_REORDER, REQ_INSERT = 0, 1, 2, 3, 4
+
+
+class TbrServeConfig(ctypes.Structure):
+    _fields_ = [("memory_cap_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
+                ("max_strokes", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("record_capacity", ctypes.c_int32), ("idle_exit_us", ctypes.c_int32)]
+
+
+class TbrRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("program", ctypes.c_uint64), ("W", ctypes.c_int32),
+                ("H", ctypes.c_int32), ("n_prefix", ctypes.c_int32), ("snap", ctypes.c_int32),
+                ("tau", ctypes.c_float), ("tau_min", ctypes.c_float), ("target", ctypes.c_void_p),
+                ("out_rgb", ctypes.c_void_p), ("out_idx", ctypes.c_void_p), ("out_loss", ctypes.c_void_p),
+                ("out_grad", ctypes.c_void_p), ("edit_a", ctypes.c_int32), ("edit_b", ctypes.c_int32),
+                ("edit_start", ctypes.c_int32), ("insert_palette", ctypes.c_int32),
+                ("insert_stroke", ctypes.c_float * 5)]
+
+
+class TbrServeCounters(ctypes.Structure):
+    _fields_ = [("admitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("refused", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("inflight", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("fixed_bytes", ctypes.c_int64),
+                ("persistent_ctas", ctypes.c_int32)]
+
+
+def _serve_lib():
+    L = lib()
+    if not getattr(L, "_serve_typed", False):
+        P = ctypes.c_void_p
+        L.tbr_serve_default_config.argtypes = [ctypes.POINTER(TbrServeConfig)]
+        L.tbr_serve_default_config.restype = None
+        L.tbr_serve_create.argtypes = [ctypes.POINTER(TbrServeConfig), ctypes.POINTER(P)]
+        L.tbr_serve_load_program.argtypes = [P, ctypes.POINTER(TbrProgram), ctypes.POINTER(ctypes.c_uint64)]
+        L.tbr_serve_submit.argtypes = [P, ctypes.POINTER(TbrRequest), ctypes.POINTER(ctypes.c_uint64)]
+        L.tbr_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]
+        L.tbr_serve_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int)]
+        L.tbr_serve_request_times.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                              ctypes.POINTER(ctypes.c_double)]
+        L.tbr_serve_release.argtypes = [P, ctypes.c_uint64]
+        L.tbr_serve_stats.argtypes = [P, ctypes.POINTER(TbrServeCounters)]
+        L.tbr_serve_destroy.argtypes = [P]
+        L.tbr_serve_destroy.restype = None
+        for f in ("tbr_serve_create", "tbr_serve_load_program", "tbr_serve_submit", "tbr_serve_poll",
+                  "tbr_serve_wait", "tbr_serve_request_times", "tbr_serve_release", "tbr_serve_stats"):
+            getattr(L, f).restype = ctypes.c_int
+        L._serve_typed = True
+    return L
+
+
+def default_serve_config(**overrides) -> TbrServeConfig:
+    c = TbrServeConfig()
+    _serve_lib().tbr_serve_default_config(ctypes.byref(c))
+    for k, v in overrides.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+class Server:
+    """tbr_serve_*: continuous-batching server on the current device."""
+
+    def __init__(self, config: Optional[TbrServeConfig] = None):
+        L = _serve_lib()
+        self.config = config if config is not None else default_serve_config()
+        h = ctypes.c_void_p()
+        check(L.tbr_serve_create(ctypes.byref(self.config), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def load_program(self, prog: DeviceProgram) -> int:
+        pid = ctypes.c_uint64()
+        s = prog.struct()
+        check(_serve_lib().tbr_serve_load_program(ctypes.c_void_p(self.handle), ctypes.byref(s), ctypes.byref(pid)))
+        return int(pid.value)
+
+    def submit(self, kind: int, program: int, W: int, H: int, out_rgb=None, out_idx=None, target=None,
+               out_loss=None, out_grad=None, tau=0.0, tau_min=1.0, snap=False, edit_a=0, edit_b=0,
+               edit_start=0, insert_palette=0, insert_stroke=(0.5, 0.5, 0.0, 0.0, 0.05)) -> int:
+        r = TbrRequest()
+        r.kind, r.program, r.W, r.H, r.n_prefix, r.snap = kind, program, W, H, -1, int(bool(snap))
+        r.tau, r.tau_min = float(tau), float(tau_min)
+        r.target, r.out_rgb, r.out_idx = _ptr(target), _ptr(out_rgb), _ptr(out_idx)
+        r.out_loss, r.out_grad = _ptr(out_loss), _ptr(out_grad)
+        r.edit_a, r.edit_b, r.edit_start, r.insert_palette = edit_a, edit_b, edit_start, insert_palette
+        r.insert_stroke = (ctypes.c_float * 5)(*[float(v) for v in insert_stroke])
+        rid = ctypes.c_uint64()
+        check(_serve_lib().tbr_serve_submit(ctypes.c_void_p(self.handle), ctypes.byref(r), ctypes.byref(rid)))
+        # keep the caller's buffers alive until the request is released
+        self._keep[int(rid.value)] = (target, out_rgb, out_idx, out_loss, out_grad)
+        return int(rid.value)
+
+    def poll(self, rid: int) -> tuple[bool, int]:
+        done, res = ctypes.c_int32(), ctypes.c_int()
+        check(_serve_lib().tbr_serve_poll(ctypes.c_void_p(self.handle), rid, ctypes.byref(done), ctypes.byref(res)))
+        return bool(done.value), int(res.value)
+
+    def wait(self, rid: int, timeout_ms: int = 60000) -> int:
+        res = ctypes.c_int()
+        check(_serve_lib().tbr_serve_wait(ctypes.c_void_p(self.handle), rid, timeout_ms, ctypes.byref(res)))
+        return int(res.value)
+
+    def times(self, rid: int) -> tuple[float, float]:
+        q, l = ctypes.c_double(), ctypes.c_double()
+        check(_serve_lib().tbr_serve_request_times(ctypes.c_void_p(self.handle), rid, ctypes.byref(q),
+                                                   ctypes.byref(l)))
+        return float(q.value), float(l.value)
+
+    def release(self, rid: int) -> None:
+        check(_serve_lib().tbr_serve_release(ctypes.c_void_p(self.handle), rid))
+        self._keep.pop(rid, None)
+
+    def stats(self) -> dict:
+        c = TbrServeCounters()
+        check(_serve_lib().tbr_serve_stats(ctypes.c_void_p(self.handle), ctypes.byref(c)))
+        return {f: getattr(c, f) for f, _ in TbrServeCounters._fields_}
+
+    def destroy(self) -> None:
+        if self.handle is not None:
+            _serve_lib().tbr_serve_destroy(ctypes.c_void_p(self.handle))
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,195 @@
+"""Serving (continuous batching in one persistent kernel): each request's result
+is the same alone and in a mix, equals the plain entry points, edits render the
+edited program, admission respects the memory cap, and the kernel is
+relaunched after it exits idle."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2609_08722_b300 import inputs, tbr
+
+pytestmark = pytest.mark.gpu
+
+GROUPS = ["cx", "cy", "theta", "length", "half_width", "logits"]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def server():
+    s = tbr.Server(tbr.default_serve_config(max_strokes=4096))
+    yield s
+    s.destroy()
+
+
+@pytest.fixture(scope="module")
+def programs():
+    hs = [inputs.make_program(n, seed=3000 + j, palette_seed=77, k=16, r_lo=0.003, r_hi=0.05)
+          for j, n in enumerate((200, 700, 2000))]
+    return hs, [tbr.DeviceProgram.from_host(h) for h in hs]
+
+
+def hard_request(server, pid, W, H):
+    rgb = torch.full((H, W, 3), float("nan"), device="cuda")
+    idx = torch.full((H, W), -7, dtype=torch.int32, device="cuda")
+    rid = server.submit(tbr.REQ_HARD, pid, W, H, out_rgb=rgb, out_idx=idx)
+    return rid, rgb, idx
+
+
+def soft_request(server, pid, n, k, target, tau=0.0, tau_min=1 / 200):
+    H, W = target.shape[0], target.shape[1]
+    grad = torch.full((5 * n + n * k,), float("nan"), device="cuda")
+    loss = torch.full((1,), float("nan"), device="cuda")
+    rgb = torch.empty((H, W, 3), device="cuda")
+    rid = server.submit(tbr.REQ_SOFT_ADJOINT, pid, W, H, out_rgb=rgb, target=target, out_loss=loss,
+                        out_grad=grad, tau=tau, tau_min=tau_min)
+    return rid, rgb, loss, grad
+
+
+def split_grad(g, n, k):
+    return {"cx": g[:n], "cy": g[n:2 * n], "theta": g[2 * n:3 * n], "length": g[3 * n:4 * n],
+            "half_width": g[4 * n:5 * n], "logits": g[5 * n:].view(n, k)}
+
+
+def test_hard_request_equals_plain_hard_render(server, programs):
+    hs, ds = programs
+    for dp, (W, H) in zip(ds, [(256, 256), (333, 97), (512, 512)]):
+        pid = server.load_program(dp)
+        rid, rgb, idx = hard_request(server, pid, W, H)
+        assert server.wait(rid) == tbr.TBR_OK
+        ref_rgb, ref_idx, _ = tbr.render_hard(dp, W, H)
+        torch.cuda.synchronize()
+        assert torch.equal(idx, ref_idx)
+        assert torch.equal(rgb, ref_rgb)
+
+
+def test_soft_request_matches_the_fused_entry_point(server, programs):
+    hs, ds = programs
+    dp = ds[1]
+    W, H = 192, 160
+    target, _, _ = tbr.render_hard(ds[0], W, H)
+    pid = server.load_program(dp)
+    rid, rgb, loss, grad = soft_request(server, pid, dp.n, dp.k, target)
+    assert server.wait(rid) == tbr.TBR_OK
+    loss_f, g_f, rgb_f, _ = tbr.soft_adjoint_mse(dp, target, 0.0, 1 / 200, want_rgb=True)
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, rgb_f)
+    assert abs(loss.item() - loss_f.item()) <= 1e-6 * abs(loss_f.item())
+    g = split_grad(grad, dp.n, dp.k)
+    for k in GROUPS:
+        assert rel(g[k].cpu().numpy().ravel(), g_f[k].cpu().numpy().ravel()) <= 1e-4, k
+
+
+def test_results_are_identical_alone_and_in_a_mix(server, programs):
+    hs, ds = programs
+    pids = [server.load_program(d) for d in ds]
+    W, H = 160, 128
+    target, _, _ = tbr.render_hard(ds[2], W, H)
+    # alone
+    alone = []
+    for j, (pid, d) in enumerate(zip(pids, ds)):
+        rid, rgb, idx = hard_request(server, pid, W + 32 * j, H)
+        server.wait(rid)
+        rs, srgb, sloss, sgrad = soft_request(server, pid, d.n, d.k, target)
+        server.wait(rs)
+        alone.append((rgb.clone(), idx.clone(), sloss.clone(), sgrad.clone()))
+    # mixed: everything submitted at once, interleaved kinds
+    mixed = []
+    rids = []
+    for j, (pid, d) in enumerate(zip(pids, ds)):
+        rid, rgb, idx = hard_request(server, pid, W + 32 * j, H)
+        rs, srgb, sloss, sgrad = soft_request(server, pid, d.n, d.k, target)
+        rids += [rid, rs]
+        mixed.append((rgb, idx, sloss, sgrad))
+    for rid in rids:
+        assert server.wait(rid) == tbr.TBR_OK
+    torch.cuda.synchronize()
+    for a, m in zip(alone, mixed):
+        for x, y in zip(a, m):
+            assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("kind", [tbr.REQ_RECOLOUR, tbr.REQ_REORDER, tbr.REQ_INSERT])
+def test_edit_requests_render_the_edited_program(server, programs, kind):
+    hs, ds = programs
+    h = hs[1]
+    pid = server.load_program(ds[1])
+    W, H = 200, 150
+    n = h.n
+    e = h.copy()
+    args = {}
+    if kind == tbr.REQ_RECOLOUR:
+        a, b, start = 2, 9, 4 * n // 5
+        lg = e.logits.copy()
+        lg[start:, [a, b]] = lg[start:, [b, a]]
+        e.logits = np.ascontiguousarray(lg)
+        args = dict(edit_a=a, edit_b=b, edit_start=start)
+    elif kind == tbr.REQ_REORDER:
+        start, length = 300, 16
+        for name in ("cx", "cy", "theta", "length", "half_width", "logits"):
+            arr = getattr(e, name).copy()
+            arr[start:start + length] = arr[start:start + length][::-1]
+            setattr(e, name, np.ascontiguousarray(arr))
+        args = dict(edit_b=length, edit_start=start)
+    else:
+        at, stroke, pal = n // 2, (0.45, 0.55, 0.0, 0.0, 0.06), 5
+        for name, v in zip(("cx", "cy", "theta", "length", "half_width"), stroke):
+            setattr(e, name, np.ascontiguousarray(np.insert(getattr(e, name), at, np.float32(v))))
+        z = np.zeros((1, h.k), np.float32)
+        z[0, pal] = 6.0
+        e.logits = np.ascontiguousarray(np.insert(e.logits, at, z, axis=0))
+        args = dict(edit_start=at, insert_palette=pal, insert_stroke=stroke)
+    rgb = torch.empty((H, W, 3), device="cuda")
+    idx = torch.empty((H, W), dtype=torch.int32, device="cuda")
+    rid = server.submit(kind, pid, W, H, out_rgb=rgb, out_idx=idx, **args)
+    assert server.wait(rid) == tbr.TBR_OK
+    ref_rgb, ref_idx, _ = tbr.render_hard(tbr.DeviceProgram.from_host(e), W, H)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, ref_idx)
+    assert torch.equal(rgb, ref_rgb)
+    if kind == tbr.REQ_RECOLOUR:
+        # transport ignores pigment: the index map of a recolour edit is the original one
+        _, idx0, _ = tbr.render_hard(ds[1], W, H)
+        assert torch.equal(idx, idx0)
+
+
+def test_admission_respects_the_memory_cap(programs):
+    hs, ds = programs
+    s = tbr.Server(tbr.default_serve_config(memory_cap_bytes=1 << 20, max_strokes=4096))
+    try:
+        pid = s.load_program(ds[2])
+        W, H = 128, 128
+        target, _, _ = tbr.render_hard(ds[0], W, H)
+        with pytest.raises(tbr.TbrError) as ei:      # a 2000-stroke soft request never fits 1 MiB
+            soft_request(s, pid, ds[2].n, ds[2].k, target)
+        assert ei.value.status == tbr.TBR_ERR_ADMISSION
+        outs = [hard_request(s, pid, W, H) for _ in range(6)]   # ~260 KB each: at most a few at a time
+        for rid, _, _ in outs:
+            assert s.wait(rid) == tbr.TBR_OK
+        ref_rgb, ref_idx, _ = tbr.render_hard(ds[2], W, H)
+        torch.cuda.synchronize()
+        for _, rgb, idx in outs:
+            assert torch.equal(idx, ref_idx)
+        st = s.stats()
+        assert st["completed"] == 6 and st["bytes_in_use"] == 0
+    finally:
+        s.destroy()
+
+
+def test_kernel_relaunches_after_idle(server, programs):
+    hs, ds = programs
+    pid = server.load_program(ds[0])
+    before = server.stats()["kernel_launches"]
+    rid, _, _ = hard_request(server, pid, 64, 64)
+    assert server.wait(rid) == tbr.TBR_OK
+    time.sleep(0.05)  # > idle_exit_us: the persistent kernel has exited
+    rid, rgb, idx = hard_request(server, pid, 64, 64)
+    assert server.wait(rid) == tbr.TBR_OK
+    assert server.stats()["kernel_launches"] >= before + 1
+    ref_rgb, ref_idx, _ = tbr.render_hard(ds[0], 64, 64)
+    torch.cuda.synchronize()
+    assert torch.equal(idx, ref_idx)
