@@ -58,6 +58,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=200,
+                    help="requests of the serving stream (0 skips the serving measurement)")
     ap.add_argument("--res", type=int, default=RES, help="square resolution (profiling cases only)")
     ap.add_argument("--strokes", type=int, default=N_STROKES, help="stroke count (profiling cases only)")
     return ap.parse_args()
@@ -398,8 +400,14 @@ def run_native(args):
                "sample": f"{info['pixels']} sampled pixels x {prog_h.n} strokes of the {RES}x{RES} workload "
                          f"(FP64 soft forward + stored-state adjoint, {info['seconds']:.1f} s)"}
 
-    launches_per_step = 5  # pack, soft, backward, grad-sum + colour epilogue (3), loss (2)
-    kernels_per_step = 1 + 1 + 1 + 3 + 2
+    serve = None
+    if rank == 0 and world == 1 and args.serve_requests > 0 and args.res == RES and args.strokes == N_STROKES:
+        from paper_2609_08722_b300 import serve_bench
+        del ctx
+        torch.cuda.empty_cache()
+        serve = serve_bench.run(n_req=args.serve_requests)
+
+    kernels_per_step = 1 + 1 + 1 + 3 + 2  # pack, soft, backward, epilogue (3), loss (2)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -419,6 +427,7 @@ def run_native(args):
                           "other": step_ms - bwd_ms - soft_ms},
             "fit_step_ms": fit_ms,
             "fused_path": fused,
+            "serve": serve,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
