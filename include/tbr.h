@@ -341,8 +341,13 @@ TBR_API void tbr_serve_default_config(tbr_serve_config* cfg);
 TBR_API tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** server);
 /* Copies a program into server memory (synchronous); *id names it in requests. */
 TBR_API tbr_status tbr_serve_load_program(tbr_server* server, const tbr_program* prog, uint64_t* id);
-/* Queues a request; returns at once.  TBR_ERR_ADMISSION if it could never fit the cap. */
-TBR_API tbr_status tbr_serve_submit(tbr_server* server, const tbr_request* req, uint64_t* req_id);
+/* Queues a request; returns at once.  `stream` is the caller's stream on which
+ * the request's inputs (target, and anything written to the output buffers
+ * before) were produced: the request's device work starts after everything
+ * enqueued there so far.  After tbr_serve_wait / tbr_serve_poll report it
+ * done, the outputs are visible to any work launched afterwards.
+ * TBR_ERR_ADMISSION if the request could never fit the memory cap. */
+TBR_API tbr_status tbr_serve_submit(tbr_server* server, const tbr_request* req, uint64_t* req_id, void* stream);
 /* *done = 1 once the request's outputs are written; *result is its status. */
 TBR_API tbr_status tbr_serve_poll(tbr_server* server, uint64_t req_id, int32_t* done, tbr_status* result);
 /* Blocks until the request is done (timeout_ms < 0: no limit). */

@@ -73,7 +73,9 @@ struct Request {
   long long seq = -1;
   int slot = -1;
   size_t bytes = 0;
-  int state = 0;  // 0 queued, 1 admitted, 2 done
+  int state = 0;  // 0 queued, 1 admitted, 2 done, 3 gradient epilogue in flight
+  cudaEvent_t ready = nullptr;     // inputs ready on the caller's stream
+  cudaEvent_t finished = nullptr;  // epilogue done (soft requests)
   tbr_status result = TBR_OK;
   Clock::time_point t_submit, t_admit, t_done;
   // resources
@@ -144,6 +146,8 @@ size_t request_bytes(const tbr_server* s, const tbr_request& r, int n, int k) {
 
 void release_request(tbr_server* s, Request& q) {
   cudaStream_t st = s->astream;
+  if (q.ready) { cudaEventDestroy(q.ready); q.ready = nullptr; }
+  if (q.finished) { cudaEventDestroy(q.finished); q.finished = nullptr; }
   dfree(q.derived, st); dfree(q.packed, st); dfree(q.probs, st); dfree(q.status, st);
   dfree(q.partial, st); dfree(q.loss_part, st); dfree(q.grad8, st);
 }
@@ -159,9 +163,10 @@ tbr_status admit(tbr_server* s, Request& q) {
   q.kind = (r.kind == TBR_REQ_SOFT_ADJOINT) ? kServeSoft : kServeHard;
   const int tiles = ((r.W + kTileW - 1) / kTileW) * ((r.H + kTileH - 1) / kTileH);
   const int n_items = q.kind == kServeHard ? tiles : std::min(tiles, s->grid);
-  cudaError_t e = cudaSuccess;
+  // the caller's inputs (and the zeroing of its outputs, if any) precede the work
+  cudaError_t e = q.ready ? cudaStreamWaitEvent(st, q.ready, 0) : cudaSuccess;
   const float* params = pg.params;
-  if (r.kind >= TBR_REQ_RECOLOUR) {
+  if (e == cudaSuccess && r.kind >= TBR_REQ_RECOLOUR) {
     e = dalloc(&q.derived, 5 * static_cast<size_t>(n_out) + static_cast<size_t>(n_out) * k, st);
     float* ins = nullptr;
     if (e == cudaSuccess) e = dalloc(&ins, 8, st);
@@ -257,13 +262,48 @@ void worker_main(tbr_server* s) {
     // completions
     for (size_t j = 0; j < s->inflight.size();) {
       Request& q = s->requests.at(s->inflight[j]);
-      if (s->ctl->done[q.slot] == q.seq) {
+      bool finished = false;
+      if (q.state == 1 && s->ctl->done[q.slot] == q.seq) {
+        if (q.kind == kServeSoft) {
+          // fixed-order sum of the group slices, colour chain rule and loss, on ordinary kernels
+          const Program& pg = s->programs.at(q.req.program);
+          const int tiles = ((q.req.W + kTileW - 1) / kTileW) * ((q.req.H + kTileH - 1) / kTileH);
+          const int G = std::min(tiles, s->grid);
+          const size_t n = static_cast<size_t>(q.n);
+          EpilogueArgs ea;
+          ea.partial = q.partial; ea.grid = G; ea.n = q.n; ea.k = q.k;
+          ea.packed = q.packed; ea.probs = q.probs; ea.palette = pg.palette;
+          ea.inv_color_temp = 1.0f / pg.color_temp; ea.grad8 = q.grad8;
+          float* g = q.req.out_grad;
+          ea.g_cx = g; ea.g_cy = g + n; ea.g_th = g + 2 * n; ea.g_len = g + 3 * n; ea.g_r = g + 4 * n;
+          ea.g_logits = g + 5 * n; ea.g_pal = nullptr; ea.status = q.status;
+          cudaError_t e = launch_backward_epilogue(ea, s->astream);
+          if (e == cudaSuccess && q.req.out_loss)
+            e = launch_loss_final(q.loss_part, G, 3ll * q.req.W * q.req.H, q.req.out_loss, s->astream);
+          if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.finished, cudaEventDisableTiming);
+          if (e == cudaSuccess) e = cudaEventRecord(q.finished, s->astream);
+          if (e != cudaSuccess) {
+            q.result = TBR_ERR_CUDA;
+            finished = true;
+          } else {
+            q.state = 3;
+          }
+        } else {
+          finished = true;
+        }
+        progress = true;
+      } else if (q.state == 3 && cudaEventQuery(q.finished) == cudaSuccess) {
+        finished = true;
+        progress = true;
+      }
+      if (finished) {
         unsigned long long host[ST_COUNT] = {0};
         if (cudaMemcpyAsync(host, q.status, sizeof(host), cudaMemcpyDeviceToHost, s->astream) == cudaSuccess)
           cudaStreamSynchronize(s->astream);
-        q.result = host[ST_INVALID] ? TBR_ERR_INVALID_ARG
-                   : host[ST_OVERFLOW] ? TBR_ERR_OVERFLOW
-                   : host[ST_TIMEOUT] ? TBR_ERR_TIMEOUT : TBR_OK;
+        if (q.result == TBR_OK)
+          q.result = host[ST_INVALID] ? TBR_ERR_INVALID_ARG
+                     : host[ST_OVERFLOW] ? TBR_ERR_OVERFLOW
+                     : host[ST_TIMEOUT] ? TBR_ERR_TIMEOUT : TBR_OK;
         q.t_done = Clock::now();
         q.state = 2;
         release_request(s, q);
@@ -271,14 +311,16 @@ void worker_main(tbr_server* s) {
         s->free_slots.push_back(q.slot);
         ++s->completed;
         s->inflight.erase(s->inflight.begin() + j);
-        progress = true;
         s->cv.notify_all();
       } else {
         ++j;
       }
     }
     long long oldest = s->next_seq;
-    for (uint64_t id : s->inflight) oldest = std::min(oldest, s->requests.at(id).seq);
+    for (uint64_t id : s->inflight) {
+      const Request& q = s->requests.at(id);
+      if (q.state == 1) oldest = std::min(oldest, q.seq);
+    }
     s->oldest_unfinished_seq = oldest;
     // admissions, in arrival order
     while (!s->queue.empty() && !s->free_slots.empty() &&
@@ -295,7 +337,10 @@ void worker_main(tbr_server* s) {
         s->cv.notify_all();
       } else {
         s->inflight.push_back(q.id);
-        if (s->inflight.size() == 1) s->oldest_unfinished_seq = q.seq;
+        bool older = false;
+        for (uint64_t id : s->inflight)
+          if (id != q.id && s->requests.at(id).state == 1) older = true;
+        if (!older) s->oldest_unfinished_seq = q.seq;
       }
       progress = true;
     }
@@ -409,7 +454,7 @@ tbr_status tbr_serve_load_program(tbr_server* s, const tbr_program* prog, uint64
   return TBR_OK;
 }
 
-tbr_status tbr_serve_submit(tbr_server* s, const tbr_request* r, uint64_t* req_id) {
+tbr_status tbr_serve_submit(tbr_server* s, const tbr_request* r, uint64_t* req_id, void* stream) {
   if (!s || !r || !req_id) return fail(TBR_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->fatal != TBR_OK) return fail(s->fatal, "the server hit a CUDA error");
@@ -444,6 +489,14 @@ tbr_status tbr_serve_submit(tbr_server* s, const tbr_request* r, uint64_t* req_i
   }
   (void)n_out;
   Request q;
+  cudaEvent_t ev = nullptr;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    if (ev) cudaEventDestroy(ev);
+    return cuda_fail(e, "tbr_serve_submit: recording the caller's stream");
+  }
+  q.ready = ev;
   q.id = s->next_req_id++;
   q.req = *r;
   q.bytes = bytes;
@@ -530,7 +583,7 @@ void tbr_serve_destroy(tbr_server* s) {
   if (s->kstream) cudaStreamSynchronize(s->kstream);
   if (s->astream) cudaStreamSynchronize(s->astream);
   for (auto& kv : s->requests)
-    if (kv.second.state == 1) release_request(s, kv.second);
+    if (kv.second.state != 2) release_request(s, kv.second);
   if (s->astream) cudaStreamSynchronize(s->astream);
   for (auto& kv : s->programs) {
     cudaFree(kv.second.params);

@@ -4,8 +4,8 @@
 // CTA claims the next item with a compare-and-swap on a device counter, runs it
 // (a 32x8 hard tile, or a group of soft tiles fused with the MSE seed and the
 // replay adjoint), and the CTA that finishes a request's last item finalises
-// it (gradient sums in a fixed order) and signals completion through mapped
-// memory.  Every wait is bounded; the kernel exits after idle_ns without work
+// signals completion through mapped memory (the host then runs the fixed-order
+// gradient sums of a soft request as ordinary kernels).  Every wait is bounded; the kernel exits after idle_ns without work
 // and the host relaunches it when new work is published.
 #include "tbr_serve.h"
 #include "tbr_tile.cuh"
@@ -17,39 +17,6 @@ namespace {
 constexpr int kServeCH = 32;
 
 __device__ __forceinline__ long long ld_volatile_ll(const volatile long long* p) { return *p; }
-
-// dL/dPal and the colour chain rule, written by one CTA (Sec. 5.1 colour parameterisation).
-__device__ void finalize_soft(const ServeDesc& d) {
-  const int n = d.n, k = d.k, G = d.n_items;
-  const bool bad = d.status[ST_INVALID] != 0ull || d.status[ST_OVERFLOW] != 0ull ||
-                   d.status[ST_TIMEOUT] != 0ull;
-  const float nan = __int_as_float(0x7fc00000);
-  // fixed-order FP64 sum over the group slices
-  for (int t = threadIdx.x; t < n * 8; t += blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += static_cast<double>(d.partial[static_cast<size_t>(g) * n * 8 + t]);
-    d.grad8[t] = static_cast<float>(s);
-  }
-  __syncthreads();
-  __threadfence_block();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float* g8 = d.grad8 + static_cast<size_t>(i) * 8;
-    for (int c = 0; c < 5; ++c) d.out_grad[static_cast<size_t>(c) * n + i] = bad ? nan : g8[c];
-    const float* R = d.packed + static_cast<size_t>(i) * kRec;
-    const float c0 = R[F_CR], c1 = R[F_CG], c2 = R[F_CB];
-    for (int q = 0; q < k; ++q) {
-      const float* pal = d.palette + 3 * q;
-      const float dd = fmaf(pal[0] - c0, g8[5], fmaf(pal[1] - c1, g8[6], (pal[2] - c2) * g8[7]));
-      d.out_grad[5 * static_cast<size_t>(n) + static_cast<size_t>(i) * k + q] =
-          bad ? nan : d.probs[static_cast<size_t>(i) * k + q] * dd * d.inv_tc;
-    }
-  }
-  if (threadIdx.x == 0 && d.out_loss) {
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += d.loss_part[g];
-    *d.out_loss = bad ? nan : static_cast<float>(s / (3.0 * static_cast<double>(d.W) * d.H));
-  }
-}
 
 __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
   __shared__ __align__(128) float sbuf[2 * kServeCH * kRec];
@@ -192,9 +159,8 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
     }
     __syncthreads();
     if (s_last) {
-      __threadfence();
-      if (d.kind == kServeSoft) finalize_soft(d);
-      __syncthreads();
+      // all items of the request are done: signal the host (which runs the
+      // gradient epilogue of soft requests with ordinary kernels)
       if (threadIdx.x == 0) {
         a.items_done[d.slot] = 0;  // the slot is reused by a later request
         __threadfence_system();

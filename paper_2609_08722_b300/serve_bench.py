@@ -14,7 +14,7 @@ insert: a drop of r = 0.06 at the middle index); programs of 200-5000 strokes
 from __future__ import annotations
 
 import math
-import threading
+import sys
 import time
 
 import numpy as np
@@ -43,6 +43,7 @@ def make_stream(n_req: int, n_prog: int, seed: int):
 
 
 def make_programs(n_prog: int, seed: int):
+    """n_prog seeded programs, stroke counts log-uniform in [200, 5000]."""
     u = inputs.uniform(seed, n_prog)
     out = []
     for j in range(n_prog):
@@ -129,7 +130,12 @@ class _Bench:
             kw.update(_edit_args(req, d.n))
             rids[j] = server.submit(req["kind"], pids[req["prog"]], req["res"], req["res"], **kw)
         for j, rid in enumerate(rids):
-            server.wait(rid, 600000)
+            try:
+                server.wait(rid, 120000)
+            except tbr.TbrError:
+                print(f"serve_bench: request {j} ({stream[j]}) not done; server {server.stats()}",
+                      file=sys.stderr, flush=True)
+                raise
             lat[j] = server.times(rid)[1]
             server.release(rid)
         wall = time.perf_counter() - t0
@@ -166,9 +172,12 @@ def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, c
     try:
         pids = [server.load_program(d) for d in b.devs]
         # warm-up and capacity: the whole stream submitted at once
+        t0 = time.perf_counter()
         warm = make_stream(20, n_prog, seed + 7)
         b.run_server(warm, [0.0] * len(warm), server, pids)
+        print(f"serve_bench: warm-up {time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
         lat_cap, wall_cap = b.run_server(stream, [0.0] * len(stream), server, pids)
+        print(f"serve_bench: capacity run {wall_cap:.1f} s", file=sys.stderr, flush=True)
         capacity = len(stream) / wall_cap
         # Poisson arrivals at rho x capacity
         gaps = -np.log(1.0 - inputs.uniform(seed + 2, len(stream))) / (rho * capacity)
@@ -177,8 +186,10 @@ def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, c
         st = server.stats()
     finally:
         server.destroy()
+    print(f"serve_bench: poisson run {wall_s:.1f} s", file=sys.stderr, flush=True)
     b.run_per_launch(make_stream(10, n_prog, seed + 7), [0.0] * 10)
     lat_p, wall_p = b.run_per_launch(stream, arrivals.tolist())
+    print(f"serve_bench: per-launch poisson run {wall_p:.1f} s", file=sys.stderr, flush=True)
     lat_pc, wall_pc = b.run_per_launch(stream, [0.0] * len(stream))
     p50s, p99s, means = _percentiles(lat_s)
     p50p, p99p, meanp = _percentiles(lat_p)

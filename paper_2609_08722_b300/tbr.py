@@ -516,7 +516,7 @@ def _serve_lib():
         L.tbr_serve_default_config.restype = None
         L.tbr_serve_create.argtypes = [ctypes.POINTER(TbrServeConfig), ctypes.POINTER(P)]
         L.tbr_serve_load_program.argtypes = [P, ctypes.POINTER(TbrProgram), ctypes.POINTER(ctypes.c_uint64)]
-        L.tbr_serve_submit.argtypes = [P, ctypes.POINTER(TbrRequest), ctypes.POINTER(ctypes.c_uint64)]
+        L.tbr_serve_submit.argtypes = [P, ctypes.POINTER(TbrRequest), ctypes.POINTER(ctypes.c_uint64), P]
         L.tbr_serve_poll.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int)]
         L.tbr_serve_wait.argtypes = [P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(ctypes.c_int)]
         L.tbr_serve_request_times.argtypes = [P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
@@ -561,7 +561,7 @@ class Server:
 
     def submit(self, kind: int, program: int, W: int, H: int, out_rgb=None, out_idx=None, target=None,
                out_loss=None, out_grad=None, tau=0.0, tau_min=1.0, snap=False, edit_a=0, edit_b=0,
-               edit_start=0, insert_palette=0, insert_stroke=(0.5, 0.5, 0.0, 0.0, 0.05)) -> int:
+               edit_start=0, insert_palette=0, insert_stroke=(0.5, 0.5, 0.0, 0.0, 0.05), stream=None) -> int:
         r = TbrRequest()
         r.kind, r.program, r.W, r.H, r.n_prefix, r.snap = kind, program, W, H, -1, int(bool(snap))
         r.tau, r.tau_min = float(tau), float(tau_min)
@@ -570,7 +570,8 @@ class Server:
         r.edit_a, r.edit_b, r.edit_start, r.insert_palette = edit_a, edit_b, edit_start, insert_palette
         r.insert_stroke = (ctypes.c_float * 5)(*[float(v) for v in insert_stroke])
         rid = ctypes.c_uint64()
-        check(_serve_lib().tbr_serve_submit(ctypes.c_void_p(self.handle), ctypes.byref(r), ctypes.byref(rid)))
+        check(_serve_lib().tbr_serve_submit(ctypes.c_void_p(self.handle), ctypes.byref(r), ctypes.byref(rid),
+                                            _stream(stream)))
         # keep the caller's buffers alive until the request is released
         self._keep[int(rid.value)] = (target, out_rgb, out_idx, out_loss, out_grad)
         return int(rid.value)
