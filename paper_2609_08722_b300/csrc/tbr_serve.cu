@@ -98,8 +98,8 @@ struct tbr_server {
   cudaStream_t astream = nullptr;  // admission (packing, edits, memsets)
   tbr::ServeCtl* ctl = nullptr;    // mapped pinned (host view)
   tbr::ServeCtl* ctl_dev = nullptr;
-  tbr::ServeDesc* ring = nullptr;  // mapped pinned (host view)
-  tbr::ServeDesc* ring_dev = nullptr;
+  tbr::ServeDesc* ring_dev = nullptr;  // device memory
+  tbr::ServeDesc* stage = nullptr;     // pinned host staging for one descriptor
   long long* next_item = nullptr;
   int* items_done = nullptr;
   float4* rec = nullptr;
@@ -209,9 +209,9 @@ tbr_status admit(tbr_server* s, Request& q) {
   q.slot = s->free_slots.back();
   s->free_slots.pop_back();
   q.seq = s->next_seq++;
-  ServeDesc& d = s->ring[q.seq % kServeRing];
-  d.seq = -1;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
+  ServeDesc& d = *s->stage;
+  std::memset(&d, 0, sizeof(d));
+  d.seq = q.seq;
   d.item_base = s->published;
   d.kind = q.kind; d.n = n_out; d.k = k; d.W = r.W; d.H = r.H;
   d.n_items = n_items; d.slot = q.slot; d.ck = s->cfg.checkpoint_every; d.cap = s->cfg.record_capacity;
@@ -221,10 +221,15 @@ tbr_status admit(tbr_server* s, Request& q) {
   d.packed = q.packed; d.out_rgb = r.out_rgb; d.out_idx = soft ? nullptr : r.out_idx; d.target = r.target;
   d.partial = q.partial; d.loss_part = q.loss_part; d.probs = q.probs; d.palette = pg.palette;
   d.grad8 = q.grad8; d.out_grad = r.out_grad; d.out_loss = r.out_loss; d.status = q.status;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  d.seq = q.seq;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
+  e = cudaMemcpyAsync(s->ring_dev + (q.seq % kServeRing), &d, sizeof(ServeDesc), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the entry is in device memory before it is published
+  if (e != cudaSuccess) {
+    s->free_slots.push_back(q.slot);
+    release_request(s, q);
+    return cuda_fail(e, "serve: publishing a request");
+  }
   s->published += n_items;
+  std::atomic_thread_fence(std::memory_order_seq_cst);
   s->ctl->published = s->published;
   std::atomic_thread_fence(std::memory_order_seq_cst);
   q.state = 1;
@@ -390,14 +395,15 @@ tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** out) {
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->astream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->ctl), sizeof(ServeCtl), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->ctl_dev), s->ctl, 0);
-  if (e == cudaSuccess)
-    e = cudaHostAlloc(reinterpret_cast<void**>(&s->ring), sizeof(ServeDesc) * kServeRing, cudaHostAllocMapped);
-  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->ring_dev), s->ring, 0);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->ring_dev), sizeof(ServeDesc) * kServeRing);
+  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->stage), sizeof(ServeDesc), cudaHostAllocDefault);
   if (e == cudaSuccess) {
     std::memset(const_cast<ServeCtl*>(s->ctl), 0, sizeof(ServeCtl));
     for (int i = 0; i < kServeMaxSlots; ++i) s->ctl->done[i] = -1;
-    std::memset(s->ring, 0, sizeof(ServeDesc) * kServeRing);
-    for (int i = 0; i < kServeRing; ++i) s->ring[i].seq = -1;
+    std::vector<ServeDesc> init(kServeRing);
+    std::memset(init.data(), 0, sizeof(ServeDesc) * kServeRing);
+    for (int i = 0; i < kServeRing; ++i) init[i].seq = -1;
+    e = cudaMemcpy(s->ring_dev, init.data(), sizeof(ServeDesc) * kServeRing, cudaMemcpyHostToDevice);
   }
   s->grid = serve_grid();
   s->nck_max = c.max_strokes > 1 ? static_cast<size_t>((c.max_strokes - 1) / c.checkpoint_every) : 0;
@@ -596,7 +602,8 @@ void tbr_serve_destroy(tbr_server* s) {
   if (s->ckpt) cudaFree(s->ckpt);
   if (s->ck_lt) cudaFree(s->ck_lt);
   if (s->ctl) cudaFreeHost(const_cast<ServeCtl*>(s->ctl));
-  if (s->ring) cudaFreeHost(s->ring);
+  if (s->ring_dev) cudaFree(s->ring_dev);
+  if (s->stage) cudaFreeHost(s->stage);
   if (s->kstream) cudaStreamDestroy(s->kstream);
   if (s->astream) cudaStreamDestroy(s->astream);
   delete s;

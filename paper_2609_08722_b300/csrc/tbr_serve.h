@@ -9,10 +9,8 @@ constexpr int kServeRing = 1024;       // request descriptors in flight (ring en
 constexpr int kServeMaxSlots = 1024;   // completion slots
 constexpr int kServeHard = 0, kServeSoft = 1;
 
-// One published request (host-written into mapped pinned memory, device-read).
-// `seq` is written last (after -1 while the entry is being filled), so a reader
-// that sees the same seq before and after reading the other fields has a
-// consistent entry.
+// One published request: copied into a device-memory ring entry before its
+// items are published, never changed while any of its items is unfinished.
 struct ServeDesc {
   long long seq;
   long long item_base;     // global index of the request's first work item
@@ -46,7 +44,7 @@ struct ServeCtl {
 
 struct ServeArgs {
   ServeCtl* ctl;
-  ServeDesc* ring;
+  ServeDesc* ring;          // device memory [kServeRing]
   long long* next_item;    // device: items claimed
   int* items_done;         // device: per slot
   float4* rec;             // per-CTA scratch [grid][cap][256]

@@ -1,6 +1,7 @@
 // Persistent serving kernel (continuous batching of hard renders, edits and
-// soft render + adjoint requests).  The host publishes request descriptors into
-// a ring in mapped pinned memory and advances a published-item counter; each
+// soft render + adjoint requests).  The host copies request descriptors into a
+// ring in device memory and then advances a published-item counter in mapped
+// pinned memory (read only when a CTA runs out of known work); each
 // CTA claims the next item with a compare-and-swap on a device counter, runs it
 // (a 32x8 hard tile, or a group of soft tiles fused with the MSE seed and the
 // replay adjoint), and the CTA that finishes a request's last item finalises
@@ -27,21 +28,27 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
   __shared__ long long s_item;
   __shared__ long long s_cursor;
   __shared__ int s_last;
+  __shared__ long long s_pub;        // last published count seen (host memory is read only when exhausted)
+  __shared__ long long s_have;       // seq of the descriptor cached in sd (-1: none)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ChunkRing<kServeCH> ring;
   ring.init(sbuf, sbar);
-  if (threadIdx.x == 0) s_cursor = a.first_seq;
+  if (threadIdx.x == 0) {
+    s_cursor = a.first_seq;
+    s_pub = 0;
+    s_have = -1;
+  }
   const size_t cta = blockIdx.x;
   while (true) {
     // ---- claim the next published item (thread 0), bounded by the idle timeout
     if (threadIdx.x == 0) {
       long long got = -1;
-      uint64_t idle0 = global_timer_ns();
+      const uint64_t idle0 = global_timer_ns();
+      unsigned backoff = 256;
       for (uint32_t it = 0;; ++it) {
-        if (a.ctl->stop) break;
-        const long long pub = ld_volatile_ll(&a.ctl->published);
-        const long long cur = atomicAdd(reinterpret_cast<unsigned long long*>(a.next_item), 0ull);
-        if (cur < pub) {
+        const long long cur = static_cast<long long>(
+            atomicAdd(reinterpret_cast<unsigned long long*>(a.next_item), 0ull));
+        if (cur < s_pub) {
           if (static_cast<long long>(atomicCAS(reinterpret_cast<unsigned long long*>(a.next_item),
                                                static_cast<unsigned long long>(cur),
                                                static_cast<unsigned long long>(cur + 1))) == cur) {
@@ -50,29 +57,38 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
           }
           continue;
         }
-        if ((it & 63u) == 63u && global_timer_ns() - idle0 > a.idle_ns) break;
-        __nanosleep(2000);
+        // nothing known to be claimable: look at the host's counter (mapped memory), back off
+        if (a.ctl->stop) break;
+        const long long pub = ld_volatile_ll(&a.ctl->published);
+        if (pub > s_pub) {
+          s_pub = pub;
+          backoff = 256;
+          continue;
+        }
+        if (global_timer_ns() - idle0 > a.idle_ns) break;
+        __nanosleep(backoff);
+        backoff = min(backoff * 2u, 32768u);
       }
       s_item = got;
-      if (got >= 0) {
-        // locate the request: items are published contiguously in request order;
-        // an entry whose seq differs from the cursor was recycled (its request is done)
+      if (got >= 0 && !(s_have >= 0 && got >= sd.item_base && got < sd.item_base + sd.n_items)) {
+        // locate the request (device-memory ring, L1 bypassed): items are published
+        // contiguously in request order; an entry whose seq differs from the cursor was
+        // recycled (its request is complete), and an entry being rewritten belongs to a
+        // request whose items are not published yet, so it cannot contain `got`
         long long c = s_cursor;
         for (int guard = 0; guard < 4 * kServeRing; ++guard) {
-          const volatile ServeDesc* vd = &a.ring[c % kServeRing];
-          const long long s1 = vd->seq;
-          const long long base = vd->item_base;
-          const int cnt = vd->n_items;
-          __threadfence_system();
-          const long long s2 = vd->seq;
-          if (s1 == c && s2 == c && got < base + cnt) break;
+          const ServeDesc* e = &a.ring[c % kServeRing];
+          const long long sq = __ldcg(&e->seq);
+          const long long base = __ldcg(&e->item_base);
+          const int cnt = __ldcg(&e->n_items);
+          if (sq == c && got >= base && got < base + cnt) break;
           ++c;
         }
         s_cursor = c;
-        const volatile unsigned int* src = reinterpret_cast<const volatile unsigned int*>(&a.ring[c % kServeRing]);
+        const unsigned int* src = reinterpret_cast<const unsigned int*>(&a.ring[c % kServeRing]);
         unsigned int* dst = reinterpret_cast<unsigned int*>(&sd);
-        for (size_t w = 0; w < sizeof(ServeDesc) / 4; ++w) dst[w] = src[w];
-        __threadfence();
+        for (size_t w = 0; w < sizeof(ServeDesc) / 4; ++w) dst[w] = __ldcg(src + w);
+        s_have = c;
       }
     }
     __syncthreads();
