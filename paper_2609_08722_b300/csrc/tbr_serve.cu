@@ -72,10 +72,12 @@ struct Request {
   int n = 0, k = 0;
   long long seq = -1;
   int slot = -1;
+  int n_items = 0;
   size_t bytes = 0;
-  int state = 0;  // 0 queued, 1 admitted, 2 done, 3 gradient epilogue in flight
+  int state = 0;  // 0 queued, 4 staged (preparation enqueued), 1 running, 3 finishing, 2 done
   cudaEvent_t ready = nullptr;     // inputs ready on the caller's stream
-  cudaEvent_t finished = nullptr;  // epilogue done (soft requests)
+  cudaEvent_t staged = nullptr;    // preparation (edit, pack, descriptor copy) done
+  cudaEvent_t finished = nullptr;  // epilogue and status copy done
   tbr_status result = TBR_OK;
   Clock::time_point t_submit, t_admit, t_done;
   // resources
@@ -99,7 +101,8 @@ struct tbr_server {
   tbr::ServeCtl* ctl = nullptr;    // mapped pinned (host view)
   tbr::ServeCtl* ctl_dev = nullptr;
   tbr::ServeDesc* ring_dev = nullptr;  // device memory
-  tbr::ServeDesc* stage = nullptr;     // pinned host staging for one descriptor
+  tbr::ServeDesc* stage = nullptr;     // pinned host staging [kServeRing]
+  unsigned long long* status_host = nullptr;  // pinned [kServeMaxSlots][ST_COUNT]
   long long* next_item = nullptr;
   int* items_done = nullptr;
   float4* rec = nullptr;
@@ -118,11 +121,12 @@ struct tbr_server {
   std::map<uint64_t, tbr::Program> programs;
   std::map<uint64_t, tbr::Request> requests;
   std::deque<uint64_t> queue;
-  std::vector<uint64_t> inflight;
+  std::vector<uint64_t> inflight;    // staged, running or finishing, in admission order
   std::vector<int> free_slots;
   uint64_t next_prog_id = 1, next_req_id = 1;
   long long next_seq = 0;
-  long long published = 0;
+  long long published = 0;     // items visible to the kernel
+  long long staged_items = 0;  // items of admitted requests (published or about to be)
   long long oldest_unfinished_seq = 0;
   size_t bytes_in_use = 0;
   int64_t kernel_launches = 0, completed = 0, admitted = 0, refused = 0;
@@ -147,6 +151,7 @@ size_t request_bytes(const tbr_server* s, const tbr_request& r, int n, int k) {
 void release_request(tbr_server* s, Request& q) {
   cudaStream_t st = s->astream;
   if (q.ready) { cudaEventDestroy(q.ready); q.ready = nullptr; }
+  if (q.staged) { cudaEventDestroy(q.staged); q.staged = nullptr; }
   if (q.finished) { cudaEventDestroy(q.finished); q.finished = nullptr; }
   dfree(q.derived, st); dfree(q.packed, st); dfree(q.probs, st); dfree(q.status, st);
   dfree(q.partial, st); dfree(q.loss_part, st); dfree(q.grad8, st);
@@ -176,8 +181,7 @@ tbr_status admit(tbr_server* s, Request& q) {
                                                    r.insert_palette, q.derived, n_out);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // ins is freed right after
-    dfree(ins, st);
+    dfree(ins, st);  // stream-ordered: after k_edit
     params = q.derived;
   }
   if (e == cudaSuccess) e = dalloc(&q.packed, static_cast<size_t>(n_out) * kRec, st);
@@ -200,7 +204,6 @@ tbr_status admit(tbr_server* s, Request& q) {
   PackArgs pa{&view, n_out, soft ? r.tau : 0.0f, soft ? r.tau_min : 1.0f, (!soft && r.snap) ? 1 : 0, q.packed,
               soft ? q.probs : nullptr, q.status};
   if (e == cudaSuccess) e = launch_pack(pa, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the published work must see the packed strokes
   if (e != cudaSuccess) {
     release_request(s, q);
     return cuda_fail(e, "serve: admitting a request");
@@ -209,10 +212,10 @@ tbr_status admit(tbr_server* s, Request& q) {
   q.slot = s->free_slots.back();
   s->free_slots.pop_back();
   q.seq = s->next_seq++;
-  ServeDesc& d = *s->stage;
+  ServeDesc& d = s->stage[q.seq % kServeRing];
   std::memset(&d, 0, sizeof(d));
   d.seq = q.seq;
-  d.item_base = s->published;
+  d.item_base = s->staged_items;
   d.kind = q.kind; d.n = n_out; d.k = k; d.W = r.W; d.H = r.H;
   d.n_items = n_items; d.slot = q.slot; d.ck = s->cfg.checkpoint_every; d.cap = s->cfg.record_capacity;
   for (int c = 0; c < 3; ++c) d.bg[c] = pg.bg[c];
@@ -222,17 +225,16 @@ tbr_status admit(tbr_server* s, Request& q) {
   d.partial = q.partial; d.loss_part = q.loss_part; d.probs = q.probs; d.palette = pg.palette;
   d.grad8 = q.grad8; d.out_grad = r.out_grad; d.out_loss = r.out_loss; d.status = q.status;
   e = cudaMemcpyAsync(s->ring_dev + (q.seq % kServeRing), &d, sizeof(ServeDesc), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the entry is in device memory before it is published
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.staged, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(q.staged, st);
   if (e != cudaSuccess) {
     s->free_slots.push_back(q.slot);
     release_request(s, q);
-    return cuda_fail(e, "serve: publishing a request");
+    return cuda_fail(e, "serve: staging a request");
   }
-  s->published += n_items;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  s->ctl->published = s->published;
-  std::atomic_thread_fence(std::memory_order_seq_cst);
-  q.state = 1;
+  s->staged_items += n_items;  // published once the staged event completes (in order)
+  q.n_items = n_items;
+  q.state = 4;
   q.t_admit = Clock::now();
   s->bytes_in_use += q.bytes;
   ++s->admitted;
@@ -243,7 +245,10 @@ void ensure_kernel(tbr_server* s) {
   if (s->kernel_running) {
     if (cudaStreamQuery(s->kstream) == cudaSuccess) s->kernel_running = false;
   }
-  if (s->kernel_running || s->inflight.empty()) return;
+  bool running_work = false;
+  for (uint64_t id : s->inflight)
+    if (s->requests.at(id).state == 1) running_work = true;
+  if (s->kernel_running || !running_work) return;
   ServeArgs a;
   a.ctl = s->ctl_dev; a.ring = s->ring_dev; a.next_item = s->next_item; a.items_done = s->items_done;
   a.rec = s->rec; a.rec_i = s->rec_i; a.ckpt = s->ckpt; a.ck_lt = s->ck_lt;
@@ -264,51 +269,60 @@ void worker_main(tbr_server* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (!s->stopping) {
     bool progress = false;
+    // publish staged requests in admission order once their preparation has run
+    for (uint64_t id : s->inflight) {
+      Request& q = s->requests.at(id);
+      if (q.state == 1 || q.state == 3) continue;
+      if (q.state != 4 || cudaEventQuery(q.staged) != cudaSuccess) break;
+      s->published += q.n_items;
+      std::atomic_thread_fence(std::memory_order_seq_cst);
+      s->ctl->published = s->published;
+      std::atomic_thread_fence(std::memory_order_seq_cst);
+      q.state = 1;
+      progress = true;
+    }
     // completions
     for (size_t j = 0; j < s->inflight.size();) {
       Request& q = s->requests.at(s->inflight[j]);
       bool finished = false;
       if (q.state == 1 && s->ctl->done[q.slot] == q.seq) {
+        cudaError_t e = cudaSuccess;
         if (q.kind == kServeSoft) {
           // fixed-order sum of the group slices, colour chain rule and loss, on ordinary kernels
           const Program& pg = s->programs.at(q.req.program);
-          const int tiles = ((q.req.W + kTileW - 1) / kTileW) * ((q.req.H + kTileH - 1) / kTileH);
-          const int G = std::min(tiles, s->grid);
           const size_t n = static_cast<size_t>(q.n);
           EpilogueArgs ea;
-          ea.partial = q.partial; ea.grid = G; ea.n = q.n; ea.k = q.k;
+          ea.partial = q.partial; ea.grid = q.n_items; ea.n = q.n; ea.k = q.k;
           ea.packed = q.packed; ea.probs = q.probs; ea.palette = pg.palette;
           ea.inv_color_temp = 1.0f / pg.color_temp; ea.grad8 = q.grad8;
           float* g = q.req.out_grad;
           ea.g_cx = g; ea.g_cy = g + n; ea.g_th = g + 2 * n; ea.g_len = g + 3 * n; ea.g_r = g + 4 * n;
           ea.g_logits = g + 5 * n; ea.g_pal = nullptr; ea.status = q.status;
-          cudaError_t e = launch_backward_epilogue(ea, s->astream);
+          e = launch_backward_epilogue(ea, s->astream);
           if (e == cudaSuccess && q.req.out_loss)
-            e = launch_loss_final(q.loss_part, G, 3ll * q.req.W * q.req.H, q.req.out_loss, s->astream);
-          if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.finished, cudaEventDisableTiming);
-          if (e == cudaSuccess) e = cudaEventRecord(q.finished, s->astream);
-          if (e != cudaSuccess) {
-            q.result = TBR_ERR_CUDA;
-            finished = true;
-          } else {
-            q.state = 3;
-          }
-        } else {
+            e = launch_loss_final(q.loss_part, q.n_items, 3ll * q.req.W * q.req.H, q.req.out_loss, s->astream);
+        }
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(s->status_host + static_cast<size_t>(q.slot) * ST_COUNT, q.status,
+                              ST_COUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->astream);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.finished, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(q.finished, s->astream);
+        if (e != cudaSuccess) {
+          q.result = TBR_ERR_CUDA;
           finished = true;
+        } else {
+          q.state = 3;
         }
         progress = true;
       } else if (q.state == 3 && cudaEventQuery(q.finished) == cudaSuccess) {
+        const unsigned long long* host = s->status_host + static_cast<size_t>(q.slot) * ST_COUNT;
+        q.result = host[ST_INVALID] ? TBR_ERR_INVALID_ARG
+                   : host[ST_OVERFLOW] ? TBR_ERR_OVERFLOW
+                   : host[ST_TIMEOUT] ? TBR_ERR_TIMEOUT : TBR_OK;
         finished = true;
         progress = true;
       }
       if (finished) {
-        unsigned long long host[ST_COUNT] = {0};
-        if (cudaMemcpyAsync(host, q.status, sizeof(host), cudaMemcpyDeviceToHost, s->astream) == cudaSuccess)
-          cudaStreamSynchronize(s->astream);
-        if (q.result == TBR_OK)
-          q.result = host[ST_INVALID] ? TBR_ERR_INVALID_ARG
-                     : host[ST_OVERFLOW] ? TBR_ERR_OVERFLOW
-                     : host[ST_TIMEOUT] ? TBR_ERR_TIMEOUT : TBR_OK;
         q.t_done = Clock::now();
         q.state = 2;
         release_request(s, q);
@@ -324,7 +338,7 @@ void worker_main(tbr_server* s) {
     long long oldest = s->next_seq;
     for (uint64_t id : s->inflight) {
       const Request& q = s->requests.at(id);
-      if (q.state == 1) oldest = std::min(oldest, q.seq);
+      if (q.state == 1 || q.state == 4) oldest = std::min(oldest, q.seq);
     }
     s->oldest_unfinished_seq = oldest;
     // admissions, in arrival order
@@ -343,8 +357,10 @@ void worker_main(tbr_server* s) {
       } else {
         s->inflight.push_back(q.id);
         bool older = false;
-        for (uint64_t id : s->inflight)
-          if (id != q.id && s->requests.at(id).state == 1) older = true;
+        for (uint64_t id : s->inflight) {
+          const int stt = s->requests.at(id).state;
+          if (id != q.id && (stt == 1 || stt == 4)) older = true;
+        }
         if (!older) s->oldest_unfinished_seq = q.seq;
       }
       progress = true;
@@ -396,7 +412,11 @@ tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** out) {
   if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->ctl), sizeof(ServeCtl), cudaHostAllocMapped);
   if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->ctl_dev), s->ctl, 0);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->ring_dev), sizeof(ServeDesc) * kServeRing);
-  if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&s->stage), sizeof(ServeDesc), cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->stage), sizeof(ServeDesc) * kServeRing, cudaHostAllocDefault);
+  if (e == cudaSuccess)
+    e = cudaHostAlloc(reinterpret_cast<void**>(&s->status_host),
+                      sizeof(unsigned long long) * ST_COUNT * kServeMaxSlots, cudaHostAllocDefault);
   if (e == cudaSuccess) {
     std::memset(const_cast<ServeCtl*>(s->ctl), 0, sizeof(ServeCtl));
     for (int i = 0; i < kServeMaxSlots; ++i) s->ctl->done[i] = -1;
@@ -604,6 +624,7 @@ void tbr_serve_destroy(tbr_server* s) {
   if (s->ctl) cudaFreeHost(const_cast<ServeCtl*>(s->ctl));
   if (s->ring_dev) cudaFree(s->ring_dev);
   if (s->stage) cudaFreeHost(s->stage);
+  if (s->status_host) cudaFreeHost(s->status_host);
   if (s->kstream) cudaStreamDestroy(s->kstream);
   if (s->astream) cudaStreamDestroy(s->astream);
   delete s;

@@ -113,6 +113,7 @@ class _Bench:
 
     # -- continuous batching ------------------------------------------------------
     def run_server(self, stream, arrivals, server, pids):
+        self.queue_ms = []
         lat = [None] * len(stream)
         rids = [None] * len(stream)
         t0 = time.perf_counter()
@@ -136,7 +137,9 @@ class _Bench:
                 print(f"serve_bench: request {j} ({stream[j]}) not done; server {server.stats()}",
                       file=sys.stderr, flush=True)
                 raise
-            lat[j] = server.times(rid)[1]
+            qms, lms = server.times(rid)
+            lat[j] = lms
+            self.queue_ms.append(qms)
             server.release(rid)
         wall = time.perf_counter() - t0
         return lat, wall
@@ -183,6 +186,7 @@ def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, c
         gaps = -np.log(1.0 - inputs.uniform(seed + 2, len(stream))) / (rho * capacity)
         arrivals = np.cumsum(gaps) - gaps[0]
         lat_s, wall_s = b.run_server(stream, arrivals.tolist(), server, pids)
+        queue_s = float(np.mean(b.queue_ms))
         st = server.stats()
     finally:
         server.destroy()
@@ -197,6 +201,7 @@ def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, c
         "requests": len(stream), "programs": n_prog, "arrival_rate_per_s": rho * capacity, "rho": rho,
         "mix": "60% hard, 30% soft+adjoint, 10% edit; 200-5000 strokes; 256^2-2048^2",
         "server": {"capacity_req_per_s": capacity, "p50_ms": p50s, "p99_ms": p99s, "mean_ms": means,
+                   "mean_admission_wait_ms": queue_s,
                    "throughput_req_per_s": len(stream) / wall_s, "kernel_launches": st["kernel_launches"],
                    "persistent_ctas": st["persistent_ctas"]},
         "per_launch": {"capacity_req_per_s": len(stream) / wall_pc, "p50_ms": p50p, "p99_ms": p99p,
