@@ -105,6 +105,7 @@ struct tbr_server {
   unsigned long long* status_host = nullptr;  // pinned [kServeMaxSlots][ST_COUNT]
   long long* next_item = nullptr;
   int* items_done = nullptr;
+  int* idle_flags = nullptr;       // [0] idle CTAs, [1] closing
   float4* rec = nullptr;
   int* rec_i = nullptr;
   float4* ckpt = nullptr;
@@ -251,12 +252,14 @@ void ensure_kernel(tbr_server* s) {
   if (s->kernel_running || !running_work) return;
   ServeArgs a;
   a.ctl = s->ctl_dev; a.ring = s->ring_dev; a.next_item = s->next_item; a.items_done = s->items_done;
+  a.idle_ctas = s->idle_flags; a.closing = s->idle_flags + 1;
   a.rec = s->rec; a.rec_i = s->rec_i; a.ckpt = s->ckpt; a.ck_lt = s->ck_lt;
   a.cap = s->cfg.record_capacity; a.nck_max = s->nck_max;
   a.first_seq = s->oldest_unfinished_seq;
   a.idle_ns = static_cast<unsigned long long>(s->cfg.idle_exit_us) * 1000ull;
   a.grid = s->grid;
-  if (launch_serve(a, s->kstream) != cudaSuccess) {
+  if (cudaMemsetAsync(s->idle_flags, 0, 2 * sizeof(int), s->kstream) != cudaSuccess ||
+      launch_serve(a, s->kstream) != cudaSuccess) {
     s->fatal = TBR_ERR_CUDA;
     return;
   }
@@ -430,6 +433,7 @@ tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** out) {
   const size_t per = static_cast<size_t>(s->grid) * kTileThreads;
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->next_item), sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->items_done), sizeof(int) * kServeMaxSlots);
+  if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->idle_flags), 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->rec), sizeof(float4) * c.record_capacity * per);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->rec_i), sizeof(int) * c.record_capacity * per);
   if (e == cudaSuccess && s->nck_max)
@@ -617,6 +621,7 @@ void tbr_serve_destroy(tbr_server* s) {
   }
   if (s->next_item) cudaFree(s->next_item);
   if (s->items_done) cudaFree(s->items_done);
+  if (s->idle_flags) cudaFree(s->idle_flags);
   if (s->rec) cudaFree(s->rec);
   if (s->rec_i) cudaFree(s->rec_i);
   if (s->ckpt) cudaFree(s->ckpt);

@@ -47,6 +47,8 @@ struct ServeArgs {
   ServeDesc* ring;          // device memory [kServeRing]
   long long* next_item;    // device: items claimed
   int* items_done;         // device: per slot
+  int* idle_ctas;          // device: CTAs currently without work (reset before each launch)
+  int* closing;            // device: set once every CTA has been idle (reset before each launch)
   float4* rec;             // per-CTA scratch [grid][cap][256]
   int* rec_i;
   float4* ckpt;            // per-CTA scratch [grid][nck_max][256]

@@ -40,12 +40,16 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
   }
   const size_t cta = blockIdx.x;
   while (true) {
-    // ---- claim the next published item (thread 0), bounded by the idle timeout
+    // ---- claim the next published item (thread 0).  The kernel closes only when
+    // every CTA has been idle (no claimable item) for idle_ns, so no CTA leaves
+    // while others still run and new work would find the GPU partly empty.
     if (threadIdx.x == 0) {
       long long got = -1;
-      const uint64_t idle0 = global_timer_ns();
+      uint64_t idle0 = 0;
+      bool counted_idle = false;
       unsigned backoff = 256;
       for (uint32_t it = 0;; ++it) {
+        if (*reinterpret_cast<volatile int*>(a.closing)) break;
         const long long cur = static_cast<long long>(
             atomicAdd(reinterpret_cast<unsigned long long*>(a.next_item), 0ull));
         if (cur < s_pub) {
@@ -58,17 +62,29 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
           continue;
         }
         // nothing known to be claimable: look at the host's counter (mapped memory), back off
-        if (a.ctl->stop) break;
         const long long pub = ld_volatile_ll(&a.ctl->published);
         if (pub > s_pub) {
           s_pub = pub;
           backoff = 256;
           continue;
         }
-        if (global_timer_ns() - idle0 > a.idle_ns) break;
+        if (a.ctl->stop) {
+          atomicExch(a.closing, 1);
+          break;
+        }
+        if (!counted_idle) {
+          atomicAdd(a.idle_ctas, 1);
+          counted_idle = true;
+          idle0 = global_timer_ns();
+        } else if (global_timer_ns() - idle0 > a.idle_ns &&
+                   atomicAdd(a.idle_ctas, 0) == static_cast<int>(gridDim.x)) {
+          atomicExch(a.closing, 1);
+          break;
+        }
         __nanosleep(backoff);
         backoff = min(backoff * 2u, 32768u);
       }
+      if (got >= 0 && counted_idle) atomicSub(a.idle_ctas, 1);
       s_item = got;
       if (got >= 0 && !(s_have >= 0 && got >= sd.item_base && got < sd.item_base + sd.n_items)) {
         // locate the request (device-memory ring, L1 bypassed): items are published
