@@ -240,6 +240,43 @@ __device__ __forceinline__ float sgn1(float v) { return copysignf(1.0f, v); }
 // render); without it the caller guarantees sigma' > r (hard render).
 template <bool FLOOR>
 __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh) {
+  if (g.L == 0.0f) {  // drop: radial map, delta = 0 (warp-uniform branch)
+    q.sgs = sgn1(s); q.sgh = sgn1(h); q.si = s; q.hi = h;
+    const float as = fabsf(s), ah = fabsf(h);
+    q.cap_i = as > 0.0f;
+    q.sp = sqrt_a(fmaf(as, as, ah * ah));
+    if (q.cap_i) {
+      const float inv = rcp_a(q.sp);
+      q.ud = as * inv; q.uh = ah * inv;
+      q.phi = atan2_pos(as, ah);
+    } else {
+      q.ud = 0.0f; q.uh = 1.0f; q.phi = 0.0f;
+    }
+    q.t = q.sp * q.phi;
+    float C = (q.sp - g.r) * fmaf(kPiF, q.sp, g.kA);
+    q.floored = FLOOR && C < g.fl2;
+    if (q.floored) C = g.fl2;
+    q.sig = div_a(C, sqrt_a(kPiF * C));
+    q.tn = q.sig * q.phi;
+    q.cap_o = q.cap_i && q.tn > 0.0f;
+    q.beta = q.cap_o ? q.phi : 0.0f;
+    q.sb = q.cap_o ? q.ud : 0.0f;
+    q.cb = q.cap_o ? q.uh : 1.0f;
+    float dS, dH;
+    if (q.floored) {                   // direct form, same ray
+      dS = q.sig * q.sb - as;
+      dH = q.sig * q.cb - ah;
+    } else {
+      const float dsig = -div_a(g.Ar, kPiF * (q.sp + q.sig));
+      dS = dsig * q.ud;
+      dH = dsig * q.uh;
+    }
+    ds = q.sgs * dS;
+    dh = q.sgh * dH;
+    q.so = s + ds;
+    q.ho = h + dh;
+    return;
+  }
   q.sgs = sgn1(s); q.sgh = sgn1(h); q.si = s; q.hi = h;
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
@@ -302,6 +339,32 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
 //   sigma' - sigma = A_L(r) / (2L + pi (sigma + sigma')),
 //   cap to cap: phi - beta = (sigma' - sigma) L (pi/2 - beta) / (Q sigma').
 __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh) {
+  if (g.L == 0.0f) {  // drop: radial map, delta = 0 (warp-uniform branch)
+    q.sgs = sgn1(s); q.sgh = sgn1(h); q.so = s; q.ho = h;
+    const float as = fabsf(s), ah = fabsf(h);
+    q.cap_o = as > 0.0f;
+    q.sig = sqrt_a(fmaf(as, as, ah * ah));
+    if (q.cap_o) {
+      const float inv = rcp_a(q.sig);
+      q.sb = as * inv; q.cb = ah * inv;
+      q.beta = atan2_pos(as, ah);
+    } else {
+      q.sb = 0.0f; q.cb = 1.0f; q.beta = 0.0f;
+    }
+    q.tn = q.sig * q.beta;
+    const float B = fmaf(q.sig, kPiF * q.sig, g.Ar);
+    q.sp = div_a(B, sqrt_a(kPiF * B));
+    const float dsp = div_a(g.Ar, kPiF * (q.sig + q.sp));
+    q.t = q.sp * q.beta;
+    q.cap_i = q.cap_o;
+    q.phi = q.beta; q.ud = q.sb; q.uh = q.cb;
+    q.floored = false;
+    ds = q.sgs * (dsp * q.sb);
+    dh = q.sgh * (dsp * q.cb);
+    q.si = s + ds;
+    q.hi = h + dh;
+    return;
+  }
   q.sgs = sgn1(s); q.sgh = sgn1(h); q.so = s; q.ho = h;
   const float as = fabsf(s), ah = fabsf(h);
   const float d = as - g.hl;
@@ -350,6 +413,33 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
   dh = q.sgh * dH;
   q.si = s + ds;
   q.hi = h + dh;
+}
+
+// Drop (L = 0) forward step in world coordinates: the map is radial,
+// x_{i-1} = m + (x_i - m) sigma / rho with sigma = sqrt(rho^2 - r^2) (Eq. back at
+// L = 0), so the displacement is (x_i - m) (sigma - rho) / rho with the
+// cancellation-free sigma - rho = -A_0(r) / (pi (rho + sigma)).  Returns rho
+// (the distance sigma' used by the coverage) and the world displacement.
+// FLOOR applies the epsilon-floor (then the point lands at distance
+// sqrt((eps r)^2 / pi) on the same ray; at rho = 0 on the e_perp ray).
+template <bool FLOOR>
+__device__ __forceinline__ float drop_step(float dx, float dy, const StrokeF& g, float& ddx, float& ddy,
+                                           bool& floored) {
+  const float rho = sqrt_a(fmaf(dx, dx, dy * dy));
+  float C = (rho - g.r) * fmaf(kPiF, rho, g.kA);
+  floored = FLOOR && C < g.fl2;
+  if (floored) C = g.fl2;
+  const float sig = div_a(C, sqrt_a(kPiF * C));
+  const float dsig = floored ? sig - rho : -div_a(g.Ar, kPiF * (rho + sig));
+  if (rho > 0.0f) {
+    const float k = dsig * rcp_a(rho);
+    ddx = k * dx;
+    ddy = k * dy;
+  } else {  // the centre itself: the fold convention sends it along +e_perp
+    ddx = -dsig * g.ey;
+    ddy = dsig * g.ex;
+  }
+  return rho;
 }
 
 // Frame coordinates of a hi/lo position.

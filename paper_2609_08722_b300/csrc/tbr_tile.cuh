@@ -80,19 +80,28 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         }
         const float* S = S0 + j * kRec;
         const StrokeF g = load_stroke(S);
-        float s, h;
-        to_frame(st.xh, st.yh, st.xl, st.yl, g, s, h);
-        float sp, ds = 0.0f, dh = 0.0f;
+        float sp, ds = 0.0f, dh = 0.0f, ddx = 0.0f, ddy = 0.0f;
         bool floored = false;
-        if (INERT) {
-          const float as = fabsf(s), ah = fabsf(h);
-          const float d = as - g.hl;
-          sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
+        const bool drop = g.L == 0.0f;  // warp-uniform
+        if (drop) {
+          const float dx = (st.xh - g.mx) + st.xl, dy = (st.yh - g.my) + st.yl;
+          if (INERT) sp = sqrt_a(fmaf(dx, dx, dy * dy));
+          else sp = drop_step<true>(dx, dy, g, ddx, ddy, floored);
         } else {
-          Geo q;
-          psi_local<true>(s, h, g, q, ds, dh);
-          sp = q.sp;
-          floored = q.floored;
+          float s, h;
+          to_frame(st.xh, st.yh, st.xl, st.yl, g, s, h);
+          if (INERT) {
+            const float as = fabsf(s), ah = fabsf(h);
+            const float d = as - g.hl;
+            sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
+          } else {
+            Geo q;
+            psi_local<true>(s, h, g, q, ds, dh);
+            sp = q.sp;
+            floored = q.floored;
+            ddx = fmaf(ds, g.ex, -dh * g.ey);
+            ddy = fmaf(ds, g.ey, dh * g.ex);
+          }
         }
         const Cover cv = coverage(sp, g);
         const float w = ex2_a(st.lt) * cv.alpha;
@@ -109,7 +118,8 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
             }
             ++st.cnt;
           }
-          add_frame_disp(st.xh, st.yh, st.xl, st.yl, g, ds, dh);
+          pos_add(st.xh, st.xl, ddx);
+          pos_add(st.yh, st.yl, ddy);
         }
       }
     }
@@ -159,6 +169,22 @@ static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& x
 __device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float& yl,
                                           const float* __restrict__ S, unsigned& band) {
   const StrokeF g = load_stroke(S);
+  if (g.L == 0.0f) {  // drop (warp-uniform): radial step in world coordinates
+    const float dx = (xh - g.mx) + xl, dy = (yh - g.my) + yl;
+    const float rho = sqrt_a(fmaf(dx, dx, dy * dy));
+    const float diff = rho - g.r;
+    if (fabsf(diff) < kBand) {
+      ++band;
+      return hard_step_f64(xh, yh, xl, yl, S);
+    }
+    if (diff <= 0.0f) return true;
+    float ddx, ddy;
+    bool floored;
+    drop_step<false>(dx, dy, g, ddx, ddy, floored);
+    pos_add(xh, xl, ddx);
+    pos_add(yh, yl, ddy);
+    return false;
+  }
   float s, h;
   to_frame(xh, yh, xl, yl, g, s, h);
   const float as = fabsf(s), ah = fabsf(h);
