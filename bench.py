@@ -159,7 +159,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle (soft forward + stored-state adjoint)
 # ---------------------------------------------------------------------------
-def oracle_rate(prog, seconds, max_pixels=65536):
+def oracle_rate(prog, seconds, max_pixels=1 << 20):
     """evals/s of the oracle's soft forward + stored-state adjoint on a pixel
     sample of the operating-point workload sized to ~``seconds`` of CPU time."""
     import numpy as np
@@ -176,10 +176,14 @@ def oracle_rate(prog, seconds, max_pixels=65536):
         oracle.soft_vjp(prog, RES, RES, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot, pix=pix)
         return time.perf_counter() - t0
 
-    m = 64
-    dt = run(m)
-    m2 = int(min(max_pixels, max(64, m * seconds / max(dt, 1e-3))))
-    dt2 = run(m2)
+    m, dt = 256, 0.0
+    while True:
+        dt = run(m)
+        if dt >= 0.2 * seconds or m >= max_pixels:
+            break
+        m = min(max_pixels, m * 4)
+    m2 = int(min(max_pixels, max(m, m * seconds / max(dt, 1e-3))))
+    dt2 = run(m2) if m2 != m else dt
     rate = m2 * prog.n / dt2
     return rate, {"pixels": m2, "seconds": dt2, "threads": oracle.num_threads()}
 
