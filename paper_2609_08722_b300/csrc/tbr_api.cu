@@ -57,7 +57,7 @@ cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap
   const size_t P = static_cast<size_t>(W) * H;
   c->n = n; c->k = k; c->W = W; c->H = H;
   c->ck = ck; c->cap = cap; c->inert = inert;
-  c->grid = backward_grid(W, H);
+  c->grid = backward_grid(W, H, inert);
   c->last_stream = st;
   const size_t nck = n > 1 ? static_cast<size_t>((n - 1) / ck) : 0;
   cudaError_t e = dalloc(&c->packed, static_cast<size_t>(n) * kRec, st);

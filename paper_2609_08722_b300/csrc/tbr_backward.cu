@@ -14,7 +14,7 @@
 // an epilogue sums the slices in a fixed order, so the result is reproducible.
 #include <math.h>
 
-#include "tbr_tile.cuh"
+#include "tbr_pair.cuh"
 
 namespace tbr {
 
@@ -57,6 +57,65 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_backward(BwdArgs a) {
                   const_cast<float*>(a.ck_lt), P, p, a.cap, a.ck_every};
     if (!backward_tile<CH, INERT>(ring, a.packed, n, valid, st, lC0, lC1, lC2, a.bg, rv, red, slice, first,
                                   drift, status))
+      break;
+    first = false;
+  }
+  const unsigned dsum = __reduce_add_sync(0xffffffffu, drift);
+  if (lane == 0 && dsum) atomicAdd(status + ST_DRIFT, static_cast<unsigned long long>(dsum));
+}
+
+// The same replay adjoint with two vertically adjacent pixels per thread
+// (32 x 16 tiles, packed FP32 pair arithmetic; tbr_pair.cuh).  Used for the
+// exterior-transport model; the inert-mark model keeps k_backward.
+template <int CH>
+__global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
+  __shared__ __align__(128) float sbuf[2 * CH * kRec];
+  __shared__ __align__(8) uint64_t sbar[2];
+  __shared__ float red[2][kTileThreads / 32][CH * 8];
+  __shared__ __align__(16) f2 pbuf[CH * kPairRec];
+  const int lane = threadIdx.x & 31;
+  const int W = a.W, H = a.H, n = a.n;
+  const int ntiles = ((W + kPairTileW - 1) / kPairTileW) * ((H + kPairTileH - 1) / kPairTileH);
+  const size_t P = static_cast<size_t>(W) * H;
+  unsigned long long* status = a.status;
+  const bool skip = status[ST_INVALID] != 0ull || status[ST_OVERFLOW] != 0ull;
+  ChunkRing<CH> ring;
+  ring.init(sbuf, sbar);
+  float* slice = a.partial + static_cast<size_t>(blockIdx.x) * n * 8;
+  unsigned drift = 0;
+  bool first = true;
+  const RecordView rv{const_cast<float4*>(a.rec), const_cast<int*>(a.rec_i), const_cast<float4*>(a.ckpt),
+                      const_cast<float*>(a.ck_lt), P, 0, a.cap, a.ck_every};
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int px, py0;
+    pair_tile_pixel(tile, W, px, py0);
+    bool valid[2];
+    size_t off[2];
+    PixelState st[2];
+    float lC[2][3];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int py = py0 + c;
+      valid[c] = px < W && py < H && !skip;
+      off[c] = valid[c] ? static_cast<size_t>(py) * W + px : 0;
+      // an invalid pixel keeps a finite position and a zero cotangent
+      st[c] = PixelState{(static_cast<float>(px) + 0.5f) / static_cast<float>(W),
+                         (static_cast<float>(py) + 0.5f) / static_cast<float>(H), 0.0f, 0.0f, 0.0f, 0,
+                         0.0f, 0.0f, 0.0f};
+      lC[c][0] = lC[c][1] = lC[c][2] = 0.0f;
+      if (valid[c]) {
+        const float4 s0 = a.s0[off[c]];
+        const float2 s0b = a.s0b[off[c]];
+        st[c].xh = s0.x; st[c].yh = s0.y; st[c].xl = s0.z; st[c].yl = s0.w;
+        st[c].lt = s0b.x;
+        st[c].cnt = __float_as_int(s0b.y);
+        lC[c][0] = a.dLdR[3 * off[c] + 0];
+        lC[c][1] = a.dLdR[3 * off[c] + 1];
+        lC[c][2] = a.dLdR[3 * off[c] + 2];
+      }
+    }
+    if (!backward_tile2<CH>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first, drift,
+                            status))
       break;
     first = false;
   }
@@ -121,18 +180,23 @@ __global__ void k_grad_palette(EpilogueArgs a) {
 
 }  // namespace
 
-int backward_grid(int W, int H) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
+int backward_grid(int W, int H, int inert) {
+  static int per_sm[2] = {-1, -1};
+  static int sms = 0;
+  if (per_sm[0] < 0) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward<kBwdCH, false>, kTileThreads, 0) !=
-            cudaSuccess || per_sm < 1)
-      per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_backward2<kBwdCH>, kTileThreads, 0) !=
+            cudaSuccess || per_sm[0] < 1)
+      per_sm[0] = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_backward<kBwdCH, true>, kTileThreads, 0) !=
+            cudaSuccess || per_sm[1] < 1)
+      per_sm[1] = 1;
   }
-  const int tiles = ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
-  const int g0 = per_sm * sms;
+  const int tiles = inert ? ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH)
+                          : ((W + kPairTileW - 1) / kPairTileW) * ((H + kPairTileH - 1) / kPairTileH);
+  const int g0 = per_sm[inert ? 1 : 0] * sms;
   const int waves = (tiles + g0 - 1) / g0;
   return (tiles + waves - 1) / waves;
 }
@@ -141,7 +205,7 @@ cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
   KernelTimer kt(TBR_K_BACKWARD, st);
   if (a.inert) k_backward<kBwdCH, true><<<a.grid, kTileThreads, 0, st>>>(a);
-  else k_backward<kBwdCH, false><<<a.grid, kTileThreads, 0, st>>>(a);
+  else k_backward2<kBwdCH><<<a.grid, kTileThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 

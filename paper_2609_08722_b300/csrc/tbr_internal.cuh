@@ -656,7 +656,7 @@ struct BwdArgs {
   int grid;
   unsigned long long* status;
 };
-int backward_grid(int W, int H);
+int backward_grid(int W, int H, int inert);  // CTAs of the persistent backward grid
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st);
 
 struct EpilogueArgs {

@@ -1,0 +1,460 @@
+// Paired replay adjoint: each thread carries two vertically adjacent pixels
+// through the replay adjoint (Sec. 5.2) with Blackwell's packed FP32 pairs
+// (FFMA2 / FADD2 / FMUL2), so one instruction advances both pixels.  The common
+// step -- regeneration by Phi (Eq. fwd, Eq. rpos), coverage (Eq. relax), the
+// adjoint step and the parameter VJP (Eq. adjstep, Eq. adjparam) -- is written
+// branch-free: on a capsule flank the cap formulas reduce to the flank ones once
+// (sin beta, cos beta, beta) = (0, 1, 0) and (sin phi, cos phi, phi) = (0, 1, 0),
+// so one instruction stream serves both.  Side-table pops, checkpoint resets and
+// the rare flank-to-cap regeneration take the scalar routines per pixel.
+#pragma once
+
+#include "tbr_tile.cuh"
+
+namespace tbr {
+
+using f2 = float2;
+
+__device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+// a - b as one FFMA2: b * (-1) + a
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ f2 sgn2(f2 a) { return make_float2(sgn1(a.x), sgn1(a.y)); }
+__device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
+__device__ __forceinline__ f2 min2(f2 a, f2 b) { return make_float2(fminf(a.x, b.x), fminf(a.y, b.y)); }
+__device__ __forceinline__ f2 sqrt2(f2 a) { return make_float2(sqrt_a(a.x), sqrt_a(a.y)); }
+__device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(rcp_a(a.x), rcp_a(a.y)); }
+// 1/a where a > 0, else 0
+__device__ __forceinline__ f2 rcp2_pos(f2 a) {
+  return make_float2(a.x > 0.0f ? rcp_a(a.x) : 0.0f, a.y > 0.0f ? rcp_a(a.y) : 0.0f);
+}
+__device__ __forceinline__ f2 ex22(f2 a) { return make_float2(ex2_a(a.x), ex2_a(a.y)); }
+__device__ __forceinline__ f2 lg22(f2 a) { return make_float2(lg2_a(a.x), lg2_a(a.y)); }
+__device__ __forceinline__ f2 sel2(bool cx, bool cy, f2 a, f2 b) {
+  return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+__device__ __forceinline__ float comp(const f2& v, int c) { return c == 0 ? v.x : v.y; }
+__device__ __forceinline__ void put(f2& v, int c, float x) {
+  if (c == 0) v.x = x;
+  else v.y = x;
+}
+
+template <int N>
+__device__ __forceinline__ f2 horner2(const float (&c)[N], f2 u) {
+  f2 acc = F2(c[N - 1]);
+#pragma unroll
+  for (int k = N - 2; k >= 0; --k) acc = fma2(acc, u, F2(c[k]));
+  return acc;
+}
+// atan2(y, x) for y, x >= 0, per component (as atan2_pos).
+__device__ __forceinline__ f2 atan2_pos2(f2 y, f2 x) {
+  const f2 mx = max2(y, x), mn = min2(y, x);
+  const f2 z = mul2(mn, rcp2_pos(mx));
+  const f2 a = mul2(z, horner2(kAtan, mul2(z, z)));
+  const f2 b = sub2(F2(0.5f * kPiF), a);
+  return sel2(y.x > x.x, y.y > x.y, b, a);
+}
+__device__ __forceinline__ f2 sin_pi2_2(f2 d) { return mul2(d, horner2(kSin, mul2(d, d))); }
+__device__ __forceinline__ f2 omc_pi2_2(f2 d) {
+  const f2 u = mul2(d, d);
+  return mul2(u, horner2(kOmc, u));
+}
+
+// ---------------------------------------------------------------------------
+// Pair record: the per-stroke constants the paired loop reads, each duplicated
+// into both halves of a float2 so that it enters FFMA2 directly.  Built in
+// shared memory from the staged 128-byte records, once per chunk.
+// ---------------------------------------------------------------------------
+enum : int {
+  P_MX = 0, P_MY, P_EX, P_EY, P_HL, P_L, P_2L, P_L2, P_AR, P_R, P_IW, P_DLW,
+  P_NPR,     // -(pi r + L) = dC/dr
+  P_CR, P_CG, P_CB,
+  kPairRec   // 16 float2 = 128 bytes
+};
+
+__device__ __forceinline__ void pair_record_fill(const float* __restrict__ S, f2* __restrict__ P, int e) {
+  float v;
+  switch (e) {
+    case P_MX: v = S[F_MX]; break;
+    case P_MY: v = S[F_MY]; break;
+    case P_EX: v = S[F_EX]; break;
+    case P_EY: v = S[F_EY]; break;
+    case P_HL: v = S[F_HL]; break;
+    case P_L: v = S[F_L]; break;
+    case P_2L: v = S[F_2L]; break;
+    case P_L2: v = S[F_L2]; break;
+    case P_AR: v = S[F_AR]; break;
+    case P_R: v = S[F_R]; break;
+    case P_IW: v = S[F_IW]; break;
+    case P_DLW: v = S[F_DLW]; break;
+    case P_NPR: v = -fmaf(kPiF, S[F_R], S[F_L]); break;
+    case P_CR: v = S[F_CR]; break;
+    case P_CG: v = S[F_CG]; break;
+    case P_CB: v = S[F_CB]; break;
+    default: v = 0.0f; break;
+  }
+  P[e] = F2(v);
+}
+
+// Per-step quantities of one regeneration step for two pixels: the fields of
+// Geo with the flank conventions above, plus Q = L + pi sigma, Q' = L + pi
+// sigma' and their reciprocals (0 where the value is 0).
+struct Geo2 {
+  f2 sgs, sgh, si, hi, so, ho, sp, sig, tn, ud, uh, phi, sb, cb, beta;
+  f2 Q, Qp, iQ, iQp;
+};
+
+// x_i = Phi_i(x_{i-1}) for two pixels at frame points (s, h) of x_{i-1}, in the
+// displacement form of phi_local.  Returns a bit mask of the pixels whose step
+// goes from the flank onto a cap (bit c for component c); their outputs are
+// not valid and the caller recomputes them with phi_local.
+__device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Geo2& q, f2& ds, f2& dh) {
+  const f2 L = P[P_L], Ar = P[P_AR];
+  q.sgs = sgn2(s); q.sgh = sgn2(h); q.so = s; q.ho = h;
+  const f2 as = abs2(s), ah = abs2(h);
+  if (L.x == 0.0f) {  // drop: radial (warp-uniform branch)
+    q.sig = sqrt2(fma2(as, as, mul2(ah, ah)));
+    const f2 is = rcp2_pos(q.sig);
+    q.sb = mul2(as, is);
+    q.cb = sel2(q.sig.x > 0.0f, q.sig.y > 0.0f, mul2(ah, is), F2(1.0f));
+    q.beta = atan2_pos2(as, ah);
+    q.tn = mul2(q.sig, q.beta);
+    const f2 B = fma2(q.sig, mul2(F2(kPiF), q.sig), Ar);
+    q.sp = sqrt2(mul2(B, F2(1.0f / kPiF)));
+    const f2 dsp = mul2(Ar, rcp2(mul2(F2(kPiF), add2(q.sig, q.sp))));
+    q.phi = q.beta; q.ud = q.sb; q.uh = q.cb;
+    q.Q = mul2(F2(kPiF), q.sig);
+    q.Qp = mul2(F2(kPiF), q.sp);
+    q.iQ = rcp2_pos(q.Q);
+    q.iQp = rcp2(q.Qp);
+    ds = mul2(q.sgs, mul2(dsp, q.sb));
+    dh = mul2(q.sgh, mul2(dsp, q.cb));
+    q.si = add2(s, ds);
+    q.hi = add2(h, dh);
+    return 0;
+  }
+  const f2 hl = P[P_HL];
+  const f2 d = sub2(as, hl);
+  const bool capo_x = d.x > 0.0f, capo_y = d.y > 0.0f;
+  const f2 dp = max2(d, F2(0.0f));
+  q.sig = sqrt2(fma2(dp, dp, mul2(ah, ah)));
+  const f2 is = rcp2_pos(q.sig);
+  q.sb = mul2(dp, is);
+  q.cb = sel2(capo_x, capo_y, mul2(ah, is), F2(1.0f));
+  q.beta = atan2_pos2(dp, ah);
+  q.tn = fma2(q.sig, q.beta, min2(as, hl));
+  const f2 B = fma2(q.sig, fma2(F2(kPiF), q.sig, P[P_2L]), Ar);
+  q.sp = mul2(B, rcp2(add2(L, sqrt2(fma2(F2(kPiF), B, P[P_L2])))));
+  const f2 dsp = mul2(Ar, rcp2(fma2(F2(kPiF), add2(q.sig, q.sp), P[P_2L])));
+  q.Q = fma2(F2(kPiF), q.sig, L);
+  q.Qp = fma2(F2(kPiF), q.sp, L);
+  q.iQ = rcp2(q.Q);
+  q.iQp = rcp2(q.Qp);
+  const f2 t = mul2(q.tn, mul2(q.Qp, q.iQ));
+  const bool capi_x = t.x > hl.x, capi_y = t.y > hl.y;
+  // cap to cap: rotation by delta, clamped to the cap
+  const f2 room = sub2(F2(0.5f * kPiF), q.beta);
+  f2 delta = mul2(mul2(mul2(dsp, L), room), mul2(q.iQ, rcp2(q.sp)));
+  delta = min2(max2(delta, F2(0.0f)), room);
+  const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
+  const f2 cD = sub2(F2(1.0f), omc);
+  const f2 dSc = fma2(dsp, q.sb, mul2(q.sp, sub2(mul2(q.cb, sD), mul2(q.sb, omc))));
+  const f2 dHc = sub2(mul2(dsp, q.cb), mul2(q.sp, fma2(q.sb, sD, mul2(q.cb, omc))));
+  // flank to flank: translation along the flank
+  const f2 dSf = mul2(mul2(q.tn, F2(kPiF)), mul2(dsp, q.iQ));
+  const f2 dS = sel2(capo_x, capo_y, dSc, dSf);
+  const f2 dH = sel2(capo_x, capo_y, dHc, dsp);
+  q.ud = sel2(capo_x, capo_y, fma2(q.sb, cD, mul2(q.cb, sD)), F2(0.0f));
+  q.uh = sel2(capo_x, capo_y, sub2(mul2(q.cb, cD), mul2(q.sb, sD)), F2(1.0f));
+  q.phi = sel2(capo_x, capo_y, add2(q.beta, delta), F2(0.0f));
+  ds = mul2(q.sgs, dS);
+  dh = mul2(q.sgh, dH);
+  q.si = add2(s, ds);
+  q.hi = add2(h, dh);
+  return ((!capo_x && capi_x) ? 1 : 0) | ((!capo_y && capi_y) ? 2 : 0);
+}
+
+// Relaxed coverage (Eq. relax, logit form) for two pixels, as coverage().
+struct Cover2 {
+  f2 z, alpha, oma, dadz, sp2;
+};
+__device__ __forceinline__ Cover2 coverage2(f2 sp, const f2* __restrict__ P) {
+  Cover2 c;
+  const f2 zr = mul2(sub2(P[P_R], sp), P[P_IW]);
+  const bool clx = zr.x > kZMax, cly = zr.y > kZMax;
+  c.z = min2(zr, F2(kZMax));
+  const f2 e = ex22(mul2(abs2(c.z), F2(-kLog2e)));
+  const f2 opl = add2(F2(1.0f), e);
+  const f2 inv = rcp2(opl);
+  const f2 ei = mul2(e, inv);
+  const bool px = c.z.x >= 0.0f, py = c.z.y >= 0.0f;
+  c.alpha = sel2(px, py, inv, ei);
+  c.oma = sel2(px, py, ei, inv);
+  c.dadz = sel2(clx, cly, F2(0.0f), mul2(ei, inv));
+  c.sp2 = fma2(max2(c.z, F2(0.0f)), F2(kLog2e), lg22(opl));
+  return c;
+}
+
+// Frame coordinates of two hi/lo positions.
+__device__ __forceinline__ void to_frame2(f2 xh, f2 yh, f2 xl, f2 yl, const f2* __restrict__ P, f2& s, f2& h) {
+  const f2 dx = add2(sub2(xh, P[P_MX]), xl), dy = add2(sub2(yh, P[P_MY]), yl);
+  s = fma2(dx, P[P_EX], mul2(dy, P[P_EY]));
+  h = sub2(mul2(dy, P[P_EX]), mul2(dx, P[P_EY]));
+}
+__device__ __forceinline__ void pos_add2(f2& hi, f2& lo, f2 d) {
+  const f2 s = add2(hi, d);
+  lo = add2(lo, sub2(d, sub2(s, hi)));
+  hi = s;
+}
+__device__ __forceinline__ void add_frame_disp2(f2& xh, f2& yh, f2& xl, f2& yl, const f2* __restrict__ P, f2 ds,
+                                                f2 dh) {
+  pos_add2(xh, xl, sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY])));
+  pos_add2(yh, yl, fma2(ds, P[P_EY], mul2(dh, P[P_EX])));
+}
+
+// VJP of one regeneration step for two pixels: step_vjp with the flank
+// conventions folded in (no branch).  Regenerated samples are never floored.
+__device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ P, f2& lamx, f2& lamy, f2 mua, f2 z,
+                                          f2& gcx, f2& gcy, f2& gth, f2& gL, f2& gr) {
+  const f2 ex = P[P_EX], ey = P[P_EY];
+  const f2 ls = fma2(lamx, ex, mul2(lamy, ey));
+  const f2 lh = sub2(mul2(lamy, ex), mul2(lamx, ey));
+  const f2 gsn = mul2(q.sgs, ls), ghn = mul2(q.sgh, lh);
+  // x_{i-1}: cap point (sigma, beta) or flank point (tn, sigma)
+  f2 g_sig = fma2(gsn, q.sb, mul2(ghn, q.cb));
+  const f2 g_tn = sub2(mul2(gsn, q.cb), mul2(ghn, q.sb));
+  f2 g_hl = sub2(gsn, g_tn);
+  g_sig = sub2(g_sig, mul2(g_tn, q.beta));
+  // tn = t Q / Q': cotangents of t, Q and (minus) Q'
+  const f2 gtt = mul2(g_tn, q.tn);
+  const f2 g_t0 = mul2(mul2(g_tn, q.Q), q.iQp);
+  const f2 g_Q = mul2(gtt, q.iQ);
+  const f2 g_Qn = mul2(gtt, q.iQp);
+  f2 g_L = sub2(g_Q, g_Qn);
+  g_sig = fma2(F2(kPiF), g_Q, g_sig);
+  // sigma solves A_L(sigma) = C(sigma', r, L): d sigma/dC = 1/(2Q), d sigma/dL = -sigma/Q,
+  // dC/dsigma' = Q', dC/dr = -(pi r + L), dC/dL = 2(sigma' - r)
+  const f2 g_C2 = mul2(g_sig, q.iQ);  // twice the cotangent of C
+  g_L = sub2(g_L, mul2(g_C2, q.sig));
+  f2 g_sp = fma2(g_C2, q.Qp, mul2(F2(-kPiF), g_Qn));
+  f2 g_r = mul2(g_C2, P[P_NPR]);
+  g_L = fma2(g_C2, sub2(q.sp, P[P_R]), g_L);
+  // coverage alpha(z), z = (r - sigma') / w(r)
+  g_sp = sub2(g_sp, mul2(mua, P[P_IW]));
+  g_r = fma2(mua, sub2(P[P_IW], mul2(z, P[P_DLW])), g_r);
+  // t = L/2 + sigma' phi and sigma' = |(|s| - L/2, |h|)| on a cap; t = |s|, sigma' = |h| on the flank
+  g_hl = add2(g_hl, g_t0);
+  g_sp = fma2(g_t0, q.phi, g_sp);
+  const f2 g_d = fma2(g_sp, q.ud, mul2(g_t0, q.uh));
+  const f2 g_ah = sub2(mul2(g_sp, q.uh), mul2(g_t0, q.ud));
+  g_hl = sub2(g_hl, g_d);
+  g_L = fma2(F2(0.5f), g_hl, g_L);
+  const f2 GS = mul2(q.sgs, g_d), GH = mul2(q.sgh, g_ah);
+  const f2 nlx = sub2(mul2(GS, ex), mul2(GH, ey));
+  const f2 nly = fma2(GS, ey, mul2(GH, ex));
+  gcx = sub2(lamx, nlx);
+  gcy = sub2(lamy, nly);
+  gth = add2(sub2(mul2(q.so, lh), mul2(q.ho, ls)), sub2(mul2(GS, q.hi), mul2(GH, q.si)));
+  gL = g_L;
+  gr = g_r;
+  lamx = nlx;
+  lamy = nly;
+}
+
+// Thread -> pixel pair of a 32 x 16 tile: column lane, rows 2 warp and 2 warp + 1.
+constexpr int kPairTileW = 32, kPairTileH = 16;
+__device__ __forceinline__ void pair_tile_pixel(int tile, int W, int& px, int& py0) {
+  const int tiles_x = (W + kPairTileW - 1) / kPairTileW;
+  px = (tile % tiles_x) * kPairTileW + (threadIdx.x & 31);
+  py0 = (tile / tiles_x) * kPairTileH + 2 * (threadIdx.x >> 5);
+}
+
+// Adjoint state of one pixel in the scalar fallback.
+struct PixAdj {
+  float xh, yh, xl, yl;  // x_{i-1} (hi/lo), replaced by x_i
+  float lt;              // log2 T_{i-1}, replaced by log2 T_i
+  float lT;              // lambda^T
+  float lx, ly;          // lambda^x
+};
+
+// One stroke of the replay adjoint for one pixel in scalar arithmetic, as in
+// backward_tile: x_i from the side table (pop), from Phi_i followed by a reset
+// to the checkpoint (at_ck), or from Phi_i; log2 T_i from the checkpoint or
+// Eq. rT; then the adjoint step and the VJP, added to v.
+__device__ __forceinline__ void scalar_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S, float lC0,
+                                              float lC1, float lC2, bool pop, bool at_ck, bool valid, float4 rp,
+                                              float4 ckp, float ck_lt, unsigned& drift, float (&v)[8]) {
+  Geo gq;
+  float s, h, ds, dh;
+  if (pop) {
+    // x_i was within the floor's reach: read it back (Lemma "Support of the replay record")
+    a.xh = rp.x; a.yh = rp.y; a.xl = rp.z; a.yl = rp.w;
+    to_frame(a.xh, a.yh, a.xl, a.yl, g, s, h);
+    psi_local<true>(s, h, g, gq, ds, dh);
+  } else if (at_ck) {
+    // regenerate, measure the drift against the stored position, then reset to it
+    to_frame(a.xh, a.yh, a.xl, a.yl, g, s, h);
+    phi_local(s, h, g, gq, ds, dh);
+    add_frame_disp(a.xh, a.yh, a.xl, a.yl, g, ds, dh);
+    if (valid) {
+      if (fabsf((a.xh - ckp.x) + (a.xl - ckp.z)) > kDriftTol || fabsf((a.yh - ckp.y) + (a.yl - ckp.w)) > kDriftTol)
+        ++drift;
+      a.xh = ckp.x; a.yh = ckp.y; a.xl = ckp.z; a.yl = ckp.w;
+    }
+    to_frame(a.xh, a.yh, a.xl, a.yl, g, s, h);
+    psi_local<true>(s, h, g, gq, ds, dh);
+  } else {
+    to_frame(a.xh, a.yh, a.xl, a.yl, g, s, h);
+    phi_local(s, h, g, gq, ds, dh);
+    add_frame_disp(a.xh, a.yh, a.xl, a.yl, g, ds, dh);
+  }
+  const Cover cv = coverage(gq.sp, g);
+  if (at_ck) a.lt = ck_lt; else a.lt += cv.sp2;
+  const float T = ex2_a(a.lt);
+  const float lCc = fmaf(lC0, S[F_CR], fmaf(lC1, S[F_CG], lC2 * S[F_CB]));
+  const float mu = T * (lCc - a.lT);
+  const float Ta = T * cv.alpha;
+  v[5] = fmaf(lC0, Ta, v[5]); v[6] = fmaf(lC1, Ta, v[6]); v[7] = fmaf(lC2, Ta, v[7]);
+  float g0, g1, g2, g3, g4;
+  step_vjp(gq, g, a.lx, a.ly, mu * cv.dadz, cv.z, g0, g1, g2, g3, g4);
+  v[0] += g0; v[1] += g1; v[2] += g2; v[3] += g3; v[4] += g4;
+  a.lT = fmaf(cv.oma, a.lT, cv.alpha * lCc);
+}
+
+// Replay adjoint (Sec. 5.2) of a 32 x 16 tile, two pixels per thread, over
+// strokes 1 .. n; otherwise as backward_tile.  st[c], lC[c][.], valid[c] and
+// off[c] (the pixel's element offset in the replay record) describe pixel c of
+// the pair; an invalid pixel must carry a finite position and a zero
+// cotangent.  pbuf is shared [CH][kPairRec] float2.  All threads of the CTA
+// must call it.  Returns false if a bounded wait gave up.
+template <int CH>
+__device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, const bool (&valid)[2],
+                               const PixelState (&st)[2], const float (&lC)[2][3], const float bg[3],
+                               const RecordView& rv, const size_t (&off)[2], f2* __restrict__ pbuf,
+                               float (*red)[kTileThreads / 32][CH * 8], float* __restrict__ slice, bool first,
+                               unsigned& drift, unsigned long long* status) {
+  static_assert(CH * 8 == kTileThreads, "one partial per thread per chunk");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ck = rv.ck;
+  const bool any = valid[0] || valid[1];
+  f2 Xh = make_float2(st[0].xh, st[1].xh), Yh = make_float2(st[0].yh, st[1].yh);
+  f2 Xl = make_float2(st[0].xl, st[1].xl), Yl = make_float2(st[0].yl, st[1].yl);
+  f2 LT = make_float2(st[0].lt, st[1].lt);
+  const f2 LC0 = make_float2(lC[0][0], lC[1][0]), LC1 = make_float2(lC[0][1], lC[1][1]),
+           LC2 = make_float2(lC[0][2], lC[1][2]);
+  f2 LTT = fma2(LC0, F2(bg[0]), fma2(LC1, F2(bg[1]), mul2(LC2, F2(bg[2]))));
+  f2 LX = F2(0.0f), LY = F2(0.0f);
+  // side table, popped last-in first-out: rc[c] records left, nri[c] the stroke of the top one
+  int rc[2], nri[2];
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    rc[c] = valid[c] ? min(st[c].cnt, rv.cap) : 0;
+    nri[c] = rc[c] > 0 ? rv.rec_i[static_cast<size_t>(rc[c] - 1) * rv.stride + off[c]] : -1;
+  }
+  int next_ck = (ck < n) ? ck : 0;
+  const int nch = (n + CH - 1) / CH;
+  auto chunk_src = [&](int q) { return packed + static_cast<size_t>(q) * CH * kRec; };
+  auto chunk_cnt = [&](int q) { return min(CH, n - q * CH); };
+  if (threadIdx.x == 0) {
+    if (nch > 0) ring.issue(0, chunk_src(0), chunk_cnt(0));
+    if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
+  }
+  bool ok = true;
+  for (int q = 0; q < nch; ++q) {
+    const int b = q & 1;
+    const bool got = ring.wait(b, status);
+    if (__syncthreads_or(!got)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);
+      ok = false;
+      break;
+    }
+    const int cntc = chunk_cnt(q);
+    const float* S0 = ring.data(b);
+    for (int e = threadIdx.x; e < cntc * kPairRec; e += kTileThreads)
+      pair_record_fill(S0 + (e / kPairRec) * kRec, pbuf + (e / kPairRec) * kPairRec, e % kPairRec);
+    __syncthreads();
+    float (*rb)[CH * 8] = red[b];
+    for (int j = 0; j < cntc; ++j) {
+      const int i1 = q * CH + j + 1;
+      float vv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      const bool at_ck = (i1 == next_ck);  // CTA-uniform
+      size_t cko = 0;
+      if (at_ck) {
+        next_ck = (next_ck + ck < n) ? next_ck + ck : 0;
+        cko = static_cast<size_t>(i1 / ck - 1) * rv.stride;
+      }
+      if (any) {
+        const float* S = S0 + j * kRec;
+        const f2* P = pbuf + j * kPairRec;
+        const bool pop0 = i1 == nri[0], pop1 = i1 == nri[1];
+        bool scalar = at_ck || pop0 || pop1;
+        Geo2 gq;
+        f2 ds, dh;
+        if (!scalar) {
+          // x_i = Phi_i(x_{i-1}) (Eq. rpos), both pixels at once
+          f2 s, h;
+          to_frame2(Xh, Yh, Xl, Yl, P, s, h);
+          scalar = phi_pair(s, h, P, gq, ds, dh) != 0;  // flank to cap: redo this stroke per pixel
+        }
+        if (scalar) {
+          const StrokeF g = load_stroke(S);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const bool pop = c == 0 ? pop0 : pop1;
+            float4 rp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (pop) {
+              rp = rv.rec[static_cast<size_t>(rc[c] - 1) * rv.stride + off[c]];
+              --rc[c];
+              nri[c] = rc[c] > 0 ? rv.rec_i[static_cast<size_t>(rc[c] - 1) * rv.stride + off[c]] : -1;
+            }
+            float4 ckp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float ckl = 0.0f;
+            if (at_ck && valid[c]) {
+              ckp = rv.ckpt[cko + off[c]];
+              ckl = rv.ck_lt[cko + off[c]];
+            }
+            PixAdj a{comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c), comp(LT, c), comp(LTT, c),
+                     comp(LX, c), comp(LY, c)};
+            scalar_stroke(a, g, S, comp(LC0, c), comp(LC1, c), comp(LC2, c), pop, at_ck, valid[c], rp, ckp, ckl,
+                          drift, vv);
+            put(Xh, c, a.xh); put(Yh, c, a.yh); put(Xl, c, a.xl); put(Yl, c, a.yl);
+            put(LT, c, a.lt); put(LTT, c, a.lT); put(LX, c, a.lx); put(LY, c, a.ly);
+          }
+        } else {
+          add_frame_disp2(Xh, Yh, Xl, Yl, P, ds, dh);
+          const Cover2 cv = coverage2(gq.sp, P);
+          LT = add2(LT, cv.sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
+          const f2 T = ex22(LT);
+          const f2 lCc = fma2(LC0, P[P_CR], fma2(LC1, P[P_CG], mul2(LC2, P[P_CB])));
+          const f2 mu = mul2(T, sub2(lCc, LTT));
+          const f2 Ta = mul2(T, cv.alpha);
+          const f2 c5 = mul2(LC0, Ta), c6 = mul2(LC1, Ta), c7 = mul2(LC2, Ta);
+          f2 gcx, gcy, gth, gL, gr;
+          step_vjp2(gq, P, LX, LY, mul2(mu, cv.dadz), cv.z, gcx, gcy, gth, gL, gr);
+          LTT = fma2(cv.oma, LTT, mul2(cv.alpha, lCc));
+          vv[0] = gcx.x + gcx.y; vv[1] = gcy.x + gcy.y; vv[2] = gth.x + gth.y;
+          vv[3] = gL.x + gL.y; vv[4] = gr.x + gr.y;
+          vv[5] = c5.x + c5.y; vv[6] = c6.x + c6.y; vv[7] = c7.x + c7.y;
+        }
+      }
+      const float r = warp_reduce8(vv);
+      if ((lane & 3) == 0) rb[warp][j * 8 + ((lane >> 2) & 7)] = r;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
+    const int t = threadIdx.x;
+    if (t < cntc * 8) {
+      float sum = 0.0f;
+#pragma unroll
+      for (int w = 0; w < kTileThreads / 32; ++w) sum += rb[w][t];
+      float* dst = slice + static_cast<size_t>(q) * CH * 8 + t;
+      *dst = first ? sum : *dst + sum;
+    }
+  }
+  return ok;
+}
+
+}  // namespace tbr
