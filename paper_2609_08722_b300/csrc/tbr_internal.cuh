@@ -128,8 +128,9 @@ struct ChunkRing {
 };
 
 // ---------------------------------------------------------------------------
-// Fast arithmetic: single-instruction PTX approximations (reciprocal and square
-// root within 1-2 ulp, base-2 exponential / logarithm within ~2^-22) and
+// Fast arithmetic: single-instruction PTX approximations (reciprocal, square
+// root and reciprocal square root within 1-2 ulp, base-2 exponential /
+// logarithm within ~2^-22) and
 // polynomial atan / sin / 1-cos on the folded ranges the maps need
 // (tbr_poly.h, generated by gen_poly.py), so that the hot loops avoid the
 // multi-instruction IEEE division, square-root and range-reduction sequences.
@@ -142,6 +143,11 @@ __device__ __forceinline__ float rcp_a(float x) {
 __device__ __forceinline__ float sqrt_a(float x) {
   float r;
   asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_a(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ float ex2_a(float x) {
@@ -537,6 +543,9 @@ __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& 
 }
 
 // Relaxed coverage (Eq. relax) in the logit form used by both soft kernels.
+// With the logit clamped at z <= ln(1e7 - 1), e^z <= 1e7 stays finite, so
+// alpha = e^z / (1 + e^z) and 1 - alpha = 1 / (1 + e^z) are both free of
+// cancellation without a case split on the sign of z.
 struct Cover {
   float z;      // clamped logit
   float alpha;  // sigmoid(z)
@@ -548,15 +557,13 @@ __device__ __forceinline__ Cover coverage(float sp, const StrokeF& g) {
   Cover c;
   const float zr = (g.r - sp) * g.iw;
   const bool clamped = zr > kZMax;
-  c.z = clamped ? kZMax : zr;
-  const float e = ex2_a(-fabsf(c.z) * kLog2e);
-  const float opl = 1.0f + e;
-  const float inv = rcp_a(opl);
-  const bool pos = c.z >= 0.0f;
-  c.alpha = pos ? inv : e * inv;
-  c.oma = pos ? e * inv : inv;
-  c.dadz = clamped ? 0.0f : e * inv * inv;
-  c.sp2 = fmaf(fmaxf(c.z, 0.0f), kLog2e, lg2_a(opl));
+  c.z = fminf(zr, kZMax);
+  const float ez = ex2_a(c.z * kLog2e);
+  const float opl = 1.0f + ez;
+  c.oma = rcp_a(opl);
+  c.alpha = ez * c.oma;
+  c.dadz = clamped ? 0.0f : c.alpha * c.oma;
+  c.sp2 = lg2_a(opl);
   return c;
 }
 

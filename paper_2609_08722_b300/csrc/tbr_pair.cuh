@@ -31,6 +31,11 @@ __device__ __forceinline__ f2 rcp2(f2 a) { return make_float2(rcp_a(a.x), rcp_a(
 __device__ __forceinline__ f2 rcp2_pos(f2 a) {
   return make_float2(a.x > 0.0f ? rcp_a(a.x) : 0.0f, a.y > 0.0f ? rcp_a(a.y) : 0.0f);
 }
+// Smallest argument of the guarded reciprocals below: x * rsqrt(max(x, kTiny))
+// is sqrt(x) for x >= kTiny and 0 at x = 0; mn * rcp(max(mx, kTiny)) is 0 when
+// 0 <= mn <= mx < kTiny.
+constexpr float kTiny = 1e-36f;
+__device__ __forceinline__ f2 rsqrt2(f2 a) { return make_float2(rsqrt_a(a.x), rsqrt_a(a.y)); }
 __device__ __forceinline__ f2 ex22(f2 a) { return make_float2(ex2_a(a.x), ex2_a(a.y)); }
 __device__ __forceinline__ f2 lg22(f2 a) { return make_float2(lg2_a(a.x), lg2_a(a.y)); }
 __device__ __forceinline__ f2 sel2(bool cx, bool cy, f2 a, f2 b) {
@@ -52,7 +57,7 @@ __device__ __forceinline__ f2 horner2(const float (&c)[N], f2 u) {
 // atan2(y, x) for y, x >= 0, per component (as atan2_pos).
 __device__ __forceinline__ f2 atan2_pos2(f2 y, f2 x) {
   const f2 mx = max2(y, x), mn = min2(y, x);
-  const f2 z = mul2(mn, rcp2_pos(mx));
+  const f2 z = mul2(mn, rcp2(max2(mx, F2(kTiny))));
   const f2 a = mul2(z, horner2(kAtan, mul2(z, z)));
   const f2 b = sub2(F2(0.5f * kPiF), a);
   return sel2(y.x > x.x, y.y > x.y, b, a);
@@ -116,10 +121,11 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   q.sgs = sgn2(s); q.sgh = sgn2(h); q.so = s; q.ho = h;
   const f2 as = abs2(s), ah = abs2(h);
   if (L.x == 0.0f) {  // drop: radial (warp-uniform branch)
-    q.sig = sqrt2(fma2(as, as, mul2(ah, ah)));
-    const f2 is = rcp2_pos(q.sig);
+    const f2 x2 = fma2(as, as, mul2(ah, ah));
+    const f2 is = rsqrt2(max2(x2, F2(kTiny)));  // 1 / sigma
+    q.sig = mul2(x2, is);
     q.sb = mul2(as, is);
-    q.cb = sel2(q.sig.x > 0.0f, q.sig.y > 0.0f, mul2(ah, is), F2(1.0f));
+    q.cb = sel2(x2.x > 0.0f, x2.y > 0.0f, mul2(ah, is), F2(1.0f));
     q.beta = atan2_pos2(as, ah);
     q.tn = mul2(q.sig, q.beta);
     const f2 B = fma2(q.sig, mul2(F2(kPiF), q.sig), Ar);
@@ -140,8 +146,9 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   const f2 d = sub2(as, hl);
   const bool capo_x = d.x > 0.0f, capo_y = d.y > 0.0f;
   const f2 dp = max2(d, F2(0.0f));
-  q.sig = sqrt2(fma2(dp, dp, mul2(ah, ah)));
-  const f2 is = rcp2_pos(q.sig);
+  const f2 x2 = fma2(dp, dp, mul2(ah, ah));
+  const f2 is = rsqrt2(max2(x2, F2(kTiny)));  // 1 / sigma
+  q.sig = mul2(x2, is);
   q.sb = mul2(dp, is);
   q.cb = sel2(capo_x, capo_y, mul2(ah, is), F2(1.0f));
   q.beta = atan2_pos2(dp, ah);
@@ -155,21 +162,22 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   q.iQp = rcp2(q.Qp);
   const f2 t = mul2(q.tn, mul2(q.Qp, q.iQ));
   const bool capi_x = t.x > hl.x, capi_y = t.y > hl.y;
-  // cap to cap: rotation by delta, clamped to the cap
+  // cap to cap: rotation by delta, clamped to the cap.  On the flank delta = 0,
+  // and with (sb, cb, beta) = (0, 1, 0) the cap formulas give dH = dsigma',
+  // (ud, uh, phi) = (0, 1, 0); only dS needs the flank's own form.
   const f2 room = sub2(F2(0.5f * kPiF), q.beta);
   f2 delta = mul2(mul2(mul2(dsp, L), room), mul2(q.iQ, rcp2(q.sp)));
-  delta = min2(max2(delta, F2(0.0f)), room);
+  delta = sel2(capo_x, capo_y, min2(max2(delta, F2(0.0f)), room), F2(0.0f));
   const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
   const f2 cD = sub2(F2(1.0f), omc);
   const f2 dSc = fma2(dsp, q.sb, mul2(q.sp, sub2(mul2(q.cb, sD), mul2(q.sb, omc))));
-  const f2 dHc = sub2(mul2(dsp, q.cb), mul2(q.sp, fma2(q.sb, sD, mul2(q.cb, omc))));
+  const f2 dH = sub2(mul2(dsp, q.cb), mul2(q.sp, fma2(q.sb, sD, mul2(q.cb, omc))));
   // flank to flank: translation along the flank
   const f2 dSf = mul2(mul2(q.tn, F2(kPiF)), mul2(dsp, q.iQ));
   const f2 dS = sel2(capo_x, capo_y, dSc, dSf);
-  const f2 dH = sel2(capo_x, capo_y, dHc, dsp);
-  q.ud = sel2(capo_x, capo_y, fma2(q.sb, cD, mul2(q.cb, sD)), F2(0.0f));
-  q.uh = sel2(capo_x, capo_y, sub2(mul2(q.cb, cD), mul2(q.sb, sD)), F2(1.0f));
-  q.phi = sel2(capo_x, capo_y, add2(q.beta, delta), F2(0.0f));
+  q.ud = fma2(q.sb, cD, mul2(q.cb, sD));
+  q.uh = sub2(mul2(q.cb, cD), mul2(q.sb, sD));
+  q.phi = add2(q.beta, delta);
   ds = mul2(q.sgs, dS);
   dh = mul2(q.sgh, dH);
   q.si = add2(s, ds);
@@ -186,15 +194,12 @@ __device__ __forceinline__ Cover2 coverage2(f2 sp, const f2* __restrict__ P) {
   const f2 zr = mul2(sub2(P[P_R], sp), P[P_IW]);
   const bool clx = zr.x > kZMax, cly = zr.y > kZMax;
   c.z = min2(zr, F2(kZMax));
-  const f2 e = ex22(mul2(abs2(c.z), F2(-kLog2e)));
-  const f2 opl = add2(F2(1.0f), e);
-  const f2 inv = rcp2(opl);
-  const f2 ei = mul2(e, inv);
-  const bool px = c.z.x >= 0.0f, py = c.z.y >= 0.0f;
-  c.alpha = sel2(px, py, inv, ei);
-  c.oma = sel2(px, py, ei, inv);
-  c.dadz = sel2(clx, cly, F2(0.0f), mul2(ei, inv));
-  c.sp2 = fma2(max2(c.z, F2(0.0f)), F2(kLog2e), lg22(opl));
+  const f2 ez = ex22(mul2(c.z, F2(kLog2e)));
+  const f2 opl = add2(F2(1.0f), ez);
+  c.oma = rcp2(opl);
+  c.alpha = mul2(ez, c.oma);
+  c.dadz = sel2(clx, cly, F2(0.0f), mul2(c.alpha, c.oma));
+  c.sp2 = lg22(opl);
   return c;
 }
 

@@ -133,6 +133,25 @@ def test_soft_ragged(small, W, H):
         assert rel(g[k].cpu().numpy().ravel(), og[k].ravel()) <= GRAD_TOL, k
 
 
+@pytest.mark.parametrize("W,H", [(75, 61), (64, 33)])
+def test_backward_long_strokes(W, H):
+    """No drops and strokes up to 0.8 long: most samples sit beside a flank,
+    and many steps cross from a flank onto a cap (the paired kernel's
+    per-pixel fallback)."""
+    p = inputs.make_program(120, seed=311, palette_seed=312, k=8, r_lo=0.004, r_hi=0.04, len_max=0.8, p_drop=0.0)
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    cot = inputs.make_cotangent(313, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    for k in GROUPS:
+        e = rel(g[k].cpu().numpy().ravel(), og[k].ravel())
+        print(f"{k}: {e:.3e}")
+        assert e <= GRAD_TOL, k
+
+
 @pytest.mark.parametrize("tau,tau_min,inert", [(0.0, 1 / 200, False), (0.3, 0.01, False),
                                                (0.3, 0.01, True)])
 def test_backward_small_program(small, tau, tau_min, inert):
