@@ -363,7 +363,7 @@ def run_native(args):
         e2e = {"value": sum_over_ranks(units, world, device) / (e2e_ms * 1e-3), "unit": "evals/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
 
-    # loss-fused forward + adjoint (tbr_render_soft_adjoint_mse): same work, record kept in L2
+    # loss-fused forward + adjoint (tbr_render_soft_adjoint_mse): the same kernels behind one call
     fused = None
     if not args.no_e2e:
         for _ in range(2):

@@ -377,7 +377,7 @@ enum {
   TBR_K_LOSS = 5,        /* MSE and adjoint seed */
   TBR_K_UPDATE = 6,      /* Adam update */
   TBR_K_SERVE = 7,       /* persistent serving kernel */
-  TBR_K_FUSED = 8,       /* loss-fused soft forward + replay adjoint */
+  TBR_K_FUSED = 8,       /* reserved: the loss-fused entry point launches the kernels above */
   TBR_K_COUNT = 9
 };
 typedef struct {

@@ -64,24 +64,21 @@ cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy
 // Reads the status words (synchronising) and maps them to a tbr_status.
 tbr_status ctx_read_status(tbr_ctx* c, unsigned long long host[ST_COUNT]);
 
-// Buffers of the loss-fused forward + adjoint (tbr_fused.cu).
+// Buffers of the loss-fused forward + adjoint (tbr_fused.cu): a replay context
+// plus the colour, the MSE seed and the loss partials.
 struct FusedWork {
-  int n = 0, k = 0, W = 0, H = 0, ck = 64, cap = 64, grid = 0;
-  float* packed = nullptr;
-  float* probs = nullptr;
-  float* palette = nullptr;
-  unsigned long long* status = nullptr;
-  float4* rec = nullptr;
-  int* rec_i = nullptr;
-  float4* ckpt = nullptr;
-  float* ck_lt = nullptr;
-  float* partial = nullptr;
-  float* grad8 = nullptr;
-  double* loss_part = nullptr;
+  tbr_ctx ctx;
+  float* rgb = nullptr;                  // [P][3] when the caller keeps no colour
+  float* dLdR = nullptr;                 // [P][3] MSE seed
+  double* loss_part = nullptr;           // [nblk] FP64 loss partials
+  float* loss_tmp = nullptr;             // [1] loss when the caller keeps none
+  unsigned long long* status = nullptr;  // the context's status words
+  int nblk = 0, cap = 0;
   size_t bytes = 0;
   cudaError_t allocate(int n, int k, int W, int H, int ck, int cap, cudaStream_t st);
   void release(cudaStream_t st);
-  // pack + fused kernel + gradient epilogue + loss; status words reset first.
+  // pack + soft forward + MSE and seed + replay adjoint + gradient epilogue;
+  // status words reset first.
   cudaError_t run(const tbr_program* prog, float tau, float tau_min, const float* target, float* out_rgb,
                   float* loss_out, float* g_cx, float* g_cy, float* g_th, float* g_len, float* g_r,
                   float* g_logits, float* g_pal, cudaStream_t st);

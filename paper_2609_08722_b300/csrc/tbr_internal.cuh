@@ -13,15 +13,20 @@ namespace tbr {
 
 // ---------------------------------------------------------------------------
 // Packed stroke record: 32 floats (128 B) per stroke, built once per call by
-// k_pack (tbr_pack.cu) and staged into shared memory chunk by chunk.
+// k_pack (tbr_pack.cu) and staged into shared memory chunk by chunk.  The first
+// 16 floats are the constants the paired adjoint loop reads (tbr_pair.cuh
+// duplicates them into float2 pairs in this order), the next two the forward's
+// floor constants.
 // ---------------------------------------------------------------------------
 constexpr int kRec = 32;
 enum : int {
   F_MX = 0, F_MY = 1, F_EX = 2, F_EY = 3,    // centre m, direction e
-  F_HL = 4, F_L = 5, F_R = 6, F_R2 = 7,      // L/2, L, r, r^2
-  F_L2 = 8, F_KA = 9, F_AR = 10, F_FL2 = 11, // L^2, 2L + pi r, A_L(r) = 2Lr + pi r^2, (eps r)^2
-  F_CR = 12, F_CG = 13, F_CB = 14, F_IW = 15,// colour c_i, 1 / max(tau r, tau_min)
-  F_DLW = 16, F_TH = 17, F_BAD = 18, F_2L = 19, // (dw/dr)/w, theta, invalid flag, 2L
+  F_HL = 4, F_L = 5, F_2L = 6, F_L2 = 7,     // L/2, L, 2L, L^2
+  F_AR = 8, F_R = 9, F_IW = 10, F_DLW = 11,  // A_L(r) = 2Lr + pi r^2, r, 1 / max(tau r, tau_min), (dw/dr)/w
+  F_NPR = 12,                                // -(pi r + L) = dC/dr
+  F_CR = 13, F_CG = 14, F_CB = 15,           // colour c_i
+  F_KA = 16, F_FL2 = 17,                     // 2L + pi r, (eps r)^2
+  F_TH = 18, F_BAD = 19,                     // theta, invalid flag
   F_D64 = 20                                 // 6 doubles: mx, my, ex, ey, L/2, r (FP64 band)
 };
 
@@ -187,19 +192,18 @@ __device__ __forceinline__ float omc_pi2(float d) {
 // Stroke fields read from shared memory as broadcasts.
 // ---------------------------------------------------------------------------
 struct StrokeF {
-  float mx, my, ex, ey, hl, L, r, r2, L2, kA, Ar, fl2, iw, dlw, twoL;
+  float mx, my, ex, ey, hl, L, r, L2, kA, Ar, fl2, iw, dlw, twoL;
 };
 __device__ __forceinline__ StrokeF load_stroke(const float* __restrict__ S) {
-  const float4 a = *reinterpret_cast<const float4*>(S);
-  const float4 b = *reinterpret_cast<const float4*>(S + 4);
-  const float4 c = *reinterpret_cast<const float4*>(S + 8);
-  const float4 d = *reinterpret_cast<const float4*>(S + 12);
-  const float4 e = *reinterpret_cast<const float4*>(S + 16);
+  const float4 a = *reinterpret_cast<const float4*>(S + F_MX);
+  const float4 b = *reinterpret_cast<const float4*>(S + F_HL);
+  const float4 c = *reinterpret_cast<const float4*>(S + F_AR);
+  const float2 e = *reinterpret_cast<const float2*>(S + F_KA);
   StrokeF g;
   g.mx = a.x; g.my = a.y; g.ex = a.z; g.ey = a.w;
-  g.hl = b.x; g.L = b.y; g.r = b.z; g.r2 = b.w;
-  g.L2 = c.x; g.kA = c.y; g.Ar = c.z; g.fl2 = c.w;
-  g.iw = d.w; g.dlw = e.x; g.twoL = e.w;
+  g.hl = b.x; g.L = b.y; g.twoL = b.z; g.L2 = b.w;
+  g.Ar = c.x; g.r = c.y; g.iw = c.z; g.dlw = c.w;
+  g.kA = e.x; g.fl2 = e.y;
   return g;
 }
 
@@ -684,25 +688,6 @@ cudaError_t launch_loss(const float* rgb, const float* target, int64_t npix, dou
 // loss_out[0] = (sum of the nparts FP64 partials, in order) / nval.
 cudaError_t launch_loss_final(const double* partial, int nparts, int64_t nval, float* loss_out, cudaStream_t st);
 
-struct FusedArgs {
-  const float* packed;
-  int n, W, H;
-  float bg[3];
-  int ck, cap;
-  const float* target;       // [P][3]
-  float* out_rgb;            // [P][3] or NULL
-  float4* rec;               // per-CTA scratch [grid][cap][256]
-  int* rec_i;
-  float4* ckpt;              // per-CTA scratch [grid][(n-1)/ck][256]
-  float* ck_lt;
-  float* partial;            // [grid][n][8]
-  double* loss_part;         // [grid]
-  int grid;
-  float seed_scale;          // 2 / (3P)
-  unsigned long long* status;
-};
-int fused_grid(int W, int H);
-cudaError_t launch_fused(const FusedArgs& a, cudaStream_t st);
 int loss_blocks(int64_t npix);
 
 }  // namespace tbr

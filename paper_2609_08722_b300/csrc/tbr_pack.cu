@@ -50,17 +50,17 @@ __global__ void k_pack(const float* __restrict__ cx, const float* __restrict__ c
   float* R = packed + static_cast<size_t>(i) * kRec;
   R[F_MX] = fx; R[F_MY] = fy;
   R[F_EX] = static_cast<float>(dex); R[F_EY] = static_cast<float>(dey);
-  R[F_HL] = 0.5f * fL; R[F_L] = fL; R[F_R] = fr; R[F_R2] = fr * fr;
-  R[F_L2] = fL * fL;
-  R[F_KA] = static_cast<float>(2.0 * fL + kPiD * fr);
+  R[F_HL] = 0.5f * fL; R[F_L] = fL; R[F_2L] = 2.0f * fL; R[F_L2] = fL * fL;
   R[F_AR] = static_cast<float>((2.0 * fL + kPiD * fr) * fr);
-  R[F_FL2] = (kEpsFloor * fr) * (kEpsFloor * fr);
-  R[F_CR] = c0; R[F_CG] = c1; R[F_CB] = c2;
+  R[F_R] = fr;
   R[F_IW] = 1.0f / w;
   R[F_DLW] = (tau * fr > tau_min) ? tau / w : 0.0f;
+  R[F_NPR] = static_cast<float>(-(kPiD * fr + fL));
+  R[F_CR] = c0; R[F_CG] = c1; R[F_CB] = c2;
+  R[F_KA] = static_cast<float>(2.0 * fL + kPiD * fr);
+  R[F_FL2] = (kEpsFloor * fr) * (kEpsFloor * fr);
   R[F_TH] = fth;
   R[F_BAD] = bad ? 1.0f : 0.0f;
-  R[F_2L] = 2.0f * fL;
   double* D = reinterpret_cast<double*>(R + F_D64);
   D[0] = fx; D[1] = fy; D[2] = dex; D[3] = dey; D[4] = 0.5 * static_cast<double>(fL);
   D[5] = fr;

@@ -69,39 +69,34 @@ __device__ __forceinline__ f2 omc_pi2_2(f2 d) {
 }
 
 // ---------------------------------------------------------------------------
-// Pair record: the per-stroke constants the paired loop reads, each duplicated
-// into both halves of a float2 so that it enters FFMA2 directly.  Built in
-// shared memory from the staged 128-byte records, once per chunk.
+// Pair record: the per-stroke constants the paired loops read, each duplicated
+// into both halves of a float2 so that it enters FFMA2 directly.  They are the
+// first 16 floats of the packed record, in its order (128 bytes of pairs per
+// stroke); the forward also reads the floor constants (KA, FL2) from a
+// separate 2-entry array.  Built in shared memory once per staged chunk by a
+// plain strided copy.  (A 144-byte record, and a fill that branched per field,
+// each measured about 5% slower in the adjoint loop.)
 // ---------------------------------------------------------------------------
 enum : int {
-  P_MX = 0, P_MY, P_EX, P_EY, P_HL, P_L, P_2L, P_L2, P_AR, P_R, P_IW, P_DLW,
-  P_NPR,     // -(pi r + L) = dC/dr
-  P_CR, P_CG, P_CB,
-  kPairRec   // 16 float2 = 128 bytes
+  P_MX = F_MX, P_MY = F_MY, P_EX = F_EX, P_EY = F_EY, P_HL = F_HL, P_L = F_L, P_2L = F_2L, P_L2 = F_L2,
+  P_AR = F_AR, P_R = F_R, P_IW = F_IW, P_DLW = F_DLW, P_NPR = F_NPR, P_CR = F_CR, P_CG = F_CG, P_CB = F_CB,
+  kPairRec = 16,
+  X_KA = F_KA - kPairRec, X_FL2 = F_FL2 - kPairRec,
+  kPairExt = 2
 };
+static_assert(P_CB == kPairRec - 1 && X_FL2 == kPairExt - 1, "pair record = packed floats 0..17");
 
-__device__ __forceinline__ void pair_record_fill(const float* __restrict__ S, f2* __restrict__ P, int e) {
-  float v;
-  switch (e) {
-    case P_MX: v = S[F_MX]; break;
-    case P_MY: v = S[F_MY]; break;
-    case P_EX: v = S[F_EX]; break;
-    case P_EY: v = S[F_EY]; break;
-    case P_HL: v = S[F_HL]; break;
-    case P_L: v = S[F_L]; break;
-    case P_2L: v = S[F_2L]; break;
-    case P_L2: v = S[F_L2]; break;
-    case P_AR: v = S[F_AR]; break;
-    case P_R: v = S[F_R]; break;
-    case P_IW: v = S[F_IW]; break;
-    case P_DLW: v = S[F_DLW]; break;
-    case P_NPR: v = -fmaf(kPiF, S[F_R], S[F_L]); break;
-    case P_CR: v = S[F_CR]; break;
-    case P_CG: v = S[F_CG]; break;
-    case P_CB: v = S[F_CB]; break;
-    default: v = 0.0f; break;
+// All threads: fill the pair records of the cnt strokes staged at S0 (and, with
+// EXT, the forward's extension).  The caller synchronises before use.
+template <bool EXT>
+__device__ __forceinline__ void pair_records_fill(const float* __restrict__ S0, int cnt, f2* __restrict__ pbuf,
+                                                  f2* __restrict__ pext) {
+  for (int e = threadIdx.x; e < cnt * kPairRec; e += kTileThreads)
+    pbuf[e] = F2(S0[(e / kPairRec) * kRec + (e % kPairRec)]);
+  if (EXT) {
+    for (int e = threadIdx.x; e < cnt * kPairExt; e += kTileThreads)
+      pext[e] = F2(S0[(e / kPairExt) * kRec + kPairRec + (e % kPairExt)]);
   }
-  P[e] = F2(v);
 }
 
 // Per-step quantities of one regeneration step for two pixels: the fields of
@@ -183,6 +178,67 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   q.si = add2(s, ds);
   q.hi = add2(h, dh);
   return ((!capo_x && capi_x) ? 1 : 0) | ((!capo_y && capi_y) ? 2 : 0);
+}
+
+// x_{i-1} = psi_i(x_i) for two pixels at frame points (s, h) of x_i (L > 0),
+// in the displacement form of psi_local<true>.  Outputs sigma' (the distance of
+// x_i) and the frame displacement.  Returns a bit mask of the pixels that the
+// floor touches or whose step leaves a cap for the flank; their outputs are not
+// valid and the caller recomputes them with psi_local<true>.
+__device__ __forceinline__ int psi_pair(f2 s, f2 h, const f2* __restrict__ P, const f2* __restrict__ X, f2& sp,
+                                        f2& ds, f2& dh) {
+  const f2 L = P[P_L], hl = P[P_HL];
+  const f2 as = abs2(s), ah = abs2(h);
+  const f2 d = sub2(as, hl);
+  const bool ci_x = d.x > 0.0f, ci_y = d.y > 0.0f;
+  const f2 dp = max2(d, F2(0.0f));
+  const f2 x2 = fma2(dp, dp, mul2(ah, ah));
+  const f2 is = rsqrt2(max2(x2, F2(kTiny)));  // 1 / sigma'
+  sp = mul2(x2, is);
+  const f2 ud = mul2(dp, is);
+  const f2 uh = sel2(ci_x, ci_y, mul2(ah, is), F2(1.0f));
+  const f2 phi = atan2_pos2(dp, ah);
+  const f2 t = fma2(sp, phi, min2(as, hl));
+  const f2 C = mul2(sub2(sp, P[P_R]), fma2(F2(kPiF), sp, X[X_KA]));
+  const bool fl_x = C.x < X[X_FL2].x, fl_y = C.y < X[X_FL2].y;
+  const f2 sig = mul2(C, rcp2(add2(L, sqrt2(fma2(F2(kPiF), C, P[P_L2])))));
+  const f2 Q = fma2(F2(kPiF), sig, L), iQp = rcp2(fma2(F2(kPiF), sp, L));
+  // sigma' - sigma = A_L(r) / (2L + pi (sigma' + sigma))
+  const f2 nds = mul2(P[P_AR], rcp2(fma2(F2(kPiF), add2(sp, sig), P[P_2L])));
+  const f2 tn = mul2(t, mul2(Q, iQp));
+  const bool co_x = tn.x > hl.x, co_y = tn.y > hl.y;
+  // cap to cap: rotation by delta = (sigma' - sigma) L (phi - pi/2) / (Q' sigma) in [-phi, 0];
+  // on the flank delta = 0 and (ud, uh) = (0, 1), so dH is the flank's -(sigma' - sigma)
+  f2 delta = mul2(mul2(mul2(nds, L), sub2(phi, F2(0.5f * kPiF))), mul2(iQp, rcp2(sig)));
+  delta = sel2(ci_x, ci_y, min2(max2(delta, mul2(phi, F2(-1.0f))), F2(0.0f)), F2(0.0f));
+  const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
+  const f2 dSc = sub2(mul2(sig, sub2(mul2(uh, sD), mul2(ud, omc))), mul2(nds, ud));
+  const f2 dH = mul2(F2(-1.0f), fma2(sig, fma2(ud, sD, mul2(uh, omc)), mul2(nds, uh)));
+  // flank to flank: tangential step |s| pi (sigma - sigma') / Q'
+  const f2 dSf = mul2(mul2(as, F2(-kPiF)), mul2(nds, iQp));
+  const f2 dS = sel2(ci_x, ci_y, dSc, dSf);
+  ds = mul2(sgn2(s), dS);
+  dh = mul2(sgn2(h), dH);
+  return ((fl_x || (ci_x && !co_x)) ? 1 : 0) | ((fl_y || (ci_y && !co_y)) ? 2 : 0);
+}
+
+// Drop (L = 0) pull-back for two pixels at world offsets (dx, dy) from the
+// centre, as drop_step<true>.  Outputs rho = sigma' and the world
+// displacement; returns the mask of pixels the floor touches (recomputed by the
+// caller with drop_step<true>).
+__device__ __forceinline__ int drop_pair(f2 dx, f2 dy, const f2* __restrict__ P, const f2* __restrict__ X, f2& rho,
+                                         f2& ddx, f2& ddy) {
+  const f2 x2 = fma2(dx, dx, mul2(dy, dy));
+  const f2 is = rsqrt2(max2(x2, F2(kTiny)));
+  rho = mul2(x2, is);
+  const f2 C = mul2(sub2(rho, P[P_R]), fma2(F2(kPiF), rho, X[X_KA]));
+  const bool fl_x = C.x < X[X_FL2].x, fl_y = C.y < X[X_FL2].y;
+  const f2 sig = sqrt2(mul2(C, F2(1.0f / kPiF)));
+  // (sigma - rho) / rho with sigma - rho = -A_0(r) / (pi (rho + sigma))
+  const f2 k = mul2(mul2(P[P_AR], F2(-1.0f / kPiF)), mul2(rcp2(add2(rho, sig)), is));
+  ddx = mul2(k, dx);
+  ddy = mul2(k, dy);
+  return (fl_x ? 1 : 0) | (fl_y ? 2 : 0);
 }
 
 // Relaxed coverage (Eq. relax, logit form) for two pixels, as coverage().
@@ -270,11 +326,131 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
 }
 
 // Thread -> pixel pair of a 32 x 16 tile: column lane, rows 2 warp and 2 warp + 1.
-constexpr int kPairTileW = 32, kPairTileH = 16;
 __device__ __forceinline__ void pair_tile_pixel(int tile, int W, int& px, int& py0) {
   const int tiles_x = (W + kPairTileW - 1) / kPairTileW;
   px = (tile % tiles_x) * kPairTileW + (threadIdx.x & 31);
   py0 = (tile / tiles_x) * kPairTileH + 2 * (threadIdx.x >> 5);
+}
+
+// Soft forward (Eq. relax, Eq. state, floored psi) of a 32 x 16 tile, two
+// pixels per thread, over strokes n-1 .. 0; otherwise as soft_forward_tile
+// (exterior-transport model).  x0/y0[c], valid[c] and off[c] describe pixel c
+// of the pair; an invalid pixel still carries a finite position.  pbuf and pext
+// are shared [CH][kPairRec] and [CH][kPairExt] float2.  All threads of the CTA
+// must call it.
+template <int CH, bool RECORD>
+__device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n,
+                                   const bool (&valid)[2], const float (&x0)[2], const float (&y0)[2],
+                                   const RecordView& rv, const size_t (&off)[2], f2* __restrict__ pbuf,
+                                   f2* __restrict__ pext, PixelState (&st)[2], unsigned long long* status) {
+  const bool any = valid[0] || valid[1];
+  f2 Xh = make_float2(x0[0], x0[1]), Yh = make_float2(y0[0], y0[1]);
+  f2 Xl = F2(0.0f), Yl = F2(0.0f), LT = F2(0.0f);
+  f2 C0 = F2(0.0f), C1 = F2(0.0f), C2 = F2(0.0f);
+  int cnt[2] = {0, 0};
+  const int ck = rv.ck;
+  int next_ck = (RECORD && n > 1) ? ((n - 1) / ck) * ck : 0;  // largest checkpoint index < n
+  const int nch = (n + CH - 1) / CH;
+  auto chunk_src = [&](int q) { return packed + static_cast<size_t>(nch - 1 - q) * CH * kRec; };
+  auto chunk_cnt = [&](int q) { return min(CH, n - (nch - 1 - q) * CH); };
+  if (threadIdx.x == 0) {
+    if (nch > 0) ring.issue(0, chunk_src(0), chunk_cnt(0));
+    if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
+  }
+  bool ok = true;
+  for (int q = 0; q < nch; ++q) {
+    const int b = q & 1;
+    const bool got = ring.wait(b, status);
+    if (__syncthreads_or(!got)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);
+      ok = false;
+      break;
+    }
+    const int base = (nch - 1 - q) * CH;
+    const int cntc = chunk_cnt(q);
+    const float* S0 = ring.data(b);
+    pair_records_fill<true>(S0, cntc, pbuf, pext);
+    __syncthreads();
+    if (any) {
+      for (int j = cntc - 1; j >= 0; --j) {
+        const int i1 = base + j + 1;  // the paper's 1-based stroke index
+        if (RECORD && i1 == next_ck) {
+          const size_t o = static_cast<size_t>(i1 / ck - 1) * rv.stride;
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (valid[c]) {
+              rv.ckpt[o + off[c]] = make_float4(comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c));
+              rv.ck_lt[o + off[c]] = comp(LT, c);
+            }
+          }
+          next_ck -= ck;
+        }
+        const f2* P = pbuf + j * kPairRec;
+        const f2* X = pext + j * kPairExt;
+        const f2 dx = add2(sub2(Xh, P[P_MX]), Xl), dy = add2(sub2(Yh, P[P_MY]), Yl);
+        const bool drop = P[P_L].x == 0.0f;  // warp-uniform
+        f2 sp, ddx, ddy;
+        int fix;
+        if (drop) {
+          fix = drop_pair(dx, dy, P, X, sp, ddx, ddy);
+        } else {
+          const f2 s = fma2(dx, P[P_EX], mul2(dy, P[P_EY]));
+          const f2 h = sub2(mul2(dy, P[P_EX]), mul2(dx, P[P_EY]));
+          f2 ds, dh;
+          fix = psi_pair(s, h, P, X, sp, ds, dh);
+          ddx = sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY]));
+          ddy = fma2(ds, P[P_EY], mul2(dh, P[P_EX]));
+        }
+        if (fix) {  // floored or cap to flank: scalar step per pixel
+          const StrokeF g = load_stroke(S0 + j * kRec);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            if (fix & (1 << c)) {
+              const float dxc = comp(dx, c), dyc = comp(dy, c);
+              float spc, ddxc, ddyc;
+              bool floored;
+              if (drop) {
+                spc = drop_step<true>(dxc, dyc, g, ddxc, ddyc, floored);
+              } else {
+                const float s = fmaf(dxc, g.ex, dyc * g.ey), h = fmaf(dyc, g.ex, -dxc * g.ey);
+                Geo gq;
+                float ds, dh;
+                psi_local<true>(s, h, g, gq, ds, dh);
+                spc = gq.sp;
+                floored = gq.floored;
+                ddxc = fmaf(ds, g.ex, -dh * g.ey);
+                ddyc = fmaf(ds, g.ey, dh * g.ex);
+              }
+              put(sp, c, spc); put(ddx, c, ddxc); put(ddy, c, ddyc);
+              if (RECORD && floored && valid[c]) {
+                if (cnt[c] < rv.cap) {
+                  const size_t o = static_cast<size_t>(cnt[c]) * rv.stride + off[c];
+                  rv.rec[o] = make_float4(comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c));
+                  rv.rec_i[o] = i1;
+                }
+                ++cnt[c];
+              }
+            }
+          }
+        }
+        const Cover2 cv = coverage2(sp, P);
+        const f2 w = mul2(ex22(LT), cv.alpha);
+        C0 = fma2(w, P[P_CR], C0);
+        C1 = fma2(w, P[P_CG], C1);
+        C2 = fma2(w, P[P_CB], C2);
+        LT = sub2(LT, cv.sp2);  // log2 T_{i-1} = log2 T_i + log2(1 - alpha_i)
+        pos_add2(Xh, Xl, ddx);
+        pos_add2(Yh, Yl, ddy);
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
+  }
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+    st[c] = PixelState{comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c), comp(LT, c), cnt[c],
+                       comp(C0, c), comp(C1, c), comp(C2, c)};
+  return ok;
 }
 
 // Adjoint state of one pixel in the scalar fallback.
@@ -378,8 +554,7 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
     }
     const int cntc = chunk_cnt(q);
     const float* S0 = ring.data(b);
-    for (int e = threadIdx.x; e < cntc * kPairRec; e += kTileThreads)
-      pair_record_fill(S0 + (e / kPairRec) * kRec, pbuf + (e / kPairRec) * kPairRec, e % kPairRec);
+    pair_records_fill<false>(S0, cntc, pbuf, nullptr);
     __syncthreads();
     float (*rb)[CH * 8] = red[b];
     for (int j = 0; j < cntc; ++j) {
@@ -426,16 +601,17 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
             scalar_stroke(a, g, S, comp(LC0, c), comp(LC1, c), comp(LC2, c), pop, at_ck, valid[c], rp, ckp, ckl,
                           drift, vv);
             put(Xh, c, a.xh); put(Yh, c, a.yh); put(Xl, c, a.xl); put(Yl, c, a.yl);
-            put(LT, c, a.lt); put(LTT, c, a.lT); put(LX, c, a.lx); put(LY, c, a.ly);
+            put(LT, c, a.lt);
+            put(LTT, c, a.lT); put(LX, c, a.lx); put(LY, c, a.ly);
           }
         } else {
           add_frame_disp2(Xh, Yh, Xl, Yl, P, ds, dh);
           const Cover2 cv = coverage2(gq.sp, P);
           LT = add2(LT, cv.sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
-          const f2 T = ex22(LT);
+          const f2 Ti = ex22(LT);
           const f2 lCc = fma2(LC0, P[P_CR], fma2(LC1, P[P_CG], mul2(LC2, P[P_CB])));
-          const f2 mu = mul2(T, sub2(lCc, LTT));
-          const f2 Ta = mul2(T, cv.alpha);
+          const f2 mu = mul2(Ti, sub2(lCc, LTT));
+          const f2 Ta = mul2(Ti, cv.alpha);
           const f2 c5 = mul2(LC0, Ta), c6 = mul2(LC1, Ta), c7 = mul2(LC2, Ta);
           f2 gcx, gcy, gth, gL, gr;
           step_vjp2(gq, P, LX, LY, mul2(mu, cv.dadz), cv.z, gcx, gcy, gth, gL, gr);

@@ -142,8 +142,7 @@ size_t request_bytes(const tbr_server* s, const tbr_request& r, int n, int k) {
   size_t b = n_out * kRec * 4 + ST_COUNT * 8;
   if (r.kind >= TBR_REQ_RECOLOUR) b += (5 * n_out + n_out * k) * 4;
   if (r.kind == TBR_REQ_SOFT_ADJOINT) {
-    const int tiles = ((r.W + kTileW - 1) / kTileW) * ((r.H + kTileH - 1) / kTileH);
-    const int groups = std::min(tiles, s->grid);
+    const int groups = std::min(pair_tile_count(r.W, r.H), s->grid);
     b += n_out * k * 4 + static_cast<size_t>(groups) * n_out * 32 + static_cast<size_t>(groups) * 8 + n_out * 32;
   }
   return b;
@@ -167,8 +166,9 @@ tbr_status admit(tbr_server* s, Request& q) {
   const int k = pg.k;
   q.n = n_out; q.k = k;
   q.kind = (r.kind == TBR_REQ_SOFT_ADJOINT) ? kServeSoft : kServeHard;
-  const int tiles = ((r.W + kTileW - 1) / kTileW) * ((r.H + kTileH - 1) / kTileH);
-  const int n_items = q.kind == kServeHard ? tiles : std::min(tiles, s->grid);
+  // a hard request is one item per 32x8 tile; a soft request one item per CTA-sized
+  // group of 32x16 tiles
+  const int n_items = q.kind == kServeHard ? tile_count(r.W, r.H) : std::min(pair_tile_count(r.W, r.H), s->grid);
   // the caller's inputs (and the zeroing of its outputs, if any) precede the work
   cudaError_t e = q.ready ? cudaStreamWaitEvent(st, q.ready, 0) : cudaSuccess;
   const float* params = pg.params;
@@ -430,7 +430,7 @@ tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** out) {
   }
   s->grid = serve_grid();
   s->nck_max = c.max_strokes > 1 ? static_cast<size_t>((c.max_strokes - 1) / c.checkpoint_every) : 0;
-  const size_t per = static_cast<size_t>(s->grid) * kTileThreads;
+  const size_t per = static_cast<size_t>(s->grid) * 2 * kTileThreads;  // pixels per record slot, all CTAs
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->next_item), sizeof(long long));
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->items_done), sizeof(int) * kServeMaxSlots);
   if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->idle_flags), 2 * sizeof(int));

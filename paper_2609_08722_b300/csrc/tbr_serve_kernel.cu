@@ -1,15 +1,16 @@
 // Persistent serving kernel (continuous batching of hard renders, edits and
 // soft render + adjoint requests).  The host copies request descriptors into a
 // ring in device memory and then advances a published-item counter in mapped
-// pinned memory (read only when a CTA runs out of known work); each
-// CTA claims the next item with a compare-and-swap on a device counter, runs it
-// (a 32x8 hard tile, or a group of soft tiles fused with the MSE seed and the
-// replay adjoint), and the CTA that finishes a request's last item finalises
-// signals completion through mapped memory (the host then runs the fixed-order
-// gradient sums of a soft request as ordinary kernels).  Every wait is bounded; the kernel exits after idle_ns without work
-// and the host relaunches it when new work is published.
+// pinned memory (read only when a CTA runs out of known work); each CTA claims
+// the next item with a compare-and-swap on a device counter and runs it: a
+// 32x8 hard tile, or a group of 32x16 soft tiles (two pixels per thread)
+// fused with the MSE seed and the replay adjoint.  The CTA that finishes a
+// request's last item signals completion through mapped memory (the host then
+// runs the fixed-order gradient sums of a soft request as ordinary kernels).
+// Every wait is bounded; the kernel exits after idle_ns without work and the
+// host relaunches it when new work is published.
 #include "tbr_serve.h"
-#include "tbr_tile.cuh"
+#include "tbr_pair.cuh"
 
 namespace tbr {
 
@@ -19,10 +20,15 @@ constexpr int kServeCH = 32;
 
 __device__ __forceinline__ long long ld_volatile_ll(const volatile long long* p) { return *p; }
 
-__global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
+// Three CTAs per SM (the register cap this implies costs the paired adjoint a
+// few spills); the host leaves one CTA slot per SM to the packing and edit
+// kernels of newly admitted requests.
+__global__ void __launch_bounds__(kTileThreads, 3) k_serve(ServeArgs a) {
   __shared__ __align__(128) float sbuf[2 * kServeCH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
   __shared__ float red[2][kTileThreads / 32][kServeCH * 8];
+  __shared__ __align__(16) f2 pbuf[kServeCH * kPairRec];
+  __shared__ __align__(16) f2 pext[kServeCH * kPairExt];
   __shared__ double lsum[kTileThreads / 32];
   __shared__ ServeDesc sd;
   __shared__ long long s_item;
@@ -120,48 +126,57 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_serve(ServeArgs a) {
       ok = hard_tile<kServeCH>(ring, d.packed, d.n, static_cast<int>(local), d.W, d.H, d.bg, poison, d.out_rgb,
                                d.out_idx, band, visited, background, d.status);
     } else {
-      // soft render + MSE seed + replay adjoint over tiles local, local + G, ...
-      const int ntiles = ((d.W + kTileW - 1) / kTileW) * ((d.H + kTileH - 1) / kTileH);
-      const size_t nck = d.n > 1 ? static_cast<size_t>((d.n - 1) / d.ck) : 0;
-      RecordView rv{a.rec + cta * a.cap * kTileThreads, a.rec_i + cta * a.cap * kTileThreads,
-                    a.ckpt + cta * a.nck_max * kTileThreads, a.ck_lt + cta * a.nck_max * kTileThreads,
-                    static_cast<size_t>(kTileThreads), static_cast<size_t>(threadIdx.x), d.cap, d.ck};
-      (void)nck;
+      // soft render + MSE seed + replay adjoint over 32x16 tiles local, local + G, ...
+      const int ntiles = pair_tile_count(d.W, d.H);
+      constexpr size_t kSlot = 2 * kTileThreads;  // pixels per record slot of one CTA
+      const RecordView rv{a.rec + cta * a.cap * kSlot, a.rec_i + cta * a.cap * kSlot,
+                          a.ckpt + cta * a.nck_max * kSlot, a.ck_lt + cta * a.nck_max * kSlot, kSlot, 0, d.cap,
+                          d.ck};
+      const size_t off[2] = {static_cast<size_t>(threadIdx.x), static_cast<size_t>(threadIdx.x) + kTileThreads};
       float* slice = d.partial + static_cast<size_t>(local) * d.n * 8;
       const bool skip = d.status[ST_INVALID] != 0ull;
       double lacc = 0.0;
       unsigned drift = 0, ovf = 0;
       bool first = true;
       for (int tile = static_cast<int>(local); tile < ntiles; tile += d.n_items) {
-        int px, py;
-        tile_pixel(tile, d.W, px, py);
-        const bool valid = px < d.W && py < d.H && !skip;
-        const size_t p = valid ? static_cast<size_t>(py) * d.W + px : 0;
-        PixelState st;
-        if (!soft_forward_tile<kServeCH, true, false>(ring, d.packed, d.n, valid,
-                                                      (static_cast<float>(px) + 0.5f) / static_cast<float>(d.W),
-                                                      (static_cast<float>(py) + 0.5f) / static_cast<float>(d.H),
-                                                      rv, st, d.status)) {
+        int px, py0;
+        pair_tile_pixel(tile, d.W, px, py0);
+        bool valid[2];
+        size_t p[2];
+        float x0[2], y0[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int py = py0 + c;
+          valid[c] = px < d.W && py < d.H && !skip;
+          p[c] = valid[c] ? static_cast<size_t>(py) * d.W + px : 0;
+          x0[c] = (static_cast<float>(px) + 0.5f) / static_cast<float>(d.W);
+          y0[c] = (static_cast<float>(py) + 0.5f) / static_cast<float>(d.H);
+        }
+        PixelState st[2];
+        if (!soft_forward_tile2<kServeCH, true>(ring, d.packed, d.n, valid, x0, y0, rv, off, pbuf, pext, st, d.status)) {
           ok = false;
           break;
         }
-        float lC0 = 0.0f, lC1 = 0.0f, lC2 = 0.0f;
-        if (valid) {
-          const float T0 = ex2_a(st.lt);
-          const float R0 = fmaf(T0, d.bg[0], st.C0), R1 = fmaf(T0, d.bg[1], st.C1),
-                      R2 = fmaf(T0, d.bg[2], st.C2);
+        float lC[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (!valid[c]) continue;
+          const size_t q = p[c];
+          const float T0 = ex2_a(st[c].lt);
+          const float R0 = fmaf(T0, d.bg[0], st[c].C0), R1 = fmaf(T0, d.bg[1], st[c].C1),
+                      R2 = fmaf(T0, d.bg[2], st[c].C2);
           if (d.out_rgb) {
-            d.out_rgb[3 * p + 0] = R0;
-            d.out_rgb[3 * p + 1] = R1;
-            d.out_rgb[3 * p + 2] = R2;
+            d.out_rgb[3 * q + 0] = R0;
+            d.out_rgb[3 * q + 1] = R1;
+            d.out_rgb[3 * q + 2] = R2;
           }
-          const float e0 = R0 - d.target[3 * p + 0], e1 = R1 - d.target[3 * p + 1], e2 = R2 - d.target[3 * p + 2];
+          const float e0 = R0 - d.target[3 * q + 0], e1 = R1 - d.target[3 * q + 1], e2 = R2 - d.target[3 * q + 2];
           lacc += static_cast<double>(e0) * e0 + static_cast<double>(e1) * e1 + static_cast<double>(e2) * e2;
-          lC0 = d.seed_scale * e0; lC1 = d.seed_scale * e1; lC2 = d.seed_scale * e2;
-          if (st.cnt > d.cap) ++ovf;
+          lC[c][0] = d.seed_scale * e0; lC[c][1] = d.seed_scale * e1; lC[c][2] = d.seed_scale * e2;
+          if (st[c].cnt > d.cap) ++ovf;
         }
-        if (!backward_tile<kServeCH, false>(ring, d.packed, d.n, valid, st, lC0, lC1, lC2, d.bg, rv, red, slice,
-                                            first, drift, d.status)) {
+        if (!backward_tile2<kServeCH>(ring, d.packed, d.n, valid, st, lC, d.bg, rv, off, pbuf, red, slice, first,
+                                      drift, d.status)) {
           ok = false;
           break;
         }

@@ -6,6 +6,9 @@
 // When recording: a sample the floor touched pushes (x_i, i) onto the pixel's
 // side table (Lemma "Support of the replay record"), every k-th stroke stores
 // (x_i, log2 T_i), and s_0 = (x_0, log2 T_0, record count) closes the pixel.
+// (A two-pixels-per-thread variant of this loop, as the adjoint uses, measured
+// slower here: the forward's per-pixel selects and MUFU work do not pair, and
+// the scalar loop keeps 40 warps per SM resident against 24.)
 #include <math.h>
 
 #include "tbr_tile.cuh"
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
 }  // namespace
 
 cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
-  const int tiles = ((a.W + kTileW - 1) / kTileW) * ((a.H + kTileH - 1) / kTileH);
+  const int tiles = tile_count(a.W, a.H);
   const bool rec = a.s0 != nullptr;
   KernelTimer kt(TBR_K_SOFT, st);
   if (rec && a.inert) k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);

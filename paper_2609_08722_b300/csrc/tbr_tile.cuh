@@ -9,6 +9,14 @@
 namespace tbr {
 
 constexpr int kTileW = 32, kTileH = 8, kTileThreads = 256;
+// Tiles of the soft kernels that carry two pixels per thread (32 x 16).
+constexpr int kPairTileW = 32, kPairTileH = 16;
+__host__ __device__ inline int tile_count(int W, int H) {
+  return ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+}
+__host__ __device__ inline int pair_tile_count(int W, int H) {
+  return ((W + kPairTileW - 1) / kPairTileW) * ((H + kPairTileH - 1) / kPairTileH);
+}
 
 // Where one pixel's replay record lives: element (slot, pixel) of each array is
 // at slot * stride + off.  The plain kernels use [slot][P] with off = pixel;

@@ -1,7 +1,9 @@
 """Serving (continuous batching in one persistent kernel): each request's result
-is the same alone and in a mix, equals the plain entry points, edits render the
-edited program, admission respects the memory cap, and the kernel is
-relaunched after it exits idle."""
+is the same alone and in a mix, hard requests equal the plain entry point bit
+for bit and soft requests match it to FP32 rounding (the serving kernel runs the
+soft forward two pixels per thread from a per-CTA record, the plain path one
+pixel per thread), edits render the edited program, admission respects the
+memory cap, and the kernel is relaunched after it exits idle."""
 import time
 
 import numpy as np
@@ -77,8 +79,8 @@ def test_soft_request_matches_the_fused_entry_point(server, programs):
     assert server.wait(rid) == tbr.TBR_OK
     loss_f, g_f, rgb_f, _ = tbr.soft_adjoint_mse(dp, target, 0.0, 1 / 200, want_rgb=True)
     torch.cuda.synchronize()
-    assert torch.equal(rgb, rgb_f)
-    assert abs(loss.item() - loss_f.item()) <= 1e-6 * abs(loss_f.item())
+    assert (rgb - rgb_f).abs().max().item() <= 1e-5
+    assert abs(loss.item() - loss_f.item()) <= 1e-5 * abs(loss_f.item())
     g = split_grad(grad, dp.n, dp.k)
     for k in GROUPS:
         assert rel(g[k].cpu().numpy().ravel(), g_f[k].cpu().numpy().ravel()) <= 1e-4, k
