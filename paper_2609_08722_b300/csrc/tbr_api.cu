@@ -6,6 +6,8 @@
 #include <cstring>
 #include <string>
 
+#include <atomic>
+
 #include "tbr_host.h"
 
 namespace tbr {
@@ -43,6 +45,20 @@ tbr_status check_program(const tbr_program* p, int n_used) {
     return fail(TBR_ERR_INVALID_ARG, "NULL stroke array");
   if (!p->palette) return fail(TBR_ERR_INVALID_ARG, "palette is NULL");
   return TBR_OK;
+}
+
+void retain_pool_memory() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  const unsigned long long bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    unsigned long long threshold = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &threshold);
+  }
+  done.fetch_or(bit, std::memory_order_acq_rel);
 }
 
 tbr_status check_size(int32_t W, int32_t H) {

@@ -39,10 +39,17 @@ tbr_status cuda_fail(cudaError_t e, const char* what);
 tbr_status check_program(const tbr_program* p, int n_used);
 tbr_status check_size(int32_t W, int32_t H);
 
+// Keeps memory freed by cudaFreeAsync in the current device's default pool
+// (release threshold = unlimited, set once per device in this process), so the
+// allocating entry points reuse it across calls instead of returning it to the
+// driver at every synchronisation.
+void retain_pool_memory();
+
 template <class T>
 cudaError_t dalloc(T** p, size_t count, cudaStream_t st) {
   *p = nullptr;
   if (count == 0) return cudaSuccess;
+  retain_pool_memory();
   return cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
 }
 template <class T>

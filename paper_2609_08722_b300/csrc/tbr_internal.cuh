@@ -209,13 +209,23 @@ __device__ __forceinline__ StrokeF load_stroke(const float* __restrict__ S) {
 
 // ---------------------------------------------------------------------------
 // Positions are carried as unevaluated float pairs x = hi + lo: the local
-// frame coordinate is formed as (hi - m) + lo, and each stroke adds its
-// displacement with a two-sum, so the FP32 rounding of a step is of the order
-// of the (small) displacement rather than of the coordinate itself.
+// frame coordinate is formed as (hi - m) + lo.  The soft loops add each
+// stroke's displacement to lo alone (one add on the loop-carried chain) and
+// fold lo into hi with a TwoSum every kRenorm strokes, so |lo| stays within a
+// few displacements and its rounding is far below ulp(hi).  pos_add is the
+// per-step two-sum used by the hard render and the rare scalar steps.
 // ---------------------------------------------------------------------------
+constexpr int kRenorm = 16;
 __device__ __forceinline__ void pos_add(float& hi, float& lo, float d) {
   const float s = hi + d;
   lo += d - (s - hi);  // exact error of hi + d when |hi| >= |d|
+  hi = s;
+}
+// hi + lo -> (hi, lo) with |lo| <= ulp(hi) / 2 (TwoSum, exact for any magnitudes).
+__device__ __forceinline__ void pos_renorm(float& hi, float& lo) {
+  const float s = hi + lo;
+  const float bp = s - hi;
+  lo = (hi - (s - bp)) + (lo - bp);
   hi = s;
 }
 

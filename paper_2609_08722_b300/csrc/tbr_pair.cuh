@@ -265,15 +265,17 @@ __device__ __forceinline__ void to_frame2(f2 xh, f2 yh, f2 xl, f2 yl, const f2* 
   s = fma2(dx, P[P_EX], mul2(dy, P[P_EY]));
   h = sub2(mul2(dy, P[P_EX]), mul2(dx, P[P_EY]));
 }
-__device__ __forceinline__ void pos_add2(f2& hi, f2& lo, f2 d) {
-  const f2 s = add2(hi, d);
-  lo = add2(lo, sub2(d, sub2(s, hi)));
+// pos_renorm for two positions.
+__device__ __forceinline__ void pos_renorm2(f2& hi, f2& lo) {
+  const f2 s = add2(hi, lo);
+  const f2 bp = sub2(s, hi);
+  lo = add2(sub2(hi, sub2(s, bp)), sub2(lo, bp));
   hi = s;
 }
-__device__ __forceinline__ void add_frame_disp2(f2& xh, f2& yh, f2& xl, f2& yl, const f2* __restrict__ P, f2 ds,
-                                                f2 dh) {
-  pos_add2(xh, xl, sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY])));
-  pos_add2(yh, yl, fma2(ds, P[P_EY], mul2(dh, P[P_EX])));
+// Adds a frame displacement to the lo parts of two hi/lo positions.
+__device__ __forceinline__ void add_frame_disp2(f2& xl, f2& yl, const f2* __restrict__ P, f2 ds, f2 dh) {
+  xl = add2(xl, sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY])));
+  yl = add2(yl, fma2(ds, P[P_EY], mul2(dh, P[P_EX])));
 }
 
 // VJP of one regeneration step for two pixels: step_vjp with the flank
@@ -439,8 +441,12 @@ __device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict_
         C1 = fma2(w, P[P_CG], C1);
         C2 = fma2(w, P[P_CB], C2);
         LT = sub2(LT, cv.sp2);  // log2 T_{i-1} = log2 T_i + log2(1 - alpha_i)
-        pos_add2(Xh, Xl, ddx);
-        pos_add2(Yh, Yl, ddy);
+        Xl = add2(Xl, ddx);
+        Yl = add2(Yl, ddy);
+        if ((i1 & (kRenorm - 1)) == 1) {
+          pos_renorm2(Xh, Xl);
+          pos_renorm2(Yh, Yl);
+        }
       }
     }
     __syncthreads();
@@ -605,7 +611,11 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
             put(LTT, c, a.lT); put(LX, c, a.lx); put(LY, c, a.ly);
           }
         } else {
-          add_frame_disp2(Xh, Yh, Xl, Yl, P, ds, dh);
+          add_frame_disp2(Xl, Yl, P, ds, dh);
+          if ((i1 & (kRenorm - 1)) == 0) {
+            pos_renorm2(Xh, Xl);
+            pos_renorm2(Yh, Yl);
+          }
           const Cover2 cv = coverage2(gq.sp, P);
           LT = add2(LT, cv.sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
           const f2 Ti = ex22(LT);

@@ -126,8 +126,12 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
             }
             ++st.cnt;
           }
-          pos_add(st.xh, st.xl, ddx);
-          pos_add(st.yh, st.yl, ddy);
+          st.xl += ddx;
+          st.yl += ddy;
+          if ((i1 & (kRenorm - 1)) == 1) {
+            pos_renorm(st.xh, st.xl);
+            pos_renorm(st.yh, st.yl);
+          }
         }
       }
     }
