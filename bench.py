@@ -34,15 +34,19 @@ CHECKPOINT_EVERY = 64
 # Algorithmic FP32 work per pixel-stroke (FP32 arithmetic instructions: add, mul
 # and fused multiply-add each count 1; transcendental / reciprocal operations are
 # counted separately), counted from the step formulas of the kernels at this
-# workload's measured branch mix (95% of steps on a capsule cap).  Derivation
-# table in DESIGN.md ("Roofline").
+# workload's measured branch mix (95% of steps on a capsule cap): forward =
+# frame + distance 9, coverage + compositing 11, radial root 7, tangential map
+# 7, back to world 6 (cap path); adjoint = Phi regeneration 31, coverage +
+# adjoint step 21, VJP of psi and alpha 61, reduce-scatter 9 (cap path).
 OPS_FWD = 40.6
 OPS_BWD = 120.8
 XU_FWD = 11.8
 XU_BWD = 15.7
-# FP32 lane peak: 148 SMs x 128 FP32 lanes x 2032 MHz (one op per lane per cycle).
-SMS, LANES, SM_MAX_MHZ = 148, 128, 2032.0
+# FP32 lane peak: 148 SMs x 128 FP32 lanes x 2032 MHz (one op per lane per cycle);
+# XU (MUFU) peak: 16 results per clock per SM (4 per sub-partition).
+SMS, LANES, SM_MAX_MHZ, XU_PER_SM = 148, 128, 2032.0, 16
 PEAK_GOPS = SMS * LANES * SM_MAX_MHZ * 1e-3
+PEAK_XU_GOPS = SMS * XU_PER_SM * SM_MAX_MHZ * 1e-3
 
 METRIC = "pixel·stroke evals/s fwd+adjoint @2000 strokes 1024²"
 
@@ -58,6 +62,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fit-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-hard", action="store_true", help="skip the hard-render resolution sweep")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving stream (0 skips the serving measurement)")
     ap.add_argument("--res", type=int, default=RES, help="square resolution (profiling cases only)")
@@ -397,6 +402,32 @@ def run_native(args):
         fit_ms = fs.elapsed_time(fe) / args.fit_steps
         fit.destroy()
 
+    # hard render of one 2000-stroke program at 512^2 .. 4096^2: nominal P*N/s and
+    # executed (visited pixel-steps)/s, device time by CUDA events, L2 flushed first
+    hard = None
+    if rank == 0 and not args.no_hard and args.res == RES and args.strokes == N_STROKES:
+        hp = tbr.DeviceProgram.from_host(inputs.resolution_program(), device)
+        hard = []
+        for r in (512, 1024, 2048, 4096):
+            rgb_h = torch.empty((r, r, 3), device=device)
+            idx_h = torch.empty((r, r), dtype=torch.int32, device=device)
+            _, _, st_h = tbr.render_hard(hp, r, r, stats=True, out_rgb=rgb_h, out_idx=idx_h)
+            ts = []
+            for i in range(3):
+                flush.fill_(float(i))
+                hs, he = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                hs.record()
+                tbr.render_hard(hp, r, r, out_rgb=rgb_h, out_idx=idx_h)
+                he.record()
+                torch.cuda.synchronize()
+                ts.append(hs.elapsed_time(he))
+            hms = sum(ts) / len(ts)
+            hard.append({"res": r, "ms": hms, "nominal_evals_per_s": r * r * hp.n / (hms * 1e-3),
+                         "executed_evals_per_s": st_h["visited_steps"] / (hms * 1e-3),
+                         "visited_steps_per_pixel": st_h["visited_steps"] / (r * r),
+                         "fp64_band_steps": st_h["band_steps"], "background_pixels": st_h["background_pixels"]})
+            del rgb_h, idx_h
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.res == RES and args.strokes == N_STROKES:
         rate, info = oracle_rate(prog_h, args.cpu_seconds)
@@ -426,12 +457,18 @@ def run_native(args):
             "roofline": {"bound": "alu", "kernel": "k_backward (replay adjoint)", "achieved": achieved,
                          "peak": PEAK_GOPS, "unit": "Gop/s", "frac": achieved / PEAK_GOPS,
                          "traffic": traffic, "ops_per_unit": OPS_BWD,
+                         "xu": {"ops_per_unit": XU_BWD, "achieved": XU_BWD * units / (bwd_ms * 1e-3) * 1e-9,
+                                "peak": PEAK_XU_GOPS, "frac": XU_BWD * units / (bwd_ms * 1e-3) * 1e-9 / PEAK_XU_GOPS,
+                                "peak_basis": "148 SMs x 16 MUFU results per clock x 2032 MHz"},
+                         "combined_bound_frac": max(OPS_BWD / PEAK_GOPS, XU_BWD / PEAK_XU_GOPS) * units * 1e-9
+                                                / (bwd_ms * 1e-3),
                          "peak_basis": "148 SMs x 128 FP32 lanes x 2032 MHz (recipe unit counts and clock)"},
             "kernel_ms": {"backward": bwd_ms, "soft_forward": soft_ms,
                           "other": step_ms - bwd_ms - soft_ms},
             "fit_step_ms": fit_ms,
             "fused_path": fused,
             "serve": serve,
+            "hard": hard,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,

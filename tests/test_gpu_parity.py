@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
 
-Tolerances (see the design doc for the derivation):
+Tolerances:
   * hard render: terminating stroke index bit-exact except pixels whose oracle
     margin min_j |sigma'_j - r_j| < 1e-5 (counted); a mismatch outside that band
     is accepted only where the oracle's chain condition kappa makes an FP32
