@@ -138,6 +138,13 @@ typedef struct {
                                conditioning); 0 = library default (32) */
   int32_t record_capacity;  /* side-table records per pixel; 0 = default (64) */
   int32_t inert;            /* 1: psi = id (inert-mark model, Definition 1) */
+  float drift_tolerance;    /* FP32 regeneration drift at a checkpoint (canvas
+                               units) above which the pixel's segment is
+                               regenerated in FP64 by the adjoint (Sec. 5.2
+                               conditioning); <= 0 = default (1e-5) */
+  int32_t repair_capacity;  /* pixels the adjoint can repair per call, at most
+                               1024; 0 = default (256).  Memory: 32 B x n per
+                               pixel of capacity. */
 } tbr_soft_opts;
 
 typedef struct tbr_ctx tbr_ctx;
@@ -163,7 +170,10 @@ TBR_API tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H
  * (Eq. rpos), or pop it from the side table, or reset it from a checkpoint;
  * regenerate log T_i (Eq. rT); take the adjoint step (Eq. adjstep) and
  * accumulate the parameter gradients (Eq. adjparam) of
- * J = sum_pixels dL_drgb . R.
+ * J = sum_pixels dL_drgb . R.  A pixel whose FP32 regeneration drifts past the
+ * drift tolerance at a checkpoint is replayed again from the start of that
+ * segment with its positions regenerated in FP64, and its gradient
+ * contributions from there on are replaced (counted in repaired_pixels).
  *   dL_drgb   [H][W][3] cotangent of the rendered image
  *   g_*       [n] gradients w.r.t. cx, cy, theta, length, half_width (written)
  *   g_logits  [n][k] (written)
@@ -180,9 +190,14 @@ struct tbr_ctx_stats {
   int64_t max_records;      /* largest per-pixel record count */
   int64_t overflow_pixels;  /* pixels whose records exceeded the capacity */
   int64_t drift_resets;     /* checkpoint resets where the regenerated position
-                               differed from the stored one by more than 1e-5 */
+                               differed from the stored one by more than the
+                               drift tolerance */
   int64_t timeouts;         /* bounded waits that gave up */
   int64_t invalid_params;   /* strokes that failed the value checks */
+  int64_t repaired_pixels;  /* pixels whose drifting segment (and the rest of
+                               their replay) the adjoint regenerated in FP64 */
+  int64_t repair_overflow;  /* drifting pixels when they outnumbered the repair
+                               capacity (then none is repaired) */
 };
 typedef struct tbr_ctx_stats tbr_ctx_stats;
 

@@ -68,11 +68,13 @@ tbr_status check_size(int32_t W, int32_t H) {
   return TBR_OK;
 }
 
-cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert,
-                         cudaStream_t st) {
+cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert, float drift_tol,
+                         int repair_cap, cudaStream_t st) {
   const size_t P = static_cast<size_t>(W) * H;
   c->n = n; c->k = k; c->W = W; c->H = H;
   c->ck = ck; c->cap = cap; c->inert = inert;
+  c->drift_tol = drift_tol;
+  c->repair_cap = inert ? 0 : repair_cap;
   c->grid = backward_grid(W, H, inert);
   c->last_stream = st;
   const size_t nck = n > 1 ? static_cast<size_t>((n - 1) / ck) : 0;
@@ -88,10 +90,17 @@ cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap
   if (e == cudaSuccess && !inert) e = dalloc(&c->rec_i, static_cast<size_t>(cap) * P, st);
   if (e == cudaSuccess) e = dalloc(&c->partial, static_cast<size_t>(c->grid) * n * 8, st);
   if (e == cudaSuccess) e = dalloc(&c->grad8, static_cast<size_t>(n) * 8, st);
+  if (e == cudaSuccess && c->repair_cap > 0) e = dalloc(&c->repair_list, static_cast<size_t>(c->repair_cap), st);
+  if (e == cudaSuccess && c->repair_cap > 0) e = dalloc(&c->repair_count, 1, st);
+  if (e == cudaSuccess && c->repair_cap > 0)
+    e = dalloc(&c->corr, static_cast<size_t>(c->repair_cap) * n * 8, st);
+  if (e == cudaSuccess && c->repair_cap > 0) e = dalloc(&c->repair_first, P, st);
   c->bytes = static_cast<size_t>(n) * kRec * 4 + ST_COUNT * 8 + static_cast<size_t>(n) * k * 4 +
              static_cast<size_t>(k) * 12 + P * 24 + nck * P * 20 +
              (inert ? 0 : static_cast<size_t>(cap) * P * 20) + static_cast<size_t>(c->grid) * n * 32 +
-             static_cast<size_t>(n) * 32;
+             static_cast<size_t>(n) * 32 +
+             static_cast<size_t>(c->repair_cap) * (8 + static_cast<size_t>(n) * 32) + 4 +
+             (c->repair_cap > 0 ? P : 0);
   return e;
 }
 
@@ -101,6 +110,7 @@ void ctx_release(tbr_ctx* c) {
   dfree(c->s0, st); dfree(c->s0b, st); dfree(c->ckpt, st); dfree(c->ck_lt, st);
   dfree(c->rec, st); dfree(c->rec_i, st);
   dfree(c->status, st); dfree(c->partial, st); dfree(c->grad8, st);
+  dfree(c->repair_list, st); dfree(c->repair_count, st); dfree(c->corr, st); dfree(c->repair_first, st);
 }
 
 cudaError_t ctx_forward(tbr_ctx* c, const tbr_program* prog, float tau, float tau_min, float* out_rgb,
@@ -137,6 +147,9 @@ cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy
   ba.s0 = c->s0; ba.s0b = c->s0b; ba.ckpt = c->ckpt; ba.ck_lt = c->ck_lt;
   ba.rec = c->rec; ba.rec_i = c->rec_i; ba.dLdR = dLdR;
   ba.partial = c->partial; ba.grid = c->grid; ba.status = c->status;
+  ba.drift_tol = c->drift_tol;
+  ba.repair_list = c->repair_list; ba.repair_count = c->repair_count; ba.repair_cap = c->repair_cap;
+  ba.corr = c->corr; ba.repair_first = c->repair_first;
   cudaError_t e = launch_backward(ba, st);
   if (e != cudaSuccess) return e;
   EpilogueArgs ea;
@@ -145,6 +158,9 @@ cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy
   ea.grad8 = c->grad8;
   ea.g_cx = g_cx; ea.g_cy = g_cy; ea.g_th = g_th; ea.g_len = g_len; ea.g_r = g_r;
   ea.g_logits = g_logits; ea.g_pal = g_pal; ea.status = c->status;
+  if (c->repair_cap > 0) {
+    ea.corr = c->corr; ea.repair_count = c->repair_count; ea.repair_cap = c->repair_cap;
+  }
   return launch_backward_epilogue(ea, st);
 }
 
@@ -224,9 +240,13 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return fail(TBR_ERR_INVALID_ARG, "need tau >= 0 and tau_min > 0");
   if (opts->checkpoint_every < 0 || opts->record_capacity < 0)
     return fail(TBR_ERR_INVALID_ARG, "negative checkpoint interval or record capacity");
+  if (opts->repair_capacity < 0 || opts->repair_capacity > kRepairMax || !std::isfinite(opts->drift_tolerance))
+    return fail(TBR_ERR_INVALID_ARG, "repair capacity outside [0, %d] or non-finite drift tolerance", kRepairMax);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ck = opts->checkpoint_every > 0 ? opts->checkpoint_every : 32;
   const int cap = opts->record_capacity > 0 ? opts->record_capacity : 64;
+  const float drift_tol = opts->drift_tolerance > 0.0f ? opts->drift_tolerance : kDriftTol;
+  const int repair_cap = opts->repair_capacity > 0 ? opts->repair_capacity : kDefaultRepairCap;
   if (!ctx) {
     // forward only: the packed strokes and the status words are the only scratch
     float* packed = nullptr;
@@ -253,13 +273,15 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
   if (c) {
     // reuse an existing context of the same shape: no allocation
     if (c->n != prog->n || c->k != prog->k || c->W != W || c->H != H || c->ck != ck || c->cap != cap ||
-        c->inert != inert)
-      return fail(TBR_ERR_INVALID_ARG, "context shape differs from this call (n, k, W, H, k_ckpt, capacity, inert)");
+        c->inert != inert || c->repair_cap != (inert ? 0 : repair_cap))
+      return fail(TBR_ERR_INVALID_ARG,
+                  "context shape differs from this call (n, k, W, H, k_ckpt, capacity, inert, repair capacity)");
+    c->drift_tol = drift_tol;
     TBR_CUDA(ctx_forward(c, prog, opts->tau, opts->tau_min, out_rgb, st), "tbr_render_soft");
     return TBR_OK;
   }
   c = new tbr_ctx();
-  cudaError_t e = ctx_allocate(c, prog->n, prog->k, W, H, ck, cap, inert, st);
+  cudaError_t e = ctx_allocate(c, prog->n, prog->k, W, H, ck, cap, inert, drift_tol, repair_cap, st);
   if (e == cudaSuccess) e = ctx_forward(c, prog, opts->tau, opts->tau_min, out_rgb, st);
   if (e != cudaSuccess) {
     ctx_release(c);
@@ -294,6 +316,8 @@ tbr_status tbr_ctx_status(tbr_ctx* c, tbr_ctx_stats* stats) {
     stats->drift_resets = static_cast<int64_t>(host[ST_DRIFT]);
     stats->timeouts = static_cast<int64_t>(host[ST_TIMEOUT]);
     stats->invalid_params = static_cast<int64_t>(host[ST_INVALID]);
+    stats->repaired_pixels = static_cast<int64_t>(host[ST_REPAIRED]);
+    stats->repair_overflow = static_cast<int64_t>(host[ST_REPAIR_OVF]);
   }
   return s;
 }

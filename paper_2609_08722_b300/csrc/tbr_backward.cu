@@ -12,6 +12,7 @@
 // over the warp by a reduce-scatter of shuffles, over the CTA through shared
 // memory, and written to the CTA's own slice of a partial buffer (no atomics);
 // an epilogue sums the slices in a fixed order, so the result is reproducible.
+#include <limits.h>
 #include <math.h>
 
 #include "tbr_pair.cuh"
@@ -64,10 +65,41 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_backward(BwdArgs a) {
   if (lane == 0 && dsum) atomicAdd(status + ST_DRIFT, static_cast<unsigned long long>(dsum));
 }
 
+// The pixel pair (px, py0), (px, py0 + 1) as k_backward2 starts it: validity,
+// record offsets, the forward's s_0 and the cotangent.  An invalid pixel keeps
+// a finite position and a zero cotangent.
+__device__ __forceinline__ void load_pair(const BwdArgs& a, int px, int py0, bool skip, bool (&valid)[2],
+                                          size_t (&off)[2], PixelState (&st)[2], float (&lC)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int py = py0 + c;
+    valid[c] = px < a.W && py < a.H && !skip;
+    off[c] = valid[c] ? static_cast<size_t>(py) * a.W + px : 0;
+    st[c] = PixelState{(static_cast<float>(px) + 0.5f) / static_cast<float>(a.W),
+                       (static_cast<float>(py) + 0.5f) / static_cast<float>(a.H), 0.0f, 0.0f, 0.0f, 0,
+                       0.0f, 0.0f, 0.0f};
+    lC[c][0] = lC[c][1] = lC[c][2] = 0.0f;
+    if (valid[c]) {
+      const float4 s0 = a.s0[off[c]];
+      const float2 s0b = a.s0b[off[c]];
+      st[c].xh = s0.x; st[c].yh = s0.y; st[c].xl = s0.z; st[c].yl = s0.w;
+      st[c].lt = s0b.x;
+      st[c].cnt = __float_as_int(s0b.y);
+      lC[c][0] = a.dLdR[3 * off[c] + 0];
+      lC[c][1] = a.dLdR[3 * off[c] + 1];
+      lC[c][2] = a.dLdR[3 * off[c] + 2];
+    }
+  }
+}
+
 // The same replay adjoint with two vertically adjacent pixels per thread
 // (32 x 16 tiles, packed FP32 pair arithmetic; tbr_pair.cuh).  Used for the
-// exterior-transport model; the inert-mark model keeps k_backward.
-template <int CH>
+// exterior-transport model; the inert-mark model keeps k_backward.  The QUEUE
+// instance runs only when the plain one counted checkpoint drift: it repeats
+// the same computation (rewriting identical slices) and queues each drifting
+// pixel for the FP64 repair; otherwise it returns at once.  Keeping the queue
+// out of the plain instance keeps its hot loop free of that code.
+template <int CH, bool QUEUE>
 __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
@@ -78,14 +110,20 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
   const int ntiles = ((W + kPairTileW - 1) / kPairTileW) * ((H + kPairTileH - 1) / kPairTileH);
   const size_t P = static_cast<size_t>(W) * H;
   unsigned long long* status = a.status;
+  if (QUEUE && status[ST_DRIFT] == 0ull) return;
   const bool skip = status[ST_INVALID] != 0ull || status[ST_OVERFLOW] != 0ull;
   ChunkRing<CH> ring;
   ring.init(sbuf, sbar);
   float* slice = a.partial + static_cast<size_t>(blockIdx.x) * n * 8;
   unsigned drift = 0;
   bool first = true;
-  const RecordView rv{const_cast<float4*>(a.rec), const_cast<int*>(a.rec_i), const_cast<float4*>(a.ckpt),
-                      const_cast<float*>(a.ck_lt), P, 0, a.cap, a.ck_every};
+  RecordView rv{const_cast<float4*>(a.rec), const_cast<int*>(a.rec_i), const_cast<float4*>(a.ckpt),
+                const_cast<float*>(a.ck_lt), P, 0, a.cap, a.ck_every};
+  rv.drift_tol = a.drift_tol;
+  rv.repair_list = a.repair_list;
+  rv.repair_count = a.repair_count;
+  rv.repair_cap = a.repair_cap;
+  rv.repair_first = a.repair_first;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     int px, py0;
     pair_tile_pixel(tile, W, px, py0);
@@ -93,42 +131,152 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
     size_t off[2];
     PixelState st[2];
     float lC[2][3];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int py = py0 + c;
-      valid[c] = px < W && py < H && !skip;
-      off[c] = valid[c] ? static_cast<size_t>(py) * W + px : 0;
-      // an invalid pixel keeps a finite position and a zero cotangent
-      st[c] = PixelState{(static_cast<float>(px) + 0.5f) / static_cast<float>(W),
-                         (static_cast<float>(py) + 0.5f) / static_cast<float>(H), 0.0f, 0.0f, 0.0f, 0,
-                         0.0f, 0.0f, 0.0f};
-      lC[c][0] = lC[c][1] = lC[c][2] = 0.0f;
-      if (valid[c]) {
-        const float4 s0 = a.s0[off[c]];
-        const float2 s0b = a.s0b[off[c]];
-        st[c].xh = s0.x; st[c].yh = s0.y; st[c].xl = s0.z; st[c].yl = s0.w;
-        st[c].lt = s0b.x;
-        st[c].cnt = __float_as_int(s0b.y);
-        lC[c][0] = a.dLdR[3 * off[c] + 0];
-        lC[c][1] = a.dLdR[3 * off[c] + 1];
-        lC[c][2] = a.dLdR[3 * off[c] + 2];
-      }
-    }
-    if (!backward_tile2<CH>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first, drift,
-                            status))
+    load_pair(a, px, py0, skip, valid, off, st, lC);
+    if (!backward_tile2<CH, QUEUE>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first,
+                                   drift, status))
       break;
     first = false;
   }
-  const unsigned dsum = __reduce_add_sync(0xffffffffu, drift);
-  if (lane == 0 && dsum) atomicAdd(status + ST_DRIFT, static_cast<unsigned long long>(dsum));
+  if (!QUEUE) {
+    const unsigned dsum = __reduce_add_sync(0xffffffffu, drift);
+    if (lane == 0 && dsum) atomicAdd(status + ST_DRIFT, static_cast<unsigned long long>(dsum));
+  }
 }
 
-// grad8[t] = sum over CTAs g (in order) of partial[g][t], carried in FP64.
-__global__ void k_grad_sum(const float* __restrict__ partial, int G, int n8, float* __restrict__ grad8) {
+// Sorts the repair list by pixel index (one CTA, bitonic in shared memory) so
+// that the repair and the correction sums run in a fixed order.  With more
+// drifting pixels than the list holds, nothing is repaired and the count is
+// reported instead.
+__global__ void __launch_bounds__(kRepairMax) k_repair_sort(int2* list, const int* count, int cap,
+                                                           unsigned long long* status) {
+  __shared__ int2 sh[kRepairMax];
+  const int c = *count;
+  if (c > cap) {
+    if (threadIdx.x == 0) atomicAdd(status + ST_REPAIR_OVF, static_cast<unsigned long long>(c));
+    return;
+  }
+  int m = 1;
+  while (m < c) m <<= 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sh[i] = i < c ? list[i] : make_int2(INT_MAX, 0);
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const bool up = (i & k) == 0;
+          const int2 u = sh[i], v = sh[l];
+          if ((u.x > v.x) == up) { sh[i] = v; sh[l] = u; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < c; i += blockDim.x) list[i] = sh[i];
+  if (threadIdx.x == 0 && c > 0) atomicAdd(status + ST_REPAIRED, static_cast<unsigned long long>(c));
+}
+
+// FP64 repair of a drifting checkpoint segment (the conditioning safeguard of
+// Sec. 5.2): entry e replays its pixel's pair exactly as k_backward2 did (the
+// main values), and from the start of the drifting segment on a second copy of
+// the pixel whose positions are regenerated by Phi in FP64 -- side-table pops
+// and checkpoint resets as in the main replay -- with coverage, adjoint step
+// and VJP in FP32 at those positions.  It writes, per stroke, the repaired
+// minus the main gradient values of the pixel; the epilogue adds them.
+__global__ void __launch_bounds__(64) k_repair(BwdArgs a) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int count = *a.repair_count;
+  if (count > a.repair_cap || e >= count) return;
+  const int2 ent = a.repair_list[e];
+  const int p = ent.x, seg = ent.y;
+  const int W = a.W, n = a.n, ck = a.ck_every;
+  const int px = p % W, py = p / W, py0 = py & ~1, ct = py & 1;
+  const size_t P = static_cast<size_t>(W) * a.H;
+  bool valid[2];
+  size_t off[2];
+  PixelState st[2];
+  float lC[2][3];
+  load_pair(a, px, py0, false, valid, off, st, lC);
+  RecordView rv{const_cast<float4*>(a.rec), const_cast<int*>(a.rec_i), const_cast<float4*>(a.ckpt),
+                const_cast<float*>(a.ck_lt), P, 0, a.cap, ck};
+  rv.drift_tol = a.drift_tol;
+  PairState ps;
+  pair_state_init(ps, valid, st, lC, a.bg, rv, off);
+  PixAdj ra{};
+  double x64 = 0.0, y64 = 0.0;
+  bool active = false;
+  auto start = [&]() {
+    ra = PixAdj{comp(ps.Xh, ct), comp(ps.Yh, ct), comp(ps.Xl, ct), comp(ps.Yl, ct), comp(ps.LT, ct),
+                comp(ps.LTT, ct), comp(ps.LX, ct), comp(ps.LY, ct)};
+    x64 = static_cast<double>(ra.xh) + static_cast<double>(ra.xl);
+    y64 = static_cast<double>(ra.yh) + static_cast<double>(ra.yl);
+    active = true;
+  };
+  if (seg == 0) start();
+  float* out = a.corr + static_cast<size_t>(e) * n * 8;
+  int next_ck = (ck < n) ? ck : 0;
+  f2 Pr[kPairRec];
+  for (int i1 = 1; i1 <= n; ++i1) {
+    const float* S = a.packed + static_cast<size_t>(i1 - 1) * kRec;
+#pragma unroll
+    for (int k = 0; k < kPairRec; ++k) Pr[k] = F2(S[k]);
+    const bool at_ck = (i1 == next_ck);
+    size_t cko = 0;
+    if (at_ck) {
+      next_ck = (next_ck + ck < n) ? next_ck + ck : 0;
+      cko = static_cast<size_t>(i1 / ck - 1) * P;
+    }
+    // the repaired copy pops the same record as the main replay (read before it advances)
+    const bool pop = i1 == ps.nri[ct];
+    const float4 rp = pop ? rv.rec[static_cast<size_t>(ps.rc[ct] - 1) * P + off[ct]] : make_float4(0, 0, 0, 0);
+    float g[2][8];
+    unsigned drift = 0;
+    pair_stroke<false>(ps, S, Pr, i1, at_ck, cko, rv, valid, off, g, drift);
+    float* o = out + static_cast<size_t>(i1 - 1) * 8;
+    if (active) {
+      float4 ckp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float ckl = 0.0f;
+      if (at_ck) {
+        ckp = rv.ckpt[cko + off[ct]];
+        ckl = rv.ck_lt[cko + off[ct]];
+      }
+      ra.xh = static_cast<float>(x64); ra.xl = static_cast<float>(x64 - static_cast<double>(ra.xh));
+      ra.yh = static_cast<float>(y64); ra.yl = static_cast<float>(y64 - static_cast<double>(ra.yh));
+      float v[8];
+      scalar_stroke(ra, load_stroke(S), S, lC[ct][0], lC[ct][1], lC[ct][2], pop, at_ck, true, rp, ckp, ckl,
+                    a.drift_tol, v);
+      if (pop) {
+        x64 = static_cast<double>(rp.x) + static_cast<double>(rp.z);
+        y64 = static_cast<double>(rp.y) + static_cast<double>(rp.w);
+      } else if (at_ck) {
+        x64 = static_cast<double>(ckp.x) + static_cast<double>(ckp.z);
+        y64 = static_cast<double>(ckp.y) + static_cast<double>(ckp.w);
+      } else {
+        phi_f64(x64, y64, S);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = v[k] - g[ct][k];
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = 0.0f;
+      if (i1 == seg) start();
+    }
+  }
+}
+
+// grad8[t] = sum over CTAs g (in order) of partial[g][t], then over the repair
+// entries (in pixel order) of their corrections, carried in FP64.
+__global__ void k_grad_sum(const float* __restrict__ partial, int G, int n8, const float* __restrict__ corr,
+                           const int* __restrict__ repair_count, int repair_cap, float* __restrict__ grad8) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n8) return;
   double s = 0.0;
   for (int g = 0; g < G; ++g) s += static_cast<double>(partial[static_cast<size_t>(g) * n8 + t]);
+  if (corr) {
+    const int c = *repair_count;
+    if (c <= repair_cap)
+      for (int e = 0; e < c; ++e) s += static_cast<double>(corr[static_cast<size_t>(e) * n8 + t]);
+  }
   grad8[t] = static_cast<float>(s);
 }
 
@@ -187,7 +335,7 @@ int backward_grid(int W, int H, int inert) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_backward2<kBwdCH>, kTileThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_backward2<kBwdCH, false>, kTileThreads, 0) !=
             cudaSuccess || per_sm[0] < 1)
       per_sm[0] = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_backward<kBwdCH, true>, kTileThreads, 0) !=
@@ -203,9 +351,22 @@ int backward_grid(int W, int H, int inert) {
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
-  KernelTimer kt(TBR_K_BACKWARD, st);
-  if (a.inert) k_backward<kBwdCH, true><<<a.grid, kTileThreads, 0, st>>>(a);
-  else k_backward2<kBwdCH><<<a.grid, kTileThreads, 0, st>>>(a);
+  const bool repair = !a.inert && a.repair_list && a.repair_cap > 0;
+  if (repair) {
+    cudaError_t e = cudaMemsetAsync(a.repair_count, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.repair_first, 0, static_cast<size_t>(a.W) * a.H, st);
+    if (e != cudaSuccess) return e;
+  }
+  {
+    KernelTimer kt(TBR_K_BACKWARD, st);
+    if (a.inert) k_backward<kBwdCH, true><<<a.grid, kTileThreads, 0, st>>>(a);
+    else k_backward2<kBwdCH, false><<<a.grid, kTileThreads, 0, st>>>(a);
+  }
+  if (repair) {
+    k_backward2<kBwdCH, true><<<a.grid, kTileThreads, 0, st>>>(a);  // returns at once without drift
+    k_repair_sort<<<1, kRepairMax, 0, st>>>(a.repair_list, a.repair_count, a.repair_cap, a.status);
+    k_repair<<<(a.repair_cap + 63) / 64, 64, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
@@ -215,7 +376,8 @@ cudaError_t launch_backward_epilogue(const EpilogueArgs& a, cudaStream_t st) {
   }
   const int n8 = a.n * 8;
   KernelTimer kt(TBR_K_EPILOGUE, st);
-  k_grad_sum<<<(n8 + 255) / 256, 256, 0, st>>>(a.partial, a.grid, n8, a.grad8);
+  k_grad_sum<<<(n8 + 255) / 256, 256, 0, st>>>(a.partial, a.grid, n8, a.corr, a.repair_count, a.repair_cap,
+                                               a.grad8);
   k_grad_out<<<(a.n + 127) / 128, 128, 0, st>>>(a);
   if (a.g_pal) k_grad_palette<<<a.k * 3, 256, 0, st>>>(a);
   return cudaGetLastError();

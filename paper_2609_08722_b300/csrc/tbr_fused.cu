@@ -9,6 +9,8 @@
 // tile from a per-CTA record measured slower on B300: the adjoint's register
 // budget caps the forward's occupancy.  The serving kernel keeps that form,
 // where a bounded per-CTA record matters more.)
+#include <cmath>
+
 #include "tbr_host.h"
 
 namespace tbr {
@@ -16,8 +18,9 @@ namespace tbr {
 // ---------------------------------------------------------------------------
 // Work buffers of the fused path (also held by a fit across steps).
 // ---------------------------------------------------------------------------
-cudaError_t FusedWork::allocate(int n, int k, int W, int H, int ck_, int cap_, cudaStream_t st) {
-  cudaError_t e = ctx_allocate(&ctx, n, k, W, H, ck_, cap_, 0, st);
+cudaError_t FusedWork::allocate(int n, int k, int W, int H, int ck_, int cap_, cudaStream_t st, float drift_tol,
+                                int repair_cap) {
+  cudaError_t e = ctx_allocate(&ctx, n, k, W, H, ck_, cap_, 0, drift_tol, repair_cap, st);
   const int64_t P = static_cast<int64_t>(W) * H;
   nblk = loss_blocks(P);
   if (e == cudaSuccess) e = dalloc(&rgb, static_cast<size_t>(P) * 3, st);
@@ -66,12 +69,16 @@ tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32
   if (opts->inert) return fail(TBR_ERR_INVALID_ARG, "the loss-fused path renders the transport model only");
   if (opts->checkpoint_every < 0 || opts->record_capacity < 0)
     return fail(TBR_ERR_INVALID_ARG, "negative checkpoint interval or record capacity");
+  if (opts->repair_capacity < 0 || opts->repair_capacity > kRepairMax || !std::isfinite(opts->drift_tolerance))
+    return fail(TBR_ERR_INVALID_ARG, "repair capacity outside [0, %d] or non-finite drift tolerance", kRepairMax);
   if (prog->n > 0 && (!g_cx || !g_cy || !g_theta || !g_length || !g_half_width || !g_logits))
     return fail(TBR_ERR_INVALID_ARG, "NULL gradient output");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   FusedWork w;
   cudaError_t e = w.allocate(prog->n, prog->k, W, H, opts->checkpoint_every > 0 ? opts->checkpoint_every : 64,
-                             opts->record_capacity > 0 ? opts->record_capacity : 64, st);
+                             opts->record_capacity > 0 ? opts->record_capacity : 64, st,
+                             opts->drift_tolerance > 0.0f ? opts->drift_tolerance : kDriftTol,
+                             opts->repair_capacity > 0 ? opts->repair_capacity : kDefaultRepairCap);
   if (e == cudaSuccess)
     e = w.run(prog, opts->tau, opts->tau_min, target, out_rgb, loss_out, g_cx, g_cy, g_theta, g_length,
               g_half_width, g_logits, g_palette, st);
@@ -89,6 +96,8 @@ tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32
     stats->drift_resets = static_cast<int64_t>(host[ST_DRIFT]);
     stats->timeouts = static_cast<int64_t>(host[ST_TIMEOUT]);
     stats->invalid_params = static_cast<int64_t>(host[ST_INVALID]);
+    stats->repaired_pixels = static_cast<int64_t>(host[ST_REPAIRED]);
+    stats->repair_overflow = static_cast<int64_t>(host[ST_REPAIR_OVF]);
     if (host[ST_INVALID]) return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);
     if (host[ST_OVERFLOW]) return fail(TBR_ERR_OVERFLOW, "%llu pixels exceeded the side-table capacity", host[ST_OVERFLOW]);
     if (host[ST_TIMEOUT]) return fail(TBR_ERR_TIMEOUT, "a bounded device wait gave up");

@@ -27,6 +27,12 @@ struct tbr_ctx {
   unsigned long long* status = nullptr;  // [ST_COUNT]
   float* partial = nullptr;           // [grid][n][8] per-CTA gradient partials
   float* grad8 = nullptr;             // [n][8]
+  float drift_tol = 1e-5f;            // checkpoint drift that triggers the FP64 repair
+  int repair_cap = 0;                 // repair list capacity (0: no repair)
+  int2* repair_list = nullptr;        // [repair_cap] (pixel, segment start)
+  int* repair_count = nullptr;        // [1]
+  float* corr = nullptr;              // [repair_cap][n][8] gradient corrections
+  unsigned char* repair_first = nullptr;  // [P] per-pixel "queued" flags
   cudaStream_t last_stream = nullptr;
   size_t bytes = 0;
 };
@@ -59,8 +65,10 @@ void dfree(T*& p, cudaStream_t st) {
 }
 
 // Allocates every buffer of a context for n strokes, palette k, W x H pixels.
-cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert,
-                         cudaStream_t st);
+// repair_cap pixels can have a drifting segment regenerated in FP64 (0: none).
+cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert, float drift_tol,
+                         int repair_cap, cudaStream_t st);
+constexpr int kDefaultRepairCap = 256;
 void ctx_release(tbr_ctx* c);
 // Soft forward into an allocated context (resets its status words).
 cudaError_t ctx_forward(tbr_ctx* c, const tbr_program* prog, float tau, float tau_min,
@@ -82,7 +90,8 @@ struct FusedWork {
   unsigned long long* status = nullptr;  // the context's status words
   int nblk = 0, cap = 0;
   size_t bytes = 0;
-  cudaError_t allocate(int n, int k, int W, int H, int ck, int cap, cudaStream_t st);
+  cudaError_t allocate(int n, int k, int W, int H, int ck, int cap, cudaStream_t st, float drift_tol = 1e-5f,
+                       int repair_cap = kDefaultRepairCap);
   void release(cudaStream_t st);
   // pack + soft forward + MSE and seed + replay adjoint + gradient epilogue;
   // status words reset first.

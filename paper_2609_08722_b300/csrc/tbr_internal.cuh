@@ -41,7 +41,8 @@ constexpr float kDriftTol = 1e-5f;           // checkpoint drift threshold
 // Device status words (unsigned long long[ST_COUNT]).
 enum : int {
   ST_TIMEOUT = 0, ST_OVERFLOW = 1, ST_DRIFT = 2, ST_BAND = 3, ST_INVALID = 4,
-  ST_RECORDS = 5, ST_MAXREC = 6, ST_BG = 7, ST_VISITED = 8, ST_COUNT = 16
+  ST_RECORDS = 5, ST_MAXREC = 6, ST_BG = 7, ST_VISITED = 8, ST_REPAIRED = 9, ST_REPAIR_OVF = 10,
+  ST_COUNT = 16
 };
 
 // ---------------------------------------------------------------------------
@@ -676,13 +677,26 @@ struct BwdArgs {
   float* partial;            // [grid][n][8]
   int grid;
   unsigned long long* status;
+  // FP64 repair of drifting checkpoint segments (all NULL / 0: off)
+  float drift_tol = kDriftTol;
+  int2* repair_list = nullptr;  // [repair_cap] (pixel, segment start)
+  int* repair_count = nullptr;  // [1], zeroed by launch_backward
+  int repair_cap = 0;           // <= kRepairMax
+  float* corr = nullptr;        // [repair_cap][n][8] gradient corrections
+  unsigned char* repair_first = nullptr;  // [P] per-pixel "queued" flags, zeroed by launch_backward
 };
+constexpr int kRepairMax = 1024;  // largest repair list (sorted by one CTA)
 int backward_grid(int W, int H, int inert);  // CTAs of the persistent backward grid
+// Replay adjoint, then (with a repair list) the FP64 repair of the pixels whose
+// checkpoint drift exceeded drift_tol.
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st);
 
 struct EpilogueArgs {
   const float* partial;
   int grid, n, k;
+  const float* corr = nullptr;          // [repair_cap][n][8] or NULL
+  const int* repair_count = nullptr;    // entries in corr (used only if <= repair_cap)
+  int repair_cap = 0;
   const float* packed;
   const float* probs;
   const float* palette;

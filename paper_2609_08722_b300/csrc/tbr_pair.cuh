@@ -470,12 +470,15 @@ struct PixAdj {
 // One stroke of the replay adjoint for one pixel in scalar arithmetic, as in
 // backward_tile: x_i from the side table (pop), from Phi_i followed by a reset
 // to the checkpoint (at_ck), or from Phi_i; log2 T_i from the checkpoint or
-// Eq. rT; then the adjoint step and the VJP, added to v.
-__device__ __forceinline__ void scalar_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S, float lC0,
+// Eq. rT; then the adjoint step and the VJP, whose 8 gradient values are
+// written to v.  Returns true if, at a checkpoint of a valid pixel, the
+// regenerated position differed from the stored one by more than drift_tol.
+__device__ __forceinline__ bool scalar_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S, float lC0,
                                               float lC1, float lC2, bool pop, bool at_ck, bool valid, float4 rp,
-                                              float4 ckp, float ck_lt, unsigned& drift, float (&v)[8]) {
+                                              float4 ckp, float ck_lt, float drift_tol, float (&v)[8]) {
   Geo gq;
   float s, h, ds, dh;
+  bool drifted = false;
   if (pop) {
     // x_i was within the floor's reach: read it back (Lemma "Support of the replay record")
     a.xh = rp.x; a.yh = rp.y; a.xl = rp.z; a.yl = rp.w;
@@ -487,8 +490,8 @@ __device__ __forceinline__ void scalar_stroke(PixAdj& a, const StrokeF& g, const
     phi_local(s, h, g, gq, ds, dh);
     add_frame_disp(a.xh, a.yh, a.xl, a.yl, g, ds, dh);
     if (valid) {
-      if (fabsf((a.xh - ckp.x) + (a.xl - ckp.z)) > kDriftTol || fabsf((a.yh - ckp.y) + (a.yl - ckp.w)) > kDriftTol)
-        ++drift;
+      drifted = fabsf((a.xh - ckp.x) + (a.xl - ckp.z)) > drift_tol ||
+                fabsf((a.yh - ckp.y) + (a.yl - ckp.w)) > drift_tol;
       a.xh = ckp.x; a.yh = ckp.y; a.xl = ckp.z; a.yl = ckp.w;
     }
     to_frame(a.xh, a.yh, a.xl, a.yl, g, s, h);
@@ -504,20 +507,125 @@ __device__ __forceinline__ void scalar_stroke(PixAdj& a, const StrokeF& g, const
   const float lCc = fmaf(lC0, S[F_CR], fmaf(lC1, S[F_CG], lC2 * S[F_CB]));
   const float mu = T * (lCc - a.lT);
   const float Ta = T * cv.alpha;
-  v[5] = fmaf(lC0, Ta, v[5]); v[6] = fmaf(lC1, Ta, v[6]); v[7] = fmaf(lC2, Ta, v[7]);
-  float g0, g1, g2, g3, g4;
-  step_vjp(gq, g, a.lx, a.ly, mu * cv.dadz, cv.z, g0, g1, g2, g3, g4);
-  v[0] += g0; v[1] += g1; v[2] += g2; v[3] += g3; v[4] += g4;
+  v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;
+  step_vjp(gq, g, a.lx, a.ly, mu * cv.dadz, cv.z, v[0], v[1], v[2], v[3], v[4]);
   a.lT = fmaf(cv.oma, a.lT, cv.alpha * lCc);
+  return drifted;
+}
+
+// Adjoint state of a pixel pair (component c = pixel c).
+struct PairState {
+  f2 Xh, Yh, Xl, Yl;  // x_{i-1}, hi/lo
+  f2 LT;              // log2 T_{i-1}
+  f2 LTT, LX, LY;     // lambda^T, lambda^x
+  f2 LC0, LC1, LC2;   // lambda^C_0 (constant)
+  int rc[2], nri[2];  // side-table records left; stroke index of the top one (-1: none)
+};
+
+// Initial pair state from the forward's s_0 and the cotangent (Eq. adjstep
+// initial values: lambda^T_0 = lambda^C_0 . c_0, lambda^x_0 = 0).
+__device__ __forceinline__ void pair_state_init(PairState& ps, const bool (&valid)[2], const PixelState (&st)[2],
+                                                const float (&lC)[2][3], const float bg[3], const RecordView& rv,
+                                                const size_t (&off)[2]) {
+  ps.Xh = make_float2(st[0].xh, st[1].xh); ps.Yh = make_float2(st[0].yh, st[1].yh);
+  ps.Xl = make_float2(st[0].xl, st[1].xl); ps.Yl = make_float2(st[0].yl, st[1].yl);
+  ps.LT = make_float2(st[0].lt, st[1].lt);
+  ps.LC0 = make_float2(lC[0][0], lC[1][0]); ps.LC1 = make_float2(lC[0][1], lC[1][1]);
+  ps.LC2 = make_float2(lC[0][2], lC[1][2]);
+  ps.LTT = fma2(ps.LC0, F2(bg[0]), fma2(ps.LC1, F2(bg[1]), mul2(ps.LC2, F2(bg[2]))));
+  ps.LX = F2(0.0f); ps.LY = F2(0.0f);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    ps.rc[c] = valid[c] ? min(st[c].cnt, rv.cap) : 0;
+    ps.nri[c] = ps.rc[c] > 0 ? rv.rec_i[static_cast<size_t>(ps.rc[c] - 1) * rv.stride + off[c]] : -1;
+  }
+}
+
+// Stroke i1 of the paired replay adjoint (S: packed record, P: pair record;
+// at_ck / cko: checkpoint stroke and its record offset).  Writes each pixel's 8
+// gradient values to g[c][.].  At a checkpoint, counts in drift the pixels
+// whose regenerated position drifted past rv.drift_tol and, with QUEUE, queues
+// a pixel's first drifting segment on rv.repair_list.
+template <bool QUEUE>
+__device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restrict__ S, const f2* __restrict__ P,
+                                            int i1, bool at_ck, size_t cko, const RecordView& rv,
+                                            const bool (&valid)[2], const size_t (&off)[2], float (&g)[2][8],
+                                            unsigned& drift) {
+  const bool pop0 = i1 == ps.nri[0], pop1 = i1 == ps.nri[1];
+  bool scalar = at_ck || pop0 || pop1;
+  Geo2 gq;
+  f2 ds, dh;
+  if (!scalar) {
+    // x_i = Phi_i(x_{i-1}) (Eq. rpos), both pixels at once
+    f2 s, h;
+    to_frame2(ps.Xh, ps.Yh, ps.Xl, ps.Yl, P, s, h);
+    scalar = phi_pair(s, h, P, gq, ds, dh) != 0;  // flank to cap: redo this stroke per pixel
+  }
+  if (scalar) {
+    const StrokeF sg = load_stroke(S);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const bool pop = c == 0 ? pop0 : pop1;
+      float4 rp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (pop) {
+        rp = rv.rec[static_cast<size_t>(ps.rc[c] - 1) * rv.stride + off[c]];
+        --ps.rc[c];
+        ps.nri[c] = ps.rc[c] > 0 ? rv.rec_i[static_cast<size_t>(ps.rc[c] - 1) * rv.stride + off[c]] : -1;
+      }
+      float4 ckp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float ckl = 0.0f;
+      if (at_ck && valid[c]) {
+        ckp = rv.ckpt[cko + off[c]];
+        ckl = rv.ck_lt[cko + off[c]];
+      }
+      PixAdj a{comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), comp(ps.LT, c), comp(ps.LTT, c),
+               comp(ps.LX, c), comp(ps.LY, c)};
+      if (scalar_stroke(a, sg, S, comp(ps.LC0, c), comp(ps.LC1, c), comp(ps.LC2, c), pop, at_ck, valid[c], rp,
+                        ckp, ckl, rv.drift_tol, g[c])) {
+        ++drift;
+        // first drift of this pixel: queue the segment (i1 - ck, i1] for the FP64 repair
+        if (QUEUE && rv.repair_first[off[c]] == 0) {
+          rv.repair_first[off[c]] = 1;
+          const int idx = atomicAdd(rv.repair_count, 1);
+          if (idx < rv.repair_cap) rv.repair_list[idx] = make_int2(static_cast<int>(off[c]), i1 - rv.ck);
+        }
+      }
+      put(ps.Xh, c, a.xh); put(ps.Yh, c, a.yh); put(ps.Xl, c, a.xl); put(ps.Yl, c, a.yl);
+      put(ps.LT, c, a.lt); put(ps.LTT, c, a.lT); put(ps.LX, c, a.lx); put(ps.LY, c, a.ly);
+    }
+  } else {
+    add_frame_disp2(ps.Xl, ps.Yl, P, ds, dh);
+    if ((i1 & (kRenorm - 1)) == 0) {
+      pos_renorm2(ps.Xh, ps.Xl);
+      pos_renorm2(ps.Yh, ps.Yl);
+    }
+    const Cover2 cv = coverage2(gq.sp, P);
+    ps.LT = add2(ps.LT, cv.sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
+    const f2 T = ex22(ps.LT);
+    const f2 lCc = fma2(ps.LC0, P[P_CR], fma2(ps.LC1, P[P_CG], mul2(ps.LC2, P[P_CB])));
+    const f2 mu = mul2(T, sub2(lCc, ps.LTT));
+    const f2 Ta = mul2(T, cv.alpha);
+    const f2 c5 = mul2(ps.LC0, Ta), c6 = mul2(ps.LC1, Ta), c7 = mul2(ps.LC2, Ta);
+    f2 gcx, gcy, gth, gL, gr;
+    step_vjp2(gq, P, ps.LX, ps.LY, mul2(mu, cv.dadz), cv.z, gcx, gcy, gth, gL, gr);
+    ps.LTT = fma2(cv.oma, ps.LTT, mul2(cv.alpha, lCc));
+    g[0][0] = gcx.x; g[0][1] = gcy.x; g[0][2] = gth.x; g[0][3] = gL.x; g[0][4] = gr.x;
+    g[0][5] = c5.x; g[0][6] = c6.x; g[0][7] = c7.x;
+    g[1][0] = gcx.y; g[1][1] = gcy.y; g[1][2] = gth.y; g[1][3] = gL.y; g[1][4] = gr.y;
+    g[1][5] = c5.y; g[1][6] = c6.y; g[1][7] = c7.y;
+  }
 }
 
 // Replay adjoint (Sec. 5.2) of a 32 x 16 tile, two pixels per thread, over
 // strokes 1 .. n; otherwise as backward_tile.  st[c], lC[c][.], valid[c] and
 // off[c] (the pixel's element offset in the replay record) describe pixel c of
 // the pair; an invalid pixel must carry a finite position and a zero
-// cotangent.  pbuf is shared [CH][kPairRec] float2.  All threads of the CTA
-// must call it.  Returns false if a bounded wait gave up.
-template <int CH>
+// cotangent.  pbuf is shared [CH][kPairRec] float2.  With QUEUE, a pixel whose
+// checkpoint drift first exceeds rv.drift_tol is appended, with the start of
+// that segment, to rv.repair_list (off[c] is then the pixel index) for the
+// FP64 repair pass.  All threads of the CTA must call it.  Returns false if a
+// bounded wait gave up.
+template <int CH, bool QUEUE>
 __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, const bool (&valid)[2],
                                const PixelState (&st)[2], const float (&lC)[2][3], const float bg[3],
                                const RecordView& rv, const size_t (&off)[2], f2* __restrict__ pbuf,
@@ -527,20 +635,8 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ck = rv.ck;
   const bool any = valid[0] || valid[1];
-  f2 Xh = make_float2(st[0].xh, st[1].xh), Yh = make_float2(st[0].yh, st[1].yh);
-  f2 Xl = make_float2(st[0].xl, st[1].xl), Yl = make_float2(st[0].yl, st[1].yl);
-  f2 LT = make_float2(st[0].lt, st[1].lt);
-  const f2 LC0 = make_float2(lC[0][0], lC[1][0]), LC1 = make_float2(lC[0][1], lC[1][1]),
-           LC2 = make_float2(lC[0][2], lC[1][2]);
-  f2 LTT = fma2(LC0, F2(bg[0]), fma2(LC1, F2(bg[1]), mul2(LC2, F2(bg[2]))));
-  f2 LX = F2(0.0f), LY = F2(0.0f);
-  // side table, popped last-in first-out: rc[c] records left, nri[c] the stroke of the top one
-  int rc[2], nri[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    rc[c] = valid[c] ? min(st[c].cnt, rv.cap) : 0;
-    nri[c] = rc[c] > 0 ? rv.rec_i[static_cast<size_t>(rc[c] - 1) * rv.stride + off[c]] : -1;
-  }
+  PairState ps;
+  pair_state_init(ps, valid, st, lC, bg, rv, off);
   int next_ck = (ck < n) ? ck : 0;
   const int nch = (n + CH - 1) / CH;
   auto chunk_src = [&](int q) { return packed + static_cast<size_t>(q) * CH * kRec; };
@@ -573,63 +669,10 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
         cko = static_cast<size_t>(i1 / ck - 1) * rv.stride;
       }
       if (any) {
-        const float* S = S0 + j * kRec;
-        const f2* P = pbuf + j * kPairRec;
-        const bool pop0 = i1 == nri[0], pop1 = i1 == nri[1];
-        bool scalar = at_ck || pop0 || pop1;
-        Geo2 gq;
-        f2 ds, dh;
-        if (!scalar) {
-          // x_i = Phi_i(x_{i-1}) (Eq. rpos), both pixels at once
-          f2 s, h;
-          to_frame2(Xh, Yh, Xl, Yl, P, s, h);
-          scalar = phi_pair(s, h, P, gq, ds, dh) != 0;  // flank to cap: redo this stroke per pixel
-        }
-        if (scalar) {
-          const StrokeF g = load_stroke(S);
+        float g[2][8];
+        pair_stroke<QUEUE>(ps, S0 + j * kRec, pbuf + j * kPairRec, i1, at_ck, cko, rv, valid, off, g, drift);
 #pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const bool pop = c == 0 ? pop0 : pop1;
-            float4 rp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (pop) {
-              rp = rv.rec[static_cast<size_t>(rc[c] - 1) * rv.stride + off[c]];
-              --rc[c];
-              nri[c] = rc[c] > 0 ? rv.rec_i[static_cast<size_t>(rc[c] - 1) * rv.stride + off[c]] : -1;
-            }
-            float4 ckp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            float ckl = 0.0f;
-            if (at_ck && valid[c]) {
-              ckp = rv.ckpt[cko + off[c]];
-              ckl = rv.ck_lt[cko + off[c]];
-            }
-            PixAdj a{comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c), comp(LT, c), comp(LTT, c),
-                     comp(LX, c), comp(LY, c)};
-            scalar_stroke(a, g, S, comp(LC0, c), comp(LC1, c), comp(LC2, c), pop, at_ck, valid[c], rp, ckp, ckl,
-                          drift, vv);
-            put(Xh, c, a.xh); put(Yh, c, a.yh); put(Xl, c, a.xl); put(Yl, c, a.yl);
-            put(LT, c, a.lt);
-            put(LTT, c, a.lT); put(LX, c, a.lx); put(LY, c, a.ly);
-          }
-        } else {
-          add_frame_disp2(Xl, Yl, P, ds, dh);
-          if ((i1 & (kRenorm - 1)) == 0) {
-            pos_renorm2(Xh, Xl);
-            pos_renorm2(Yh, Yl);
-          }
-          const Cover2 cv = coverage2(gq.sp, P);
-          LT = add2(LT, cv.sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
-          const f2 Ti = ex22(LT);
-          const f2 lCc = fma2(LC0, P[P_CR], fma2(LC1, P[P_CG], mul2(LC2, P[P_CB])));
-          const f2 mu = mul2(Ti, sub2(lCc, LTT));
-          const f2 Ta = mul2(Ti, cv.alpha);
-          const f2 c5 = mul2(LC0, Ta), c6 = mul2(LC1, Ta), c7 = mul2(LC2, Ta);
-          f2 gcx, gcy, gth, gL, gr;
-          step_vjp2(gq, P, LX, LY, mul2(mu, cv.dadz), cv.z, gcx, gcy, gth, gL, gr);
-          LTT = fma2(cv.oma, LTT, mul2(cv.alpha, lCc));
-          vv[0] = gcx.x + gcx.y; vv[1] = gcy.x + gcy.y; vv[2] = gth.x + gth.y;
-          vv[3] = gL.x + gL.y; vv[4] = gr.x + gr.y;
-          vv[5] = c5.x + c5.y; vv[6] = c6.x + c6.y; vv[7] = c7.x + c7.y;
-        }
+        for (int k = 0; k < 8; ++k) vv[k] = g[0][k] + g[1][k];
       }
       const float r = warp_reduce8(vv);
       if ((lane & 3) == 0) rb[warp][j * 8 + ((lane >> 2) & 7)] = r;

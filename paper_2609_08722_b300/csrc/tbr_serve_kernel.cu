@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_serve(ServeArgs a) {
           lC[c][0] = d.seed_scale * e0; lC[c][1] = d.seed_scale * e1; lC[c][2] = d.seed_scale * e2;
           if (st[c].cnt > d.cap) ++ovf;
         }
-        if (!backward_tile2<kServeCH>(ring, d.packed, d.n, valid, st, lC, d.bg, rv, off, pbuf, red, slice, first,
+        if (!backward_tile2<kServeCH, false>(ring, d.packed, d.n, valid, st, lC, d.bg, rv, off, pbuf, red, slice, first,
                                       drift, d.status)) {
           ok = false;
           break;

@@ -29,6 +29,11 @@ struct RecordView {
   size_t stride;
   size_t off;
   int cap, ck;
+  float drift_tol = kDriftTol;  // checkpoint drift that marks a segment for the FP64 repair
+  int2* repair_list = nullptr;  // [repair_cap] (pixel, segment start) of drifting pixels, or NULL
+  int* repair_count = nullptr;  // entries appended (may exceed repair_cap)
+  int repair_cap = 0;
+  unsigned char* repair_first = nullptr;  // [P] 1 once the pixel is queued (zeroed per adjoint)
 };
 
 // State of one pixel after the soft forward (s_0 of Eq. state plus the colour).
@@ -174,6 +179,38 @@ static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& x
   xh = static_cast<float>(xo); xl = static_cast<float>(xo - static_cast<double>(xh));
   yh = static_cast<float>(yo); yl = static_cast<float>(yo - static_cast<double>(yh));
   return false;
+}
+
+// x_i = Phi_i(x_{i-1}) in FP64 (Eq. fwd, with the tangential map of Eq. phi)
+// from the record's FP64 copy of (m, e, L/2, r): sigma' = B / (L + sqrt(L^2 +
+// pi B)), B = 2L(sigma + r) + pi(sigma^2 + r^2); the arclength t from the flank
+// midpoint scales by (L + pi sigma') / (L + pi sigma).  Used by the repair of a
+// drifting checkpoint segment.
+static __device__ __noinline__ void phi_f64(double& x, double& y, const float* __restrict__ S) {
+  const double* D = reinterpret_cast<const double*>(S + F_D64);
+  const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
+  const double L = 2.0 * hl;
+  const double dx = x - mx, dy = y - my;
+  const double s = dx * ex + dy * ey, h = dy * ex - dx * ey;
+  const double as = fabs(s), ah = fabs(h), d = as - hl;
+  const bool cap = d > 0.0;
+  const double sig = cap ? sqrt(d * d + ah * ah) : ah;
+  const double B = 2.0 * L * (sig + r) + kPiD * (sig * sig + r * r);
+  const double sp = B / (L + sqrt(L * L + kPiD * B));
+  const double tn = cap ? hl + sig * atan2(d, ah) : as;
+  const double q = L + kPiD * sig;
+  const double t = q > 0.0 ? tn * ((L + kPiD * sp) / q) : 0.0;
+  double sn, hn;
+  if (t <= hl) {
+    sn = t; hn = sp;
+  } else {
+    double sb, cb;
+    sincos((t - hl) / sp, &sb, &cb);
+    sn = hl + sp * sb; hn = sp * cb;
+  }
+  sn = copysign(sn, s); hn = copysign(hn, h);
+  x = mx + sn * ex - hn * ey;
+  y = my + sn * ey + hn * ex;
 }
 
 // One stroke of the hard chain in FP32.  Returns true if x lies in K_i;

@@ -57,13 +57,15 @@ class TbrHardStats(ctypes.Structure):
 class TbrSoftOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("tau_min", ctypes.c_float),
                 ("checkpoint_every", ctypes.c_int32), ("record_capacity", ctypes.c_int32),
-                ("inert", ctypes.c_int32)]
+                ("inert", ctypes.c_int32), ("drift_tolerance", ctypes.c_float),
+                ("repair_capacity", ctypes.c_int32)]
 
 
 class TbrCtxStats(ctypes.Structure):
     _fields_ = [("records", ctypes.c_int64), ("max_records", ctypes.c_int64),
                 ("overflow_pixels", ctypes.c_int64), ("drift_resets", ctypes.c_int64),
-                ("timeouts", ctypes.c_int64), ("invalid_params", ctypes.c_int64)]
+                ("timeouts", ctypes.c_int64), ("invalid_params", ctypes.c_int64),
+                ("repaired_pixels", ctypes.c_int64), ("repair_overflow", ctypes.c_int64)]
 
 
 _lib = None
@@ -237,13 +239,14 @@ class SoftContext:
 
 def render_soft(prog: DeviceProgram, W: int, H: int, tau: float, tau_min: float, record: bool = False,
                 checkpoint_every: int = 0, record_capacity: int = 0, inert: bool = False,
-                out_rgb=None, stream=None, reuse: Optional["SoftContext"] = None):
+                out_rgb=None, stream=None, reuse: Optional["SoftContext"] = None,
+                drift_tolerance: float = 0.0, repair_capacity: int = 0):
     """tbr_render_soft; returns (rgb [H,W,3], SoftContext or None).  ``reuse``
     overwrites an existing context of the same shape instead of allocating."""
     dev = prog.cx.device
     rgb = out_rgb if out_rgb is not None else torch.empty((H, W, 3), device=dev, dtype=torch.float32)
     opts = TbrSoftOpts(float(tau), float(tau_min), int(checkpoint_every), int(record_capacity),
-                       int(bool(inert)))
+                       int(bool(inert)), float(drift_tolerance), int(repair_capacity))
     handle = ctypes.c_void_p(reuse.handle if reuse is not None else None)
     s = prog.struct()
     check(lib().tbr_render_soft(ctypes.byref(s), W, H, ctypes.byref(opts), _ptr(rgb),

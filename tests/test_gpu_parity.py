@@ -191,6 +191,55 @@ def test_checkpoint_interval_does_not_change_gradients(small, k):
         assert rel(g[name].cpu().numpy().ravel(), og[name].ravel()) <= GRAD_TOL
 
 
+def test_fp64_repair_of_drifting_segments(small):
+    """A drift tolerance of 1e-12 marks (nearly) every pixel at its first
+    checkpoint: the adjoint regenerates those segments in FP64 and replaces the
+    pixels' contributions.  The result stays within the oracle tolerance, is
+    reproducible, and differs from the unrepaired gradients only by rounding
+    (which also checks that the repair's replay of each pixel pair reproduces
+    the main adjoint exactly before it substitutes the FP64 trajectory)."""
+    p, dp = small
+    W, H = 40, 24
+    cot = torch.from_numpy(inputs.make_cotangent(17, W * H)).reshape(H, W, 3).cuda()
+    _, ctx0 = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=8)
+    g0 = ctx0.backward(cot)
+    s0 = ctx0.status()
+    assert s0["repaired_pixels"] == 0 and s0["drift_resets"] == 0
+    _, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=8, drift_tolerance=1e-12,
+                             repair_capacity=1024)
+    g1 = ctx.backward(cot)
+    st = ctx.status()
+    g2 = ctx.backward(cot)
+    print(f"repair stats {st}")
+    assert st["repaired_pixels"] > W * H // 2 and st["repair_overflow"] == 0
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.double().cpu().numpy().reshape(-1, 3))
+    for k in GROUPS:
+        assert torch.equal(g1[k], g2[k]), k
+        e_rep = rel(g1[k].cpu().numpy().ravel(), og[k].ravel())
+        e_mix = rel(g1[k].cpu().numpy().ravel(), g0[k].cpu().numpy().ravel())
+        print(f"{k}: vs oracle {e_rep:.2e}, vs unrepaired {e_mix:.2e}")
+        assert e_rep <= GRAD_TOL, k
+        assert e_mix <= 1e-4, k
+
+
+def test_fp64_repair_overflow_is_reported_and_skipped(small):
+    """More drifting pixels than the repair capacity: none is repaired (so the
+    result stays deterministic), the count is reported, and the gradients are
+    those of the unrepaired adjoint."""
+    p, dp = small
+    W, H = 40, 24
+    cot = torch.from_numpy(inputs.make_cotangent(18, W * H)).reshape(H, W, 3).cuda()
+    _, ctx0 = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=8, repair_capacity=1)
+    g0 = ctx0.backward(cot)
+    _, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=8, drift_tolerance=1e-12,
+                             repair_capacity=1)
+    g1 = ctx.backward(cot)
+    st = ctx.status()
+    assert st["repair_overflow"] > 1 and st["repaired_pixels"] == 0
+    for k in GROUPS:
+        assert torch.equal(g0[k], g1[k]), k
+
+
 @pytest.fixture(scope="module")
 def operating():
     p = inputs.operating_program()
