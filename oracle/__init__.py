@@ -75,6 +75,8 @@ def _load():
                                          P, i64, ctypes.c_int, ctypes.c_int, P]
             lib.orc_soft_vjp.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
                                          P, i64, P, P, P, P, P]
+            lib.orc_map_drops.argtypes = [P, i64, dbl, dbl, dbl, dbl, dbl, ctypes.c_int, P, P, P]
+            lib.orc_map_drops.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             for f in ("orc_map", "orc_map_jacobian", "orc_render_hard", "orc_render_soft",
                       "orc_soft_jvp", "orc_soft_vjp"):
@@ -155,15 +157,43 @@ def map_jacobian(pts, stroke, direction=0, mode=MODE_FLOOR):
     return jac
 
 
-def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with_kappa=False):
-    """Hard render; returns dict rgb [m,3], idx [m], margin [m] (+ kappa [m])."""
+TRANSPORTS = {"capsule": 0, "inert": 1, "drops": 2}
+
+
+def _transport(inert, transport):
+    if transport is None:
+        return 1 if inert else 0
+    return TRANSPORTS[transport]
+
+
+def drops_map(pts, stroke, direction=0, return_binds=False, return_jacobian=False):
+    """The sixteen-drop operator of the transfer renderer R_D on points [n,2]:
+    direction 0 = the pull-back psi_D (epsilon-floored), 1 = the forward Phi_D.
+    Optionally the per-point floor binds and the 2x2 Jacobians d(out)/d(x, y)."""
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 2))
+    out = np.empty_like(pts)
+    binds = np.empty(pts.shape[0], dtype=np.int32)
+    jac = np.empty((pts.shape[0], 2, 2)) if return_jacobian else None
+    _load().orc_map_drops(_ptr(pts), pts.shape[0], *map(float, stroke), int(direction), _ptr(out),
+                          _ptr(binds), _ptr(jac))
+    res = [out]
+    if return_binds:
+        res.append(binds)
+    if return_jacobian:
+        res.append(jac)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with_kappa=False, transport=None):
+    """Hard render; returns dict rgb [m,3], idx [m], margin [m] (+ kappa [m]).
+    transport: "capsule" (R_A, default), "inert" (R_U) or "drops" (R_D)."""
     pk = _Packed(prog)
     pix, m = _pixels(W, H, pix)
     rgb = np.empty((m, 3))
     idx = np.empty(m, dtype=np.int32)
     margin = np.empty(m)
     kappa = np.empty(m) if with_kappa else None
-    _load().orc_render_hard(pk.ref, W, H, int(n_prefix), int(bool(snap)), int(bool(inert)),
+    _load().orc_render_hard(pk.ref, W, H, int(n_prefix), int(bool(snap)), _transport(inert, transport),
                             _ptr(pix), m, _ptr(rgb), _ptr(idx), _ptr(margin), _ptr(kappa))
     out = {"rgb": rgb, "idx": idx, "margin": margin}
     if with_kappa:
@@ -171,14 +201,15 @@ def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with
     return out
 
 
-def render_soft(prog, W, H, tau, tau_min, inert=False, pix=None):
-    """Soft render; returns dict rgb [m,3], T0 [m], nrec [m]."""
+def render_soft(prog, W, H, tau, tau_min, inert=False, pix=None, transport=None):
+    """Soft render; returns dict rgb [m,3], T0 [m], nrec [m] (floor binds).
+    transport as render_hard."""
     pk = _Packed(prog)
     pix, m = _pixels(W, H, pix)
     rgb = np.empty((m, 3))
     T0 = np.empty(m)
     nrec = np.empty(m, dtype=np.int32)
-    _load().orc_render_soft(pk.ref, W, H, float(tau), float(tau_min), int(bool(inert)),
+    _load().orc_render_soft(pk.ref, W, H, float(tau), float(tau_min), _transport(inert, transport),
                             _ptr(pix), m, _ptr(rgb), _ptr(T0), _ptr(nrec))
     return {"rgb": rgb, "T0": T0, "nrec": nrec}
 

@@ -14,6 +14,9 @@
 //   * the interior extension by clamping C (Sec. 4 "The chain") and the
 //     implemented epsilon-floor of Sec. 5.2;
 //   * the hard and soft renderers (Eq. chain, Eq. render, Eq. relax, Eq. state);
+//   * the sixteen-drop operator psi_D of the transfer renderer R_D (Sec.
+//     "Transfer across transport constructions"): K = 16 classical drop maps of
+//     the stroke's total area laid along its segment, with capsule coverage;
 //   * a stored-state adjoint (Eq. adjstep, Eq. adjparam) whose local Jacobians
 //     come from forward-mode dual numbers, and a forward-mode directional
 //     derivative of the whole soft render used to pin that adjoint.
@@ -34,6 +37,10 @@
 //   * Soft coverage alpha = min(sigmoid((r - sigma')/max(tau r, tau_min)), 1 - 1e-7).
 //   * epsilon-floor: C <- (eps r)^2 whenever C < (eps r)^2, eps = 1e-3; each such
 //     sample counts as one side-table record.
+//   * R_D: drop k = 0..15 (inserted k-th, one sweep from the segment's start
+//     m - L e/2 to its end) is centred at m + e L ((k + 1/2)/16 - 1/2) with
+//     radius s = sqrt(A_L(r) / (16 pi)); inside a drop's disc the pull-back
+//     uses the same epsilon-floor, sigma^2 <- (eps s)^2, on the same ray.
 
 #include <cmath>
 #include <cstdint>
@@ -253,6 +260,82 @@ void phi(const T& x, const T& y, const Stroke<T>& g, bool raw_q, T& x_out, T& y_
   from_frame(sn, hn, g, x_out, y_out);
 }
 
+// Sixteen-drop operator of the transfer renderer R_D (Sec. "Transfer across
+// transport constructions"): stroke i's displacement is a composition of
+// K = 16 classical drop maps (the radial disc insertion sigma' = sqrt(sigma^2 +
+// s^2), i.e. Eq. back at L = 0) of radius s = sqrt(A_L(r) / (K pi)), so that the
+// inserted area equals the stroke's own, laid in one sweep along the segment.
+static const int kDrops = 16;
+template <class T>
+void drop_centre(const Stroke<T>& g, int k, T& cx, T& cy) {
+  T t = g.L * ((k + 0.5) / kDrops - 0.5);
+  cx = g.cx + t * cos(g.th);
+  cy = g.cy + t * sin(g.th);
+}
+template <class T>
+T drop_radius2(const Stroke<T>& g) {
+  return (2.0 * g.L * g.r + kPi * g.r * g.r) / (kDrops * kPi);
+}
+
+// Pull-back psi_D: the inverse drops in reverse insertion order, each moving
+// the point along the ray from its centre to distance sigma = sqrt(rho^2 -
+// s^2).  Inside a disc (rho^2 - s^2 < (eps s)^2) the point is floored on the
+// same ray at eps s (as the capsule's epsilon-floor); rho = 0 takes the
+// direction e_perp.  Returns the number of floor binds.
+template <class T>
+int psi_drops(const T& x, const T& y, const Stroke<T>& g, T& x_out, T& y_out) {
+  T px = x, py = y;
+  int binds = 0;
+  const T s2 = drop_radius2(g);
+  const T fl = (kEps * kEps) * s2;
+  for (int k = kDrops - 1; k >= 0; --k) {
+    T cx, cy;
+    drop_centre(g, k, cx, cy);
+    T dx = px - cx, dy = py - cy;
+    T rho2 = dx * dx + dy * dy;
+    T sig2 = rho2 - s2;
+    if (value(sig2) < value(fl)) { sig2 = fl; ++binds; }
+    T sig = sqrt(sig2);
+    if (value(rho2) > 0.0) {
+      T f = sig / sqrt(rho2);
+      px = cx + dx * f;
+      py = cy + dy * f;
+    } else {
+      px = cx - sig * sin(g.th);
+      py = cy + sig * cos(g.th);
+    }
+  }
+  x_out = px; y_out = py;
+  return binds;
+}
+
+// Forward Phi_D: the drops in insertion order, sigma' = sqrt(rho^2 + s^2).
+template <class T>
+void phi_drops(const T& x, const T& y, const Stroke<T>& g, T& x_out, T& y_out) {
+  T px = x, py = y;
+  const T s2 = drop_radius2(g);
+  for (int k = 0; k < kDrops; ++k) {
+    T cx, cy;
+    drop_centre(g, k, cx, cy);
+    T dx = px - cx, dy = py - cy;
+    T rho2 = dx * dx + dy * dy;
+    T sp = sqrt(rho2 + s2);
+    if (value(rho2) > 0.0) {
+      T f = sp / sqrt(rho2);
+      px = cx + dx * f;
+      py = cy + dy * f;
+    } else {
+      px = cx - sp * sin(g.th);
+      py = cy + sp * cos(g.th);
+    }
+  }
+  x_out = px; y_out = py;
+}
+
+// Transport of the renderers: the capsule map (R_A), none (the inert-mark
+// renderer R_U, Definition 1), or the sixteen-drop operator (R_D).
+enum Transport { kCapsule = 0, kInert = 1, kDrops16 = 2 };
+
 // Relaxed coverage (Eq. relax), clamped at 1 - 1e-7 (Sec. 5.2 "Conditioning").
 template <class T>
 T soft_coverage(const T& sp, const T& r, double tau, double tau_min) {
@@ -370,6 +453,27 @@ int orc_map_jacobian(const double* pts, int64_t n, double cx, double cy, double 
   return 0;
 }
 
+// The sixteen-drop operator on a batch of points: direction 0 = psi_D (with
+// the floor; binds per point in `binds`, nullable), 1 = Phi_D.  If jac is
+// non-null it receives d(x_out, y_out)/d(x, y) per point (2x2, row-major).
+int orc_map_drops(const double* pts, int64_t n, double cx, double cy, double th, double L, double r,
+                  int direction, double* out, int32_t* binds, double* jac) {
+  #pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    typedef Dual<2> D2;
+    D2 x(pts[2 * i]), y(pts[2 * i + 1]), xo, yo;
+    x.d[0] = 1; y.d[1] = 1;
+    Stroke<D2> g{D2(cx), D2(cy), D2(th), D2(L), D2(r)};
+    int b = 0;
+    if (direction == 0) b = psi_drops(x, y, g, xo, yo);
+    else phi_drops(x, y, g, xo, yo);
+    out[2 * i] = xo.v; out[2 * i + 1] = yo.v;
+    if (binds) binds[i] = b;
+    if (jac) { jac[4 * i] = xo.d[0]; jac[4 * i + 1] = xo.d[1]; jac[4 * i + 2] = yo.d[0]; jac[4 * i + 3] = yo.d[1]; }
+  }
+  return 0;
+}
+
 // Hard render (Eq. chain, Eq. render with alpha = indicator of K_i).
 // Pixels: if pix is non-null, only the npix listed flat indices (row*W + col)
 // are rendered and outputs are compact [npix]; otherwise npix must be W*H.
@@ -378,8 +482,9 @@ int orc_map_jacobian(const double* pts, int64_t n, double cx, double cy, double 
 // if kappa is non-null, the product of the spectral norms of Dpsi_j over the
 // strokes passed through (the chain's condition estimate).
 // n_prefix < 0 renders all strokes; otherwise only the first n_prefix.
-// inert != 0 uses psi = id (the inert-mark renderer, Definition 1).
-int orc_render_hard(const orc_prog* p, int W, int H, int n_prefix, int snap, int inert,
+// transport: 0 = the capsule map (R_A), 1 = psi = id (the inert-mark renderer,
+// Definition 1), 2 = the sixteen-drop operator (R_D).
+int orc_render_hard(const orc_prog* p, int W, int H, int n_prefix, int snap, int transport,
                     const int64_t* pix, int64_t npix, double* rgb, int32_t* idx,
                     double* margin, double* kappa) {
   std::vector<double> col, prob;
@@ -399,18 +504,20 @@ int orc_render_hard(const orc_prog* p, int W, int H, int n_prefix, int snap, int
       double sp = segment_distance(s, h, g.L);
       mg = std::min(mg, std::fabs(sp - g.r));
       if (sp <= g.r) { hit = j; break; }       // closed footprint: the tie is inside
-      if (inert) continue;
+      if (transport == kInert) continue;
       if (kappa) {
         typedef Dual<2> D2;
         D2 xd(x), yd(y), xo, yo;
         xd.d[0] = 1; yd.d[1] = 1;
         Stroke<D2> gd{D2(g.cx), D2(g.cy), D2(g.th), D2(g.L), D2(g.r)};
-        psi(xd, yd, gd, kClamp, xo, yo);
+        if (transport == kDrops16) psi_drops(xd, yd, gd, xo, yo);
+        else psi(xd, yd, gd, kClamp, xo, yo);
         kap *= spectral_norm(xo.d[0], xo.d[1], yo.d[0], yo.d[1]);
         x = xo.v; y = yo.v;
       } else {
         double xo, yo;
-        psi(x, y, g, kClamp, xo, yo);
+        if (transport == kDrops16) psi_drops(x, y, g, xo, yo);
+        else psi(x, y, g, kClamp, xo, yo);
         x = xo; y = yo;
       }
     }
@@ -432,7 +539,7 @@ namespace {
 // forward-mode dual numbers (the directional-derivative pin).
 template <class T>
 void soft_pixel(const std::vector<Stroke<T>>& g, const std::vector<T>& col, const T bg[3],
-                double tau, double tau_min, int inert, double px, double py,
+                double tau, double tau_min, int transport, double px, double py,
                 T out[3], double* T0, int* nrec) {
   T x(px), y(py);
   T C[3] = {T(0.0), T(0.0), T(0.0)};
@@ -445,9 +552,13 @@ void soft_pixel(const std::vector<Stroke<T>>& g, const std::vector<T>& col, cons
     T a = soft_coverage(sp, g[j].r, tau, tau_min);
     for (int c = 0; c < 3; ++c) C[c] = C[c] + Tr * a * col[(size_t)j * 3 + c];
     Tr = Tr * (1.0 - a);
-    if (!inert) {
+    if (transport == kCapsule) {
       T xo, yo;
       rec += psi(x, y, g[j], kFloor, xo, yo);
+      x = xo; y = yo;
+    } else if (transport == kDrops16) {
+      T xo, yo;
+      rec += psi_drops(x, y, g[j], xo, yo);
       x = xo; y = yo;
     }
   }
@@ -463,7 +574,8 @@ extern "C" {
 // Soft render (Eq. relax coverage, Eq. state compositing, epsilon-floored psi).
 // Outputs per rendered pixel: rgb[3]; T0 (final transmittance, nullable);
 // nrec (side-table records, i.e. floor binds, nullable).
-int orc_render_soft(const orc_prog* p, int W, int H, double tau, double tau_min, int inert,
+// transport as orc_render_hard.
+int orc_render_soft(const orc_prog* p, int W, int H, double tau, double tau_min, int transport,
                     const int64_t* pix, int64_t npix, double* rgb, double* T0, int32_t* nrec) {
   std::vector<double> col, prob;
   stroke_colours(p, 0, col, prob);
@@ -476,7 +588,7 @@ int orc_render_soft(const orc_prog* p, int W, int H, double tau, double tau_min,
     pixel_centre(pidx, W, H, x, y);
     double out[3], t0;
     int nr;
-    soft_pixel<double>(g, col, p->background, tau, tau_min, inert, x, y, out, &t0, &nr);
+    soft_pixel<double>(g, col, p->background, tau, tau_min, transport, x, y, out, &t0, &nr);
     for (int c = 0; c < 3; ++c) rgb[q * 3 + c] = out[c];
     if (T0) T0[q] = t0;
     if (nrec) nrec[q] = nr;

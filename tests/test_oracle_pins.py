@@ -402,3 +402,98 @@ def test_side_table_size_is_plausible():
     mean = got["nrec"].mean()
     lo, hi = SIDE["records_per_pixel_range"]
     assert lo / 4 < mean < hi * 4
+
+
+# --------------------------------------------------------------------------- transfer renderer R_D
+
+DSTROKE = (0.42, 0.57, 0.8, 0.15, 0.03)
+
+
+def drop_sample(stroke, n=50_000, box=0.3, seed=11):
+    """Points whose pull-back through the sixteen drops never enters a disc."""
+    cx, cy = stroke[0], stroke[1]
+    u = inputs.uniform(seed, 2 * n).reshape(-1, 2)
+    pts = np.array([cx, cy]) + (2 * u - 1) * box
+    out, binds = oracle.drops_map(pts, stroke, 0, return_binds=True)
+    return pts[binds == 0], out[binds == 0]
+
+
+@pytest.mark.parametrize("stroke", [(0.3, 0.6, 0.7, 0.0, 0.04), (0.5, 0.5, 2.0, 0.0, 0.01)])
+def test_sixteen_drops_at_zero_length_are_one_drop(stroke):
+    """At L = 0 the sixteen coincident drops of radius r/4 compose to the single
+    drop of radius r, sigma = sqrt(rho^2 - r^2) along the ray (the classical drop
+    map), which is also the capsule map at L = 0."""
+    pts, out = drop_sample(stroke)
+    c = np.array(stroke[:2])
+    d = pts - c
+    rho = np.hypot(*d.T)
+    want = c + d * (np.sqrt(rho ** 2 - stroke[4] ** 2) / rho)[:, None]
+    assert np.abs(out - want).max() < 1e-13
+    assert np.abs(oracle.drops_map(pts, stroke, 1) - oracle.phi_map(pts, stroke)).max() < 1e-13
+
+
+def test_sixteen_drops_round_trip_and_area():
+    """Each drop map preserves area on its exterior: Phi_D inverts psi_D and
+    det D psi_D = 1 wherever no disc is entered (Sec. "Transfer": each drop map
+    preserves area on its exterior)."""
+    pts, out = drop_sample(DSTROKE)
+    assert np.abs(oracle.drops_map(out, DSTROKE, 1) - pts).max() < 1e-13
+    _, _, J = oracle.drops_map(pts, DSTROKE, 0, return_binds=True, return_jacobian=True)
+    # the determinant's rounding grows with the stretch near a disc boundary
+    scale = 1.0 + (J ** 2).sum(axis=(1, 2))
+    assert (np.abs(np.linalg.det(J) - 1.0) / scale).max() < 1e-13
+
+
+def test_sixteen_drops_insert_the_stroke_area():
+    """The drops have radius s = sqrt(A_L(r) / (16 pi)): Phi_D sends a circle of
+    radius R around the stroke to a curve enclosing pi R^2 + A_L(r)."""
+    cx, cy, th, L, r = DSTROKE
+    R = 0.2
+
+    def circle(n):
+        t = np.arange(n) / n * 2 * math.pi
+        return np.stack([cx + R * np.cos(t), cy + R * np.sin(t)], 1)
+
+    area = _richardson_area(lambda n: oracle.drops_map(circle(n), DSTROKE, 1), 1 << 14)
+    want = math.pi * R * R + steiner_area(L, r)
+    assert abs(area - want) / want < 1e-9
+
+
+def test_sixteen_drops_are_placed_symmetrically_and_swept_in_order():
+    """The centres sit symmetrically about m along the segment, so reversing the
+    sweep (theta + pi) is the mirror image across the perpendicular bisector;
+    for L > 0 the order matters (the ordered drops do not commute), at L = 0 it
+    does not; far from the stroke the sixteen drops act as one drop of the same
+    area at m (the capsule's far field)."""
+    rev = (DSTROKE[0], DSTROKE[1], DSTROKE[2] + math.pi, DSTROKE[3], DSTROKE[4])
+    pts, out = drop_sample(DSTROKE)
+    mirrored = reflect_bisector(oracle.drops_map(reflect_bisector(pts, DSTROKE), rev, 0), DSTROKE)
+    assert np.abs(mirrored - out).max() < 1e-13
+    assert np.abs(oracle.drops_map(pts, rev, 0) - out).max() > 1e-3
+    z = (DSTROKE[0], DSTROKE[1], DSTROKE[2], 0.0, DSTROKE[4])
+    zr = (z[0], z[1], z[2] + math.pi, 0.0, z[4])
+    pz, oz = drop_sample(z)
+    assert np.abs(oracle.drops_map(pz, zr, 0) - oz).max() < 1e-15
+    far = np.array([[DSTROKE[0] + 30.0, DSTROKE[1] + 40.0], [DSTROKE[0] - 50.0, DSTROKE[1]]])
+    one = (DSTROKE[0], DSTROKE[1], 0.0, 0.0, math.sqrt(steiner_area(DSTROKE[3], DSTROKE[4]) / math.pi))
+    assert np.abs(oracle.drops_map(far, DSTROKE, 0) - oracle.psi_map(far, one, oracle.MODE_CLAMP)).max() < 1e-8
+
+
+def test_drop_transport_renders_equal_the_capsule_renders_for_drops():
+    """A program of drops only renders identically under R_D and R_A wherever
+    no floor binds (the exterior transport is the same map at L = 0 and the
+    coverage is the capsule's in both; inside a deposit the sixteen-drop
+    operator floors once per drop, the capsule once per stroke)."""
+    p = _tiny_program(14, 23)
+    p.length[:] = 0.0
+    W = H = 24
+    a = oracle.render_soft(p, W, H, 0.1, 0.01)
+    d = oracle.render_soft(p, W, H, 0.1, 0.01, transport="drops")
+    clear = (a["nrec"] == 0) & (d["nrec"] == 0)
+    assert clear.sum() > W * H // 4
+    assert np.abs(a["rgb"] - d["rgb"])[clear].max() < 1e-12
+    ha = oracle.render_hard(p, W, H)
+    hd = oracle.render_hard(p, W, H, transport="drops")
+    assert np.array_equal(ha["idx"], hd["idx"])
+    q = _tiny_program(14, 23)
+    assert np.abs(oracle.render_soft(q, W, H, 0.1, 0.01, transport="drops")["rgb"] - oracle.render_soft(q, W, H, 0.1, 0.01)["rgb"]).max() > 1e-3
