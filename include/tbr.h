@@ -78,6 +78,16 @@ typedef struct {
   float color_temp;         /* softmax temperature tau_c > 0, host value */
 } tbr_program;
 
+/* Transport of a render: the paper's capsule insertion map psi (Eq. back), or
+ * the sixteen-drop operator psi_D of the transfer renderer R_D (Sec. "Transfer
+ * across transport constructions"): stroke i's displacement is the
+ * composition of 16 classical drop maps of radius s = sqrt(A_L(r) / (16 pi))
+ * centred at the midpoints of 16 equal sub-segments, inserted in one sweep from
+ * the segment's start; coverage and membership stay the capsule's.  Inside a
+ * drop's disc the pull-back is floored on the same ray at 1e-3 s (the
+ * epsilon-floor of Sec. 5.2 applied per drop). */
+enum { TBR_TRANSPORT_CAPSULE = 0, TBR_TRANSPORT_DROPS16 = 1 };
+
 /* Statistics of one hard render (host struct). */
 typedef struct {
   int64_t band_steps;       /* pixel-stroke steps whose |sigma' - r| fell in the
@@ -104,6 +114,14 @@ typedef struct {
 TBR_API tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
                            int32_t snap, float* out_rgb, int32_t* out_idx,
                            tbr_hard_stats* stats, void* stream);
+
+/* tbr_render_hard with a choice of transport (TBR_TRANSPORT_*): with
+ * TBR_TRANSPORT_DROPS16 each pixel that is outside K_i is pulled back through
+ * the sixteen drops instead of psi_i (membership in FP64 within the band, the
+ * drops in FP32).  Otherwise identical to tbr_render_hard. */
+TBR_API tbr_status tbr_render_hard_transport(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
+                                             int32_t snap, int32_t transport, float* out_rgb, int32_t* out_idx,
+                                             tbr_hard_stats* stats, void* stream);
 
 /* Allocation-free hard render.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory at all (a
@@ -145,6 +163,8 @@ typedef struct {
   int32_t repair_capacity;  /* pixels the adjoint can repair per call, at most
                                1024; 0 = default (256).  Memory: 32 B x n per
                                pixel of capacity. */
+  int32_t transport;        /* TBR_TRANSPORT_*; TBR_TRANSPORT_DROPS16 renders
+                               forward only (no context, not inert) */
 } tbr_soft_opts;
 
 typedef struct tbr_ctx tbr_ctx;

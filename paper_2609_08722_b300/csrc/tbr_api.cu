@@ -189,7 +189,16 @@ const char* tbr_version(void) { return "tbr-b300 0.1 (sm_103a)"; }
 tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
                            int32_t snap, float* out_rgb, int32_t* out_idx, tbr_hard_stats* stats,
                            void* stream) {
+  return tbr_render_hard_transport(prog, W, H, n_prefix, snap, TBR_TRANSPORT_CAPSULE, out_rgb, out_idx, stats,
+                                   stream);
+}
+
+tbr_status tbr_render_hard_transport(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
+                                     int32_t snap, int32_t transport, float* out_rgb, int32_t* out_idx,
+                                     tbr_hard_stats* stats, void* stream) {
   if (!prog) return fail(TBR_ERR_INVALID_ARG, "program is NULL");
+  if (transport != TBR_TRANSPORT_CAPSULE && transport != TBR_TRANSPORT_DROPS16)
+    return fail(TBR_ERR_INVALID_ARG, "unknown transport %d", transport);
   const int n = (n_prefix < 0 || n_prefix > prog->n) ? prog->n : n_prefix;
   tbr_status s = check_program(prog, n);
   if (s != TBR_OK) return s;
@@ -208,7 +217,8 @@ tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H, int32_
   PackArgs pa{prog, n, 0.0f, 1.0f, snap ? 1 : 0, packed, nullptr, status};
   if (e == cudaSuccess) e = launch_pack(pa, st);
   if (e == cudaSuccess)
-    e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status, stats != nullptr, st);
+    e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status, stats != nullptr, st,
+                    transport);
   unsigned long long host[ST_COUNT] = {0};
   if (e == cudaSuccess && stats) {
     e = cudaMemcpyAsync(host, status, sizeof(host), cudaMemcpyDeviceToHost, st);
@@ -242,6 +252,10 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return fail(TBR_ERR_INVALID_ARG, "negative checkpoint interval or record capacity");
   if (opts->repair_capacity < 0 || opts->repair_capacity > kRepairMax || !std::isfinite(opts->drift_tolerance))
     return fail(TBR_ERR_INVALID_ARG, "repair capacity outside [0, %d] or non-finite drift tolerance", kRepairMax);
+  if (opts->transport != TBR_TRANSPORT_CAPSULE && opts->transport != TBR_TRANSPORT_DROPS16)
+    return fail(TBR_ERR_INVALID_ARG, "unknown transport %d", opts->transport);
+  if (opts->transport == TBR_TRANSPORT_DROPS16 && (ctx || opts->inert))
+    return fail(TBR_ERR_INVALID_ARG, "the sixteen-drop transport renders forward only (no context, not inert)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ck = opts->checkpoint_every > 0 ? opts->checkpoint_every : 32;
   const int cap = opts->record_capacity > 0 ? opts->record_capacity : 64;
@@ -260,6 +274,7 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     sa.packed = packed; sa.n = prog->n; sa.W = W; sa.H = H;
     for (int i = 0; i < 3; ++i) sa.bg[i] = prog->background[i];
     sa.inert = opts->inert ? 1 : 0; sa.ck_every = ck; sa.cap = cap;
+    sa.transport = opts->transport;
     sa.out_rgb = out_rgb; sa.s0 = nullptr; sa.s0b = nullptr; sa.ckpt = nullptr; sa.ck_lt = nullptr;
     sa.rec = nullptr; sa.rec_i = nullptr; sa.status = status;
     if (e == cudaSuccess) e = launch_soft(sa, st);

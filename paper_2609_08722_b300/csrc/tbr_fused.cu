@@ -67,6 +67,8 @@ tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32
   if (!opts || !target) return fail(TBR_ERR_INVALID_ARG, "opts or target is NULL");
   if (!(opts->tau >= 0.0f) || !(opts->tau_min > 0.0f)) return fail(TBR_ERR_INVALID_ARG, "need tau >= 0, tau_min > 0");
   if (opts->inert) return fail(TBR_ERR_INVALID_ARG, "the loss-fused path renders the transport model only");
+  if (opts->transport != TBR_TRANSPORT_CAPSULE)
+    return fail(TBR_ERR_INVALID_ARG, "the replay adjoint is built for the capsule transport");
   if (opts->checkpoint_every < 0 || opts->record_capacity < 0)
     return fail(TBR_ERR_INVALID_ARG, "negative checkpoint interval or record capacity");
   if (opts->repair_capacity < 0 || opts->repair_capacity > kRepairMax || !std::isfinite(opts->drift_tolerance))

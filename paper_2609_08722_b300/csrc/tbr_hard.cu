@@ -3,6 +3,8 @@
 // packed strokes stream through shared memory in chunks of CH records by 1-D
 // bulk TMA (cp.async.bulk + mbarrier), last chunk first, and every thread reads
 // the current stroke as a shared-memory broadcast (hard_tile, tbr_tile.cuh).
+// The transfer renderer R_D keeps the capsule membership and replaces the
+// transport by the sixteen-drop pull-back (drops_step).
 #include "tbr_tile.cuh"
 
 namespace tbr {
@@ -11,7 +13,7 @@ namespace {
 
 constexpr int kHardCH = 64;
 
-template <int CH>
+template <int CH, bool DROPS>
 __global__ void __launch_bounds__(kTileThreads) k_hard(const float* __restrict__ packed, int n, int W, int H,
                                                        float bg0, float bg1, float bg2,
                                                        float* __restrict__ out_rgb, int* __restrict__ out_idx,
@@ -24,8 +26,8 @@ __global__ void __launch_bounds__(kTileThreads) k_hard(const float* __restrict__
   const float bg[3] = {bg0, bg1, bg2};
   unsigned band = 0, visited = 0;
   bool background = false;
-  hard_tile<CH>(ring, packed, n, blockIdx.x, W, H, bg, poison, out_rgb, out_idx, band, visited, background,
-                status);
+  hard_tile<CH, DROPS>(ring, packed, n, blockIdx.x, W, H, bg, poison, out_rgb, out_idx, band, visited,
+                       background, status);
   if (want_stats) {
     const unsigned bsum = __reduce_add_sync(0xffffffffu, band);
     const unsigned vsum = __reduce_add_sync(0xffffffffu, visited);
@@ -41,11 +43,15 @@ __global__ void __launch_bounds__(kTileThreads) k_hard(const float* __restrict__
 }  // namespace
 
 cudaError_t launch_hard(const float* packed, int n, int W, int H, const float bg[3], float* out_rgb,
-                        int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st) {
-  const int tiles = ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+                        int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st, int transport) {
+  const int tiles = tile_count(W, H);
   KernelTimer kt(TBR_K_HARD, st);
-  k_hard<kHardCH><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb, out_idx,
-                                                  status, want_stats);
+  if (transport == 1)
+    k_hard<kHardCH, true><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb, out_idx,
+                                                          status, want_stats);
+  else
+    k_hard<kHardCH, false><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb,
+                                                           out_idx, status, want_stats);
   return cudaGetLastError();
 }
 

@@ -463,6 +463,50 @@ __device__ __forceinline__ float drop_step(float dx, float dy, const StrokeF& g,
   return rho;
 }
 
+// Pull-back through the sixteen drops of the transfer renderer R_D (Sec.
+// "Transfer across transport constructions"): stroke i's displacement is the
+// composition of K = 16 classical drop maps of radius s, s^2 = A_L(r) / (16 pi)
+// (so the inserted area is the stroke's own), centred at m + e L ((k + 1/2)/16 -
+// 1/2) and inserted in one sweep k = 0..15; the pull-back undoes them in reverse
+// order.  In displacement form a drop moves a point at distance rho from its
+// centre by -(x - c) s^2 / (rho (rho + sigma)), sigma = sqrt(rho^2 - s^2);
+// inside its disc (rho^2 - s^2 < (eps s)^2) the point is floored on the same ray
+// at eps s (rho = 0: along e_perp).  The displacements go to the lo parts of the
+// hi/lo position, which is renormalised at the end.  Returns the floor binds.
+constexpr int kDrops = 16;
+__device__ __forceinline__ int drops_step(float& xh, float& yh, float& xl, float& yl, const StrokeF& g) {
+  const float s2 = g.Ar * (1.0f / (kDrops * kPiF));
+  const float fl = (kEpsFloor * kEpsFloor) * s2;
+  int binds = 0;
+#pragma unroll 4
+  for (int k = kDrops - 1; k >= 0; --k) {
+    const float t = g.L * ((static_cast<float>(k) + 0.5f) * (1.0f / kDrops) - 0.5f);
+    const float dx = (xh - fmaf(t, g.ex, g.mx)) + xl, dy = (yh - fmaf(t, g.ey, g.my)) + yl;
+    const float rho2 = fmaf(dx, dx, dy * dy);
+    const float sig2 = rho2 - s2;
+    if (sig2 >= fl) {
+      const float rho = sqrt_a(rho2);
+      const float kf = -s2 * rcp_a(rho * (rho + sqrt_a(sig2)));
+      xl = fmaf(kf, dx, xl);
+      yl = fmaf(kf, dy, yl);
+    } else {
+      ++binds;
+      const float sig = sqrt_a(fl);
+      if (rho2 > 0.0f) {
+        const float kf = fmaf(sig, rsqrt_a(rho2), -1.0f);
+        xl = fmaf(kf, dx, xl);
+        yl = fmaf(kf, dy, yl);
+      } else {
+        xl += -g.ey * sig - dx;
+        yl += g.ex * sig - dy;
+      }
+    }
+  }
+  pos_renorm(xh, xl);
+  pos_renorm(yh, yl);
+  return binds;
+}
+
 // Frame coordinates of a hi/lo position.
 __device__ __forceinline__ void to_frame(float xh, float yh, float xl, float yl, const StrokeF& g, float& s,
                                          float& h) {
@@ -638,14 +682,17 @@ struct PackArgs {
 };
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st);
 
+// transport: 0 = the capsule map, 1 = the sixteen drops of the transfer renderer.
 cudaError_t launch_hard(const float* packed, int n, int W, int H, const float bg[3], float* out_rgb,
-                        int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st);
+                        int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st,
+                        int transport = 0);
 
 struct SoftArgs {
   const float* packed;
   int n, W, H;
   float bg[3];
   int inert;
+  int transport = 0;         // 0: capsule map; 1: sixteen drops (forward only, no record)
   int ck_every;              // checkpoint interval k (>= 1)
   int cap;                   // side-table capacity per pixel
   float* out_rgb;

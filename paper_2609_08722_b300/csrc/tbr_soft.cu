@@ -19,7 +19,7 @@ namespace {
 
 constexpr int kSoftCH = 64;
 
-template <int CH, bool RECORD, bool INERT>
+template <int CH, bool RECORD, bool INERT, bool DROPS = false>
 __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
   ring.init(sbuf, sbar);
   RecordView rv{a.rec, a.rec_i, a.ckpt, a.ck_lt, P, p, a.cap, a.ck_every};
   PixelState st;
-  const bool ok = soft_forward_tile<CH, RECORD, INERT>(
+  const bool ok = soft_forward_tile<CH, RECORD, INERT, DROPS>(
       ring, a.packed, a.n, valid, (static_cast<float>(px) + 0.5f) / static_cast<float>(W),
       (static_cast<float>(py) + 0.5f) / static_cast<float>(H), rv, st, status);
   if (valid) {
@@ -70,7 +70,8 @@ cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
   const int tiles = tile_count(a.W, a.H);
   const bool rec = a.s0 != nullptr;
   KernelTimer kt(TBR_K_SOFT, st);
-  if (rec && a.inert) k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
+  if (a.transport == 1) k_soft<kSoftCH, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+  else if (rec && a.inert) k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
   else if (rec) k_soft<kSoftCH, true, false><<<tiles, kTileThreads, 0, st>>>(a);
   else if (a.inert) k_soft<kSoftCH, false, true><<<tiles, kTileThreads, 0, st>>>(a);
   else k_soft<kSoftCH, false, false><<<tiles, kTileThreads, 0, st>>>(a);

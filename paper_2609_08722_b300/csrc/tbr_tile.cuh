@@ -54,10 +54,11 @@ __device__ __forceinline__ void tile_pixel(int tile, int W, int& px, int& py) {
 // strokes n-1 .. 0.  With RECORD, pushes (x_i, i) for floored samples and
 // stores (x_i, log2 T_i) every ck strokes.  All threads of the CTA must call it.
 // Returns false if a bounded wait gave up (the status word is set).
-template <int CH, bool RECORD, bool INERT>
+template <int CH, bool RECORD, bool INERT, bool DROPS = false>
 __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, bool valid,
                                   float x0, float y0, const RecordView& rv, PixelState& st,
                                   unsigned long long* status) {
+  static_assert(!(DROPS && (RECORD || INERT)), "the sixteen-drop transport renders forward only");
   st.xh = x0; st.yh = y0; st.xl = 0.0f; st.yl = 0.0f;
   st.lt = 0.0f; st.cnt = 0;
   st.C0 = st.C1 = st.C2 = 0.0f;
@@ -96,7 +97,14 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         float sp, ds = 0.0f, dh = 0.0f, ddx = 0.0f, ddy = 0.0f;
         bool floored = false;
         const bool drop = g.L == 0.0f;  // warp-uniform
-        if (drop) {
+        if (DROPS) {
+          // capsule coverage; the transport (sixteen drops) is applied after compositing
+          float s, h;
+          to_frame(st.xh, st.yh, st.xl, st.yl, g, s, h);
+          const float as = fabsf(s), ah = fabsf(h);
+          const float d = as - g.hl;
+          sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
+        } else if (drop) {
           const float dx = (st.xh - g.mx) + st.xl, dy = (st.yh - g.my) + st.yl;
           if (INERT) sp = sqrt_a(fmaf(dx, dx, dy * dy));
           else sp = drop_step<true>(dx, dy, g, ddx, ddy, floored);
@@ -122,7 +130,9 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         st.C1 = fmaf(w, S[F_CG], st.C1);
         st.C2 = fmaf(w, S[F_CB], st.C2);
         st.lt -= cv.sp2;
-        if (!INERT) {
+        if (DROPS) {
+          st.cnt += drops_step(st.xh, st.yh, st.xl, st.yl, g);
+        } else if (!INERT) {
           if (RECORD && floored) {
             if (st.cnt < rv.cap) {
               const size_t o = static_cast<size_t>(st.cnt) * rv.stride + rv.off;
@@ -213,11 +223,41 @@ static __device__ __noinline__ void phi_f64(double& x, double& y, const float* _
   y = my + sn * ey + hn * ex;
 }
 
+// FP64 membership test of the hard render's band (|sigma' - r| < kBand) for
+// the transfer renderer, whose transport is applied in FP32 afterwards.
+static __device__ __noinline__ bool hard_member_f64(float xh, float yh, float xl, float yl,
+                                                   const float* __restrict__ S) {
+  const double* D = reinterpret_cast<const double*>(S + F_D64);
+  const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
+  const double x = static_cast<double>(xh) + static_cast<double>(xl);
+  const double y = static_cast<double>(yh) + static_cast<double>(yl);
+  const double dx = x - mx, dy = y - my;
+  const double as = fabs(dx * ex + dy * ey), ah = fabs(dy * ex - dx * ey), d = as - hl;
+  const double sp = d > 0.0 ? sqrt(d * d + ah * ah) : ah;
+  return sp <= r;
+}
+
 // One stroke of the hard chain in FP32.  Returns true if x lies in K_i;
 // otherwise moves x to psi_i(x) (displacement form, hi/lo position).
+template <bool DROPS = false>
 __device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float& yl,
                                           const float* __restrict__ S, unsigned& band) {
   const StrokeF g = load_stroke(S);
+  if (DROPS) {  // capsule membership, then the sixteen-drop pull-back
+    float s, h;
+    to_frame(xh, yh, xl, yl, g, s, h);
+    const float as = fabsf(s), ah = fabsf(h);
+    const float d = as - g.hl;
+    const float diff = (d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah) - g.r;
+    bool inside = diff <= 0.0f;
+    if (fabsf(diff) < kBand) {
+      ++band;
+      inside = hard_member_f64(xh, yh, xl, yl, S);
+    }
+    if (inside) return true;
+    drops_step(xh, yh, xl, yl, g);
+    return false;
+  }
   if (g.L == 0.0f) {  // drop (warp-uniform): radial step in world coordinates
     const float dx = (xh - g.mx) + xl, dy = (yh - g.my) + yl;
     const float rho = sqrt_a(fmaf(dx, dx, dy * dy));
@@ -256,7 +296,7 @@ __device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float
 // strokes last to first, each pixel stops at the first footprint containing it,
 // the CTA stops when all its pixels have.  Writes colour and index.
 // All threads of the CTA must call it.  Returns false if a bounded wait gave up.
-template <int CH>
+template <int CH, bool DROPS = false>
 __device__ bool hard_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, int tile, int W, int H,
                           const float bg[3], bool poison, float* __restrict__ out_rgb, int* __restrict__ out_idx,
                           unsigned& band, unsigned& visited, bool& background, unsigned long long* status) {
@@ -290,7 +330,7 @@ __device__ bool hard_tile(ChunkRing<CH>& ring, const float* __restrict__ packed,
     if (alive) {
       for (int j = cnt - 1; j >= 0; --j) {
         ++visited;
-        if (hard_step(xh, yh, xl, yl, S0 + j * kRec, band)) {
+        if (hard_step<DROPS>(xh, yh, xl, yl, S0 + j * kRec, band)) {
           hit = base + j;
           alive = false;
           break;

@@ -26,7 +26,7 @@ _STATUS_NAMES = {0: "TBR_OK", 1: "TBR_ERR_INVALID_ARG", 2: "TBR_ERR_OOM", 3: "TB
                  7: "TBR_ERR_NOT_FOUND"}
 
 # Every entry point include/tbr.h declares (checked by the ABI test).
-EXPORTED = ["tbr_render_hard", "tbr_render_hard_noalloc", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
+EXPORTED = ["tbr_render_hard", "tbr_render_hard_transport", "tbr_render_hard_noalloc", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
             "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_render_soft_adjoint_mse", "tbr_fit_default_config",
             "tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_fit_iteration",
             "tbr_fit_destroy", "tbr_serve_default_config", "tbr_serve_create", "tbr_serve_load_program",
@@ -58,7 +58,10 @@ class TbrSoftOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("tau_min", ctypes.c_float),
                 ("checkpoint_every", ctypes.c_int32), ("record_capacity", ctypes.c_int32),
                 ("inert", ctypes.c_int32), ("drift_tolerance", ctypes.c_float),
-                ("repair_capacity", ctypes.c_int32)]
+                ("repair_capacity", ctypes.c_int32), ("transport", ctypes.c_int32)]
+
+
+TRANSPORTS = {"capsule": 0, "drops": 1}
 
 
 class TbrCtxStats(ctypes.Structure):
@@ -85,6 +88,8 @@ def lib() -> ctypes.CDLL:
             st = ctypes.c_int
             L.tbr_render_hard.argtypes = [ctypes.POINTER(TbrProgram), i32, i32, i32, i32, P, P,
                                           ctypes.POINTER(TbrHardStats), P]
+            L.tbr_render_hard_transport.argtypes = [ctypes.POINTER(TbrProgram), i32, i32, i32, i32, i32, P, P,
+                                                    ctypes.POINTER(TbrHardStats), P]
             L.tbr_render_soft.argtypes = [ctypes.POINTER(TbrProgram), i32, i32,
                                           ctypes.POINTER(TbrSoftOpts), P, ctypes.POINTER(P), P]
             L.tbr_render_backward.argtypes = [P, P, P, P, P, P, P, P, P, P]
@@ -96,8 +101,8 @@ def lib() -> ctypes.CDLL:
             L.tbr_loss_mse.argtypes = [P, P, i64, P, P, P]
             L.tbr_last_error.restype = ctypes.c_char_p
             L.tbr_version.restype = ctypes.c_char_p
-            for f in ("tbr_render_hard", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
-                      "tbr_loss_mse"):
+            for f in ("tbr_render_hard", "tbr_render_hard_transport", "tbr_render_soft", "tbr_render_backward",
+                      "tbr_ctx_status", "tbr_loss_mse"):
                 getattr(L, f).restype = st
             _lib = L
     return _lib
@@ -170,16 +175,23 @@ class DeviceProgram:
 
 
 def render_hard(prog: DeviceProgram, W: int, H: int, n_prefix: int = -1, snap: bool = False,
-                with_idx: bool = True, stats: bool = False, out_rgb=None, out_idx=None, stream=None):
-    """tbr_render_hard; returns (rgb [H,W,3], idx [H,W] or None, stats dict or None)."""
+                with_idx: bool = True, stats: bool = False, out_rgb=None, out_idx=None, stream=None,
+                transport: str = "capsule"):
+    """tbr_render_hard (transport "capsule") or tbr_render_hard_transport;
+    returns (rgb [H,W,3], idx [H,W] or None, stats dict or None)."""
     dev = prog.cx.device
     rgb = out_rgb if out_rgb is not None else torch.empty((H, W, 3), device=dev, dtype=torch.float32)
     idx = out_idx if out_idx is not None else (
         torch.empty((H, W), device=dev, dtype=torch.int32) if with_idx else None)
     st = TbrHardStats() if stats else None
     s = prog.struct()
-    check(lib().tbr_render_hard(ctypes.byref(s), W, H, n_prefix, int(bool(snap)), _ptr(rgb), _ptr(idx),
-                                ctypes.byref(st) if st is not None else None, _stream(stream)))
+    if transport == "capsule":
+        check(lib().tbr_render_hard(ctypes.byref(s), W, H, n_prefix, int(bool(snap)), _ptr(rgb), _ptr(idx),
+                                    ctypes.byref(st) if st is not None else None, _stream(stream)))
+    else:
+        check(lib().tbr_render_hard_transport(ctypes.byref(s), W, H, n_prefix, int(bool(snap)),
+                                              TRANSPORTS[transport], _ptr(rgb), _ptr(idx),
+                                              ctypes.byref(st) if st is not None else None, _stream(stream)))
     sd = None
     if st is not None:
         sd = {"band_steps": st.band_steps, "background_pixels": st.background_pixels,
@@ -240,13 +252,14 @@ class SoftContext:
 def render_soft(prog: DeviceProgram, W: int, H: int, tau: float, tau_min: float, record: bool = False,
                 checkpoint_every: int = 0, record_capacity: int = 0, inert: bool = False,
                 out_rgb=None, stream=None, reuse: Optional["SoftContext"] = None,
-                drift_tolerance: float = 0.0, repair_capacity: int = 0):
+                drift_tolerance: float = 0.0, repair_capacity: int = 0, transport: str = "capsule"):
     """tbr_render_soft; returns (rgb [H,W,3], SoftContext or None).  ``reuse``
-    overwrites an existing context of the same shape instead of allocating."""
+    overwrites an existing context of the same shape instead of allocating.
+    ``transport="drops"`` renders with the sixteen-drop transport (forward only)."""
     dev = prog.cx.device
     rgb = out_rgb if out_rgb is not None else torch.empty((H, W, 3), device=dev, dtype=torch.float32)
     opts = TbrSoftOpts(float(tau), float(tau_min), int(checkpoint_every), int(record_capacity),
-                       int(bool(inert)), float(drift_tolerance), int(repair_capacity))
+                       int(bool(inert)), float(drift_tolerance), int(repair_capacity), TRANSPORTS[transport])
     handle = ctypes.c_void_p(reuse.handle if reuse is not None else None)
     s = prog.struct()
     check(lib().tbr_render_soft(ctypes.byref(s), W, H, ctypes.byref(opts), _ptr(rgb),

@@ -349,3 +349,56 @@ def test_fused_mse_adjoint_operating_point(operating):
     assert abs(loss_f.item() - loss_s.item()) <= 1e-6 * abs(loss_s.item())
     for k in GROUPS:
         assert rel(g_f[k].cpu().numpy().ravel(), g_s[k].cpu().numpy().ravel()) <= 1e-4, k
+
+
+# --------------------------------------------------------------------------- transfer renderer R_D
+
+def _long_program():
+    return inputs.make_program(120, seed=311, palette_seed=312, k=8, r_lo=0.004, r_hi=0.04, len_max=0.8,
+                               p_drop=0.0)
+
+
+@pytest.mark.parametrize("which", ["small", "long"])
+def test_hard_sixteen_drops(small, which):
+    """R_D hard render (capsule membership, sixteen-drop pull-back) against the
+    oracle's, with the same band rule as the capsule renderer."""
+    p = small[0] if which == "small" else _long_program()
+    dp = tbr.DeviceProgram.from_host(p)
+    W, H = 128, 96
+    rgb, idx, st = tbr.render_hard(dp, W, H, stats=True, transport="drops")
+    o = oracle.render_hard(p, W, H, with_kappa=True, transport="drops")
+    mism, band, outside, cond = hard_agreement(idx.cpu().numpy().ravel(), o)
+    print(f"R_D {which}: band {band.sum()}, mismatches {mism.sum()} (outside band {outside.sum()}), stats {st}")
+    assert not (outside & ~cond).any()
+    assert mism.mean() < 0.01
+    ok = ~mism
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3)[ok] - o["rgb"][ok]).max() < 1e-6
+
+
+@pytest.mark.parametrize("which,W,H", [("small", 128, 128), ("long", 75, 61)])
+def test_soft_sixteen_drops(small, which, W, H):
+    p = small[0] if which == "small" else _long_program()
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, _ = tbr.render_soft(dp, W, H, 0.0, 1 / 200, transport="drops")
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200, transport="drops")
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"])
+    print(f"R_D soft {which}: max {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= SOFT_TOL
+
+
+def test_soft_sixteen_drops_operating_point_sampled(operating):
+    p, dp = operating
+    W = H = 1024
+    rgb, _ = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, transport="drops")
+    pix = inputs.sample_pixels(33, W * H, 2000)
+    o = oracle.render_soft(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix, transport="drops")
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3)[pix] - o["rgb"])
+    print(f"R_D soft op max {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= SOFT_TOL
+
+
+def test_sixteen_drops_render_forward_only(small):
+    _, dp = small
+    with pytest.raises(tbr.TbrError) as ei:
+        tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, record=True, transport="drops")
+    assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
