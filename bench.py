@@ -42,6 +42,11 @@ OPS_FWD = 40.6
 OPS_BWD = 120.8
 XU_FWD = 11.8
 XU_BWD = 15.7
+# Transfer renderer R_D, soft forward per pixel-stroke: capsule distance 9 +
+# coverage and compositing 11 + 16 drops x (centre 2, offset 4, rho^2 2,
+# sigma^2 1, step 3, update 2 = 14); XU: 16 x (sqrt + rcp) + 4.
+OPS_FWD_D = 9 + 11 + 16 * 14
+XU_FWD_D = 16 * 2 + 4
 # FP32 lane peak: 148 SMs x 128 FP32 lanes x 2032 MHz (one op per lane per cycle);
 # XU (MUFU) peak: 16 results per clock per SM (4 per sub-partition).
 SMS, LANES, SM_MAX_MHZ, XU_PER_SM = 148, 128, 2032.0, 16
@@ -428,6 +433,34 @@ def run_native(args):
                          "fp64_band_steps": st_h["band_steps"], "background_pixels": st_h["background_pixels"]})
             del rgb_h, idx_h
 
+    # transfer renderer R_D (sixteen-drop transport, forward only) on the same program
+    transfer = None
+    if rank == 0 and not args.no_hard and args.res == RES and args.strokes == N_STROKES:
+        def timed(fn, reps=3):
+            fn()
+            ts = []
+            for i in range(reps):
+                flush.fill_(float(i))
+                s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record()
+                fn()
+                e0.record()
+                torch.cuda.synchronize()
+                ts.append(s0.elapsed_time(e0))
+            return sum(ts) / len(ts)
+        rgb_d = torch.empty((H, W, 3), device=device)
+        idx_d = torch.empty((H, W), dtype=torch.int32, device=device)
+        soft_d = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_d, transport="drops"))
+        hard_d = timed(lambda: tbr.render_hard(prog, W, H, out_rgb=rgb_d, out_idx=idx_d, transport="drops"))
+        ach = OPS_FWD_D * units / (soft_d * 1e-3) * 1e-9
+        transfer = {"workload": "R_D (sixteen-drop transport) soft forward and hard render of the same program",
+                    "soft_forward_ms": soft_d, "soft_evals_per_s": units / (soft_d * 1e-3),
+                    "hard_ms": hard_d,
+                    "soft_roofline": {"ops_per_unit": OPS_FWD_D, "achieved": ach, "frac": ach / PEAK_GOPS,
+                                      "xu_ops_per_unit": XU_FWD_D,
+                                      "xu_frac": XU_FWD_D * units / (soft_d * 1e-3) * 1e-9 / PEAK_XU_GOPS}}
+        del rgb_d, idx_d
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.res == RES and args.strokes == N_STROKES:
         rate, info = oracle_rate(prog_h, args.cpu_seconds)
@@ -469,6 +502,7 @@ def run_native(args):
             "fused_path": fused,
             "serve": serve,
             "hard": hard,
+            "transfer_renderer": transfer,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,

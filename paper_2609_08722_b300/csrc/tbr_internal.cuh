@@ -469,7 +469,8 @@ __device__ __forceinline__ float drop_step(float dx, float dy, const StrokeF& g,
 // (so the inserted area is the stroke's own), centred at m + e L ((k + 1/2)/16 -
 // 1/2) and inserted in one sweep k = 0..15; the pull-back undoes them in reverse
 // order.  In displacement form a drop moves a point at distance rho from its
-// centre by -(x - c) s^2 / (rho (rho + sigma)), sigma = sqrt(rho^2 - s^2);
+// centre by -(x - c) s^2 / (rho (rho + sigma)), sigma = sqrt(rho^2 - s^2), with
+// rho (rho + sigma) formed as rho^2 + sqrt(rho^2 sigma^2);
 // inside its disc (rho^2 - s^2 < (eps s)^2) the point is floored on the same ray
 // at eps s (rho = 0: along e_perp).  The displacements go to the lo parts of the
 // hi/lo position, which is renormalised at the end.  Returns the floor binds.
@@ -485,8 +486,8 @@ __device__ __forceinline__ int drops_step(float& xh, float& yh, float& xl, float
     const float rho2 = fmaf(dx, dx, dy * dy);
     const float sig2 = rho2 - s2;
     if (sig2 >= fl) {
-      const float rho = sqrt_a(rho2);
-      const float kf = -s2 * rcp_a(rho * (rho + sqrt_a(sig2)));
+      // rho (rho + sigma) = rho^2 + sqrt(rho^2 sigma^2): one square root and one reciprocal
+      const float kf = -s2 * rcp_a(rho2 + sqrt_a(rho2 * sig2));
       xl = fmaf(kf, dx, xl);
       yl = fmaf(kf, dy, yl);
     } else {
