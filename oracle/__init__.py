@@ -77,6 +77,8 @@ def _load():
                                          P, i64, P, P, P, P, P]
             lib.orc_map_drops.argtypes = [P, i64, dbl, dbl, dbl, dbl, dbl, ctypes.c_int, P, P, P]
             lib.orc_map_drops.restype = ctypes.c_int
+            lib.orc_compensate.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+            lib.orc_compensate.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             for f in ("orc_map", "orc_map_jacobian", "orc_render_hard", "orc_render_soft",
                       "orc_soft_jvp", "orc_soft_vjp"):
@@ -182,6 +184,19 @@ def drops_map(pts, stroke, direction=0, return_binds=False, return_jacobian=Fals
     if return_jacobian:
         res.append(jac)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def compensate(prog, endpoint=False, skip_blocked=False):
+    """One-pass closed-form compensation of a program (anchor or endpoint
+    variant); returns dict cx, cy, theta, length [n] (FP64), blocked [n]."""
+    pk = _Packed(prog)
+    n = pk.n
+    out = {k: np.empty(n) for k in ("cx", "cy", "theta", "length")}
+    blocked = np.empty(n, dtype=np.int32)
+    _load().orc_compensate(pk.ref, int(bool(endpoint)), int(bool(skip_blocked)), _ptr(out["cx"]), _ptr(out["cy"]),
+                           _ptr(out["theta"]), _ptr(out["length"]), _ptr(blocked))
+    out["blocked"] = blocked
+    return out
 
 
 def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with_kappa=False, transport=None):

@@ -14,6 +14,9 @@
 //   * the interior extension by clamping C (Sec. 4 "The chain") and the
 //     implemented epsilon-floor of Sec. 5.2;
 //   * the hard and soft renderers (Eq. chain, Eq. render, Eq. relax, Eq. state);
+//   * the one-pass closed-form compensation baseline (Sec. "Closed-form
+//     compensation baseline"): anchor or endpoint pre-images through every
+//     later stroke's inverse map, with blocked steps clamped or skipped;
 //   * the sixteen-drop operator psi_D of the transfer renderer R_D (Sec.
 //     "Transfer across transport constructions"): K = 16 classical drop maps of
 //     the stroke's total area laid along its segment, with capsule coverage;
@@ -237,6 +240,10 @@ int psi(const T& x, const T& y, const Stroke<T>& g, int mode, T& x_out, T& y_out
     if (value(C) < value(fl)) { C = fl; floored = 1; }
   } else if (value(C) < 0.0) {
     C = T(0.0);
+    if (value(g.L) == 0.0) {  // the ideal extension maps a drop's disc onto its centre
+      x_out = g.cx; y_out = g.cy;
+      return 0;
+    }
   }
   T sig = C / (g.L + sqrt(g.L * g.L + kPi * C));
   T sn, hn;
@@ -751,6 +758,62 @@ int orc_soft_vjp(const orc_prog* p, int W, int H, double tau, double tau_min, in
       }
   }
   return 0;
+}
+
+// One-pass closed-form compensation (Sec. "Closed-form compensation
+// baseline"): from the last stroke to the first, each stroke of the given
+// (inert-mark) program is moved so that the transport of every later, already
+// compensated stroke carries it back to where the program puts it.  Its segment
+// start (anchor variant: the offset vector is kept) or both ends (endpoint
+// variant) are pre-imaged through psi_j (Eq. back) of the strokes j after it,
+// the last one first.  A point inside K_j has no pre-image (Lemma
+// "obstruction"); that step is clamped onto the segment by the ideal extension
+// of psi_j (skip = 0) or skipped (skip = 1), and the stroke counts as blocked.
+// Outputs the compensated cx, cy, th, L (r and colours are unchanged) and the
+// blocked flags; returns the number of blocked strokes.
+int orc_compensate(const orc_prog* p, int endpoint, int skip, double* cx, double* cy, double* th, double* L,
+                   int32_t* blocked) {
+  const int n = p->n;
+  std::vector<Stroke<double>> c(n);
+  int nblocked = 0;
+  for (int i = n - 1; i >= 0; --i) {
+    const Stroke<double> g = stroke_of<double>(p, i);
+    const double ex = std::cos(g.th), ey = std::sin(g.th);
+    double pt[2][2] = {{g.cx - 0.5 * g.L * ex, g.cy - 0.5 * g.L * ey},
+                       {g.cx + 0.5 * g.L * ex, g.cy + 0.5 * g.L * ey}};
+    int blk = 0;
+    for (int q = 0; q < (endpoint ? 2 : 1); ++q) {
+      double x = pt[q][0], y = pt[q][1];
+      for (int j = n - 1; j > i; --j) {
+        double s, h;
+        to_frame(x, y, c[j], s, h);
+        if (segment_distance(s, h, c[j].L) <= c[j].r) {
+          blk = 1;
+          if (skip) continue;
+        }
+        double xo, yo;
+        psi(x, y, c[j], kClamp, xo, yo);
+        x = xo; y = yo;
+      }
+      pt[q][0] = x; pt[q][1] = y;
+    }
+    Stroke<double> o = g;
+    if (endpoint) {
+      const double dx = pt[1][0] - pt[0][0], dy = pt[1][1] - pt[0][1];
+      o.L = std::hypot(dx, dy);
+      if (o.L > 0.0) o.th = std::atan2(dy, dx);
+      o.cx = 0.5 * (pt[0][0] + pt[1][0]);
+      o.cy = 0.5 * (pt[0][1] + pt[1][1]);
+    } else {
+      o.cx = pt[0][0] + 0.5 * g.L * ex;
+      o.cy = pt[0][1] + 0.5 * g.L * ey;
+    }
+    c[i] = o;
+    cx[i] = o.cx; cy[i] = o.cy; th[i] = o.th; L[i] = o.L;
+    blocked[i] = blk;
+    nblocked += blk;
+  }
+  return nblocked;
 }
 
 int orc_num_threads(void) {

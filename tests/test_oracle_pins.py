@@ -497,3 +497,70 @@ def test_drop_transport_renders_equal_the_capsule_renders_for_drops():
     assert np.array_equal(ha["idx"], hd["idx"])
     q = _tiny_program(14, 23)
     assert np.abs(oracle.render_soft(q, W, H, 0.1, 0.01, transport="drops")["rgb"] - oracle.render_soft(q, W, H, 0.1, 0.01)["rgb"]).max() > 1e-3
+
+
+# --------------------------------------------------------------------------- one-pass compensation
+
+def _carry_forward(points, owner, comp, n):
+    """Insert strokes 0..n-1 of the compensated program in order: a point that
+    belongs to stroke i is moved by Phi_j (Eq. fwd) of every later stroke j."""
+    pts = points.copy()
+    for j in range(n):
+        later = owner < j
+        if later.any():
+            st = (comp["cx"][j], comp["cy"][j], comp["theta"][j], comp["length"][j], comp["r"][j])
+            pts[later] = oracle.phi_map(pts[later], st)
+    return pts
+
+
+def _ends(cx, cy, th, L):
+    e = np.stack([np.cos(th), np.sin(th)], 1)
+    m = np.stack([cx, cy], 1)
+    return m - 0.5 * L[:, None] * e, m + 0.5 * L[:, None] * e
+
+
+@pytest.mark.parametrize("endpoint", [False, True])
+def test_compensation_round_trip(endpoint):
+    """Sec. "Closed-form compensation baseline": where no step is blocked, the
+    later strokes' forward maps carry each compensated stroke back to the given
+    program's anchor (and end); the anchor variant keeps length and angle, and
+    the last stroke is unchanged."""
+    p = inputs.make_program(40, seed=5, palette_seed=6, k=4, r_lo=0.01, r_hi=0.05)
+    o = oracle.compensate(p, endpoint=endpoint)
+    o["r"] = p.half_width.astype(np.float64)
+    n = p.n
+    ok = o["blocked"] == 0
+    assert ok.sum() > n // 2 and (~ok).sum() > 0
+    a0, b0 = _ends(p.cx.astype(np.float64), p.cy.astype(np.float64), p.theta.astype(np.float64),
+                   p.length.astype(np.float64))
+    a1, b1 = _ends(o["cx"], o["cy"], o["theta"], o["length"])
+    idx = np.arange(n)
+    assert np.abs(_carry_forward(a1, idx, o, n)[ok] - a0[ok]).max() < 1e-11
+    if endpoint:
+        assert np.abs(_carry_forward(b1, idx, o, n)[ok] - b0[ok]).max() < 1e-11
+    else:
+        assert np.array_equal(o["length"], p.length.astype(np.float64))
+        assert np.array_equal(o["theta"], p.theta.astype(np.float64))
+    assert o["cx"][-1] == p.cx[-1] and o["cy"][-1] == p.cy[-1]
+
+
+def test_compensation_blocked_step():
+    """A point inside a later footprint has no pre-image (Lemma "obstruction"):
+    the step is clamped onto the later segment (a drop's disc onto its centre)
+    or skipped, and the stroke is counted as blocked."""
+    def prog(cx, cy, th, L, r):
+        n = len(cx)
+        return inputs.Program(cx=np.array(cx), cy=np.array(cy), theta=np.array(th), length=np.array(L),
+                              half_width=np.array(r), logits=np.zeros((n, 1)), palette=np.zeros((1, 3)),
+                              background=np.ones(3), color_temp=1.0)
+    p = prog([0.55, 0.5], [0.5, 0.5], [0.0, 0.0], [0.0, 0.0], [0.01, 0.2])
+    c = oracle.compensate(p)
+    assert list(c["blocked"]) == [1, 0]
+    assert (c["cx"][0], c["cy"][0]) == (0.5, 0.5)
+    s = oracle.compensate(p, skip_blocked=True)
+    assert list(s["blocked"]) == [1, 0] and (s["cx"][0], s["cy"][0]) == (0.55, 0.5)
+    q = prog([0.53, 0.5], [0.54, 0.5], [0.0, 0.4], [0.0, 0.3], [0.01, 0.08])
+    c = oracle.compensate(q)
+    assert c["blocked"][0] == 1
+    seg = (0.5, 0.5, 0.4, 0.3, 0.08)
+    assert seg_distance(np.array([[c["cx"][0], c["cy"][0]]]), seg)[0] < 1e-12
