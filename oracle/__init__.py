@@ -8,6 +8,10 @@ and recomputes everything from the paper's definitions in ``tbr_oracle.cpp``.
 Functions (all FP64, citing the paper's passages in the C++ source):
   * ``psi_map`` / ``phi_map``     -- Eq. back / Eq. fwd on a batch of points;
   * ``map_jacobian``             -- their 2x7 Jacobians by dual numbers;
+  * ``coupled_map``              -- the coupling variant Phi_g / psi_g (Eq. coupling);
+  * ``profile_min``              -- exact minimum of its profile g (Eq. profile);
+  * ``drops_map``                -- the sixteen-drop operator of R_D;
+  * ``compensate``               -- the one-pass closed-form compensation baseline;
   * ``render_hard``              -- Eq. chain + Eq. render with indicator coverage;
   * ``render_soft``              -- Eq. relax + Eq. state;
   * ``soft_jvp``                 -- forward-mode derivative of the soft render;
@@ -17,7 +21,8 @@ Functions (all FP64, citing the paper's passages in the C++ source):
 
 A program is any object with attributes ``cx, cy, theta, length, half_width``
 ([n]), ``logits`` ([n, k]), ``palette`` ([k, 3]), ``background`` ([3]) and
-``color_temp`` (float).
+``color_temp`` (float), and optionally ``coupling`` ([n, 3] c_1..c_3 of Eq.
+profile, or None for the capsule map).
 """
 from __future__ import annotations
 
@@ -55,6 +60,7 @@ class _Prog(ctypes.Structure):
         ("L", ctypes.c_void_p), ("r", ctypes.c_void_p),
         ("logits", ctypes.c_void_p), ("palette", ctypes.c_void_p),
         ("background", ctypes.c_double * 3), ("color_temp", ctypes.c_double),
+        ("coupling", ctypes.c_void_p),
     ]
 
 
@@ -79,6 +85,11 @@ def _load():
             lib.orc_map_drops.restype = ctypes.c_int
             lib.orc_compensate.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
             lib.orc_compensate.restype = ctypes.c_int
+            lib.orc_map_coupled.argtypes = [P, i64, dbl, dbl, dbl, dbl, dbl, dbl, dbl, dbl, ctypes.c_int,
+                                            ctypes.c_int, P, P, P, P]
+            lib.orc_map_coupled.restype = ctypes.c_int
+            lib.orc_profile_min.argtypes = [dbl, dbl, dbl]
+            lib.orc_profile_min.restype = dbl
             lib.orc_num_threads.restype = ctypes.c_int
             for f in ("orc_map", "orc_map_jacobian", "orc_render_hard", "orc_render_soft",
                       "orc_soft_jvp", "orc_soft_vjp"):
@@ -115,6 +126,13 @@ class _Packed:
         bg = np.asarray(prog.background, dtype=np.float64)
         s.background = (ctypes.c_double * 3)(*bg.tolist())
         s.color_temp = float(prog.color_temp)
+        cpl = getattr(prog, "coupling", None)
+        self.coupling = None
+        if cpl is not None:
+            self.coupling = f64(cpl)
+            if self.coupling.shape != (n, 3):
+                raise ValueError("coupling must be [n, 3]")
+            s.coupling = _ptr(self.coupling)
         self.struct = s
         self.n, self.k = n, k
 
@@ -162,10 +180,11 @@ def map_jacobian(pts, stroke, direction=0, mode=MODE_FLOOR):
 TRANSPORTS = {"capsule": 0, "inert": 1, "drops": 2}
 
 
-def _transport(inert, transport):
-    if transport is None:
-        return 1 if inert else 0
-    return TRANSPORTS[transport]
+def _transport(inert, transport, prog=None):
+    t = (1 if inert else 0) if transport is None else TRANSPORTS[transport]
+    if t == TRANSPORTS["drops"] and getattr(prog, "coupling", None) is not None:
+        raise ValueError("the coupling variant applies to the capsule transport only")
+    return t
 
 
 def drops_map(pts, stroke, direction=0, return_binds=False, return_jacobian=False):
@@ -184,6 +203,33 @@ def drops_map(pts, stroke, direction=0, return_binds=False, return_jacobian=Fals
     if return_jacobian:
         res.append(jac)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def coupled_map(pts, stroke, coeffs, direction=0, mode=MODE_CLAMP, return_jacobian=False, return_v=False):
+    """The coupling variant (Eq. coupling) of stroke (cx, cy, th, L, r) with the
+    profile coeffs (c1, c2, c3) of Eq. profile on points [n,2]: direction 0 =
+    psi_g (mode MODE_CLAMP or MODE_FLOOR), 1 = Phi_g.  Optionally the 2x2
+    Jacobians d(out)/d(x, y), and the centred coordinate v of each input point
+    with the deposit boundary sigma_b(v) there."""
+    pts = np.ascontiguousarray(np.asarray(pts, dtype=np.float64).reshape(-1, 2))
+    m = pts.shape[0]
+    out = np.empty_like(pts)
+    jac = np.empty((m, 2, 2)) if return_jacobian else None
+    v = np.empty(m) if return_v else None
+    sb = np.empty(m) if return_v else None
+    _load().orc_map_coupled(_ptr(pts), m, *map(float, stroke), *map(float, coeffs), int(direction), int(mode),
+                            _ptr(out), _ptr(jac), _ptr(v), _ptr(sb))
+    res = [out]
+    if return_jacobian:
+        res.append(jac)
+    if return_v:
+        res += [v, sb]
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def profile_min(coeffs):
+    """min over v of g(v) = 1 + sum_k c_k cos(4 pi k v) (Eq. profile), exact."""
+    return float(_load().orc_profile_min(*map(float, coeffs)))
 
 
 def compensate(prog, endpoint=False, skip_blocked=False):
@@ -208,7 +254,7 @@ def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with
     idx = np.empty(m, dtype=np.int32)
     margin = np.empty(m)
     kappa = np.empty(m) if with_kappa else None
-    _load().orc_render_hard(pk.ref, W, H, int(n_prefix), int(bool(snap)), _transport(inert, transport),
+    _load().orc_render_hard(pk.ref, W, H, int(n_prefix), int(bool(snap)), _transport(inert, transport, prog),
                             _ptr(pix), m, _ptr(rgb), _ptr(idx), _ptr(margin), _ptr(kappa))
     out = {"rgb": rgb, "idx": idx, "margin": margin}
     if with_kappa:
@@ -224,7 +270,7 @@ def render_soft(prog, W, H, tau, tau_min, inert=False, pix=None, transport=None)
     rgb = np.empty((m, 3))
     T0 = np.empty(m)
     nrec = np.empty(m, dtype=np.int32)
-    _load().orc_render_soft(pk.ref, W, H, float(tau), float(tau_min), _transport(inert, transport),
+    _load().orc_render_soft(pk.ref, W, H, float(tau), float(tau_min), _transport(inert, transport, prog),
                             _ptr(pix), m, _ptr(rgb), _ptr(T0), _ptr(nrec))
     return {"rgb": rgb, "T0": T0, "nrec": nrec}
 

@@ -20,6 +20,10 @@
 //   * the sixteen-drop operator psi_D of the transfer renderer R_D (Sec.
 //     "Transfer across transport constructions"): K = 16 classical drop maps of
 //     the stroke's total area laid along its segment, with capsule coverage;
+//   * the coupling variant Phi_g (Sec. "A variant closer to line-source
+//     potential flow", Eq. coupling, Eq. profile): the area coordinate shifted
+//     by A_L(r) g(v) with v kept, the deposit {u <= A_L(r) g(v)}, and the exact
+//     positivity check of g;
 //   * a stored-state adjoint (Eq. adjstep, Eq. adjparam) whose local Jacobians
 //     come from forward-mode dual numbers, and a forward-mode directional
 //     derivative of the whole soft render used to pin that adjoint.
@@ -40,6 +44,10 @@
 //   * Soft coverage alpha = min(sigmoid((r - sigma')/max(tau r, tau_min)), 1 - 1e-7).
 //   * epsilon-floor: C <- (eps r)^2 whenever C < (eps r)^2, eps = 1e-3; each such
 //     sample counts as one side-table record.
+//   * Phi_g: v is the centred arclength of the point's own leaf; the soft
+//     coverage is sigmoid((sigma_b(v) - sigma') / w), sigma_b(v) the root of
+//     A_L(sigma) = A_L(r) g(v) (= r when g = 1); the coupling applies to the
+//     capsule transport only.
 //   * R_D: drop k = 0..15 (inserted k-th, one sweep from the segment's start
 //     m - L e/2 to its end) is centred at m + e L ((k + 1/2)/16 - 1/2) with
 //     radius s = sqrt(A_L(r) / (16 pi)); inside a drop's disc the pull-back
@@ -124,7 +132,12 @@ template <int D> inline Dual<D> atan2(const Dual<D>& y, const Dual<D>& x) {
 using std::sqrt; using std::sin; using std::cos; using std::exp; using std::log1p;
 using std::fabs; using std::atan2;
 
-template <class T> struct Stroke { T cx, cy, th, L, r; };
+// c1..c3: the profile of the coupling variant Phi_g (Eq. coupling, Eq.
+// profile); all zero for the capsule map (g = 1).
+template <class T> struct Stroke {
+  T cx, cy, th, L, r;
+  double c1 = 0.0, c2 = 0.0, c3 = 0.0;
+};
 
 // ---------------------------------------------------------------------------
 // Stroke frame.  Sec. 3: the footprint is the capsule about [a, a+d]; with the
@@ -196,6 +209,48 @@ void stadium_point(T a, const T& sig, const T& L, T& s, T& h) {
   s = -hl - sig * sin(ang); h = sig * cos(ang);
 }
 
+// ---------------------------------------------------------------------------
+// Coupling variant Phi_g (Sec. "A variant closer to line-source potential
+// flow", Eq. coupling): in the area chart (u, v) with u = A_L(sigma) the map
+// shifts u by A_L(r) g(v) and keeps v, g(v) = 1 + sum_k c_k cos(4 pi k v)
+// (Eq. profile).  The deposit is {u <= A_L(r) g(v)}.
+// ---------------------------------------------------------------------------
+template <class T>
+bool coupled(const Stroke<T>& g) { return g.c1 != 0.0 || g.c2 != 0.0 || g.c3 != 0.0; }
+
+// Centred arclength coordinate v = q - L / (2 P_L(sigma)) (Eq. phi) of a point
+// on the leaf at distance sig: its arclength from the lower flank's midpoint
+// over the leaf's perimeter.
+template <class T>
+T centred_v(const T& s, const T& h, const T& sig, const T& L) {
+  T per = 2.0 * L + 2.0 * kPi * sig;
+  if (value(per) <= 0.0) return T(0.0);
+  return (stadium_arclength(s, h, sig, L) - 0.5 * L) / per;
+}
+
+// g(v) - 1 (Eq. profile).
+template <class T>
+T profile_m1(const Stroke<T>& g, const T& v) {
+  return g.c1 * cos(4.0 * kPi * v) + g.c2 * cos(8.0 * kPi * v) + g.c3 * cos(12.0 * kPi * v);
+}
+
+// Distance of the deposit boundary u = A_L(r) g(v) at coordinate v: the root
+// sigma_b of 2 L sigma + pi sigma^2 = A_L(r) g(v).
+template <class T>
+T deposit_sigma(const Stroke<T>& g, const T& v) {
+  T Ag = (2.0 * g.L * g.r + kPi * g.r * g.r) * (1.0 + profile_m1(g, v));
+  return Ag / (g.L + sqrt(g.L * g.L + kPi * Ag));
+}
+
+// Signed distance from the deposit boundary along sigma at the point's own v:
+// sigma' - r for the capsule, sigma' - sigma_b(v') under Eq. coupling.  The
+// point is in the deposit iff it is <= 0 (the tie counts as inside).
+template <class T>
+T deposit_margin(const T& s, const T& h, const T& sp, const Stroke<T>& g) {
+  if (!coupled(g)) return sp - g.r;
+  return sp - deposit_sigma(g, centred_v(s, h, sp, g.L));
+}
+
 enum Mode { kClamp = 0, kFloor = 1, kRawQ = 2, kFloorRawQ = 3 };
 
 // Move a point from the parallel curve at distance sig_from to the one at
@@ -234,6 +289,8 @@ int psi(const T& x, const T& y, const Stroke<T>& g, int mode, T& x_out, T& y_out
   to_frame(x, y, g, s, h);
   T sp = segment_distance(s, h, g.L);
   T C = (sp - g.r) * (2.0 * g.L + kPi * (sp + g.r));
+  if (coupled(g))  // Eq. coupling: subtract A_L(r) g(v) instead of A_L(r)
+    C = C - (2.0 * g.L * g.r + kPi * g.r * g.r) * profile_m1(g, centred_v(s, h, sp, g.L));
   int floored = 0;
   if (mode == kFloor || mode == kFloorRawQ) {
     T fl = (kEps * g.r) * (kEps * g.r);
@@ -261,6 +318,8 @@ void phi(const T& x, const T& y, const Stroke<T>& g, bool raw_q, T& x_out, T& y_
   to_frame(x, y, g, s, h);
   T sg = segment_distance(s, h, g.L);
   T B = 2.0 * g.L * (sg + g.r) + kPi * (sg * sg + g.r * g.r);
+  if (coupled(g))  // Eq. coupling: add A_L(r) g(v) instead of A_L(r)
+    B = B + (2.0 * g.L * g.r + kPi * g.r * g.r) * profile_m1(g, centred_v(s, h, sg, g.L));
   T sp = B / (g.L + sqrt(g.L * g.L + kPi * B));
   T sn, hn;
   keep_tangential(s, h, sg, sp, g.L, raw_q, sn, hn);
@@ -344,11 +403,12 @@ void phi_drops(const T& x, const T& y, const Stroke<T>& g, T& x_out, T& y_out) {
 enum Transport { kCapsule = 0, kInert = 1, kDrops16 = 2 };
 
 // Relaxed coverage (Eq. relax), clamped at 1 - 1e-7 (Sec. 5.2 "Conditioning").
+// margin: deposit_margin (sigma' - r for the capsule).
 template <class T>
-T soft_coverage(const T& sp, const T& r, double tau, double tau_min) {
+T soft_coverage(const T& margin, const T& r, double tau, double tau_min) {
   T w = tau * r;
   if (value(w) < tau_min) w = T(tau_min);
-  T z = (r - sp) / w;
+  T z = -margin / w;
   T a = 1.0 / (1.0 + exp(-z));
   if (value(a) > kAlphaMax) a = T(kAlphaMax);
   return a;
@@ -369,6 +429,7 @@ typedef struct {
   const double* palette;  // [k][3]
   double background[3];   // c_0
   double color_temp;      // tau_c
+  const double* coupling; // [n][3] c_1..c_3 of Eq. profile, or NULL (g = 1)
 } orc_prog;
 
 }  // extern "C"
@@ -379,6 +440,9 @@ template <class T>
 Stroke<T> stroke_of(const orc_prog* p, int j) {
   Stroke<T> g;
   g.cx = T(p->cx[j]); g.cy = T(p->cy[j]); g.th = T(p->th[j]); g.L = T(p->L[j]); g.r = T(p->r[j]);
+  if (p->coupling) {
+    g.c1 = p->coupling[3 * j]; g.c2 = p->coupling[3 * j + 1]; g.c3 = p->coupling[3 * j + 2];
+  }
   return g;
 }
 
@@ -509,14 +573,15 @@ int orc_render_hard(const orc_prog* p, int W, int H, int n_prefix, int snap, int
       double s, h;
       to_frame(x, y, g, s, h);
       double sp = segment_distance(s, h, g.L);
-      mg = std::min(mg, std::fabs(sp - g.r));
-      if (sp <= g.r) { hit = j; break; }       // closed footprint: the tie is inside
+      const double dm = deposit_margin(s, h, sp, g);
+      mg = std::min(mg, std::fabs(dm));
+      if (dm <= 0.0) { hit = j; break; }       // closed footprint: the tie is inside
       if (transport == kInert) continue;
       if (kappa) {
         typedef Dual<2> D2;
         D2 xd(x), yd(y), xo, yo;
         xd.d[0] = 1; yd.d[1] = 1;
-        Stroke<D2> gd{D2(g.cx), D2(g.cy), D2(g.th), D2(g.L), D2(g.r)};
+        Stroke<D2> gd{D2(g.cx), D2(g.cy), D2(g.th), D2(g.L), D2(g.r), g.c1, g.c2, g.c3};
         if (transport == kDrops16) psi_drops(xd, yd, gd, xo, yo);
         else psi(xd, yd, gd, kClamp, xo, yo);
         kap *= spectral_norm(xo.d[0], xo.d[1], yo.d[0], yo.d[1]);
@@ -556,7 +621,7 @@ void soft_pixel(const std::vector<Stroke<T>>& g, const std::vector<T>& col, cons
     T s, h;
     to_frame(x, y, g[j], s, h);
     T sp = segment_distance(s, h, g[j].L);
-    T a = soft_coverage(sp, g[j].r, tau, tau_min);
+    T a = soft_coverage(deposit_margin(s, h, sp, g[j]), g[j].r, tau, tau_min);
     for (int c = 0; c < 3; ++c) C[c] = C[c] + Tr * a * col[(size_t)j * 3 + c];
     Tr = Tr * (1.0 - a);
     if (transport == kCapsule) {
@@ -692,7 +757,7 @@ int orc_soft_vjp(const orc_prog* p, int W, int H, double tau, double tau_min, in
         xs[j] = x; ys[j] = y; Ts[j] = Tr;
         double s, h;
         to_frame(x, y, g, s, h);
-        double a = soft_coverage(segment_distance(s, h, g.L), g.r, tau, tau_min);
+        double a = soft_coverage(deposit_margin(s, h, segment_distance(s, h, g.L), g), g.r, tau, tau_min);
         Tr = Tr * (1.0 - a);
         if (!inert) { double xo, yo; psi(x, y, g, kFloor, xo, yo); x = xo; y = yo; }
       }
@@ -708,7 +773,7 @@ int orc_soft_vjp(const orc_prog* p, int W, int H, double tau, double tau_min, in
         gd.cx.d[2] = 1; gd.cy.d[3] = 1; gd.th.d[4] = 1; gd.L.d[5] = 1; gd.r.d[6] = 1;
         D7 s, h;
         to_frame(xd, yd, gd, s, h);
-        D7 a = soft_coverage(segment_distance(s, h, gd.L), gd.r, tau, tau_min);
+        D7 a = soft_coverage(deposit_margin(s, h, segment_distance(s, h, gd.L), gd), gd.r, tau, tau_min);
         double J[2][7];
         if (inert) {
           for (int r = 0; r < 2; ++r) for (int c = 0; c < 7; ++c) J[r][c] = (r == c) ? 1.0 : 0.0;
@@ -787,7 +852,7 @@ int orc_compensate(const orc_prog* p, int endpoint, int skip, double* cx, double
       for (int j = n - 1; j > i; --j) {
         double s, h;
         to_frame(x, y, c[j], s, h);
-        if (segment_distance(s, h, c[j].L) <= c[j].r) {
+        if (deposit_margin(s, h, segment_distance(s, h, c[j].L), c[j]) <= 0.0) {
           blk = 1;
           if (skip) continue;
         }
@@ -814,6 +879,61 @@ int orc_compensate(const orc_prog* p, int endpoint, int skip, double* cx, double
     nblocked += blk;
   }
   return nblocked;
+}
+
+// The coupling variant on a batch of points (Eq. coupling with the profile
+// c1..c3 of Eq. profile): direction 0 = psi_g (mode as orc_map: 0 clamp,
+// 1 floor), 1 = Phi_g.  If jac is non-null it receives d(x_out, y_out)/d(x, y)
+// per point (2x2, row-major).  If v is non-null it receives the centred
+// coordinate v of each input point, and sig_b (nullable) the deposit boundary
+// sigma_b(v) there.
+int orc_map_coupled(const double* pts, int64_t n, double cx, double cy, double th, double L, double r,
+                    double c1, double c2, double c3, int direction, int mode, double* out, double* jac,
+                    double* v, double* sig_b) {
+  #pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    typedef Dual<2> D2;
+    D2 x(pts[2 * i]), y(pts[2 * i + 1]), xo, yo;
+    x.d[0] = 1; y.d[1] = 1;
+    Stroke<D2> g{D2(cx), D2(cy), D2(th), D2(L), D2(r), c1, c2, c3};
+    if (direction == 0) psi(x, y, g, mode, xo, yo);
+    else phi(x, y, g, false, xo, yo);
+    out[2 * i] = xo.v; out[2 * i + 1] = yo.v;
+    if (jac) { jac[4 * i] = xo.d[0]; jac[4 * i + 1] = xo.d[1]; jac[4 * i + 2] = yo.d[0]; jac[4 * i + 3] = yo.d[1]; }
+    if (v || sig_b) {
+      Stroke<double> gv{cx, cy, th, L, r, c1, c2, c3};
+      double s, h;
+      to_frame(pts[2 * i], pts[2 * i + 1], gv, s, h);
+      const double vv = centred_v(s, h, segment_distance(s, h, L), L);
+      if (v) v[i] = vv;
+      if (sig_b) sig_b[i] = deposit_sigma(gv, vv);
+    }
+  }
+  return 0;
+}
+
+// Smallest value of g over a leaf (Eq. profile).  In w = cos(4 pi v) the
+// modes are Chebyshev polynomials, so g is the cubic
+// 1 + c1 w + c2 (2 w^2 - 1) + c3 (4 w^3 - 3 w) on [-1, 1]; its minimum is at
+// w = +-1 or at a root of its derivative 12 c3 w^2 + 4 c2 w + (c1 - 3 c3).
+double orc_profile_min(double c1, double c2, double c3) {
+  auto gw = [&](double w) { return 1.0 + c1 * w + c2 * (2.0 * w * w - 1.0) + c3 * (4.0 * w * w * w - 3.0 * w); };
+  double m = std::min(gw(-1.0), gw(1.0));
+  const double a = 12.0 * c3, b = 4.0 * c2, c = c1 - 3.0 * c3;
+  if (a == 0.0) {
+    if (b != 0.0) {
+      const double w = -c / b;
+      if (w > -1.0 && w < 1.0) m = std::min(m, gw(w));
+    }
+  } else {
+    const double disc = b * b - 4.0 * a * c;
+    if (disc >= 0.0) {
+      const double sq = std::sqrt(disc);
+      for (double w : {(-b - sq) / (2.0 * a), (-b + sq) / (2.0 * a)})
+        if (w > -1.0 && w < 1.0) m = std::min(m, gw(w));
+    }
+  }
+  return m;
 }
 
 int orc_num_threads(void) {

@@ -67,6 +67,7 @@ class Program:
     palette: np.ndarray
     background: np.ndarray
     color_temp: float = 1.0
+    coupling: np.ndarray | None = None  # [n, 3] c_1..c_3 of the coupling profile, or None
 
     @property
     def n(self) -> int:
@@ -86,6 +87,8 @@ class Program:
         p = self.copy()
         for name in ("cx", "cy", "theta", "length", "half_width", "logits"):
             setattr(p, name, np.ascontiguousarray(getattr(p, name)[:m]))
+        if p.coupling is not None:
+            p.coupling = np.ascontiguousarray(p.coupling[:m])
         return p
 
 
@@ -111,6 +114,17 @@ def make_program(n: int, seed: int, palette_seed: int, k: int, r_lo: float, r_hi
     return Program(cx=f32(cx), cy=f32(cy), theta=f32(theta), length=f32(length),
                    half_width=f32(r), logits=f32(logits), palette=f32(pal),
                    background=np.ones(3, dtype=np.float32), color_temp=1.0)
+
+
+def make_coupling(seed: int, n: int, c1_max: float = 0.4, c2_max: float = 0.15,
+                  c3_max: float = 0.1) -> np.ndarray:
+    """Seeded profiles (c_1, c_2, c_3) of the coupling variant, [n, 3] float32:
+    c_1 ~ U[0, c1_max] (a positive first mode widens the flank and shortens the
+    tips), c_2 ~ U[-c2_max, c2_max], c_3 ~ U[-c3_max, c3_max].  With the defaults
+    |c_1| + |c_2| + |c_3| <= 0.65, so g >= 0.35 on every leaf."""
+    u = uniform(seed, 3 * n).reshape(n, 3)
+    c = np.stack([c1_max * u[:, 0], c2_max * (2 * u[:, 1] - 1), c3_max * (2 * u[:, 2] - 1)], 1)
+    return np.ascontiguousarray(c.astype(np.float32))
 
 
 def make_cotangent(seed: int, npix: int) -> np.ndarray:

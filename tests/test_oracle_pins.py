@@ -564,3 +564,187 @@ def test_compensation_blocked_step():
     assert c["blocked"][0] == 1
     seg = (0.5, 0.5, 0.4, 0.3, 0.08)
     assert seg_distance(np.array([[c["cx"][0], c["cy"][0]]]), seg)[0] < 1e-12
+
+
+# --------------------------------------------------------------------------- coupling variant Phi_g
+
+CPL_STROKE = (0.31, 0.62, 1.1, 0.13, 0.045)
+CPL = (0.35, -0.1, 0.05)
+
+
+def _leaf_points(stroke, sig, v):
+    """Points of the leaf {sigma = sig} (sig may vary per point) at centred
+    coordinate v: arclength v P + L/2 from the corner (-L/2, -sig), counter-
+    clockwise (lower flank, right cap, upper flank, left cap)."""
+    cx, cy, th, L, r = stroke
+    sig = np.broadcast_to(np.asarray(sig, dtype=np.float64), np.shape(v))
+    per = 2 * L + 2 * math.pi * sig
+    a = np.mod(np.asarray(v) * per + 0.5 * L, per)
+    s = np.empty_like(a)
+    h = np.empty_like(a)
+    for i in range(a.size):
+        ai, si = a.flat[i], sig.flat[i]
+        if ai < L:
+            s.flat[i], h.flat[i] = -L / 2 + ai, -si
+        elif ai < L + math.pi * si:
+            ang = (ai - L) / si - math.pi / 2
+            s.flat[i], h.flat[i] = L / 2 + si * math.cos(ang), si * math.sin(ang)
+        elif ai < 2 * L + math.pi * si:
+            s.flat[i], h.flat[i] = L / 2 - (ai - L - math.pi * si), si
+        else:
+            ang = (ai - 2 * L - math.pi * si) / si
+            s.flat[i], h.flat[i] = -L / 2 - si * math.sin(ang), si * math.cos(ang)
+    e = np.array([math.cos(th), math.sin(th)])
+    en = np.array([-math.sin(th), math.cos(th)])
+    return np.array([cx, cy]) + s.reshape(-1, 1) * e + h.reshape(-1, 1) * en
+
+
+def _coupled_exterior(stroke, c, n=50_000):
+    pts = exterior_sample(stroke, 4 * n)
+    _, _, sb = oracle.coupled_map(pts, stroke, c, return_v=True)
+    return pts[seg_distance(pts, stroke) > sb + 1e-9][:n]
+
+
+@pytest.mark.parametrize("c", [(0.5, 0.0, 0.0), (0.0, 0.0, 0.3), (0.35, -0.1, 0.05), (0.2, 0.45, -0.3),
+                               (-0.6, 0.3, 0.25)])
+def test_coupling_profile_minimum_is_exact(c):
+    """Positivity of g is decided exactly (Eq. profile: g is a cubic in
+    w = cos 4 pi v): the closed-form minimum against dense sampling of
+    1 + sum c_k cos(4 pi k v) over a quarter leaf, refined by golden section."""
+    v = np.linspace(0.0, 0.25, 200_001)
+    g = 1 + sum(ck * np.cos(4 * math.pi * (k + 1) * v) for k, ck in enumerate(c))
+    i = int(np.argmin(g))
+    lo, hi = v[max(i - 1, 0)], v[min(i + 1, v.size - 1)]
+    f = lambda t: 1 + sum(ck * math.cos(4 * math.pi * (k + 1) * t) for k, ck in enumerate(c))
+    for _ in range(200):
+        m1, m2 = lo + (hi - lo) * 0.382, lo + (hi - lo) * 0.618
+        if f(m1) < f(m2):
+            hi = m2
+        else:
+            lo = m1
+    sampled = min(g.min(), f(0.5 * (lo + hi)))
+    assert abs(oracle.profile_min(c) - sampled) < 1e-12
+
+
+@pytest.mark.parametrize("stroke", [CPL_STROKE, (0.5, 0.5, 0.4, 0.0, 0.03)])
+def test_coupling_round_trip_and_unit_jacobian(stroke):
+    """Phi_g o psi_g = id outside the deposit and psi_g o Phi_g = id off the
+    segment; the Jacobian is unit triangular in the area chart, so det D psi_g
+    = det D Phi_g = 1 (Eq. coupling)."""
+    pts = _coupled_exterior(stroke, CPL)
+    back = oracle.coupled_map(pts, stroke, CPL, direction=0)
+    assert np.abs(oracle.coupled_map(back, stroke, CPL, direction=1) - pts).max() < 1e-13
+    u = inputs.uniform(3, 2 * 20_000).reshape(-1, 2) - 0.5 + np.array(stroke[:2])
+    fw = oracle.coupled_map(u, stroke, CPL, direction=1)
+    assert np.abs(oracle.coupled_map(fw, stroke, CPL, direction=0) - u).max() < 1e-13
+    for d, p in ((0, pts), (1, u)):
+        _, J = oracle.coupled_map(p, stroke, CPL, direction=d, return_jacobian=True)
+        det = J[:, 0, 0] * J[:, 1, 1] - J[:, 0, 1] * J[:, 1, 0]
+        assert np.abs(det - 1.0).max() < 1e-11
+    # a profile that is not constant moves points differently from the capsule
+    assert np.abs(back - oracle.psi_map(pts, stroke, oracle.MODE_CLAMP)).max() > 1e-4
+
+
+def test_coupling_inserts_the_stroke_area():
+    """g has unit mean over a leaf, so Phi_g sends the leaf {sigma = s0} to a
+    curve enclosing A_L(s0) + A_L(r), as the capsule map does."""
+    cx, cy, th, L, r = CPL_STROKE
+    s0 = 0.02
+    curve = lambda n: oracle.coupled_map(_leaf_points(CPL_STROKE, s0, np.arange(n) / n), CPL_STROKE, CPL,
+                                         direction=1)
+    area = _richardson_area(curve, 1 << 13)
+    want = steiner_area(L, s0) + steiner_area(L, r)
+    assert abs(area - want) / want < 1e-9
+
+
+def test_coupling_reflection_symmetry():
+    """The modes cos(4 pi k v) respect both mirror symmetries of the capsule
+    (Eq. profile), so psi_g commutes with them."""
+    pts = _coupled_exterior(CPL_STROKE, CPL)
+    for refl in (reflect_bisector, reflect_line):
+        a = oracle.coupled_map(refl(pts, CPL_STROKE), CPL_STROKE, CPL)
+        b = refl(oracle.coupled_map(pts, CPL_STROKE, CPL), CPL_STROKE)
+        assert np.abs(a - b).max() < 1e-13
+
+
+def test_coupling_deposit_boundary():
+    """The deposit is {u <= A_L(r) g(v)} with an explicit boundary: the leaf
+    point at distance sigma_b(v), 2 L sigma_b + pi sigma_b^2 = A_L(r) g(v), has
+    centred coordinate v and is carried by psi_g onto the segment; a positive
+    first mode widens the flank (v = 0) and shortens the tips (v = 1/4)."""
+    cx, cy, th, L, r = CPL_STROKE
+    A = 2 * L * r + math.pi * r * r
+    v = np.linspace(-0.5, 0.5, 801)[:-1]
+    g = 1 + sum(ck * np.cos(4 * math.pi * (k + 1) * v) for k, ck in enumerate(CPL))
+    sb = (-L + np.sqrt(L * L + math.pi * A * g)) / math.pi
+    pts = _leaf_points(CPL_STROKE, sb, v)
+    out, vo, sbo = oracle.coupled_map(pts, CPL_STROKE, CPL, direction=0, return_v=True)
+    assert np.abs(np.mod(vo - v + 0.5, 1.0) - 0.5).max() < 1e-12
+    assert np.abs(sbo - sb).max() < 1e-12
+    assert seg_distance(out, CPL_STROKE).max() < 1e-9
+    c1 = (0.3, 0.0, 0.0)
+    _, _, s_flank = oracle.coupled_map(_leaf_points(CPL_STROKE, r, np.array([0.0])), CPL_STROKE, c1, return_v=True)
+    _, _, s_tip = oracle.coupled_map(_leaf_points(CPL_STROKE, r, np.array([0.25])), CPL_STROKE, c1, return_v=True)
+    assert s_flank[0] > r * 1.01 and s_tip[0] < r * 0.99
+    for got, gval in ((s_flank[0], 1.3), (s_tip[0], 0.7)):
+        assert abs(2 * L * got + math.pi * got * got - A * gval) < 1e-14
+
+
+def test_zero_profile_is_the_capsule():
+    """c = 0 is the capsule map: renders with an all-zero coupling array equal
+    those without one bit for bit."""
+    p = _tiny_program(12, 61, r_lo=0.03, r_hi=0.1)
+    q = p.copy()
+    q.coupling = np.zeros((p.n, 3))
+    for fn in (lambda x: oracle.render_hard(x, 20, 20)["rgb"], lambda x: oracle.render_soft(x, 20, 20, 0.2, 0.01)["rgb"]):
+        assert np.array_equal(fn(p), fn(q))
+
+
+def test_coupled_single_stroke_hard_render_is_the_deposit():
+    """One stroke under Eq. coupling: a pixel is coloured iff its distance to
+    the segment is at most sigma_b(v) at its own v."""
+    st = (0.45, 0.55, 0.6, 0.3, 0.12)
+    c = (0.3, -0.1, 0.08)
+    p = inputs.Program(cx=np.array([st[0]]), cy=np.array([st[1]]), theta=np.array([st[2]]),
+                       length=np.array([st[3]]), half_width=np.array([st[4]]),
+                       logits=np.zeros((1, 1)), palette=np.array([[0.2, 0.4, 0.6]]),
+                       background=np.ones(3), color_temp=1.0, coupling=np.array([c]))
+    W = H = 64
+    got = oracle.render_hard(p, W, H)
+    jj, ii = np.meshgrid(np.arange(W), np.arange(H))
+    pts = np.stack([(jj.ravel() + 0.5) / W, (ii.ravel() + 0.5) / H], 1)
+    _, _, sb = oracle.coupled_map(pts, st, c, return_v=True)
+    inside = seg_distance(pts, st) <= sb
+    assert np.array_equal(got["idx"] == 0, inside)
+    assert inside.sum() != (seg_distance(pts, st) <= st[4]).sum()
+
+
+def test_coupled_soft_render_tends_to_hard():
+    """As the relaxation width goes to zero the coupled soft render tends to
+    the coupled hard render away from deposit boundaries."""
+    p = _tiny_program(10, 31, r_lo=0.03, r_hi=0.1)
+    p.coupling = inputs.make_coupling(33, p.n)
+    W = H = 24
+    hard = oracle.render_hard(p, W, H)
+    soft = oracle.render_soft(p, W, H, 0.0, 1e-5)["rgb"]
+    far = hard["margin"] > 2e-2
+    assert far.sum() > 0.5 * W * H
+    assert np.abs(soft - hard["rgb"])[far].max() < 1e-6
+    plain = p.copy()
+    plain.coupling = None
+    assert not np.array_equal(oracle.render_hard(plain, W, H)["idx"], hard["idx"])
+
+
+def test_coupled_adjoint_matches_finite_differences():
+    """The stored-state adjoint through psi_g and the coupled coverage against
+    FP64 central differences."""
+    p = _tiny_program(5, 41, r_lo=0.08, r_hi=0.2)
+    p.coupling = inputs.make_coupling(43, p.n)
+    W = H = 10
+    tau, tau_min = 0.3, 0.02
+    cot = inputs.make_cotangent(9, W * H).astype(np.float64)
+    g = oracle.soft_vjp(p, W, H, tau, tau_min, cot)
+    params = [(j, q) for j in range(p.n) for q in list(range(5)) + [5 + t for t in range(p.k)]]
+    fd = oracle.fd_gradient(p, W, H, tau, tau_min, cot, params, h_geo=1e-6, h_logit=1e-6)
+    got = np.array([g[oracle._FIELD[q]][j] if q < 5 else g["logits"][j, q - 5] for (j, q) in params])
+    assert np.abs(got - fd).max() < 1e-6 * np.abs(fd).max()
