@@ -47,6 +47,11 @@ XU_BWD = 15.7
 # sigma^2 1, step 3, update 2 = 14); XU: 16 x (sqrt + rcp) + 4.
 OPS_FWD_D = 9 + 11 + 16 * 14
 XU_FWD_D = 16 * 2 + 4
+# Coupling variant Phi_g, soft forward: the capsule forward plus the profile at
+# the point's v (angle 3, sine polynomial 6, cubic in w 3), the coupled C and
+# area 2, and the deposit boundary sigma_b 3; XU: sqrt and rcp of sigma_b.
+OPS_FWD_G = OPS_FWD + 17
+XU_FWD_G = XU_FWD + 2
 # FP32 lane peak: 148 SMs x 128 FP32 lanes x 2032 MHz (one op per lane per cycle);
 # XU (MUFU) peak: 16 results per clock per SM (4 per sub-partition).
 SMS, LANES, SM_MAX_MHZ, XU_PER_SM = 148, 128, 2032.0, 16
@@ -196,6 +201,18 @@ def oracle_rate(prog, seconds, max_pixels=1 << 20):
     dt2 = run(m2) if m2 != m else dt
     rate = m2 * prog.n / dt2
     return rate, {"pixels": m2, "seconds": dt2, "threads": oracle.num_threads()}
+
+
+def oracle_compensate_ms(prog):
+    """Milliseconds of the oracle's FP64 one-pass compensation (anchor and
+    endpoint variants) of the whole program, one host thread."""
+    import oracle
+    out = {}
+    for name, ep in (("anchor", False), ("endpoint", True)):
+        t0 = time.perf_counter()
+        oracle.compensate(prog, endpoint=ep)
+        out[name] = (time.perf_counter() - t0) * 1e3
+    return out
 
 
 def run_reference(args):
@@ -433,21 +450,22 @@ def run_native(args):
                          "fp64_band_steps": st_h["band_steps"], "background_pixels": st_h["background_pixels"]})
             del rgb_h, idx_h
 
+    def timed(fn, reps=3):
+        fn()
+        ts = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record()
+            fn()
+            e0.record()
+            torch.cuda.synchronize()
+            ts.append(s0.elapsed_time(e0))
+        return sum(ts) / len(ts)
+
     # transfer renderer R_D (sixteen-drop transport, forward only) on the same program
     transfer = None
     if rank == 0 and not args.no_hard and args.res == RES and args.strokes == N_STROKES:
-        def timed(fn, reps=3):
-            fn()
-            ts = []
-            for i in range(reps):
-                flush.fill_(float(i))
-                s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                s0.record()
-                fn()
-                e0.record()
-                torch.cuda.synchronize()
-                ts.append(s0.elapsed_time(e0))
-            return sum(ts) / len(ts)
         rgb_d = torch.empty((H, W, 3), device=device)
         idx_d = torch.empty((H, W), dtype=torch.int32, device=device)
         soft_d = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_d, transport="drops"))
@@ -461,12 +479,54 @@ def run_native(args):
                                       "xu_frac": XU_FWD_D * units / (soft_d * 1e-3) * 1e-9 / PEAK_XU_GOPS}}
         del rgb_d, idx_d
 
+    # coupling variant Phi_g (seeded profiles) on the same program: soft forward
+    # and hard render, beside the capsule map's forward-only soft render
+    coupling = None
+    if rank == 0 and not args.no_hard and args.res == RES and args.strokes == N_STROKES:
+        pg = prog_h.copy()
+        pg.coupling = inputs.make_coupling(403, pg.n)
+        dpg = tbr.DeviceProgram.from_host(pg, device)
+        rgb_g = torch.empty((H, W, 3), device=device)
+        idx_g = torch.empty((H, W), dtype=torch.int32, device=device)
+        soft_c = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_g))
+        soft_g = timed(lambda: tbr.render_soft(dpg, W, H, tau, tau_min, out_rgb=rgb_g))
+        hard_g = timed(lambda: tbr.render_hard(dpg, W, H, out_rgb=rgb_g, out_idx=idx_g))
+        ach = OPS_FWD_G * units / (soft_g * 1e-3) * 1e-9
+        coupling = {"workload": "Phi_g (profiles c_1 in [0, 0.4], |c_2| <= 0.15, |c_3| <= 0.1, seed 403) soft "
+                                "forward and hard render of the same program",
+                    "soft_forward_ms": soft_g, "soft_evals_per_s": units / (soft_g * 1e-3),
+                    "capsule_soft_forward_ms": soft_c, "hard_ms": hard_g,
+                    "soft_roofline": {"ops_per_unit": OPS_FWD_G, "achieved": ach, "frac": ach / PEAK_GOPS,
+                                      "xu_ops_per_unit": XU_FWD_G,
+                                      "xu_frac": XU_FWD_G * units / (soft_g * 1e-3) * 1e-9 / PEAK_XU_GOPS}}
+        del rgb_g, idx_g, dpg
+
+    # one-pass closed-form compensation of the same program (anchor and endpoint
+    # variants): N (N - 1) / 2 pre-image steps per segment end on one CTA; the
+    # call time includes packing and the blocked-count read-back
+    comp = None
+    if rank == 0 and not args.no_hard and args.res == RES and args.strokes == N_STROKES:
+        comp = {"workload": f"one-pass compensation of the {prog.n}-stroke program"}
+        for name, ep in (("anchor", False), ("endpoint", True)):
+            nb = tbr.compensate(prog, endpoint=ep)["n_blocked"]
+            tbr.profile_reset()
+            tbr.profile_enable(True)
+            call_ms = timed(lambda: tbr.compensate(prog, endpoint=ep))
+            tbr.profile_enable(False)
+            launches, kms = tbr.profile_read("compensate")
+            kms /= max(1, launches)
+            steps_c = prog.n * (prog.n - 1) // 2 * (2 if ep else 1)
+            comp[name] = {"call_ms": call_ms, "kernel_ms": kms, "point_steps_per_s": steps_c / (kms * 1e-3),
+                          "blocked": nb}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.res == RES and args.strokes == N_STROKES:
         rate, info = oracle_rate(prog_h, args.cpu_seconds)
         cpu = {"value": rate, "unit": "evals/s", "cores": info["threads"], "kind": "oracle",
                "sample": f"{info['pixels']} sampled pixels x {prog_h.n} strokes of the {RES}x{RES} workload "
                          f"(FP64 soft forward + stored-state adjoint, {info['seconds']:.1f} s)"}
+        if comp is not None:
+            comp["cpu_oracle_ms"] = oracle_compensate_ms(prog_h)
 
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0 and args.res == RES and args.strokes == N_STROKES:
@@ -475,7 +535,10 @@ def run_native(args):
         torch.cuda.empty_cache()
         serve = serve_bench.run(n_req=args.serve_requests)
 
-    kernels_per_step = 1 + 1 + 1 + 3 + 2  # pack, soft, backward, epilogue (3), loss (2)
+    # pack, soft, loss (2), backward, FP64-repair launches (3: the queueing pass,
+    # the sort and the repair, which return at once when no checkpoint drifted),
+    # epilogue (3)
+    kernels_per_step = 1 + 1 + 2 + 1 + 3 + 3
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -503,6 +566,8 @@ def run_native(args):
             "serve": serve,
             "hard": hard,
             "transfer_renderer": transfer,
+            "coupling_variant": coupling,
+            "compensation": comp,
             "e2e": e2e,
             "cpu_baseline": cpu,
             "clocks": clk,
@@ -518,12 +583,16 @@ def run_native(args):
 
 
 def _kernel_source_sha():
+    """Hash of the sources the adjoint kernel is compiled from: its translation
+    unit, the device headers it includes and the public header."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2609_08722_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    files = [os.path.join(csrc, n) for n in ("tbr_backward.cu", "tbr_pair.cuh", "tbr_tile.cuh", "tbr_internal.cuh",
+                                             "tbr_poly.h")]
+    files.append(os.path.join(ROOT, "include", "tbr.h"))
+    for f in files:
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -76,6 +76,15 @@ typedef struct {
   const float* palette;     /* [k][3] sRGB colours */
   float background[3];      /* c_0, host value */
   float color_temp;         /* softmax temperature tau_c > 0, host value */
+  const float* coupling;    /* [n][3] c_1..c_3 of the coupling variant's profile
+                               g(v) = 1 + sum_k c_k cos(4 pi k v) (Sec. "A variant
+                               closer to line-source potential flow", Eq. coupling,
+                               Eq. profile), or NULL for the capsule map (g = 1).
+                               Each stroke's g must be positive on the whole leaf
+                               (checked exactly; else the stroke fails the value
+                               checks).  Supported by the hard render and the
+                               forward-only soft render (capsule transport); the
+                               other entry points reject a non-NULL coupling. */
 } tbr_program;
 
 /* Transport of a render: the paper's capsule insertion map psi (Eq. back), or
@@ -122,6 +131,27 @@ TBR_API tbr_status tbr_render_hard(const tbr_program* prog, int32_t W, int32_t H
 TBR_API tbr_status tbr_render_hard_transport(const tbr_program* prog, int32_t W, int32_t H, int32_t n_prefix,
                                              int32_t snap, int32_t transport, float* out_rgb, int32_t* out_idx,
                                              tbr_hard_stats* stats, void* stream);
+
+/* One-pass closed-form compensation (Sec. "Closed-form compensation
+ * baseline"): returns a program whose hard render under the transport puts
+ * each stroke where the given program's strokes would sit without transport.
+ * From the last stroke to the first, the stroke's segment start (endpoint = 0,
+ * the anchor variant: theta and length kept) or both segment ends
+ * (endpoint = 1: centre, theta and length from the pre-imaged ends) are pulled
+ * back through psi_j (Eq. back) of every later stroke j, already compensated,
+ * last first.  A point inside K_j (sigma' <= r) has no pre-image: with
+ * skip_blocked = 0 the step takes the ideal extension (sigma = 0: the point
+ * goes onto the segment, a drop's disc onto its centre), with skip_blocked = 1
+ * the step is skipped; either way the stroke is flagged as blocked.  Positions
+ * are carried as float pairs; N (N - 1) / 2 point steps run on one CTA.
+ *   out_cx, out_cy, out_theta, out_length  [n] device float32 outputs
+ *   out_blocked                            [n] device int32, 1 = blocked
+ *   n_blocked   host pointer or NULL; when non-NULL the call synchronises the
+ *               stream, reports device-side value errors and returns the count.
+ * half_width, logits and palette are unchanged and not returned. */
+TBR_API tbr_status tbr_compensate(const tbr_program* prog, int32_t endpoint, int32_t skip_blocked,
+                                  float* out_cx, float* out_cy, float* out_theta, float* out_length,
+                                  int32_t* out_blocked, int64_t* n_blocked, void* stream);
 
 /* Allocation-free hard render.  The paper has no counterpart: this entry
  * point exists for callers that may not allocate device memory at all (a
@@ -412,7 +442,7 @@ enum {
   TBR_K_LOSS = 5,        /* MSE and adjoint seed */
   TBR_K_UPDATE = 6,      /* Adam update */
   TBR_K_SERVE = 7,       /* persistent serving kernel */
-  TBR_K_FUSED = 8,       /* reserved: the loss-fused entry point launches the kernels above */
+  TBR_K_COMPENSATE = 8,  /* one-pass closed-form compensation */
   TBR_K_COUNT = 9
 };
 typedef struct {

@@ -199,6 +199,8 @@ tbr_status tbr_render_hard_transport(const tbr_program* prog, int32_t W, int32_t
   if (!prog) return fail(TBR_ERR_INVALID_ARG, "program is NULL");
   if (transport != TBR_TRANSPORT_CAPSULE && transport != TBR_TRANSPORT_DROPS16)
     return fail(TBR_ERR_INVALID_ARG, "unknown transport %d", transport);
+  if (prog->coupling && transport != TBR_TRANSPORT_CAPSULE)
+    return fail(TBR_ERR_INVALID_ARG, "the coupling variant applies to the capsule transport only");
   const int n = (n_prefix < 0 || n_prefix > prog->n) ? prog->n : n_prefix;
   tbr_status s = check_program(prog, n);
   if (s != TBR_OK) return s;
@@ -218,7 +220,7 @@ tbr_status tbr_render_hard_transport(const tbr_program* prog, int32_t W, int32_t
   if (e == cudaSuccess) e = launch_pack(pa, st);
   if (e == cudaSuccess)
     e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status, stats != nullptr, st,
-                    transport);
+                    prog->coupling ? kTransportCoupled : transport);
   unsigned long long host[ST_COUNT] = {0};
   if (e == cudaSuccess && stats) {
     e = cudaMemcpyAsync(host, status, sizeof(host), cudaMemcpyDeviceToHost, st);
@@ -256,6 +258,9 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return fail(TBR_ERR_INVALID_ARG, "unknown transport %d", opts->transport);
   if (opts->transport == TBR_TRANSPORT_DROPS16 && (ctx || opts->inert))
     return fail(TBR_ERR_INVALID_ARG, "the sixteen-drop transport renders forward only (no context, not inert)");
+  if (prog->coupling && (ctx || opts->inert || opts->transport != TBR_TRANSPORT_CAPSULE))
+    return fail(TBR_ERR_INVALID_ARG,
+                "the coupling variant renders forward only (no context, not inert, capsule transport)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ck = opts->checkpoint_every > 0 ? opts->checkpoint_every : 32;
   const int cap = opts->record_capacity > 0 ? opts->record_capacity : 64;
@@ -274,7 +279,7 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     sa.packed = packed; sa.n = prog->n; sa.W = W; sa.H = H;
     for (int i = 0; i < 3; ++i) sa.bg[i] = prog->background[i];
     sa.inert = opts->inert ? 1 : 0; sa.ck_every = ck; sa.cap = cap;
-    sa.transport = opts->transport;
+    sa.transport = prog->coupling ? kTransportCoupled : opts->transport;
     sa.out_rgb = out_rgb; sa.s0 = nullptr; sa.s0b = nullptr; sa.ckpt = nullptr; sa.ck_lt = nullptr;
     sa.rec = nullptr; sa.rec_i = nullptr; sa.status = status;
     if (e == cudaSuccess) e = launch_soft(sa, st);

@@ -89,7 +89,7 @@ __global__ void k_width_window(const float* __restrict__ r0, int n, float lo, fl
 }
 
 tbr_program view_of(const tbr_fit* f, float color_temp) {
-  tbr_program p;
+  tbr_program p{};
   const size_t n = f->n;
   p.n = f->n; p.k = f->k;
   p.cx = f->params; p.cy = f->params + n; p.theta = f->params + 2 * n;
@@ -144,6 +144,7 @@ tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t 
   *out = nullptr;
   tbr_status s = check_program(init, init ? init->n : 0);
   if (s != TBR_OK) return s;
+  if (init->coupling) return fail(TBR_ERR_INVALID_ARG, "the fit trains the capsule map (coupling must be NULL)");
   if ((s = check_size(W, H)) != TBR_OK) return s;
   if (!target) return fail(TBR_ERR_INVALID_ARG, "target is NULL");
   tbr_fit_config c;

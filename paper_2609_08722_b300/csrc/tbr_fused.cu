@@ -63,6 +63,7 @@ tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32
                                        float* g_logits, float* g_palette, tbr_ctx_stats* stats, void* stream) {
   tbr_status s = check_program(prog, prog ? prog->n : 0);
   if (s != TBR_OK) return s;
+  if (prog->coupling) return fail(TBR_ERR_INVALID_ARG, "the adjoint differentiates the capsule map (coupling must be NULL)");
   if ((s = check_size(W, H)) != TBR_OK) return s;
   if (!opts || !target) return fail(TBR_ERR_INVALID_ARG, "opts or target is NULL");
   if (!(opts->tau >= 0.0f) || !(opts->tau_min > 0.0f)) return fail(TBR_ERR_INVALID_ARG, "need tau >= 0, tau_min > 0");

@@ -4,7 +4,9 @@
 // bulk TMA (cp.async.bulk + mbarrier), last chunk first, and every thread reads
 // the current stroke as a shared-memory broadcast (hard_tile, tbr_tile.cuh).
 // The transfer renderer R_D keeps the capsule membership and replaces the
-// transport by the sixteen-drop pull-back (drops_step).
+// transport by the sixteen-drop pull-back (drops_step); the coupling variant
+// (Eq. coupling) replaces footprint and map by the deposit {u <= A_L(r) g(v)}
+// and psi_g.
 #include "tbr_tile.cuh"
 
 namespace tbr {
@@ -13,7 +15,7 @@ namespace {
 
 constexpr int kHardCH = 64;
 
-template <int CH, bool DROPS>
+template <int CH, bool DROPS, bool COUPLED>
 __global__ void __launch_bounds__(kTileThreads) k_hard(const float* __restrict__ packed, int n, int W, int H,
                                                        float bg0, float bg1, float bg2,
                                                        float* __restrict__ out_rgb, int* __restrict__ out_idx,
@@ -26,7 +28,7 @@ __global__ void __launch_bounds__(kTileThreads) k_hard(const float* __restrict__
   const float bg[3] = {bg0, bg1, bg2};
   unsigned band = 0, visited = 0;
   bool background = false;
-  hard_tile<CH, DROPS>(ring, packed, n, blockIdx.x, W, H, bg, poison, out_rgb, out_idx, band, visited,
+  hard_tile<CH, DROPS, COUPLED>(ring, packed, n, blockIdx.x, W, H, bg, poison, out_rgb, out_idx, band, visited,
                        background, status);
   if (want_stats) {
     const unsigned bsum = __reduce_add_sync(0xffffffffu, band);
@@ -46,12 +48,15 @@ cudaError_t launch_hard(const float* packed, int n, int W, int H, const float bg
                         int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st, int transport) {
   const int tiles = tile_count(W, H);
   KernelTimer kt(TBR_K_HARD, st);
-  if (transport == 1)
-    k_hard<kHardCH, true><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb, out_idx,
-                                                          status, want_stats);
+  if (transport == kTransportDrops)
+    k_hard<kHardCH, true, false><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb,
+                                                                 out_idx, status, want_stats);
+  else if (transport == kTransportCoupled)
+    k_hard<kHardCH, false, true><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb,
+                                                                 out_idx, status, want_stats);
   else
-    k_hard<kHardCH, false><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb,
-                                                           out_idx, status, want_stats);
+    k_hard<kHardCH, false, false><<<tiles, kTileThreads, 0, st>>>(packed, n, W, H, bg[0], bg[1], bg[2], out_rgb,
+                                                                  out_idx, status, want_stats);
   return cudaGetLastError();
 }
 

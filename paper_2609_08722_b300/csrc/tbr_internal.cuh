@@ -27,7 +27,9 @@ enum : int {
   F_CR = 13, F_CG = 14, F_CB = 15,           // colour c_i
   F_KA = 16, F_FL2 = 17,                     // 2L + pi r, (eps r)^2
   F_TH = 18, F_BAD = 19,                     // theta, invalid flag
-  F_D64 = 20                                 // 6 doubles: mx, my, ex, ey, L/2, r (FP64 band)
+  F_D64 = 20,                                // 2 doubles: e in FP64 (FP64 band and repair)
+  F_G0 = 24,                                 // g - 1 = G0 + G1 w + G2 w^2 + G3 w^3, w = cos 4 pi v
+  F_C1 = 28                                  // c_1, c_2, c_3 of the profile (FP64 band), 1 spare
 };
 
 constexpr float kPiF = 3.14159265358979323846f;
@@ -246,10 +248,19 @@ struct Geo {
   float ud, uh;       // at x_i: cap ? (sin phi, cos phi) : (0, 1)
   float phi;          // at x_i on a cap: angle from the flank normal
   float sb, cb, beta; // at x_{i-1} on a cap: angle and its sine / cosine
+  float rb;           // coupling variant: distance of the deposit boundary at v
   bool cap_i, cap_o, floored;
 };
 
 __device__ __forceinline__ float sgn1(float v) { return copysignf(1.0f, v); }
+
+// g(v) - 1 of the coupling variant (Eq. profile) at the angle 4 pi v in
+// [0, pi] (folded v, both mirror symmetries): w = cos(4 pi v) = -sin(4 pi v -
+// pi/2), then the cubic in w the record holds (the Chebyshev form of the modes).
+__device__ __forceinline__ float profile_gm1(float ang, const float4& gp) {
+  const float w = -sin_pi2(fminf(fmaxf(ang, 0.0f), kPiF) - 0.5f * kPiF);
+  return fmaf(w, fmaf(w, fmaf(w, gp.w, gp.z), gp.y), gp.x);
+}
 
 // psi_i in displacement form at the frame point (s, h) of x_i (Eq. back with the
 // centred arclength of Eq. phi).  The normal step uses
@@ -259,8 +270,14 @@ __device__ __forceinline__ float sgn1(float v) { return copysignf(1.0f, v); }
 // both free of cancellation, so (ds, dh) keeps full relative precision even
 // when the stroke is far.  FLOOR selects the epsilon-floor of Sec. 5.2 (soft
 // render); without it the caller guarantees sigma' > r (hard render).
-template <bool FLOOR>
-__device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh) {
+// COUPLED selects the coupling variant (Eq. coupling): the area removed is
+// A_L(r) g(v) with g - 1 the cubic gp (F_G0..F_G3) in w = cos 4 pi v, v the
+// folded centred arclength t / (2 Q'), so C and the normal step change and the
+// tangential map, which keeps v, does not; q.rb receives the deposit boundary
+// sigma_b(v), the root of 2 L sigma + pi sigma^2 = A_L(r) g(v).
+template <bool FLOOR, bool COUPLED = false>
+__device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh,
+                                          const float4 gp = make_float4(0.0f, 0.0f, 0.0f, 0.0f)) {
   if (g.L == 0.0f) {  // drop: radial map, delta = 0 (warp-uniform branch)
     q.sgs = sgn1(s); q.sgh = sgn1(h); q.si = s; q.hi = h;
     const float as = fabsf(s), ah = fabsf(h);
@@ -275,6 +292,13 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
     }
     q.t = q.sp * q.phi;
     float C = (q.sp - g.r) * fmaf(kPiF, q.sp, g.kA);
+    float Ag = g.Ar;
+    if (COUPLED) {  // v = phi / (2 pi) on a drop's leaf
+      const float gm1 = profile_gm1(2.0f * q.phi, gp);
+      C = fmaf(-g.Ar, gm1, C);
+      Ag = fmaf(g.Ar, gm1, g.Ar);
+      q.rb = sqrt_a(Ag * (1.0f / kPiF));
+    }
     q.floored = FLOOR && C < g.fl2;
     if (q.floored) C = g.fl2;
     q.sig = div_a(C, sqrt_a(kPiF * C));
@@ -288,7 +312,7 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
       dS = q.sig * q.sb - as;
       dH = q.sig * q.cb - ah;
     } else {
-      const float dsig = -div_a(g.Ar, kPiF * (q.sp + q.sig));
+      const float dsig = -div_a(Ag, kPiF * (q.sp + q.sig));
       dS = dsig * q.ud;
       dH = dsig * q.uh;
     }
@@ -312,12 +336,20 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
     q.sp = ah; q.ud = 0.0f; q.uh = 1.0f; q.phi = 0.0f; q.t = as;
   }
   float C = (q.sp - g.r) * fmaf(kPiF, q.sp, g.kA);
+  const float Qp = fmaf(kPiF, q.sp, g.L);
+  const float iQp = Qp > 0.0f ? rcp_a(Qp) : 0.0f;
+  float Ag = g.Ar;
+  if (COUPLED) {  // 4 pi v = 2 pi t / Q'
+    const float gm1 = profile_gm1(2.0f * kPiF * q.t * iQp, gp);
+    C = fmaf(-g.Ar, gm1, C);
+    Ag = fmaf(g.Ar, gm1, g.Ar);
+    q.rb = div_a(Ag, g.L + sqrt_a(fmaf(kPiF, Ag, g.L2)));
+  }
   q.floored = FLOOR && C < g.fl2;
   if (q.floored) C = g.fl2;
   q.sig = div_a(C, g.L + sqrt_a(fmaf(kPiF, C, g.L2)));
-  const float Qp = fmaf(kPiF, q.sp, g.L), Q = fmaf(kPiF, q.sig, g.L);
-  const float iQp = Qp > 0.0f ? rcp_a(Qp) : 0.0f;
-  const float dsig = q.floored ? q.sig - q.sp : -div_a(g.Ar, fmaf(kPiF, q.sp + q.sig, g.twoL));
+  const float Q = fmaf(kPiF, q.sig, g.L);
+  const float dsig = q.floored ? q.sig - q.sp : -div_a(Ag, fmaf(kPiF, q.sp + q.sig, g.twoL));
   q.tn = q.t * (Q * iQp);
   q.cap_o = q.tn > g.hl;
   float dS, dH;
@@ -613,9 +645,11 @@ struct Cover {
   float dadz;   // alpha (1 - alpha), 0 where the clamp binds
   float sp2;    // -log2(1 - alpha) = softplus(z) / ln 2
 };
-__device__ __forceinline__ Cover coverage(float sp, const StrokeF& g) {
+// Coverage of a point at distance sp from the segment whose deposit boundary
+// lies at distance rb on its ray (rb = r for the capsule).
+__device__ __forceinline__ Cover coverage(float sp, float rb, const StrokeF& g) {
   Cover c;
-  const float zr = (g.r - sp) * g.iw;
+  const float zr = (rb - sp) * g.iw;
   const bool clamped = zr > kZMax;
   c.z = fminf(zr, kZMax);
   const float ez = ex2_a(c.z * kLog2e);
@@ -626,6 +660,7 @@ __device__ __forceinline__ Cover coverage(float sp, const StrokeF& g) {
   c.sp2 = lg2_a(opl);
   return c;
 }
+__device__ __forceinline__ Cover coverage(float sp, const StrokeF& g) { return coverage(sp, g.r, g); }
 
 // Warp reduce-scatter of 8 values: afterwards every lane holds the warp total
 // of value (lane >> 2) & 7.
@@ -683,7 +718,10 @@ struct PackArgs {
 };
 cudaError_t launch_pack(const PackArgs& a, cudaStream_t st);
 
-// transport: 0 = the capsule map, 1 = the sixteen drops of the transfer renderer.
+// Internal transport codes: the capsule map, the sixteen drops of the transfer
+// renderer, and the capsule map of the coupling variant (the program carries a
+// profile; the packed record holds it).
+enum : int { kTransportCapsule = 0, kTransportDrops = 1, kTransportCoupled = 2 };
 cudaError_t launch_hard(const float* packed, int n, int W, int H, const float bg[3], float* out_rgb,
                         int* out_idx, unsigned long long* status, int want_stats, cudaStream_t st,
                         int transport = 0);
@@ -693,7 +731,7 @@ struct SoftArgs {
   int n, W, H;
   float bg[3];
   int inert;
-  int transport = 0;         // 0: capsule map; 1: sixteen drops (forward only, no record)
+  int transport = 0;         // kTransport*: drops and coupled render forward only, no record
   int ck_every;              // checkpoint interval k (>= 1)
   int cap;                   // side-table capacity per pixel
   float* out_rgb;

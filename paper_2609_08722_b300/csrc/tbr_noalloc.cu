@@ -70,7 +70,9 @@ tbr_status tbr_render_hard_noalloc(const tbr_program* prog, int32_t W, int32_t H
   cudaError_t e = cudaMemsetAsync(status, 0, ST_COUNT * sizeof(unsigned long long), st);
   PackArgs pa{prog, n, 0.0f, 1.0f, snap ? 1 : 0, packed, nullptr, status};
   if (e == cudaSuccess) e = launch_pack(pa, st);
-  if (e == cudaSuccess) e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status, 0, st);
+  if (e == cudaSuccess)
+    e = launch_hard(packed, n, W, H, prog->background, out_rgb, out_idx, status, 0, st,
+                    prog->coupling ? kTransportCoupled : kTransportCapsule);
   if (e != cudaSuccess) return cuda_fail(e, "tbr_render_hard_noalloc");
   return TBR_OK;
 }

@@ -457,6 +457,7 @@ tbr_status tbr_serve_load_program(tbr_server* s, const tbr_program* prog, uint64
   if (!s || !id) return fail(TBR_ERR_INVALID_ARG, "NULL argument");
   tbr_status st = check_program(prog, prog ? prog->n : 0);
   if (st != TBR_OK) return st;
+  if (prog->coupling) return fail(TBR_ERR_INVALID_ARG, "the server renders the capsule map (coupling must be NULL)");
   if (prog->n > s->cfg.max_strokes - 1)
     return fail(TBR_ERR_INVALID_ARG, "program of %d strokes exceeds the server's max_strokes - 1 = %d", prog->n,
                 s->cfg.max_strokes - 1);

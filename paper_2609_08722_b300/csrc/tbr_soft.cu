@@ -1,4 +1,6 @@
-// Soft forward render (Eq. relax, Eq. state) with the replay record of Sec. 5.2.
+// Soft forward render (Eq. relax, Eq. state) with the replay record of Sec. 5.2;
+// forward-only instances for the sixteen-drop transport and the coupling
+// variant (Eq. coupling: coverage sigmoid((sigma_b(v) - sigma') / w) and psi_g).
 // One thread per pixel, a CTA per 32x8 tile, strokes streamed last-to-first
 // through a two-deep shared-memory ring filled by 1-D bulk TMA.  Per stroke:
 // distance sigma', coverage alpha = sigmoid(z) in logit form, compositing
@@ -19,7 +21,7 @@ namespace {
 
 constexpr int kSoftCH = 64;
 
-template <int CH, bool RECORD, bool INERT, bool DROPS = false>
+template <int CH, bool RECORD, bool INERT, bool DROPS = false, bool COUPLED = false>
 __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
   ring.init(sbuf, sbar);
   RecordView rv{a.rec, a.rec_i, a.ckpt, a.ck_lt, P, p, a.cap, a.ck_every};
   PixelState st;
-  const bool ok = soft_forward_tile<CH, RECORD, INERT, DROPS>(
+  const bool ok = soft_forward_tile<CH, RECORD, INERT, DROPS, COUPLED>(
       ring, a.packed, a.n, valid, (static_cast<float>(px) + 0.5f) / static_cast<float>(W),
       (static_cast<float>(py) + 0.5f) / static_cast<float>(H), rv, st, status);
   if (valid) {
@@ -70,7 +72,9 @@ cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
   const int tiles = tile_count(a.W, a.H);
   const bool rec = a.s0 != nullptr;
   KernelTimer kt(TBR_K_SOFT, st);
-  if (a.transport == 1) k_soft<kSoftCH, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+  if (a.transport == kTransportDrops) k_soft<kSoftCH, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+  else if (a.transport == kTransportCoupled)
+    k_soft<kSoftCH, false, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
   else if (rec && a.inert) k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
   else if (rec) k_soft<kSoftCH, true, false><<<tiles, kTileThreads, 0, st>>>(a);
   else if (a.inert) k_soft<kSoftCH, false, true><<<tiles, kTileThreads, 0, st>>>(a);

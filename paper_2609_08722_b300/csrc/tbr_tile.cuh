@@ -54,11 +54,13 @@ __device__ __forceinline__ void tile_pixel(int tile, int W, int& px, int& py) {
 // strokes n-1 .. 0.  With RECORD, pushes (x_i, i) for floored samples and
 // stores (x_i, log2 T_i) every ck strokes.  All threads of the CTA must call it.
 // Returns false if a bounded wait gave up (the status word is set).
-template <int CH, bool RECORD, bool INERT, bool DROPS = false>
+template <int CH, bool RECORD, bool INERT, bool DROPS = false, bool COUPLED = false>
 __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, bool valid,
                                   float x0, float y0, const RecordView& rv, PixelState& st,
                                   unsigned long long* status) {
   static_assert(!(DROPS && (RECORD || INERT)), "the sixteen-drop transport renders forward only");
+  static_assert(!(COUPLED && (RECORD || INERT || DROPS)),
+                "the coupling variant renders forward only, with the capsule transport");
   st.xh = x0; st.yh = y0; st.xl = 0.0f; st.yl = 0.0f;
   st.lt = 0.0f; st.cnt = 0;
   st.C0 = st.C1 = st.C2 = 0.0f;
@@ -94,7 +96,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         }
         const float* S = S0 + j * kRec;
         const StrokeF g = load_stroke(S);
-        float sp, ds = 0.0f, dh = 0.0f, ddx = 0.0f, ddy = 0.0f;
+        float sp, rb = g.r, ds = 0.0f, dh = 0.0f, ddx = 0.0f, ddy = 0.0f;
         bool floored = false;
         const bool drop = g.L == 0.0f;  // warp-uniform
         if (DROPS) {
@@ -104,7 +106,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
           const float as = fabsf(s), ah = fabsf(h);
           const float d = as - g.hl;
           sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
-        } else if (drop) {
+        } else if (drop && !COUPLED) {
           const float dx = (st.xh - g.mx) + st.xl, dy = (st.yh - g.my) + st.yl;
           if (INERT) sp = sqrt_a(fmaf(dx, dx, dy * dy));
           else sp = drop_step<true>(dx, dy, g, ddx, ddy, floored);
@@ -117,14 +119,19 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
             sp = d > 0.0f ? sqrt_a(fmaf(d, d, ah * ah)) : ah;
           } else {
             Geo q;
-            psi_local<true>(s, h, g, q, ds, dh);
+            if (COUPLED) {
+              psi_local<true, true>(s, h, g, q, ds, dh, *reinterpret_cast<const float4*>(S + F_G0));
+              rb = q.rb;
+            } else {
+              psi_local<true>(s, h, g, q, ds, dh);
+            }
             sp = q.sp;
             floored = q.floored;
             ddx = fmaf(ds, g.ex, -dh * g.ey);
             ddy = fmaf(ds, g.ey, dh * g.ex);
           }
         }
-        const Cover cv = coverage(sp, g);
+        const Cover cv = coverage(sp, rb, g);
         const float w = ex2_a(st.lt) * cv.alpha;
         st.C0 = fmaf(w, S[F_CR], st.C0);
         st.C1 = fmaf(w, S[F_CG], st.C1);
@@ -156,12 +163,26 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
   return ok;
 }
 
+// The record's stroke frame in FP64: m, L/2 and r are exact as floats, e is
+// held as doubles (cos and sin of theta in FP64).
+struct FrameF64 {
+  double mx, my, ex, ey, hl, r;
+};
+__device__ __forceinline__ FrameF64 frame_f64(const float* __restrict__ S) {
+  const double* D = reinterpret_cast<const double*>(S + F_D64);
+  return FrameF64{static_cast<double>(S[F_MX]), static_cast<double>(S[F_MY]), D[0], D[1],
+                  static_cast<double>(S[F_HL]), static_cast<double>(S[F_R])};
+}
+
 // Membership test and psi (Eq. back) recomputed in FP64 from the hi/lo
-// position, used where |sigma' - r| < kBand.  Returns true if the point is inside.
+// position, used where |sigma' - r| < kBand (|sigma' - sigma_b(v)| for the
+// coupling variant, whose membership is A_L(sigma') <= A_L(r) g(v), i.e. C <= 0).
+// Returns true if the point is inside.
+template <bool COUPLED = false>
 static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& xl, float& yl,
                                            const float* __restrict__ S) {
-  const double* D = reinterpret_cast<const double*>(S + F_D64);
-  const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
+  const FrameF64 f = frame_f64(S);
+  const double mx = f.mx, my = f.my, ex = f.ex, ey = f.ey, hl = f.hl, r = f.r;
   const double L = 2.0 * hl;
   const double x = static_cast<double>(xh) + static_cast<double>(xl);
   const double y = static_cast<double>(yh) + static_cast<double>(yl);
@@ -170,11 +191,19 @@ static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& x
   const double as = fabs(s), ah = fabs(h), d = as - hl;
   const bool cap = d > 0.0;
   const double sp = cap ? sqrt(d * d + ah * ah) : ah;
-  if (sp <= r) return true;
-  const double C = (sp - r) * (2.0 * L + kPiD * (sp + r));
-  const double sig = C / (L + sqrt(L * L + kPiD * C));
-  const double Qp = L + kPiD * sp, Q = L + kPiD * sig;
+  if (!COUPLED && sp <= r) return true;
+  double C = (sp - r) * (2.0 * L + kPiD * (sp + r));
+  const double Qp = L + kPiD * sp;
   const double t = cap ? hl + sp * atan2(d, ah) : as;
+  if (COUPLED) {  // Eq. coupling, w = cos 4 pi v = cos(2 pi t / Q')
+    const double w = Qp > 0.0 ? cos(2.0 * kPiD * t / Qp) : 1.0;
+    const double c1 = S[F_C1], c2 = S[F_C1 + 1], c3 = S[F_C1 + 2];
+    const double gm1 = c1 * w + c2 * (2.0 * w * w - 1.0) + c3 * (4.0 * w * w * w - 3.0 * w);
+    C -= (2.0 * L * r + kPiD * r * r) * gm1;
+    if (C <= 0.0) return true;
+  }
+  const double sig = C / (L + sqrt(L * L + kPiD * C));
+  const double Q = L + kPiD * sig;
   const double tn = t * (Q / Qp);
   double sn, hn;
   if (tn <= hl) {
@@ -197,8 +226,8 @@ static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& x
 // midpoint scales by (L + pi sigma') / (L + pi sigma).  Used by the repair of a
 // drifting checkpoint segment.
 static __device__ __noinline__ void phi_f64(double& x, double& y, const float* __restrict__ S) {
-  const double* D = reinterpret_cast<const double*>(S + F_D64);
-  const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
+  const FrameF64 f = frame_f64(S);
+  const double mx = f.mx, my = f.my, ex = f.ex, ey = f.ey, hl = f.hl, r = f.r;
   const double L = 2.0 * hl;
   const double dx = x - mx, dy = y - my;
   const double s = dx * ex + dy * ey, h = dy * ex - dx * ey;
@@ -227,8 +256,8 @@ static __device__ __noinline__ void phi_f64(double& x, double& y, const float* _
 // the transfer renderer, whose transport is applied in FP32 afterwards.
 static __device__ __noinline__ bool hard_member_f64(float xh, float yh, float xl, float yl,
                                                    const float* __restrict__ S) {
-  const double* D = reinterpret_cast<const double*>(S + F_D64);
-  const double mx = D[0], my = D[1], ex = D[2], ey = D[3], hl = D[4], r = D[5];
+  const FrameF64 f = frame_f64(S);
+  const double mx = f.mx, my = f.my, ex = f.ex, ey = f.ey, hl = f.hl, r = f.r;
   const double x = static_cast<double>(xh) + static_cast<double>(xl);
   const double y = static_cast<double>(yh) + static_cast<double>(yl);
   const double dx = x - mx, dy = y - my;
@@ -238,11 +267,27 @@ static __device__ __noinline__ bool hard_member_f64(float xh, float yh, float xl
 }
 
 // One stroke of the hard chain in FP32.  Returns true if x lies in K_i;
-// otherwise moves x to psi_i(x) (displacement form, hi/lo position).
-template <bool DROPS = false>
+// otherwise moves x to psi_i(x) (displacement form, hi/lo position).  COUPLED:
+// the coupling variant's deposit and map (every stroke through the frame).
+template <bool DROPS = false, bool COUPLED = false>
 __device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float& yl,
                                           const float* __restrict__ S, unsigned& band) {
   const StrokeF g = load_stroke(S);
+  if (COUPLED) {
+    float s, h;
+    to_frame(xh, yh, xl, yl, g, s, h);
+    Geo q;
+    float ds, dh;
+    psi_local<false, true>(s, h, g, q, ds, dh, *reinterpret_cast<const float4*>(S + F_G0));
+    const float diff = q.sp - q.rb;
+    if (fabsf(diff) < kBand) {
+      ++band;
+      return hard_step_f64<true>(xh, yh, xl, yl, S);
+    }
+    if (diff <= 0.0f) return true;  // (the displacement computed inside K_i is not used)
+    add_frame_disp(xh, yh, xl, yl, g, ds, dh);
+    return false;
+  }
   if (DROPS) {  // capsule membership, then the sixteen-drop pull-back
     float s, h;
     to_frame(xh, yh, xl, yl, g, s, h);
@@ -296,7 +341,7 @@ __device__ __forceinline__ bool hard_step(float& xh, float& yh, float& xl, float
 // strokes last to first, each pixel stops at the first footprint containing it,
 // the CTA stops when all its pixels have.  Writes colour and index.
 // All threads of the CTA must call it.  Returns false if a bounded wait gave up.
-template <int CH, bool DROPS = false>
+template <int CH, bool DROPS = false, bool COUPLED = false>
 __device__ bool hard_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, int tile, int W, int H,
                           const float bg[3], bool poison, float* __restrict__ out_rgb, int* __restrict__ out_idx,
                           unsigned& band, unsigned& visited, bool& background, unsigned long long* status) {
@@ -330,7 +375,7 @@ __device__ bool hard_tile(ChunkRing<CH>& ring, const float* __restrict__ packed,
     if (alive) {
       for (int j = cnt - 1; j >= 0; --j) {
         ++visited;
-        if (hard_step<DROPS>(xh, yh, xl, yl, S0 + j * kRec, band)) {
+        if (hard_step<DROPS, COUPLED>(xh, yh, xl, yl, S0 + j * kRec, band)) {
           hit = base + j;
           alive = false;
           break;

@@ -26,7 +26,7 @@ _STATUS_NAMES = {0: "TBR_OK", 1: "TBR_ERR_INVALID_ARG", 2: "TBR_ERR_OOM", 3: "TB
                  7: "TBR_ERR_NOT_FOUND"}
 
 # Every entry point include/tbr.h declares (checked by the ABI test).
-EXPORTED = ["tbr_render_hard", "tbr_render_hard_transport", "tbr_render_hard_noalloc", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
+EXPORTED = ["tbr_render_hard", "tbr_render_hard_transport", "tbr_render_hard_noalloc", "tbr_compensate", "tbr_render_soft", "tbr_render_backward", "tbr_ctx_status",
             "tbr_ctx_bytes", "tbr_ctx_destroy", "tbr_loss_mse", "tbr_render_soft_adjoint_mse", "tbr_fit_default_config",
             "tbr_fit_create", "tbr_fit_step", "tbr_fit_get_program", "tbr_fit_iteration",
             "tbr_fit_destroy", "tbr_serve_default_config", "tbr_serve_create", "tbr_serve_load_program",
@@ -46,7 +46,8 @@ class TbrProgram(ctypes.Structure):
                 ("cx", ctypes.c_void_p), ("cy", ctypes.c_void_p), ("theta", ctypes.c_void_p),
                 ("length", ctypes.c_void_p), ("half_width", ctypes.c_void_p),
                 ("logits", ctypes.c_void_p), ("palette", ctypes.c_void_p),
-                ("background", ctypes.c_float * 3), ("color_temp", ctypes.c_float)]
+                ("background", ctypes.c_float * 3), ("color_temp", ctypes.c_float),
+                ("coupling", ctypes.c_void_p)]
 
 
 class TbrHardStats(ctypes.Structure):
@@ -90,6 +91,8 @@ def lib() -> ctypes.CDLL:
                                           ctypes.POINTER(TbrHardStats), P]
             L.tbr_render_hard_transport.argtypes = [ctypes.POINTER(TbrProgram), i32, i32, i32, i32, i32, P, P,
                                                     ctypes.POINTER(TbrHardStats), P]
+            L.tbr_compensate.argtypes = [ctypes.POINTER(TbrProgram), i32, i32, P, P, P, P, P,
+                                         ctypes.POINTER(ctypes.c_int64), P]
             L.tbr_render_soft.argtypes = [ctypes.POINTER(TbrProgram), i32, i32,
                                           ctypes.POINTER(TbrSoftOpts), P, ctypes.POINTER(P), P]
             L.tbr_render_backward.argtypes = [P, P, P, P, P, P, P, P, P, P]
@@ -101,7 +104,7 @@ def lib() -> ctypes.CDLL:
             L.tbr_loss_mse.argtypes = [P, P, i64, P, P, P]
             L.tbr_last_error.restype = ctypes.c_char_p
             L.tbr_version.restype = ctypes.c_char_p
-            for f in ("tbr_render_hard", "tbr_render_hard_transport", "tbr_render_soft", "tbr_render_backward",
+            for f in ("tbr_render_hard", "tbr_render_hard_transport", "tbr_compensate", "tbr_render_soft", "tbr_render_backward",
                       "tbr_ctx_status", "tbr_loss_mse"):
                 getattr(L, f).restype = st
             _lib = L
@@ -139,6 +142,7 @@ class DeviceProgram:
     palette: torch.Tensor     # [k, 3]
     background: tuple = (1.0, 1.0, 1.0)
     color_temp: float = 1.0
+    coupling: Optional[torch.Tensor] = None  # [n, 3] profile c_1..c_3 of the coupling variant, or None
 
     @property
     def n(self) -> int:
@@ -152,10 +156,11 @@ class DeviceProgram:
     def from_host(cls, prog, device="cuda") -> "DeviceProgram":
         """From any object with numpy arrays (``inputs.Program``)."""
         t = lambda a: torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32))).to(device)
+        cpl = getattr(prog, "coupling", None)
         return cls(cx=t(prog.cx), cy=t(prog.cy), theta=t(prog.theta), length=t(prog.length),
                    half_width=t(prog.half_width), logits=t(prog.logits), palette=t(prog.palette),
                    background=tuple(float(v) for v in np.asarray(prog.background)),
-                   color_temp=float(prog.color_temp))
+                   color_temp=float(prog.color_temp), coupling=None if cpl is None else t(cpl))
 
     def struct(self) -> TbrProgram:
         for name in ("cx", "cy", "theta", "length", "half_width", "logits", "palette"):
@@ -171,6 +176,11 @@ class DeviceProgram:
         s.logits, s.palette = _ptr(self.logits), _ptr(self.palette)
         s.background = (ctypes.c_float * 3)(*self.background)
         s.color_temp = float(self.color_temp)
+        if self.coupling is not None:
+            c = self.coupling
+            if not (c.is_cuda and c.dtype == torch.float32 and c.is_contiguous() and c.shape == (self.n, 3)):
+                raise ValueError("coupling must be a contiguous float32 CUDA tensor [n, 3]")
+            s.coupling = _ptr(c)
         return s
 
 
@@ -197,6 +207,22 @@ def render_hard(prog: DeviceProgram, W: int, H: int, n_prefix: int = -1, snap: b
         sd = {"band_steps": st.band_steps, "background_pixels": st.background_pixels,
               "visited_steps": st.visited_steps}
     return rgb, idx, sd
+
+
+def compensate(prog: DeviceProgram, endpoint: bool = False, skip_blocked: bool = False, stream=None) -> dict:
+    """tbr_compensate: the one-pass closed-form compensation of a program
+    (anchor variant, or endpoint with endpoint=True); returns dict cx, cy,
+    theta, length [n] float32, blocked [n] int32 and n_blocked (int)."""
+    dev = prog.cx.device
+    out = {k: torch.empty(prog.n, device=dev, dtype=torch.float32) for k in ("cx", "cy", "theta", "length")}
+    out["blocked"] = torch.empty(prog.n, device=dev, dtype=torch.int32)
+    nb = ctypes.c_int64(0)
+    s = prog.struct()
+    check(lib().tbr_compensate(ctypes.byref(s), int(bool(endpoint)), int(bool(skip_blocked)), _ptr(out["cx"]),
+                               _ptr(out["cy"]), _ptr(out["theta"]), _ptr(out["length"]), _ptr(out["blocked"]),
+                               ctypes.byref(nb), _stream(stream)))
+    out["n_blocked"] = int(nb.value)
+    return out
 
 
 class SoftContext:
@@ -310,7 +336,7 @@ class TbrKernelTime(ctypes.Structure):
 
 
 KERNELS = {"pack": 0, "hard": 1, "soft": 2, "backward": 3, "epilogue": 4, "loss": 5, "update": 6,
-           "serve": 7, "fused": 8}
+           "serve": 7, "compensate": 8}
 
 
 def _fit_lib():

@@ -1,0 +1,163 @@
+"""One-pass closed-form compensation (Sec. "Closed-form compensation baseline")
+on the GPU against the FP64 oracle.
+
+- Anchor and endpoint variants, clamped and skipped blocked steps, at 40
+  strokes: the compensated segment ends agree with the oracle's within 1e-6.
+- At 2000 and 2500 strokes (two and three thread strides of the one-CTA
+  wavefront, a ragged last one) the chain is ill-conditioned wherever points
+  are clamped onto later segments: perturbing the FP32 inputs by one rounding
+  (relative 6e-8) moves the oracle's own FP64 result by up to 2e-5 (operating
+  program, anchor) and 5e-3 (dense 2500-stroke program, endpoints).  Each
+  stroke's end error is bounded by 1e-6 + 50 x that sensitivity, measured per
+  stroke by re-running the oracle on perturbed inputs; a sparse 2500-stroke
+  program, whose sensitivity stays below 3e-6, is held to 2e-5 absolute.
+- The anchor variant keeps theta and length bit for bit; the last stroke keeps
+  its centre; the blocked flags agree except for points that sit on a
+  footprint boundary to FP32 precision.
+- The blocked-step cases of the oracle pins (a drop inside a later disc goes to
+  its centre or stays; a point inside a later capsule goes onto its segment).
+- Empty and one-stroke programs, and bitwise reproducibility.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_08722_b300 import inputs, tbr
+
+pytestmark = pytest.mark.gpu
+
+SENS_FACTOR = 50.0
+SENS_NOISE = 6e-8  # one FP32 rounding, relative
+
+
+def ends(cx, cy, th, L):
+    cx, cy, th, L = (np.asarray(v, dtype=np.float64) for v in (cx, cy, th, L))
+    e = np.stack([np.cos(th), np.sin(th)], 1)
+    m = np.stack([cx, cy], 1)
+    return m - 0.5 * L[:, None] * e, m + 0.5 * L[:, None] * e
+
+
+def end_dist(a, b):
+    """Per-stroke max coordinate distance between two (start, end) pairs."""
+    return np.maximum(np.abs(a[0] - b[0]).max(1), np.abs(a[1] - b[1]).max(1))
+
+
+def gpu_comp(p, endpoint, skip):
+    g = tbr.compensate(tbr.DeviceProgram.from_host(p), endpoint=endpoint, skip_blocked=skip)
+    torch.cuda.synchronize()
+    out = {k: v.cpu().numpy() for k, v in g.items() if k != "n_blocked"}
+    out["n_blocked"] = g["n_blocked"]
+    return out
+
+
+def sensitivity(p, endpoint, skip, base, trials=3):
+    """Per stroke: the largest move of the oracle's compensated segment ends
+    when every stroke parameter is perturbed by one FP32 rounding."""
+    rng = np.random.default_rng(2024)
+    worst = np.zeros(p.n)
+    for _ in range(trials):
+        q = p.copy()
+        for k in ("cx", "cy", "theta", "length", "half_width"):
+            v = getattr(q, k).astype(np.float64)
+            setattr(q, k, v * (1.0 + rng.uniform(-SENS_NOISE, SENS_NOISE, v.shape)))
+        o = oracle.compensate(q, endpoint=endpoint, skip_blocked=skip)
+        worst = np.maximum(worst, end_dist(ends(o["cx"], o["cy"], o["theta"], o["length"]), base))
+    return worst
+
+
+def compare(p, endpoint, skip, flag_slack, tol=None, sens_bound=False):
+    g = gpu_comp(p, endpoint, skip)
+    o = oracle.compensate(p, endpoint=endpoint, skip_blocked=skip)
+    oe = ends(o["cx"], o["cy"], o["theta"], o["length"])
+    err = end_dist(ends(g["cx"], g["cy"], g["theta"], g["length"]), oe)
+    flips = int((g["blocked"] != o["blocked"]).sum())
+    msg = (f"n={p.n} endpoint={endpoint} skip={skip}: end error max {err.max():.2e} median {np.median(err):.2e}, "
+           f"blocked gpu {g['n_blocked']} oracle {int(o['blocked'].sum())}, flag flips {flips}")
+    if sens_bound:
+        sens = sensitivity(p, endpoint, skip, oe)
+        ratio = err / (1e-6 + SENS_FACTOR * sens)
+        msg += f"; sensitivity max {sens.max():.2e}, worst error / bound {ratio.max():.3f}"
+        print(msg)
+        assert ratio.max() <= 1.0
+    else:
+        print(msg)
+    if tol is not None:
+        assert err.max() <= tol
+    assert g["n_blocked"] == int(g["blocked"].sum())
+    assert flips <= flag_slack
+    if not endpoint:
+        assert np.array_equal(g["theta"], p.theta) and np.array_equal(g["length"], p.length)
+    assert g["cx"][-1] == p.cx[-1] and g["cy"][-1] == p.cy[-1]
+    return g, o
+
+
+@pytest.mark.parametrize("endpoint", [False, True])
+@pytest.mark.parametrize("skip", [False, True])
+def test_small_program(endpoint, skip):
+    p = inputs.make_program(40, seed=5, palette_seed=6, k=4, r_lo=0.01, r_hi=0.05)
+    g, o = compare(p, endpoint, skip, flag_slack=0, tol=1e-6)
+    assert 0 < g["n_blocked"] < p.n
+
+
+@pytest.mark.parametrize("endpoint", [False, True])
+def test_operating_program(endpoint):
+    """The 2000-stroke operating program (r log-uniform in [0.003, 0.05]): 91%
+    of its strokes are blocked."""
+    compare(inputs.operating_program(), endpoint, False, flag_slack=10, sens_bound=True)
+
+
+@pytest.mark.parametrize("endpoint", [False, True])
+def test_three_strides_dense(endpoint):
+    """2500 strokes: each of the 1024 threads owns two or three strokes."""
+    p = inputs.make_program(2500, seed=77, palette_seed=78, k=8, r_lo=0.003, r_hi=0.03)
+    compare(p, endpoint, False, flag_slack=10, sens_bound=True)
+
+
+@pytest.mark.parametrize("endpoint", [False, True])
+@pytest.mark.parametrize("skip", [False, True])
+def test_three_strides_sparse(endpoint, skip):
+    """A sparse 2500-stroke program (r in [0.001, 0.004], L <= 0.05; about 10%
+    blocked), well conditioned: 2e-5 absolute."""
+    p = inputs.make_program(2500, seed=79, palette_seed=78, k=8, r_lo=0.001, r_hi=0.004, len_max=0.05)
+    compare(p, endpoint, skip, flag_slack=2, tol=2e-5)
+
+
+def _prog(cx, cy, th, L, r):
+    n = len(cx)
+    f = lambda a: np.asarray(a, dtype=np.float32)
+    return inputs.Program(cx=f(cx), cy=f(cy), theta=f(th), length=f(L), half_width=f(r),
+                          logits=np.zeros((n, 1), np.float32), palette=np.zeros((1, 3), np.float32),
+                          background=np.ones(3, np.float32), color_temp=1.0)
+
+
+def test_blocked_steps():
+    p = _prog([0.55, 0.5], [0.5, 0.5], [0.0, 0.0], [0.0, 0.0], [0.01, 0.2])
+    c = gpu_comp(p, False, False)
+    assert list(c["blocked"]) == [1, 0] and c["n_blocked"] == 1
+    assert (c["cx"][0], c["cy"][0]) == (np.float32(0.5), np.float32(0.5))
+    s = gpu_comp(p, False, True)
+    assert list(s["blocked"]) == [1, 0] and (s["cx"][0], s["cy"][0]) == (np.float32(0.55), np.float32(0.5))
+    q = _prog([0.53, 0.5], [0.54, 0.5], [0.0, 0.4], [0.0, 0.3], [0.01, 0.08])
+    c = gpu_comp(q, False, False)
+    o = oracle.compensate(q)
+    assert c["blocked"][0] == 1
+    assert abs(c["cx"][0] - o["cx"][0]) < 1e-6 and abs(c["cy"][0] - o["cy"][0]) < 1e-6
+
+
+def test_empty_and_single():
+    p = inputs.make_program(1, seed=3, palette_seed=4, k=2, r_lo=0.01, r_hi=0.05)
+    c = gpu_comp(p, True, False)
+    assert c["n_blocked"] == 0 and c["blocked"][0] == 0
+    assert abs(c["cx"][0] - p.cx[0]) < 1e-7 and abs(c["length"][0] - p.length[0]) < 1e-7
+    e = p.prefix(0)
+    g = tbr.compensate(tbr.DeviceProgram.from_host(e))
+    assert g["n_blocked"] == 0 and g["cx"].numel() == 0
+
+
+def test_reproducible():
+    p = inputs.operating_program()
+    a = gpu_comp(p, True, False)
+    b = gpu_comp(p, True, False)
+    for k in ("cx", "cy", "theta", "length", "blocked"):
+        assert np.array_equal(a[k], b[k])

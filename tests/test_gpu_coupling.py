@@ -1,0 +1,152 @@
+"""Coupling variant Phi_g (Sec. "A variant closer to line-source potential
+flow", Eq. coupling, Eq. profile) on the GPU against the FP64 oracle.
+
+Tolerances as for the capsule renderer: hard-render index bit-exact outside
+the band where the oracle's margin |sigma' - sigma_b(v)| < 1e-5 (a mismatch
+outside it only where the chain condition kappa * 6e-8 > 1e-5); soft render
+|R_gpu - R_oracle| <= 1e-4 per channel.  Profiles are seeded draws with
+c_1 in [0, 0.4], |c_2| <= 0.15, |c_3| <= 0.1 (g >= 0.35), on the 50-stroke
+program (half drops), a long-stroke program and the 2000-stroke operating
+program.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_08722_b300 import inputs, tbr
+
+pytestmark = pytest.mark.gpu
+
+SOFT_TOL = 1e-4
+BAND = 1e-5
+
+
+def coupled(p, seed, **kw):
+    q = p.copy()
+    q.coupling = inputs.make_coupling(seed, p.n, **kw)
+    return q
+
+
+def small_coupled():
+    return coupled(inputs.small_program(), 401)
+
+
+def long_coupled():
+    p = inputs.make_program(120, seed=311, palette_seed=312, k=8, r_lo=0.004, r_hi=0.04, len_max=0.8, p_drop=0.0)
+    return coupled(p, 402, c1_max=0.6, c2_max=0.2, c3_max=0.15)
+
+
+def hard_check(p, W, H, label):
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, idx, st = tbr.render_hard(dp, W, H, stats=True)
+    o = oracle.render_hard(p, W, H, with_kappa=True)
+    idx = idx.cpu().numpy().ravel()
+    mism = idx != o["idx"]
+    band = o["margin"] < BAND
+    outside = mism & ~band
+    cond = o["kappa"] * 6e-8 > BAND
+    print(f"coupled hard {label}: band {band.sum()}, mismatches {mism.sum()} (outside band {outside.sum()}), "
+          f"stats {st}")
+    assert not (outside & ~cond).any()
+    assert mism.mean() < 0.01
+    ok = ~mism
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3)[ok] - o["rgb"][ok]).max() < 1e-6
+    return rgb, idx, o
+
+
+@pytest.mark.parametrize("which,W,H", [("small", 128, 128), ("long", 128, 96), ("small", 77, 45)])
+def test_hard_coupled(which, W, H):
+    p = small_coupled() if which == "small" else long_coupled()
+    _, idx, o = hard_check(p, W, H, which)
+    # the profile changes the render: the capsule map's indices differ
+    plain = p.copy()
+    plain.coupling = None
+    assert (oracle.render_hard(plain, W, H)["idx"] != o["idx"]).sum() > 0.005 * W * H
+
+
+@pytest.mark.parametrize("which,W,H", [("small", 128, 128), ("long", 75, 61)])
+def test_soft_coupled(which, W, H):
+    p = small_coupled() if which == "small" else long_coupled()
+    rgb, _ = tbr.render_soft(tbr.DeviceProgram.from_host(p), W, H, 0.0, 1 / 200)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"])
+    print(f"coupled soft {which}: max {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= SOFT_TOL
+    plain = p.copy()
+    plain.coupling = None
+    assert np.abs(oracle.render_soft(plain, W, H, 0.0, 1 / 200)["rgb"] - o["rgb"]).max() > 1e-2
+
+
+def test_coupled_operating_point_sampled():
+    """The 2000-stroke operating program at 1024^2 with seeded profiles:
+    soft render on 2000 sampled pixels, hard render on 4000."""
+    p = coupled(inputs.operating_program(), 403)
+    dp = tbr.DeviceProgram.from_host(p)
+    W = H = 1024
+    rgb, _ = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN)
+    pix = inputs.sample_pixels(35, W * H, 2000)
+    o = oracle.render_soft(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3)[pix] - o["rgb"])
+    print(f"coupled soft op: max {err.max():.3e} mean {err.mean():.3e}")
+    assert err.max() <= SOFT_TOL
+    _, idx, _ = tbr.render_hard(dp, W, H)
+    pix = inputs.sample_pixels(36, W * H, 4000)
+    oh = oracle.render_hard(p, W, H, pix=pix, with_kappa=True)
+    mism = idx.cpu().numpy().ravel()[pix] != oh["idx"]
+    outside = mism & (oh["margin"] >= BAND) & (oh["kappa"] * 6e-8 <= BAND)
+    print(f"coupled hard op: mismatches {mism.sum()} of {pix.size}, unexplained {outside.sum()}")
+    assert not outside.any()
+
+
+def test_zero_profile_is_the_capsule_render():
+    """c = 0: the coupled kernels give the capsule renders (indices equal
+    outside the band, colours within 1e-5)."""
+    p = inputs.small_program()
+    q = p.copy()
+    q.coupling = np.zeros((p.n, 3), np.float32)
+    W = H = 128
+    a, b = tbr.DeviceProgram.from_host(p), tbr.DeviceProgram.from_host(q)
+    _, ia, _ = tbr.render_hard(a, W, H)
+    _, ib, _ = tbr.render_hard(b, W, H)
+    o = oracle.render_hard(p, W, H)
+    mism = (ia != ib).cpu().numpy().ravel()
+    assert not (mism & (o["margin"] >= BAND)).any()
+    sa, _ = tbr.render_soft(a, W, H, 0.0, 1 / 200)
+    sb, _ = tbr.render_soft(b, W, H, 0.0, 1 / 200)
+    assert (sa - sb).abs().max().item() <= 1e-5
+
+
+def test_nonpositive_profile_fails_the_value_checks():
+    """g must stay positive on the whole leaf (checked exactly): c_1 = 1 gives
+    g = 0 at the tips."""
+    p = inputs.small_program()
+    p.coupling = np.zeros((p.n, 3), np.float32)
+    p.coupling[7] = (1.0, 0.0, 0.0)
+    dp = tbr.DeviceProgram.from_host(p)
+    with pytest.raises(tbr.TbrError) as ei:
+        tbr.render_hard(dp, 32, 32, stats=True)
+    assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
+    rgb, _ = tbr.render_soft(dp, 32, 32, 0.0, 1 / 200)
+    assert torch.isnan(rgb).all()
+    p.coupling[7] = (0.99, 0.0, 0.0)
+    tbr.render_hard(tbr.DeviceProgram.from_host(p), 32, 32, stats=True)
+
+
+def test_coupled_program_is_rejected_where_unsupported():
+    p = small_coupled()
+    dp = tbr.DeviceProgram.from_host(p)
+    target = torch.zeros((32, 32, 3), device="cuda")
+    calls = [
+        lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, record=True),
+        lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, inert=True),
+        lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, transport="drops"),
+        lambda: tbr.render_hard(dp, 32, 32, transport="drops"),
+        lambda: tbr.soft_adjoint_mse(dp, target, 0.0, 1 / 200),
+        lambda: tbr.compensate(dp),
+        lambda: tbr.Fit(dp, target, tbr.default_fit_config(iterations=2)),
+    ]
+    for c in calls:
+        with pytest.raises(tbr.TbrError) as ei:
+            c()
+        assert ei.value.status == tbr.TBR_ERR_INVALID_ARG

@@ -29,6 +29,12 @@ def _noalloc():
     return f
 
 
+def _coupled_small():
+    p = inputs.small_program()
+    p.coupling = inputs.make_coupling(401, p.n)
+    return p
+
+
 def _render_noalloc(dp, W, H, n_prefix=-1, snap=False):
     rgb = torch.full((H, W, 3), float("nan"), device="cuda")
     idx = torch.full((H, W), -7, device="cuda", dtype=torch.int32)
@@ -43,6 +49,7 @@ def test_noalloc_hard_render_matches_the_allocating_entry_point():
     cases = [
         (inputs.operating_program(), 256, 192, -1, False),   # 2000 strokes
         (inputs.small_program(), 131, 77, 37, True),          # shorter program, prefix, snapped colours
+        (_coupled_small(), 96, 96, -1, False),                # coupling variant (Eq. coupling)
     ]
     for prog, W, H, n_prefix, snap in cases:
         dp = tbr.DeviceProgram.from_host(prog)
