@@ -203,6 +203,22 @@ def oracle_rate(prog, seconds, max_pixels=1 << 20):
     return rate, {"pixels": m2, "seconds": dt2, "threads": oracle.num_threads()}
 
 
+def oracle_forward_rates(prog, hard_prog, m=20000):
+    """Nominal pixel-stroke evals/s of the oracle's FP64 soft forward (the
+    operating program) and hard render (the resolution-sweep program) on m
+    sampled pixels of the 1024^2 canvas, all host threads."""
+    import oracle
+    from paper_2609_08722_b300 import inputs
+    pix = inputs.sample_pixels(79, RES * RES, m)
+    t0 = time.perf_counter()
+    oracle.render_soft(prog, RES, RES, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+    t1 = time.perf_counter()
+    oracle.render_hard(hard_prog, RES, RES, pix=pix)
+    t2 = time.perf_counter()
+    return {"pixels": m, "soft_forward_evals_per_s": m * prog.n / (t1 - t0),
+            "hard_nominal_evals_per_s": m * hard_prog.n / (t2 - t1)}
+
+
 def oracle_compensate_ms(prog):
     """Milliseconds of the oracle's FP64 one-pass compensation (anchor and
     endpoint variants) of the whole program, one host thread."""
@@ -326,6 +342,15 @@ def run_native(args):
         launches, total = tbr.profile_read(name)
         kernel_ms[name] = (launches, total)
     st = ctx.status()
+
+    # memory of the replay record against the alternatives the paper weighs
+    # (Sec. 5.2): every (x_i, log T_i) stored (12 B per pixel-stroke), and
+    # autograd checkpoints every 20 strokes (their states alone, a lower bound)
+    memory = {"replay_context_bytes": ctx.nbytes(),
+              "side_table_records_per_pixel": st["records"] / P,
+              "checkpoint_every": CHECKPOINT_EVERY,
+              "stored_state_bytes": 12 * P * prog.n,
+              "checkpointed_ad_every_20_states_bytes": 12 * P * -(-prog.n // 20)}
 
     step_ms_max = max_over_ranks(step_ms, world, device)
     units = float(P) * prog.n
@@ -489,6 +514,7 @@ def run_native(args):
         rgb_g = torch.empty((H, W, 3), device=device)
         idx_g = torch.empty((H, W), dtype=torch.int32, device=device)
         soft_c = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_g))
+        soft_x = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_g, early_exit=1e-12))
         soft_g = timed(lambda: tbr.render_soft(dpg, W, H, tau, tau_min, out_rgb=rgb_g))
         hard_g = timed(lambda: tbr.render_hard(dpg, W, H, out_rgb=rgb_g, out_idx=idx_g))
         ach = OPS_FWD_G * units / (soft_g * 1e-3) * 1e-9
@@ -496,6 +522,8 @@ def run_native(args):
                                 "forward and hard render of the same program",
                     "soft_forward_ms": soft_g, "soft_evals_per_s": units / (soft_g * 1e-3),
                     "capsule_soft_forward_ms": soft_c, "hard_ms": hard_g,
+                    "capsule_soft_forward_early_exit_ms": soft_x,
+                    "early_exit": "forward-only capsule render stopping each pixel once T < 1e-12",
                     "soft_roofline": {"ops_per_unit": OPS_FWD_G, "achieved": ach, "frac": ach / PEAK_GOPS,
                                       "xu_ops_per_unit": XU_FWD_G,
                                       "xu_frac": XU_FWD_G * units / (soft_g * 1e-3) * 1e-9 / PEAK_XU_GOPS}}
@@ -527,6 +555,7 @@ def run_native(args):
                          f"(FP64 soft forward + stored-state adjoint, {info['seconds']:.1f} s)"}
         if comp is not None:
             comp["cpu_oracle_ms"] = oracle_compensate_ms(prog_h)
+        cpu["forward_rates"] = oracle_forward_rates(prog_h, inputs.resolution_program())
 
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0 and args.res == RES and args.strokes == N_STROKES:
@@ -566,6 +595,7 @@ def run_native(args):
             "serve": serve,
             "hard": hard,
             "transfer_renderer": transfer,
+            "memory": memory,
             "coupling_variant": coupling,
             "compensation": comp,
             "e2e": e2e,

@@ -195,6 +195,13 @@ typedef struct {
                                pixel of capacity. */
   int32_t transport;        /* TBR_TRANSPORT_*; TBR_TRANSPORT_DROPS16 renders
                                forward only (no context, not inert) */
+  float early_exit;         /* forward-only renders (no context): a pixel stops
+                               once its transmittance T falls below this value
+                               after compositing a stroke, and a CTA once all its
+                               pixels have; the output is C + T c_0 with that T,
+                               so the skipped strokes change each channel by at
+                               most early_exit.  0 = off (every pixel visits all
+                               N strokes); must be in [0, 1). */
 } tbr_soft_opts;
 
 typedef struct tbr_ctx tbr_ctx;

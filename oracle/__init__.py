@@ -76,7 +76,7 @@ def _load():
             lib.orc_render_hard.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_int, P, i64, P, P, P, P]
             lib.orc_render_soft.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
-                                            P, i64, P, P, P]
+                                            P, i64, P, P, P, dbl]
             lib.orc_soft_jvp.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
                                          P, i64, ctypes.c_int, ctypes.c_int, P]
             lib.orc_soft_vjp.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int,
@@ -262,16 +262,17 @@ def render_hard(prog, W, H, n_prefix=-1, snap=False, inert=False, pix=None, with
     return out
 
 
-def render_soft(prog, W, H, tau, tau_min, inert=False, pix=None, transport=None):
+def render_soft(prog, W, H, tau, tau_min, inert=False, pix=None, transport=None, early_exit=0.0):
     """Soft render; returns dict rgb [m,3], T0 [m], nrec [m] (floor binds).
-    transport as render_hard."""
+    transport as render_hard.  early_exit > 0 stops a pixel once its
+    transmittance falls below that value (T0 is then the T at the exit)."""
     pk = _Packed(prog)
     pix, m = _pixels(W, H, pix)
     rgb = np.empty((m, 3))
     T0 = np.empty(m)
     nrec = np.empty(m, dtype=np.int32)
     _load().orc_render_soft(pk.ref, W, H, float(tau), float(tau_min), _transport(inert, transport, prog),
-                            _ptr(pix), m, _ptr(rgb), _ptr(T0), _ptr(nrec))
+                            _ptr(pix), m, _ptr(rgb), _ptr(T0), _ptr(nrec), float(early_exit))
     return {"rgb": rgb, "T0": T0, "nrec": nrec}
 
 

@@ -13,7 +13,9 @@
 //     the full stadium (no quadrant folding) from the definitions in Sec. 4;
 //   * the interior extension by clamping C (Sec. 4 "The chain") and the
 //     implemented epsilon-floor of Sec. 5.2;
-//   * the hard and soft renderers (Eq. chain, Eq. render, Eq. relax, Eq. state);
+//   * the hard and soft renderers (Eq. chain, Eq. render, Eq. relax, Eq. state),
+//     the soft one with the optional early exit of the forward render (a pixel
+//     stops once its transmittance falls below a threshold);
 //   * the one-pass closed-form compensation baseline (Sec. "Closed-form
 //     compensation baseline"): anchor or endpoint pre-images through every
 //     later stroke's inverse map, with blocked steps clamped or skipped;
@@ -608,11 +610,14 @@ namespace {
 // One pixel of the soft render (Eq. state): s_N = (x, 0, 1);
 // C_{i-1} = C_i + T_i alpha_i c_i, T_{i-1} = T_i (1 - alpha_i), x_{i-1} = psi_i(x_i),
 // R = C_0 + T_0 c_0.  Templated so that the same steps run in FP64 and in
-// forward-mode dual numbers (the directional-derivative pin).
+// forward-mode dual numbers (the directional-derivative pin).  exit_T > 0 is the
+// optional early exit of the forward render: the pixel stops once T falls below
+// exit_T after compositing a stroke, and R = C + T c_0 with that T (the strokes
+// below would add at most T).
 template <class T>
 void soft_pixel(const std::vector<Stroke<T>>& g, const std::vector<T>& col, const T bg[3],
                 double tau, double tau_min, int transport, double px, double py,
-                T out[3], double* T0, int* nrec) {
+                T out[3], double* T0, int* nrec, double exit_T = 0.0) {
   T x(px), y(py);
   T C[3] = {T(0.0), T(0.0), T(0.0)};
   T Tr(1.0);
@@ -624,6 +629,7 @@ void soft_pixel(const std::vector<Stroke<T>>& g, const std::vector<T>& col, cons
     T a = soft_coverage(deposit_margin(s, h, sp, g[j]), g[j].r, tau, tau_min);
     for (int c = 0; c < 3; ++c) C[c] = C[c] + Tr * a * col[(size_t)j * 3 + c];
     Tr = Tr * (1.0 - a);
+    if (exit_T > 0.0 && value(Tr) < exit_T) break;
     if (transport == kCapsule) {
       T xo, yo;
       rec += psi(x, y, g[j], kFloor, xo, yo);
@@ -646,9 +652,9 @@ extern "C" {
 // Soft render (Eq. relax coverage, Eq. state compositing, epsilon-floored psi).
 // Outputs per rendered pixel: rgb[3]; T0 (final transmittance, nullable);
 // nrec (side-table records, i.e. floor binds, nullable).
-// transport as orc_render_hard.
+// transport as orc_render_hard.  exit_T > 0: early exit once T < exit_T.
 int orc_render_soft(const orc_prog* p, int W, int H, double tau, double tau_min, int transport,
-                    const int64_t* pix, int64_t npix, double* rgb, double* T0, int32_t* nrec) {
+                    const int64_t* pix, int64_t npix, double* rgb, double* T0, int32_t* nrec, double exit_T) {
   std::vector<double> col, prob;
   stroke_colours(p, 0, col, prob);
   std::vector<Stroke<double>> g(p->n);
@@ -660,7 +666,7 @@ int orc_render_soft(const orc_prog* p, int W, int H, double tau, double tau_min,
     pixel_centre(pidx, W, H, x, y);
     double out[3], t0;
     int nr;
-    soft_pixel<double>(g, col, p->background, tau, tau_min, transport, x, y, out, &t0, &nr);
+    soft_pixel<double>(g, col, p->background, tau, tau_min, transport, x, y, out, &t0, &nr, exit_T);
     for (int c = 0; c < 3; ++c) rgb[q * 3 + c] = out[c];
     if (T0) T0[q] = t0;
     if (nrec) nrec[q] = nr;

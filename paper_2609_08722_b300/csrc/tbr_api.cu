@@ -258,6 +258,10 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return fail(TBR_ERR_INVALID_ARG, "unknown transport %d", opts->transport);
   if (opts->transport == TBR_TRANSPORT_DROPS16 && (ctx || opts->inert))
     return fail(TBR_ERR_INVALID_ARG, "the sixteen-drop transport renders forward only (no context, not inert)");
+  if (!(opts->early_exit >= 0.0f && opts->early_exit < 1.0f))
+    return fail(TBR_ERR_INVALID_ARG, "early_exit must be in [0, 1)");
+  if (opts->early_exit > 0.0f && ctx)
+    return fail(TBR_ERR_INVALID_ARG, "early exit applies to forward-only renders (the adjoint needs every stroke)");
   if (prog->coupling && (ctx || opts->inert || opts->transport != TBR_TRANSPORT_CAPSULE))
     return fail(TBR_ERR_INVALID_ARG,
                 "the coupling variant renders forward only (no context, not inert, capsule transport)");
@@ -280,6 +284,7 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     for (int i = 0; i < 3; ++i) sa.bg[i] = prog->background[i];
     sa.inert = opts->inert ? 1 : 0; sa.ck_every = ck; sa.cap = cap;
     sa.transport = prog->coupling ? kTransportCoupled : opts->transport;
+    if (opts->early_exit > 0.0f) sa.exit_lt = log2f(opts->early_exit);
     sa.out_rgb = out_rgb; sa.s0 = nullptr; sa.s0b = nullptr; sa.ckpt = nullptr; sa.ck_lt = nullptr;
     sa.rec = nullptr; sa.rec_i = nullptr; sa.status = status;
     if (e == cudaSuccess) e = launch_soft(sa, st);

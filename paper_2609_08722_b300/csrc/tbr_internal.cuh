@@ -732,6 +732,7 @@ struct SoftArgs {
   float bg[3];
   int inert;
   int transport = 0;         // kTransport*: drops and coupled render forward only, no record
+  float exit_lt = -3.0e38f;  // forward only: a pixel stops once log2 T < exit_lt (this value: off)
   int ck_every;              // checkpoint interval k (>= 1)
   int cap;                   // side-table capacity per pixel
   float* out_rgb;

@@ -21,8 +21,8 @@ namespace {
 
 constexpr int kSoftCH = 64;
 
-template <int CH, bool RECORD, bool INERT, bool DROPS = false, bool COUPLED = false>
-__global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
+template <int CH, bool RECORD, bool INERT, bool DROPS, bool COUPLED, bool EXIT>
+__device__ __forceinline__ void soft_body(const SoftArgs& a) {
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
   const int lane = threadIdx.x & 31;
@@ -38,9 +38,9 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
   ring.init(sbuf, sbar);
   RecordView rv{a.rec, a.rec_i, a.ckpt, a.ck_lt, P, p, a.cap, a.ck_every};
   PixelState st;
-  const bool ok = soft_forward_tile<CH, RECORD, INERT, DROPS, COUPLED>(
+  const bool ok = soft_forward_tile<CH, RECORD, INERT, DROPS, COUPLED, EXIT>(
       ring, a.packed, a.n, valid, (static_cast<float>(px) + 0.5f) / static_cast<float>(W),
-      (static_cast<float>(py) + 0.5f) / static_cast<float>(H), rv, st, status);
+      (static_cast<float>(py) + 0.5f) / static_cast<float>(H), rv, st, status, a.exit_lt);
   if (valid) {
     const float T0 = ex2_a(st.lt);
     float o0 = fmaf(T0, a.bg[0], st.C0), o1 = fmaf(T0, a.bg[1], st.C1), o2 = fmaf(T0, a.bg[2], st.C2);
@@ -66,19 +66,37 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
   }
 }
 
+template <int CH, bool RECORD, bool INERT, bool DROPS = false, bool COUPLED = false, bool EXIT = false>
+__global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
+  soft_body<CH, RECORD, INERT, DROPS, COUPLED, EXIT>(a);
+}
+
 }  // namespace
 
 cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
   const int tiles = tile_count(a.W, a.H);
   const bool rec = a.s0 != nullptr;
   KernelTimer kt(TBR_K_SOFT, st);
-  if (a.transport == kTransportDrops) k_soft<kSoftCH, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
-  else if (a.transport == kTransportCoupled)
-    k_soft<kSoftCH, false, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
-  else if (rec && a.inert) k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
-  else if (rec) k_soft<kSoftCH, true, false><<<tiles, kTileThreads, 0, st>>>(a);
-  else if (a.inert) k_soft<kSoftCH, false, true><<<tiles, kTileThreads, 0, st>>>(a);
-  else k_soft<kSoftCH, false, false><<<tiles, kTileThreads, 0, st>>>(a);
+  // forward-only renders that ask for the early exit run their own instances,
+  // so the others carry no per-stroke test
+  const bool ex = !rec && a.exit_lt > -1.0e38f;
+  if (a.transport == kTransportDrops) {
+    if (ex) k_soft<kSoftCH, false, false, true, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+    else k_soft<kSoftCH, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+  } else if (a.transport == kTransportCoupled) {
+    if (ex) k_soft<kSoftCH, false, false, false, true, true><<<tiles, kTileThreads, 0, st>>>(a);
+    else k_soft<kSoftCH, false, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+  } else if (rec && a.inert) {
+    k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
+  } else if (rec) {
+    k_soft<kSoftCH, true, false><<<tiles, kTileThreads, 0, st>>>(a);
+  } else if (a.inert) {
+    if (ex) k_soft<kSoftCH, false, true, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+    else k_soft<kSoftCH, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+  } else {
+    if (ex) k_soft<kSoftCH, false, false, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+    else k_soft<kSoftCH, false, false><<<tiles, kTileThreads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -52,15 +52,18 @@ __device__ __forceinline__ void tile_pixel(int tile, int W, int& px, int& py) {
 
 // Soft forward (Eq. relax, Eq. state, floored psi) of one pixel per thread over
 // strokes n-1 .. 0.  With RECORD, pushes (x_i, i) for floored samples and
-// stores (x_i, log2 T_i) every ck strokes.  All threads of the CTA must call it.
-// Returns false if a bounded wait gave up (the status word is set).
-template <int CH, bool RECORD, bool INERT, bool DROPS = false, bool COUPLED = false>
+// stores (x_i, log2 T_i) every ck strokes.  With EXIT (forward only), a pixel
+// stops once log2 T < exit_lt after compositing a stroke (the early exit of the
+// forward render) and the CTA once all its pixels have.  All threads of the CTA
+// must call it.  Returns false if a bounded wait gave up (the status word is set).
+template <int CH, bool RECORD, bool INERT, bool DROPS = false, bool COUPLED = false, bool EXIT = false>
 __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, bool valid,
                                   float x0, float y0, const RecordView& rv, PixelState& st,
-                                  unsigned long long* status) {
+                                  unsigned long long* status, float exit_lt = -3.0e38f) {
   static_assert(!(DROPS && (RECORD || INERT)), "the sixteen-drop transport renders forward only");
   static_assert(!(COUPLED && (RECORD || INERT || DROPS)),
                 "the coupling variant renders forward only, with the capsule transport");
+  static_assert(!(EXIT && RECORD), "the early exit applies to forward-only renders");
   st.xh = x0; st.yh = y0; st.xl = 0.0f; st.yl = 0.0f;
   st.lt = 0.0f; st.cnt = 0;
   st.C0 = st.C1 = st.C2 = 0.0f;
@@ -74,6 +77,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
     if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
   }
   bool ok = true;
+  bool live = valid;  // false once the pixel has taken its early exit (EXIT)
   for (int q = 0; q < nch; ++q) {
     const int b = q & 1;
     const bool got = ring.wait(b, status);
@@ -85,7 +89,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
     const int base = (nch - 1 - q) * CH;
     const int cntc = chunk_cnt(q);
     const float* S0 = ring.data(b);
-    if (valid) {
+    if (live) {
       for (int j = cntc - 1; j >= 0; --j) {
         const int i1 = base + j + 1;  // the paper's 1-based stroke index
         if (RECORD && i1 == next_ck) {
@@ -137,6 +141,10 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         st.C1 = fmaf(w, S[F_CG], st.C1);
         st.C2 = fmaf(w, S[F_CB], st.C2);
         st.lt -= cv.sp2;
+        if (EXIT && st.lt < exit_lt) {
+          live = false;
+          break;
+        }
         if (DROPS) {
           st.cnt += drops_step(st.xh, st.yh, st.xl, st.yl, g);
         } else if (!INERT) {
@@ -157,7 +165,12 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         }
       }
     }
-    __syncthreads();
+    if (!EXIT) {
+      __syncthreads();
+    } else if (!__syncthreads_or(live)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);  // drain the prefetched chunk
+      break;
+    }
     if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
   }
   return ok;

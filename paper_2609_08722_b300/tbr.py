@@ -59,7 +59,8 @@ class TbrSoftOpts(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_float), ("tau_min", ctypes.c_float),
                 ("checkpoint_every", ctypes.c_int32), ("record_capacity", ctypes.c_int32),
                 ("inert", ctypes.c_int32), ("drift_tolerance", ctypes.c_float),
-                ("repair_capacity", ctypes.c_int32), ("transport", ctypes.c_int32)]
+                ("repair_capacity", ctypes.c_int32), ("transport", ctypes.c_int32),
+                ("early_exit", ctypes.c_float)]
 
 
 TRANSPORTS = {"capsule": 0, "drops": 1}
@@ -278,14 +279,17 @@ class SoftContext:
 def render_soft(prog: DeviceProgram, W: int, H: int, tau: float, tau_min: float, record: bool = False,
                 checkpoint_every: int = 0, record_capacity: int = 0, inert: bool = False,
                 out_rgb=None, stream=None, reuse: Optional["SoftContext"] = None,
-                drift_tolerance: float = 0.0, repair_capacity: int = 0, transport: str = "capsule"):
+                drift_tolerance: float = 0.0, repair_capacity: int = 0, transport: str = "capsule",
+                early_exit: float = 0.0):
     """tbr_render_soft; returns (rgb [H,W,3], SoftContext or None).  ``reuse``
     overwrites an existing context of the same shape instead of allocating.
-    ``transport="drops"`` renders with the sixteen-drop transport (forward only)."""
+    ``transport="drops"`` renders with the sixteen-drop transport (forward only).
+    ``early_exit`` > 0 (forward only) stops a pixel once T < early_exit."""
     dev = prog.cx.device
     rgb = out_rgb if out_rgb is not None else torch.empty((H, W, 3), device=dev, dtype=torch.float32)
     opts = TbrSoftOpts(float(tau), float(tau_min), int(checkpoint_every), int(record_capacity),
-                       int(bool(inert)), float(drift_tolerance), int(repair_capacity), TRANSPORTS[transport])
+                       int(bool(inert)), float(drift_tolerance), int(repair_capacity), TRANSPORTS[transport],
+                       float(early_exit))
     handle = ctypes.c_void_p(reuse.handle if reuse is not None else None)
     s = prog.struct()
     check(lib().tbr_render_soft(ctypes.byref(s), W, H, ctypes.byref(opts), _ptr(rgb),

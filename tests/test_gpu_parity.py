@@ -402,3 +402,58 @@ def test_sixteen_drops_render_forward_only(small):
     with pytest.raises(tbr.TbrError) as ei:
         tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, record=True, transport="drops")
     assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
+
+
+# --------------------------------------------------------------------------- early exit of the forward render
+
+def _dense_program():
+    return inputs.make_program(400, seed=71, palette_seed=72, k=6, r_lo=0.03, r_hi=0.1)
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-12])
+def test_soft_early_exit_against_oracle(eps):
+    """A pixel stops once T < eps (forward only): against the oracle's render
+    with the same exit, and within eps of the GPU's full render."""
+    p = _dense_program()
+    dp = tbr.DeviceProgram.from_host(p)
+    W, H = 97, 61
+    ex, _ = tbr.render_soft(dp, W, H, 0.0, 1 / 200, early_exit=eps)
+    full, _ = tbr.render_soft(dp, W, H, 0.0, 1 / 200)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200, early_exit=eps)
+    err = np.abs(ex.cpu().numpy().reshape(-1, 3) - o["rgb"])
+    gap = (ex - full).abs().max().item()
+    print(f"early exit {eps:g}: vs oracle max {err.max():.3e}; vs full render {gap:.3e}; "
+          f"oracle exited {(o['T0'] < eps).mean():.3f}")
+    assert err.max() <= SOFT_TOL
+    assert gap <= eps + 1e-6
+
+
+def test_soft_early_exit_operating_point(operating):
+    p, dp = operating
+    W = H = 1024
+    ex, _ = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, early_exit=1e-12)
+    pix = inputs.sample_pixels(37, W * H, 2000)
+    o = oracle.render_soft(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix, early_exit=1e-12)
+    err = np.abs(ex.cpu().numpy().reshape(-1, 3)[pix] - o["rgb"])
+    print(f"early exit op: max {err.max():.3e}, oracle exited {(o['T0'] < 1e-12).mean():.3f}")
+    assert err.max() <= SOFT_TOL
+
+
+@pytest.mark.parametrize("variant", ["drops", "coupled"])
+def test_early_exit_with_other_transports(variant):
+    p = _dense_program()
+    if variant == "coupled":
+        p.coupling = inputs.make_coupling(404, p.n)
+    dp = tbr.DeviceProgram.from_host(p)
+    tr = "drops" if variant == "drops" else "capsule"
+    ex, _ = tbr.render_soft(dp, 64, 64, 0.0, 1 / 200, transport=tr, early_exit=1e-9)
+    full, _ = tbr.render_soft(dp, 64, 64, 0.0, 1 / 200, transport=tr)
+    assert (ex - full).abs().max().item() <= 1e-6
+
+
+def test_early_exit_arguments(small):
+    _, dp = small
+    for kw in ({"early_exit": 1e-9, "record": True}, {"early_exit": 1.0}, {"early_exit": -1e-3}):
+        with pytest.raises(tbr.TbrError) as ei:
+            tbr.render_soft(dp, 16, 16, 0.0, 1 / 200, **kw)
+        assert ei.value.status == tbr.TBR_ERR_INVALID_ARG

@@ -748,3 +748,19 @@ def test_coupled_adjoint_matches_finite_differences():
     fd = oracle.fd_gradient(p, W, H, tau, tau_min, cot, params, h_geo=1e-6, h_logit=1e-6)
     got = np.array([g[oracle._FIELD[q]][j] if q < 5 else g["logits"][j, q - 5] for (j, q) in params])
     assert np.abs(got - fd).max() < 1e-6 * np.abs(fd).max()
+
+
+def test_early_exit_changes_the_render_by_at_most_the_exit_transmittance():
+    """Early exit of the forward render (stop once T < eps_T): the strokes it
+    skips could add at most T < eps_T to each channel (colours and background
+    in [0, 1]); pixels that never exit are unchanged."""
+    p = inputs.make_program(400, seed=71, palette_seed=72, k=6, r_lo=0.03, r_hi=0.1)
+    W = H = 40
+    full = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    for eps in (1e-3, 1e-6, 1e-12):
+        ex = oracle.render_soft(p, W, H, 0.0, 1 / 200, early_exit=eps)
+        d = np.abs(ex["rgb"] - full["rgb"]).max(1)
+        exited = ex["T0"] < eps
+        assert exited.sum() > 0.5 * W * H
+        assert (d <= ex["T0"] + 1e-15).all()
+        assert np.array_equal(ex["rgb"][~exited], full["rgb"][~exited])
