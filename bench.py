@@ -123,6 +123,25 @@ def sum_over_ranks(x, world, device):
     return float(t.item())
 
 
+def rank_programs(rank, strokes=N_STROKES):
+    """Replicas: each rank renders its own seeded operating-point program
+    (seed 102 + 1000 rank) against the hard render of another (103 + 1000 rank),
+    so the per-GPU work is fixed as the rank count grows (weak scaling)."""
+    from paper_2609_08722_b300 import inputs
+    prog_h = inputs.operating_program(seed=102 + 1000 * rank)
+    targ_h = inputs.operating_program(seed=103 + 1000 * rank)
+    if strokes != N_STROKES:
+        prog_h, targ_h = prog_h.prefix(strokes), targ_h.prefix(strokes)
+    return prog_h, targ_h
+
+
+def whole_job_rate(units, step_ms, world, device):
+    """(slowest rank's ms per step, whole-job units per second): the units all
+    ranks processed in one step over the slowest rank's step time."""
+    ms = max_over_ranks(step_ms, world, device)
+    return ms, sum_over_ranks(units, world, device) / (ms * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -288,11 +307,7 @@ def run_native(args):
     init_dist(world, "nccl")
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
 
-    # per-rank independent program (weak scaling); target = hard render of another program
-    prog_h = inputs.operating_program(seed=102 + 1000 * rank)
-    targ_h = inputs.operating_program(seed=103 + 1000 * rank)
-    if args.strokes != N_STROKES:
-        prog_h, targ_h = prog_h.prefix(args.strokes), targ_h.prefix(args.strokes)
+    prog_h, targ_h = rank_programs(rank, args.strokes)
     prog = tbr.DeviceProgram.from_host(prog_h, device)
     targ = tbr.DeviceProgram.from_host(targ_h, device)
     W = H = args.res
@@ -352,9 +367,8 @@ def run_native(args):
               "stored_state_bytes": 12 * P * prog.n,
               "checkpointed_ad_every_20_states_bytes": 12 * P * -(-prog.n // 20)}
 
-    step_ms_max = max_over_ranks(step_ms, world, device)
     units = float(P) * prog.n
-    value = sum_over_ranks(units, world, device) / (step_ms_max * 1e-3)
+    step_ms_max, value = whole_job_rate(units, step_ms, world, device)
 
     # roofline of the dominant kernel (replay adjoint), timed with events on its stream
     bl, bt = kernel_ms["backward"]
