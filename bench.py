@@ -531,12 +531,26 @@ def run_native(args):
         soft_x = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_g, early_exit=1e-12))
         soft_g = timed(lambda: tbr.render_soft(dpg, W, H, tau, tau_min, out_rgb=rgb_g))
         hard_g = timed(lambda: tbr.render_hard(dpg, W, H, out_rgb=rgb_g, out_idx=idx_g))
+        # the coupled fwd + adjoint step (record, MSE seed, replay adjoint with
+        # dual-number local Jacobians) against the same target
+        _, cctx = tbr.render_soft(dpg, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
+                                  out_rgb=rgb_g)
+
+        def coupled_step():
+            tbr.render_soft(dpg, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
+                            out_rgb=rgb_g, reuse=cctx)
+            _, dLg = tbr.loss_mse(rgb_g, target)
+            cctx.backward(dLg)
+
+        step_g = timed(coupled_step)
+        cctx.destroy()
         ach = OPS_FWD_G * units / (soft_g * 1e-3) * 1e-9
         coupling = {"workload": "Phi_g (profiles c_1 in [0, 0.4], |c_2| <= 0.15, |c_3| <= 0.1, seed 403) soft "
                                 "forward and hard render of the same program",
                     "soft_forward_ms": soft_g, "soft_evals_per_s": units / (soft_g * 1e-3),
                     "capsule_soft_forward_ms": soft_c, "hard_ms": hard_g,
                     "capsule_soft_forward_early_exit_ms": soft_x,
+                    "fwd_adjoint_step_ms": step_g, "fwd_adjoint_evals_per_s": units / (step_g * 1e-3),
                     "early_exit": "forward-only capsule render stopping each pixel once T < 1e-12",
                     "soft_roofline": {"ops_per_unit": OPS_FWD_G, "achieved": ach, "frac": ach / PEAK_GOPS,
                                       "xu_ops_per_unit": XU_FWD_G,

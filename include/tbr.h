@@ -82,9 +82,12 @@ typedef struct {
                                Eq. profile), or NULL for the capsule map (g = 1).
                                Each stroke's g must be positive on the whole leaf
                                (checked exactly; else the stroke fails the value
-                               checks).  Supported by the hard render and the
-                               forward-only soft render (capsule transport); the
-                               other entry points reject a non-NULL coupling. */
+                               checks).  Supported by the hard render, the soft
+                               render (capsule transport, not inert) with or
+                               without a replay context, and its replay adjoint
+                               (tbr_render_backward; local Jacobians by dual
+                               numbers, no FP64 repair); the other entry points
+                               reject a non-NULL coupling. */
 } tbr_program;
 
 /* Transport of a render: the paper's capsule insertion map psi (Eq. back), or

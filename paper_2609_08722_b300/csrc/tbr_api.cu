@@ -69,13 +69,13 @@ tbr_status check_size(int32_t W, int32_t H) {
 }
 
 cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert, float drift_tol,
-                         int repair_cap, cudaStream_t st) {
+                         int repair_cap, cudaStream_t st, int coupled) {
   const size_t P = static_cast<size_t>(W) * H;
   c->n = n; c->k = k; c->W = W; c->H = H;
-  c->ck = ck; c->cap = cap; c->inert = inert;
+  c->ck = ck; c->cap = cap; c->inert = inert; c->coupled = coupled;
   c->drift_tol = drift_tol;
-  c->repair_cap = inert ? 0 : repair_cap;
-  c->grid = backward_grid(W, H, inert);
+  c->repair_cap = (inert || coupled) ? 0 : repair_cap;
+  c->grid = coupled ? backward_grid_coupled(W, H) : backward_grid(W, H, inert);
   c->last_stream = st;
   const size_t nck = n > 1 ? static_cast<size_t>((n - 1) / ck) : 0;
   cudaError_t e = dalloc(&c->packed, static_cast<size_t>(n) * kRec, st);
@@ -127,6 +127,7 @@ cudaError_t ctx_forward(tbr_ctx* c, const tbr_program* prog, float tau, float ta
   sa.packed = c->packed; sa.n = c->n; sa.W = c->W; sa.H = c->H;
   for (int i = 0; i < 3; ++i) sa.bg[i] = c->bg[i];
   sa.inert = c->inert; sa.ck_every = c->ck; sa.cap = c->cap;
+  sa.transport = c->coupled ? kTransportCoupled : kTransportCapsule;
   sa.out_rgb = out_rgb; sa.s0 = c->s0; sa.s0b = c->s0b; sa.ckpt = c->ckpt; sa.ck_lt = c->ck_lt;
   sa.rec = c->rec; sa.rec_i = c->rec_i; sa.status = c->status;
   if (e == cudaSuccess) e = launch_soft(sa, st);
@@ -150,6 +151,7 @@ cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy
   ba.drift_tol = c->drift_tol;
   ba.repair_list = c->repair_list; ba.repair_count = c->repair_count; ba.repair_cap = c->repair_cap;
   ba.corr = c->corr; ba.repair_first = c->repair_first;
+  ba.coupled = c->coupled;
   cudaError_t e = launch_backward(ba, st);
   if (e != cudaSuccess) return e;
   EpilogueArgs ea;
@@ -262,9 +264,8 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return fail(TBR_ERR_INVALID_ARG, "early_exit must be in [0, 1)");
   if (opts->early_exit > 0.0f && ctx)
     return fail(TBR_ERR_INVALID_ARG, "early exit applies to forward-only renders (the adjoint needs every stroke)");
-  if (prog->coupling && (ctx || opts->inert || opts->transport != TBR_TRANSPORT_CAPSULE))
-    return fail(TBR_ERR_INVALID_ARG,
-                "the coupling variant renders forward only (no context, not inert, capsule transport)");
+  if (prog->coupling && (opts->inert || opts->transport != TBR_TRANSPORT_CAPSULE))
+    return fail(TBR_ERR_INVALID_ARG, "the coupling variant uses the capsule transport (not inert)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ck = opts->checkpoint_every > 0 ? opts->checkpoint_every : 32;
   const int cap = opts->record_capacity > 0 ? opts->record_capacity : 64;
@@ -294,19 +295,21 @@ tbr_status tbr_render_soft(const tbr_program* prog, int32_t W, int32_t H, const 
     return TBR_OK;
   }
   const int inert = opts->inert ? 1 : 0;
+  const int coupled = prog->coupling ? 1 : 0;
   tbr_ctx* c = *ctx;
   if (c) {
     // reuse an existing context of the same shape: no allocation
     if (c->n != prog->n || c->k != prog->k || c->W != W || c->H != H || c->ck != ck || c->cap != cap ||
-        c->inert != inert || c->repair_cap != (inert ? 0 : repair_cap))
+        c->inert != inert || c->coupled != coupled || c->repair_cap != ((inert || coupled) ? 0 : repair_cap))
       return fail(TBR_ERR_INVALID_ARG,
-                  "context shape differs from this call (n, k, W, H, k_ckpt, capacity, inert, repair capacity)");
+                  "context shape differs from this call (n, k, W, H, k_ckpt, capacity, inert, coupling, "
+                  "repair capacity)");
     c->drift_tol = drift_tol;
     TBR_CUDA(ctx_forward(c, prog, opts->tau, opts->tau_min, out_rgb, st), "tbr_render_soft");
     return TBR_OK;
   }
   c = new tbr_ctx();
-  cudaError_t e = ctx_allocate(c, prog->n, prog->k, W, H, ck, cap, inert, drift_tol, repair_cap, st);
+  cudaError_t e = ctx_allocate(c, prog->n, prog->k, W, H, ck, cap, inert, drift_tol, repair_cap, st, coupled);
   if (e == cudaSuccess) e = ctx_forward(c, prog, opts->tau, opts->tau_min, out_rgb, st);
   if (e != cudaSuccess) {
     ctx_release(c);

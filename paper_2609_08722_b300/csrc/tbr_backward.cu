@@ -351,6 +351,7 @@ int backward_grid(int W, int H, int inert) {
 
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st) {
   if (a.n <= 0) return cudaSuccess;
+  if (a.coupled) return launch_backward_coupled(a, st);
   const bool repair = !a.inert && a.repair_list && a.repair_cap > 0;
   if (repair) {
     cudaError_t e = cudaMemsetAsync(a.repair_count, 0, sizeof(int), st);

@@ -13,6 +13,7 @@
 // replay adjoint of Sec. 5.2, plus the backward's reduction scratch.
 struct tbr_ctx {
   int n = 0, k = 0, W = 0, H = 0, ck = 32, cap = 64, inert = 0, grid = 0;
+  int coupled = 0;                    // 1: the program carries a coupling profile (Eq. coupling)
   float bg[3] = {0, 0, 0};
   float inv_tc = 1.0f;
   float* packed = nullptr;            // [n][kRec]
@@ -66,8 +67,9 @@ void dfree(T*& p, cudaStream_t st) {
 
 // Allocates every buffer of a context for n strokes, palette k, W x H pixels.
 // repair_cap pixels can have a drifting segment regenerated in FP64 (0: none).
+// coupled: the coupling variant's record and adjoint (no FP64 repair).
 cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap, int inert, float drift_tol,
-                         int repair_cap, cudaStream_t st);
+                         int repair_cap, cudaStream_t st, int coupled = 0);
 constexpr int kDefaultRepairCap = 256;
 void ctx_release(tbr_ctx* c);
 // Soft forward into an allocated context (resets its status words).

@@ -391,7 +391,11 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
 // them exactly on the exterior):
 //   sigma' - sigma = A_L(r) / (2L + pi (sigma + sigma')),
 //   cap to cap: phi - beta = (sigma' - sigma) L (pi/2 - beta) / (Q sigma').
-__device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh) {
+// COUPLED: the coupling variant's forward map (Eq. coupling), which adds
+// A_L(r) g(v) with v taken at x_{i-1} (v is kept, so it is the same at x_i).
+template <bool COUPLED = false>
+__device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Geo& q, float& ds, float& dh,
+                                          const float4 gp = make_float4(0.0f, 0.0f, 0.0f, 0.0f)) {
   if (g.L == 0.0f) {  // drop: radial map, delta = 0 (warp-uniform branch)
     q.sgs = sgn1(s); q.sgh = sgn1(h); q.so = s; q.ho = h;
     const float as = fabsf(s), ah = fabsf(h);
@@ -405,9 +409,11 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
       q.sb = 0.0f; q.cb = 1.0f; q.beta = 0.0f;
     }
     q.tn = q.sig * q.beta;
-    const float B = fmaf(q.sig, kPiF * q.sig, g.Ar);
+    float Ag = g.Ar;
+    if (COUPLED) Ag = fmaf(g.Ar, profile_gm1(2.0f * q.beta, gp), g.Ar);
+    const float B = fmaf(q.sig, kPiF * q.sig, Ag);
     q.sp = div_a(B, sqrt_a(kPiF * B));
-    const float dsp = div_a(g.Ar, kPiF * (q.sig + q.sp));
+    const float dsp = div_a(Ag, kPiF * (q.sig + q.sp));
     q.t = q.sp * q.beta;
     q.cap_i = q.cap_o;
     q.phi = q.beta; q.ud = q.sb; q.uh = q.cb;
@@ -431,11 +437,14 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
   } else {
     q.sig = ah; q.sb = 0.0f; q.cb = 1.0f; q.beta = 0.0f; q.tn = as;
   }
-  const float B = fmaf(q.sig, fmaf(kPiF, q.sig, g.twoL), g.Ar);
-  q.sp = div_a(B, g.L + sqrt_a(fmaf(kPiF, B, g.L2)));
-  const float dsp = div_a(g.Ar, fmaf(kPiF, q.sig + q.sp, g.twoL));
-  const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
+  const float Q = fmaf(kPiF, q.sig, g.L);
   const float iQ = Q > 0.0f ? rcp_a(Q) : 0.0f;
+  float Ag = g.Ar;
+  if (COUPLED) Ag = fmaf(g.Ar, profile_gm1(2.0f * kPiF * q.tn * iQ, gp), g.Ar);  // 4 pi v = 2 pi t / Q
+  const float B = fmaf(q.sig, fmaf(kPiF, q.sig, g.twoL), Ag);
+  q.sp = div_a(B, g.L + sqrt_a(fmaf(kPiF, B, g.L2)));
+  const float dsp = div_a(Ag, fmaf(kPiF, q.sig + q.sp, g.twoL));
+  const float Qp = fmaf(kPiF, q.sp, g.L);
   q.t = q.tn * (Qp * iQ);
   q.cap_i = q.t > g.hl;
   float dS, dH;
@@ -771,9 +780,12 @@ struct BwdArgs {
   int repair_cap = 0;           // <= kRepairMax
   float* corr = nullptr;        // [repair_cap][n][8] gradient corrections
   unsigned char* repair_first = nullptr;  // [P] per-pixel "queued" flags, zeroed by launch_backward
+  int coupled = 0;              // 1: the coupling variant (one pixel per thread, no repair)
 };
 constexpr int kRepairMax = 1024;  // largest repair list (sorted by one CTA)
 int backward_grid(int W, int H, int inert);  // CTAs of the persistent backward grid
+int backward_grid_coupled(int W, int H);     // the same for the coupling variant's adjoint
+cudaError_t launch_backward_coupled(const BwdArgs& a, cudaStream_t st);
 // Replay adjoint, then (with a repair list) the FP64 repair of the pixels whose
 // checkpoint drift exceeded drift_tol.
 cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st);

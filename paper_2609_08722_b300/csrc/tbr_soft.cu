@@ -84,7 +84,8 @@ cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
     if (ex) k_soft<kSoftCH, false, false, true, false, true><<<tiles, kTileThreads, 0, st>>>(a);
     else k_soft<kSoftCH, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
   } else if (a.transport == kTransportCoupled) {
-    if (ex) k_soft<kSoftCH, false, false, false, true, true><<<tiles, kTileThreads, 0, st>>>(a);
+    if (rec) k_soft<kSoftCH, true, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
+    else if (ex) k_soft<kSoftCH, false, false, false, true, true><<<tiles, kTileThreads, 0, st>>>(a);
     else k_soft<kSoftCH, false, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
   } else if (rec && a.inert) {
     k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);

@@ -61,8 +61,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
                                   float x0, float y0, const RecordView& rv, PixelState& st,
                                   unsigned long long* status, float exit_lt = -3.0e38f) {
   static_assert(!(DROPS && (RECORD || INERT)), "the sixteen-drop transport renders forward only");
-  static_assert(!(COUPLED && (RECORD || INERT || DROPS)),
-                "the coupling variant renders forward only, with the capsule transport");
+  static_assert(!(COUPLED && (INERT || DROPS)), "the coupling variant uses the capsule transport");
   static_assert(!(EXIT && RECORD), "the early exit applies to forward-only renders");
   st.xh = x0; st.yh = y0; st.xl = 0.0f; st.yl = 0.0f;
   st.lt = 0.0f; st.cnt = 0;

@@ -4,7 +4,8 @@ flow", Eq. coupling, Eq. profile) on the GPU against the FP64 oracle.
 Tolerances as for the capsule renderer: hard-render index bit-exact outside
 the band where the oracle's margin |sigma' - sigma_b(v)| < 1e-5 (a mismatch
 outside it only where the chain condition kappa * 6e-8 > 1e-5); soft render
-|R_gpu - R_oracle| <= 1e-4 per channel.  Profiles are seeded draws with
+|R_gpu - R_oracle| <= 1e-4 per channel; replay-adjoint gradients within 1e-3
+relative per parameter group of the oracle's stored-state adjoint.  Profiles are seeded draws with
 c_1 in [0, 0.4], |c_2| <= 0.15, |c_3| <= 0.1 (g >= 0.35), on the 50-stroke
 program (half drops), a long-stroke program and the 2000-stroke operating
 program.
@@ -19,7 +20,13 @@ from paper_2609_08722_b300 import inputs, tbr
 pytestmark = pytest.mark.gpu
 
 SOFT_TOL = 1e-4
+GRAD_TOL = 1e-3
 BAND = 1e-5
+GROUPS = ["cx", "cy", "theta", "length", "half_width", "logits", "palette"]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def coupled(p, seed, **kw):
@@ -138,7 +145,6 @@ def test_coupled_program_is_rejected_where_unsupported():
     dp = tbr.DeviceProgram.from_host(p)
     target = torch.zeros((32, 32, 3), device="cuda")
     calls = [
-        lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, record=True),
         lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, inert=True),
         lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, transport="drops"),
         lambda: tbr.render_hard(dp, 32, 32, transport="drops"),
@@ -150,3 +156,61 @@ def test_coupled_program_is_rejected_where_unsupported():
         with pytest.raises(tbr.TbrError) as ei:
             c()
         assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
+
+
+# --------------------------------------------------------------------------- replay adjoint under Phi_g
+
+@pytest.mark.parametrize("which,W,H,tau,tau_min", [("small", 128, 128, 0.0, 1 / 200), ("small", 96, 96, 0.3, 0.01),
+                                                   ("long", 75, 61, 0.0, 1 / 200)])
+def test_backward_coupled(which, W, H, tau, tau_min):
+    """The replay adjoint of the coupled soft render (Phi_g regeneration, local
+    Jacobians by dual numbers) against the oracle's stored-state adjoint."""
+    p = small_coupled() if which == "small" else long_coupled()
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, ctx = tbr.render_soft(dp, W, H, tau, tau_min, record=True)
+    fwd, _ = tbr.render_soft(dp, W, H, tau, tau_min)
+    assert torch.equal(rgb, fwd)  # recording does not change the render
+    cot = inputs.make_cotangent(405, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    st = ctx.status()
+    og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64))
+    errs = {k: rel(g[k].cpu().numpy().ravel(), og[k].ravel()) for k in GROUPS}
+    print(f"coupled adjoint {which} tau={tau}: " + ", ".join(f"{k} {e:.2e}" for k, e in errs.items())
+          + f"; records {st['records']}")
+    for k, e in errs.items():
+        assert e <= GRAD_TOL, k
+    assert st["overflow_pixels"] == 0
+    # the profile matters: the capsule map's gradients differ
+    plain = p.copy()
+    plain.coupling = None
+    op = oracle.soft_vjp(plain, W, H, tau, tau_min, cot.astype(np.float64))
+    assert rel(op["cx"].ravel(), og["cx"].ravel()) > 10 * GRAD_TOL
+
+
+def test_backward_coupled_operating_point_sampled():
+    """The 2000-stroke operating program at 1024^2 with seeded profiles, the
+    cotangent supported on 1024 sampled pixels."""
+    p = coupled(inputs.operating_program(), 403)
+    dp = tbr.DeviceProgram.from_host(p)
+    W = H = 1024
+    _, ctx = tbr.render_soft(dp, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, record=True)
+    pix = inputs.sample_pixels(43, W * H, 1024)
+    cot = inputs.make_cotangent(44, pix.size)
+    full = torch.zeros((H * W, 3), device="cuda")
+    full[torch.from_numpy(pix).cuda()] = torch.from_numpy(cot).cuda()
+    g = ctx.backward(full.view(H, W, 3))
+    og = oracle.soft_vjp(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), pix=pix)
+    for k in GROUPS:
+        e = rel(g[k].cpu().numpy().ravel(), og[k].ravel())
+        print(f"coupled adjoint op {k}: {e:.3e}")
+        assert e <= GRAD_TOL, k
+
+
+def test_coupled_context_is_not_reused_for_the_capsule_map():
+    p = small_coupled()
+    _, ctx = tbr.render_soft(tbr.DeviceProgram.from_host(p), 32, 32, 0.0, 1 / 200, record=True)
+    plain = p.copy()
+    plain.coupling = None
+    with pytest.raises(tbr.TbrError) as ei:
+        tbr.render_soft(tbr.DeviceProgram.from_host(plain), 32, 32, 0.0, 1 / 200, reuse=ctx)
+    assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
