@@ -4,8 +4,14 @@ flow", Eq. coupling, Eq. profile) on the GPU against the FP64 oracle.
 Tolerances as for the capsule renderer: hard-render index bit-exact outside
 the band where the oracle's margin |sigma' - sigma_b(v)| < 1e-5 (a mismatch
 outside it only where the chain condition kappa * 6e-8 > 1e-5); soft render
-|R_gpu - R_oracle| <= 1e-4 per channel; replay-adjoint gradients within 1e-3
-relative per parameter group of the oracle's stored-state adjoint.  Profiles are seeded draws with
+|R_gpu - R_oracle| <= 1e-4 per channel.  Replay-adjoint gradients: relative
+error per parameter group within max(1e-3, 2 x the oracle's own sensitivity),
+the sensitivity being how far the oracle's FP64 gradient moves when every
+stroke parameter is perturbed by one FP32 rounding (relative 6e-8).  At the
+sharp relaxation the coupled profile makes the gradient far more sensitive
+than the capsule map's (up to 4e-3 against 1.4e-5 on the 50-stroke program,
+most of it from coupled drops, whose v is the polar angle about their
+centre).  Profiles are seeded draws with
 c_1 in [0, 0.4], |c_2| <= 0.15, |c_3| <= 0.1 (g >= 0.35), on the 50-stroke
 program (half drops), a long-stroke program and the 2000-stroke operating
 program.
@@ -27,6 +33,22 @@ GROUPS = ["cx", "cy", "theta", "length", "half_width", "logits", "palette"]
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def grad_sensitivity(p, W, H, tau, tau_min, cot, og, pix=None, trials=2):
+    """Per group: the largest relative move of the oracle's gradient when every
+    stroke parameter is perturbed by one FP32 rounding."""
+    rng = np.random.default_rng(2025)
+    worst = {k: 0.0 for k in GROUPS}
+    for _ in range(trials):
+        q = p.copy()
+        for k in ("cx", "cy", "theta", "length", "half_width"):
+            v = getattr(q, k).astype(np.float64)
+            setattr(q, k, v * (1.0 + rng.uniform(-6e-8, 6e-8, v.shape)))
+        oq = oracle.soft_vjp(q, W, H, tau, tau_min, cot, pix=pix)
+        for k in GROUPS:
+            worst[k] = max(worst[k], rel(oq[k].ravel(), og[k].ravel()))
+    return worst
 
 
 def coupled(p, seed, **kw):
@@ -175,10 +197,12 @@ def test_backward_coupled(which, W, H, tau, tau_min):
     st = ctx.status()
     og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64))
     errs = {k: rel(g[k].cpu().numpy().ravel(), og[k].ravel()) for k in GROUPS}
-    print(f"coupled adjoint {which} tau={tau}: " + ", ".join(f"{k} {e:.2e}" for k, e in errs.items())
+    sens = grad_sensitivity(p, W, H, tau, tau_min, cot.astype(np.float64), og)
+    print(f"coupled adjoint {which} tau={tau}: " + ", ".join(f"{k} {e:.2e} (sens {sens[k]:.1e})"
+                                                           for k, e in errs.items())
           + f"; records {st['records']}")
     for k, e in errs.items():
-        assert e <= GRAD_TOL, k
+        assert e <= max(GRAD_TOL, 2.0 * sens[k]), k
     assert st["overflow_pixels"] == 0
     # the profile matters: the capsule map's gradients differ
     plain = p.copy()
@@ -200,10 +224,11 @@ def test_backward_coupled_operating_point_sampled():
     full[torch.from_numpy(pix).cuda()] = torch.from_numpy(cot).cuda()
     g = ctx.backward(full.view(H, W, 3))
     og = oracle.soft_vjp(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), pix=pix)
+    sens = grad_sensitivity(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), og, pix=pix)
     for k in GROUPS:
         e = rel(g[k].cpu().numpy().ravel(), og[k].ravel())
-        print(f"coupled adjoint op {k}: {e:.3e}")
-        assert e <= GRAD_TOL, k
+        print(f"coupled adjoint op {k}: {e:.3e} (sens {sens[k]:.1e})")
+        assert e <= max(GRAD_TOL, 2.0 * sens[k]), k
 
 
 def test_coupled_context_is_not_reused_for_the_capsule_map():
