@@ -84,10 +84,12 @@ typedef struct {
                                (checked exactly; else the stroke fails the value
                                checks).  Supported by the hard render, the soft
                                render (capsule transport, not inert) with or
-                               without a replay context, and its replay adjoint
+                               without a replay context, its replay adjoint
                                (tbr_render_backward; local Jacobians by dual
-                               numbers, no FP64 repair); the other entry points
-                               reject a non-NULL coupling. */
+                               numbers, no FP64 repair), the loss-fused call and
+                               the fit (which keeps the profile fixed); the
+                               serving and compensation entry points reject a
+                               non-NULL coupling. */
 } tbr_program;
 
 /* Transport of a render: the paper's capsule insertion map psi (Eq. back), or

@@ -26,6 +26,7 @@ struct tbr_fit {
   float* target = nullptr;   // [P][3]
   float* scal = nullptr;     // [2]: MSE, sum of lengths
   float* host = nullptr;     // pinned [2]
+  float* coupling = nullptr; // [n][3] the coupling variant's fixed profile, or NULL (capsule map)
   tbr::FusedWork work;       // loss-fused forward + replay adjoint buffers
   cudaStream_t last_stream = nullptr;
 };
@@ -98,6 +99,7 @@ tbr_program view_of(const tbr_fit* f, float color_temp) {
   p.palette = f->params + 5 * n + n * f->k;
   for (int c = 0; c < 3; ++c) p.background[c] = f->bg[c];
   p.color_temp = color_temp;
+  p.coupling = f->coupling;
   return p;
 }
 
@@ -109,7 +111,7 @@ float geometric(float a, float b, int t, int T) {
 void fit_free(tbr_fit* f, cudaStream_t st) {
   f->work.release(st);
   dfree(f->params, st); dfree(f->grads, st); dfree(f->m, st); dfree(f->v, st);
-  dfree(f->rlo, st); dfree(f->rhi, st); dfree(f->target, st); dfree(f->scal, st);
+  dfree(f->rlo, st); dfree(f->rhi, st); dfree(f->target, st); dfree(f->scal, st); dfree(f->coupling, st);
   if (f->host) cudaFreeHost(f->host);
   f->host = nullptr;
 }
@@ -144,7 +146,6 @@ tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t 
   *out = nullptr;
   tbr_status s = check_program(init, init ? init->n : 0);
   if (s != TBR_OK) return s;
-  if (init->coupling) return fail(TBR_ERR_INVALID_ARG, "the fit trains the capsule map (coupling must be NULL)");
   if ((s = check_size(W, H)) != TBR_OK) return s;
   if (!target) return fail(TBR_ERR_INVALID_ARG, "target is NULL");
   tbr_fit_config c;
@@ -173,7 +174,14 @@ tbr_status tbr_fit_create(const tbr_program* init, const float* target, int32_t 
   if (e == cudaSuccess) e = dalloc(&f->target, 3 * P, st);
   if (e == cudaSuccess) e = dalloc(&f->scal, 2, st);
   if (e == cudaSuccess) e = cudaMallocHost(reinterpret_cast<void**>(&f->host), 2 * sizeof(float));
-  if (e == cudaSuccess) e = f->work.allocate(f->n, f->k, W, H, c.checkpoint_every, c.record_capacity, st);
+  if (e == cudaSuccess && init->coupling && n > 0) {
+    // the profile is an input of the program, kept fixed while the fit trains the rest
+    e = dalloc(&f->coupling, 3 * n, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->coupling, init->coupling, 3 * n * 4, cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess)
+    e = f->work.allocate(f->n, f->k, W, H, c.checkpoint_every, c.record_capacity, st, kDriftTol, kDefaultRepairCap,
+                         f->coupling ? 1 : 0);
   const float* src[5] = {init->cx, init->cy, init->theta, init->length, init->half_width};
   for (int g = 0; g < 5 && e == cudaSuccess && n > 0; ++g)
     e = cudaMemcpyAsync(f->params + g * n, src[g], n * 4, cudaMemcpyDeviceToDevice, st);
@@ -241,7 +249,9 @@ tbr_status tbr_fit_step(tbr_fit* f, float* loss_out, void* stream) {
       // the update was skipped on the device; grow the side table and redo the step
       const int cap = f->work.cap * 2;
       f->work.release(st);
-      TBR_CUDA(f->work.allocate(f->n, f->k, f->W, f->H, c.checkpoint_every, cap, st), "fit: growing the side table");
+      TBR_CUDA(f->work.allocate(f->n, f->k, f->W, f->H, c.checkpoint_every, cap, st, kDriftTol, kDefaultRepairCap,
+                                f->coupling ? 1 : 0),
+               "fit: growing the side table");
       continue;
     }
     if (host[ST_INVALID]) return fail(TBR_ERR_INVALID_ARG, "%llu strokes failed the value checks", host[ST_INVALID]);

@@ -19,8 +19,8 @@ namespace tbr {
 // Work buffers of the fused path (also held by a fit across steps).
 // ---------------------------------------------------------------------------
 cudaError_t FusedWork::allocate(int n, int k, int W, int H, int ck_, int cap_, cudaStream_t st, float drift_tol,
-                                int repair_cap) {
-  cudaError_t e = ctx_allocate(&ctx, n, k, W, H, ck_, cap_, 0, drift_tol, repair_cap, st);
+                                int repair_cap, int coupled) {
+  cudaError_t e = ctx_allocate(&ctx, n, k, W, H, ck_, cap_, 0, drift_tol, repair_cap, st, coupled);
   const int64_t P = static_cast<int64_t>(W) * H;
   nblk = loss_blocks(P);
   if (e == cudaSuccess) e = dalloc(&rgb, static_cast<size_t>(P) * 3, st);
@@ -63,7 +63,6 @@ tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32
                                        float* g_logits, float* g_palette, tbr_ctx_stats* stats, void* stream) {
   tbr_status s = check_program(prog, prog ? prog->n : 0);
   if (s != TBR_OK) return s;
-  if (prog->coupling) return fail(TBR_ERR_INVALID_ARG, "the adjoint differentiates the capsule map (coupling must be NULL)");
   if ((s = check_size(W, H)) != TBR_OK) return s;
   if (!opts || !target) return fail(TBR_ERR_INVALID_ARG, "opts or target is NULL");
   if (!(opts->tau >= 0.0f) || !(opts->tau_min > 0.0f)) return fail(TBR_ERR_INVALID_ARG, "need tau >= 0, tau_min > 0");
@@ -81,7 +80,8 @@ tbr_status tbr_render_soft_adjoint_mse(const tbr_program* prog, int32_t W, int32
   cudaError_t e = w.allocate(prog->n, prog->k, W, H, opts->checkpoint_every > 0 ? opts->checkpoint_every : 64,
                              opts->record_capacity > 0 ? opts->record_capacity : 64, st,
                              opts->drift_tolerance > 0.0f ? opts->drift_tolerance : kDriftTol,
-                             opts->repair_capacity > 0 ? opts->repair_capacity : kDefaultRepairCap);
+                             opts->repair_capacity > 0 ? opts->repair_capacity : kDefaultRepairCap,
+                             prog->coupling ? 1 : 0);
   if (e == cudaSuccess)
     e = w.run(prog, opts->tau, opts->tau_min, target, out_rgb, loss_out, g_cx, g_cy, g_theta, g_length,
               g_half_width, g_logits, g_palette, st);

@@ -92,8 +92,9 @@ struct FusedWork {
   unsigned long long* status = nullptr;  // the context's status words
   int nblk = 0, cap = 0;
   size_t bytes = 0;
+  // coupled: the program carries a coupling profile (its record and adjoint)
   cudaError_t allocate(int n, int k, int W, int H, int ck, int cap, cudaStream_t st, float drift_tol = 1e-5f,
-                       int repair_cap = kDefaultRepairCap);
+                       int repair_cap = kDefaultRepairCap, int coupled = 0);
   void release(cudaStream_t st);
   // pack + soft forward + MSE and seed + replay adjoint + gradient epilogue;
   // status words reset first.

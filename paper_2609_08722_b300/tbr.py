@@ -423,10 +423,13 @@ class Fit:
         total = 5 * n + n * k + 3 * k
         buf = torch.as_tensor(_DeviceArray(v.cx, total), device=self.device)
         sl = lambda a, b: buf[a:b].clone()
+        cpl = None
+        if v.coupling:  # the fixed coupling profile, [n, 3]
+            cpl = torch.as_tensor(_DeviceArray(v.coupling, 3 * n), device=self.device).clone().view(n, 3)
         return DeviceProgram(cx=sl(0, n), cy=sl(n, 2 * n), theta=sl(2 * n, 3 * n), length=sl(3 * n, 4 * n),
                              half_width=sl(4 * n, 5 * n), logits=sl(5 * n, 5 * n + n * k).view(n, k),
                              palette=sl(5 * n + n * k, total).view(k, 3),
-                             background=tuple(v.background), color_temp=float(v.color_temp))
+                             background=tuple(v.background), color_temp=float(v.color_temp), coupling=cpl)
 
     def destroy(self):
         if self.handle is not None:

@@ -170,9 +170,7 @@ def test_coupled_program_is_rejected_where_unsupported():
         lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, inert=True),
         lambda: tbr.render_soft(dp, 32, 32, 0.0, 1 / 200, transport="drops"),
         lambda: tbr.render_hard(dp, 32, 32, transport="drops"),
-        lambda: tbr.soft_adjoint_mse(dp, target, 0.0, 1 / 200),
         lambda: tbr.compensate(dp),
-        lambda: tbr.Fit(dp, target, tbr.default_fit_config(iterations=2)),
     ]
     for c in calls:
         with pytest.raises(tbr.TbrError) as ei:
@@ -239,3 +237,51 @@ def test_coupled_context_is_not_reused_for_the_capsule_map():
     with pytest.raises(tbr.TbrError) as ei:
         tbr.render_soft(tbr.DeviceProgram.from_host(plain), 32, 32, 0.0, 1 / 200, reuse=ctx)
     assert ei.value.status == tbr.TBR_ERR_INVALID_ARG
+
+
+def test_loss_fused_call_under_the_coupling():
+    """The loss-fused call (pack, record, MSE seed, adjoint) gives the split
+    path's loss and gradients for a coupled program."""
+    p = small_coupled()
+    dp = tbr.DeviceProgram.from_host(p)
+    W = H = 96
+    target, _, _ = tbr.render_hard(tbr.DeviceProgram.from_host(inputs.make_program(
+        50, seed=406, palette_seed=201, k=8, r_lo=0.01, r_hi=0.08)), W, H)
+    loss_f, g_f, rgb_f, _ = tbr.soft_adjoint_mse(dp, target, 0.0, 1 / 200, want_rgb=True)
+    rgb_s, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=64)
+    loss_s, dL = tbr.loss_mse(rgb_s, target)
+    g_s = ctx.backward(dL)
+    assert torch.equal(rgb_f, rgb_s)
+    assert abs(loss_f.item() - loss_s.item()) <= 1e-6 * loss_s.item()
+    for k in GROUPS:
+        assert rel(g_f[k].cpu().numpy().ravel(), g_s[k].cpu().numpy().ravel()) <= 1e-5, k
+
+
+def test_fit_under_the_coupling():
+    """A short fit of a coupled program: the loss falls, the profile stays as
+    given, and the final FP32 soft loss agrees with the FP64 oracle's."""
+    init = coupled(inputs.make_program(60, seed=901, palette_seed=903, k=8, r_lo=0.01, r_hi=0.06), 407)
+    targ = inputs.make_program(60, seed=902, palette_seed=903, k=8, r_lo=0.01, r_hi=0.06)
+    W = H = 96
+    target, _, _ = tbr.render_hard(tbr.DeviceProgram.from_host(targ), W, H)
+    cfg = tbr.default_fit_config(iterations=30)
+    fit = tbr.Fit(tbr.DeviceProgram.from_host(init), target, cfg)
+    losses = [fit.step() for _ in range(30)]
+    prog = fit.program()
+    fit.destroy()
+    print(f"coupled fit loss {losses[0]:.5f} -> {losses[-1]:.5f}")
+    assert losses[-1] < 0.9 * losses[0]
+    assert np.array_equal(prog.coupling.cpu().numpy(), init.coupling)
+    tau, tc = cfg.tau_end, cfg.color_temp_end  # the schedule's values at the last step
+    a = lambda t: t.detach().cpu().numpy().astype(np.float32).copy()
+    final = inputs.Program(cx=a(prog.cx), cy=a(prog.cy), theta=a(prog.theta), length=a(prog.length),
+                           half_width=a(prog.half_width), logits=a(prog.logits), palette=a(prog.palette),
+                           background=np.asarray(prog.background, np.float32), color_temp=tc,
+                           coupling=a(prog.coupling))
+    tau_min = 0.7 / max(W, H)
+    rgb, _ = tbr.render_soft(tbr.DeviceProgram.from_host(final), W, H, tau, tau_min)
+    loss_gpu, _ = tbr.loss_mse(rgb, target, want_grad=False)
+    o = oracle.render_soft(final, W, H, tau, tau_min)
+    loss_o = float(np.mean((o["rgb"] - target.double().cpu().numpy().reshape(-1, 3)) ** 2))
+    print(f"final coupled loss gpu {loss_gpu.item():.8f} oracle {loss_o:.8f}")
+    assert abs(loss_gpu.item() - loss_o) <= 1e-4 * loss_o
