@@ -17,7 +17,10 @@ Functions (all FP64, citing the paper's passages in the C++ source):
   * ``soft_jvp``                 -- forward-mode derivative of the soft render;
   * ``soft_vjp``                 -- stored-state adjoint (Eq. adjstep, Eq. adjparam);
   * ``fd_gradient``              -- central finite differences of a linear
-                                    functional of the soft render.
+                                    functional of the soft render;
+  * ``count_ops``                -- operation counts per pixel-stroke of the
+                                    hard render, the soft render and the
+                                    replay adjoint (measurement only).
 
 A program is any object with attributes ``cx, cy, theta, length, half_width``
 ([n]), ``logits`` ([n, k]), ``palette`` ([k, 3]), ``background`` ([3]) and
@@ -90,6 +93,8 @@ def _load():
             lib.orc_map_coupled.restype = ctypes.c_int
             lib.orc_profile_min.argtypes = [dbl, dbl, dbl]
             lib.orc_profile_min.restype = dbl
+            lib.orc_count_ops.argtypes = [P, ctypes.c_int, ctypes.c_int, dbl, dbl, ctypes.c_int, P, i64, P]
+            lib.orc_count_ops.restype = ctypes.c_int
             lib.orc_num_threads.restype = ctypes.c_int
             for f in ("orc_map", "orc_map_jacobian", "orc_render_hard", "orc_render_soft",
                       "orc_soft_jvp", "orc_soft_vjp"):
@@ -338,3 +343,30 @@ def fd_gradient(prog, W, H, tau, tau_min, cot, params, h_geo=1e-6, h_logit=1e-5,
         else:
             out.append((J(perturbed(j, q, h)) - J(perturbed(j, q, -h))) / (2 * h))
     return np.array(out)
+
+
+def count_ops(prog, W, H, tau, tau_min, pix=None, transport="capsule"):
+    """Tallied operations per unit (see ``orc_count_ops``): a dict with
+    ``hard`` per visited step of the hard render, ``soft`` per pixel-stroke of
+    the soft render and, for the capsule map (with or without a coupling
+    profile), ``adjoint`` per pixel-stroke of the replay adjoint with its
+    parts; each as FP32-pipe and XU operation counts, plus the unit totals.
+    transport: "capsule" or "drops" (R_D, forward only)."""
+    pk = _Packed(prog)
+    pix, m = _pixels(W, H, pix)
+    out = np.zeros(14)
+    t = TRANSPORTS[transport]
+    if _load().orc_count_ops(pk.ref, W, H, float(tau), float(tau_min), t, _ptr(pix), m, _ptr(out)) != 0:
+        raise ValueError("operation counts cover the capsule map (optionally coupled) and R_D")
+    steps, ps = out[0], out[3]
+    res = {
+        "hard": {"fp32": out[1] / steps, "xu": out[2] / steps, "visited_steps": steps, "pixels": m},
+        "soft": {"fp32": out[4] / ps, "xu": out[5] / ps, "pixel_strokes": ps},
+    }
+    if transport == "capsule":
+        parts = {"regeneration": (out[6], out[7]), "coverage": (out[8], out[9]),
+                 "reverse_sweep": (out[10], out[11]), "scalar_step": (out[12], out[13])}
+        adj = {k: {"fp32": f / ps, "xu": x / ps} for k, (f, x) in parts.items()}
+        res["adjoint"] = {"fp32": sum(v["fp32"] for v in adj.values()), "xu": sum(v["xu"] for v in adj.values()),
+                          "parts": adj, "pixel_strokes": ps}
+    return res

@@ -131,6 +131,128 @@ template <int D> inline Dual<D> atan2(const Dual<D>& y, const Dual<D>& x) {
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// Operation counting (measurement only: no render calls it).  Ops carries a
+// value and two flags: px, the value depends on the pixel's state, and act, it
+// depends on the pixel's state or on a stroke parameter.  Only an operation
+// whose result depends on the pixel is per pixel-stroke work; one on stroke
+// parameters and constants alone can be hoisted out of the pixel loop and is
+// not tallied.  Tallies are FP32-pipe operations (an add, subtract or multiply
+// is one; this file writes no fused multiply-add, so a*b + c is two, the FLOP
+// count) and special-function (XU) operations, as they run when the same
+// formula is evaluated for one pixel-stroke:
+//   forward:  +, -, *: 1.  a / b: 1 when b is per-stroke (a multiply by its
+//             hoisted reciprocal), else a reciprocal (1 XU) and a multiply (1;
+//             none when a is the constant 1).  sqrt, sin, cos, atan2: 1 XU.
+//             exp and log1p: 1 XU + 1 (base-2 form).  Negation, fabs and
+//             comparisons: 0.
+//   reverse:  what a reverse sweep over the same operation costs, tallied as
+//             the forward runs: the local partial times the result's adjoint
+//             for each active operand -- a * b: 1 multiply per active operand;
+//             a / b: 1 (adjoint times the reciprocal) + 1 when b is active;
+//             sqrt: 1 XU + 2; sin, cos: 1 XU + 1; exp: 1; log1p: 1 XU + 1;
+//             atan2: 1 XU + 4 + 1 per active operand; +, -, negation, fabs:
+//             0 -- plus the additions that sum an adjoint's contributions:
+//             (uses - 1) for a pixel-dependent value, and one per use for a
+//             per-stroke active value (its adjoint is summed over pixels
+//             before it is chained to the stroke's parameters).
+// The per-thread node table below records each active value's uses.
+// ---------------------------------------------------------------------------
+struct OpTally {
+  double f = 0.0, x = 0.0;     // forward FP32, XU
+  double rf = 0.0, rx = 0.0;   // reverse contributions FP32, XU
+  std::vector<unsigned char> px;
+  std::vector<int> uses;
+  void reset() { f = x = rf = rx = 0.0; px.clear(); uses.clear(); }
+  int add_node(bool p) { px.push_back(p ? 1 : 0); uses.push_back(0); return (int)px.size() - 1; }
+  // additions that sum the adjoint contributions of every recorded value
+  double accumulation_adds() const {
+    double a = 0.0;
+    for (size_t i = 0; i < px.size(); ++i) a += px[i] ? std::max(0, uses[i] - 1) : uses[i];
+    return a;
+  }
+};
+static thread_local OpTally g_tally;
+
+struct Ops {
+  double v = 0.0;
+  bool px = false, act = false;
+  int id = -1;
+  Ops() {}
+  Ops(double x) : v(x) {}  // NOLINT: a constant
+  static Ops leaf(double x, bool pixel) {
+    Ops r(x);
+    r.px = pixel; r.act = true; r.id = g_tally.add_node(pixel);
+    return r;
+  }
+};
+inline double value(const Ops& a) { return a.v; }
+
+inline Ops ops_result(double v, const Ops& a, const Ops& b) {
+  Ops r(v);
+  r.px = a.px || b.px;
+  r.act = a.act || b.act;
+  if (r.act) r.id = g_tally.add_node(r.px);
+  return r;
+}
+inline void ops_use(const Ops& a) { if (a.act && a.id >= 0) g_tally.uses[a.id] += 1; }
+
+inline Ops operator+(const Ops& a, const Ops& b) {
+  Ops r = ops_result(a.v + b.v, a, b);
+  if (r.px) { g_tally.f += 1; ops_use(a); ops_use(b); }
+  return r;
+}
+inline Ops operator-(const Ops& a, const Ops& b) {
+  Ops r = ops_result(a.v - b.v, a, b);
+  if (r.px) { g_tally.f += 1; ops_use(a); ops_use(b); }
+  return r;
+}
+inline Ops operator-(const Ops& a) {
+  Ops r = ops_result(-a.v, a, Ops());
+  if (r.px) ops_use(a);
+  return r;
+}
+inline Ops operator*(const Ops& a, const Ops& b) {
+  Ops r = ops_result(a.v * b.v, a, b);
+  if (r.px) {
+    g_tally.f += 1;
+    if (a.act) { g_tally.rf += 1; ops_use(a); }
+    if (b.act) { g_tally.rf += 1; ops_use(b); }
+  }
+  return r;
+}
+inline Ops operator/(const Ops& a, const Ops& b) {
+  Ops r = ops_result(a.v / b.v, a, b);
+  if (r.px) {
+    if (!b.px) g_tally.f += 1;
+    else { g_tally.x += 1; if (a.act || std::fabs(a.v) != 1.0) g_tally.f += 1; }
+    g_tally.rf += 1 + (b.act ? 1 : 0);
+    ops_use(a); ops_use(b);
+  }
+  return r;
+}
+inline Ops ops_unary(double v, const Ops& a, double ff, double fx, double rf, double rx) {
+  Ops r = ops_result(v, a, Ops());
+  if (r.px) { g_tally.f += ff; g_tally.x += fx; g_tally.rf += rf; g_tally.rx += rx; ops_use(a); }
+  return r;
+}
+inline Ops sqrt(const Ops& a) { return ops_unary(std::sqrt(a.v), a, 0, 1, 2, 1); }
+inline Ops sin(const Ops& a) { return ops_unary(std::sin(a.v), a, 0, 1, 1, 1); }
+inline Ops cos(const Ops& a) { return ops_unary(std::cos(a.v), a, 0, 1, 1, 1); }
+inline Ops exp(const Ops& a) { return ops_unary(std::exp(a.v), a, 1, 1, 1, 0); }
+inline Ops log1p(const Ops& a) { return ops_unary(std::log1p(a.v), a, 1, 1, 1, 1); }
+inline Ops fabs(const Ops& a) { return ops_unary(std::fabs(a.v), a, 0, 0, 0, 0); }
+inline Ops atan2(const Ops& y, const Ops& x) {
+  Ops r = ops_result(std::atan2(y.v, x.v), y, x);
+  if (r.px) {
+    g_tally.x += 1;
+    g_tally.rx += 1;
+    g_tally.rf += 4 + (y.act ? 1 : 0) + (x.act ? 1 : 0);
+    ops_use(y); ops_use(x);
+  }
+  return r;
+}
+
 using std::sqrt; using std::sin; using std::cos; using std::exp; using std::log1p;
 using std::fabs; using std::atan2;
 
@@ -286,10 +408,20 @@ void keep_tangential(const T& s, const T& h, const T& sig_from, const T& sig_to,
 // chain") or floored at (eps r)^2 (the implemented map, Sec. 5.2).
 // Returns 1 if the floor bound (a side-table record), else 0.
 template <class T>
+int psi_from_frame(const T& s, const T& h, const T& sp, const Stroke<T>& g, int mode, T& x_out, T& y_out);
+
+template <class T>
 int psi(const T& x, const T& y, const Stroke<T>& g, int mode, T& x_out, T& y_out) {
   T s, h;
   to_frame(x, y, g, s, h);
   T sp = segment_distance(s, h, g.L);
+  return psi_from_frame(s, h, sp, g, mode, x_out, y_out);
+}
+
+// The part of psi after the frame coordinates (s, h) and the distance sp of
+// the point have been computed (shared with the coverage of the same point).
+template <class T>
+int psi_from_frame(const T& s, const T& h, const T& sp, const Stroke<T>& g, int mode, T& x_out, T& y_out) {
   T C = (sp - g.r) * (2.0 * g.L + kPi * (sp + g.r));
   if (coupled(g))  // Eq. coupling: subtract A_L(r) g(v) instead of A_L(r)
     C = C - (2.0 * g.L * g.r + kPi * g.r * g.r) * profile_m1(g, centred_v(s, h, sp, g.L));
@@ -940,6 +1072,130 @@ double orc_profile_min(double c1, double c2, double c3) {
     }
   }
   return m;
+}
+
+// Operation counts per pixel-stroke (the tallies of the Ops scalar above;
+// measurement only).  transport: 0 the capsule map (with the coupling profile
+// when the program carries one), 2 the sixteen-drop operator of R_D (hard and
+// soft render only: the paper uses R_D forward only).  For each listed pixel:
+//   hard:     every visited step of Eq. chain (frame, distance, membership,
+//             and psi with the ideal clamp when the point passes on);
+//   soft:     every step of the soft render (frame, distance, Eq. relax
+//             coverage, Eq. state compositing as written in soft_pixel, psi
+//             with the floor);
+//   adjoint:  every step of the replay adjoint of Sec. 5.2 in program order:
+//             regeneration x_i = Phi_i(x_{i-1}) (Eq. rpos), the frame, distance
+//             and coverage of x_i, the reverse sweep through psi_i and alpha_i
+//             (psi's own forward is not tallied: its intermediates are Phi's),
+//             and the scalar lines of Eq. rT / Eq. adjstep as the stored-state
+//             adjoint writes them (T_i = T_{i-1} / (1 - alpha_i); lambda_C . c_i;
+//             mu; the colour gradient; lambda_T).
+// out[0..2]  hard: visited steps, FP32, XU (totals)
+// out[3..5]  soft: pixel-strokes, FP32, XU
+// out[6..7]  adjoint regeneration FP32, XU
+// out[8..9]  adjoint coverage FP32, XU
+// out[10..11] adjoint reverse sweep FP32 (contributions + accumulation adds), XU
+// out[12..13] adjoint scalar step FP32, XU
+int orc_count_ops(const orc_prog* p, int W, int H, double tau, double tau_min, int transport, const int64_t* pix,
+                  int64_t npix, double* out) {
+  if (transport != kCapsule && transport != kDrops16) return -1;
+  if (transport == kDrops16 && p->coupling) return -1;
+  const int n = p->n;
+  std::vector<double> col, prob;
+  stroke_colours(p, 0, col, prob);
+  double tot[14] = {0};
+  #pragma omp parallel
+  {
+    double my[14] = {0};
+    std::vector<double> xs(n), ys(n);
+    #pragma omp for schedule(dynamic, 16)
+    for (int64_t q = 0; q < npix; ++q) {
+      int64_t pidx = pix ? pix[q] : q;
+      double px0, py0;
+      pixel_centre(pidx, W, H, px0, py0);
+      auto stroke_ops = [&](int j) {
+        Stroke<Ops> g;
+        g.cx = Ops::leaf(p->cx[j], false); g.cy = Ops::leaf(p->cy[j], false);
+        g.th = Ops::leaf(p->th[j], false); g.L = Ops::leaf(p->L[j], false); g.r = Ops::leaf(p->r[j], false);
+        if (p->coupling) {
+          g.c1 = p->coupling[3 * j]; g.c2 = p->coupling[3 * j + 1]; g.c3 = p->coupling[3 * j + 2];
+        }
+        return g;
+      };
+      // the pull-back of one step from the frame quantities already computed
+      auto pull_back = [&](const Ops& X, const Ops& Y, const Ops& s, const Ops& h, const Ops& sp,
+                           const Stroke<Ops>& g, int mode, Ops& xo, Ops& yo) {
+        if (transport == kDrops16) psi_drops(X, Y, g, xo, yo);
+        else psi_from_frame(s, h, sp, g, mode, xo, yo);
+      };
+      // hard render
+      double x = px0, y = py0;
+      for (int j = n - 1; j >= 0; --j) {
+        g_tally.reset();
+        Stroke<Ops> g = stroke_ops(j);
+        Ops X = Ops::leaf(x, true), Y = Ops::leaf(y, true), s, h, xo, yo;
+        to_frame(X, Y, g, s, h);
+        Ops sp = segment_distance(s, h, g.L);
+        Ops m = deposit_margin(s, h, sp, g);
+        my[0] += 1;
+        if (value(m) <= 0.0) { my[1] += g_tally.f; my[2] += g_tally.x; break; }
+        pull_back(X, Y, s, h, sp, g, kClamp, xo, yo);
+        my[1] += g_tally.f; my[2] += g_tally.x;
+        x = value(xo); y = value(yo);
+      }
+      // soft render, storing the position at which each stroke is evaluated
+      x = px0; y = py0;
+      double Tv = 1.0;
+      for (int j = n - 1; j >= 0; --j) {
+        xs[j] = x; ys[j] = y;
+        g_tally.reset();
+        Stroke<Ops> g = stroke_ops(j);
+        Ops X = Ops::leaf(x, true), Y = Ops::leaf(y, true), s, h, xo, yo;
+        Ops Tr = Ops::leaf(Tv, true);
+        Ops C[3] = {Ops::leaf(0.1, true), Ops::leaf(0.2, true), Ops::leaf(0.3, true)};
+        to_frame(X, Y, g, s, h);
+        Ops sp = segment_distance(s, h, g.L);
+        Ops a = soft_coverage(deposit_margin(s, h, sp, g), g.r, tau, tau_min);
+        for (int c = 0; c < 3; ++c) C[c] = C[c] + Tr * a * Ops::leaf(col[(size_t)j * 3 + c], false);
+        Tr = Tr * (1.0 - a);
+        pull_back(X, Y, s, h, sp, g, kFloor, xo, yo);
+        my[3] += 1; my[4] += g_tally.f; my[5] += g_tally.x;
+        x = value(xo); y = value(yo); Tv = value(Tr);
+      }
+      // replay adjoint, program order; x is now the pulled-back point x_0
+      for (int j = 0; j < n && transport == kCapsule; ++j) {
+        // regeneration of x_j from the point below it
+        g_tally.reset();
+        {
+          Stroke<Ops> g = stroke_ops(j);
+          Ops X = Ops::leaf(x, true), Y = Ops::leaf(y, true), xo, yo;
+          phi(X, Y, g, false, xo, yo);
+        }
+        my[6] += g_tally.f; my[7] += g_tally.x;
+        // coverage of x_j, then the reverse sweep through psi_j and alpha_j
+        g_tally.reset();
+        Stroke<Ops> g = stroke_ops(j);
+        Ops X = Ops::leaf(xs[j], true), Y = Ops::leaf(ys[j], true), s, h, xo, yo;
+        to_frame(X, Y, g, s, h);
+        Ops sp = segment_distance(s, h, g.L);
+        Ops a = soft_coverage(deposit_margin(s, h, sp, g), g.r, tau, tau_min);
+        my[8] += g_tally.f; my[9] += g_tally.x;
+        psi_from_frame(s, h, sp, g, kFloor, xo, yo);
+        ops_use(xo); ops_use(yo); ops_use(a);  // the seeds lambda_x and mu
+        my[10] += g_tally.rf + g_tally.accumulation_adds(); my[11] += g_tally.rx;
+        // T_i = T_{i-1} / (1 - alpha_i): 1 + a reciprocal + 1; lambda_C . c_i: 5;
+        // mu = T_i (lambda_C . c_i - lambda_T): 2; colour gradient
+        // g_c += lambda_C T_i alpha_i: 3 x 3; lambda_T = (1 - alpha) lambda_T +
+        // alpha (lambda_C . c_i): 4
+        my[12] += 2 + 5 + 2 + 9 + 4; my[13] += 1;
+        x = xs[j]; y = ys[j];  // the next stroke's regeneration starts from x_j
+      }
+    }
+    #pragma omp critical
+    for (int i = 0; i < 14; ++i) tot[i] += my[i];
+  }
+  for (int i = 0; i < 14; ++i) out[i] = tot[i];
+  return 0;
 }
 
 int orc_num_threads(void) {

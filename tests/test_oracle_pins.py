@@ -326,6 +326,81 @@ def test_hard_chain_against_forward_replay():
     assert checked > 0.95 * W * H
 
 
+def _drops_program(strokes):
+    a = np.asarray(strokes, dtype=np.float64)
+    n = a.shape[0]
+    return inputs.Program(cx=a[:, 0], cy=a[:, 1], theta=a[:, 2], length=a[:, 3], half_width=a[:, 4],
+                          logits=np.zeros((n, 1)), palette=np.array([[0.2, 0.4, 0.6]]),
+                          background=np.ones(3), color_temp=1.0)
+
+
+def _pixel_points(W, H):
+    jj, ii = np.meshgrid(np.arange(W), np.arange(H))
+    return np.stack([(jj.ravel() + 0.5) / W, (ii.ravel() + 0.5) / H], 1)
+
+
+def test_chain_condition_of_concentric_drops_is_the_radial_stretch():
+    """kappa (the product over the passed strokes of ||D psi_j||_2) in closed
+    form.  A drop's pull-back sends radius rho to sqrt(rho^2 - r^2): it
+    stretches radially by rho / sqrt(rho^2 - r^2) (> 1) and shrinks
+    tangentially by the inverse, so ||D psi||_2 is the radial factor.  Two
+    concentric drops telescope: rho / rho_1 for a pixel stopped by the first
+    (program index 0), rho / rho_0 for one that passes both, 1 for a pixel
+    inside the last.  A Frobenius norm, a smaller singular value or a missing
+    factor fails it."""
+    c = (0.5, 0.5)
+    r0, r1 = 0.09, 0.07
+    p = _drops_program([(c[0], c[1], 0.3, 0.0, r0), (c[0], c[1], 1.2, 0.0, r1)])
+    W = H = 64
+    got = oracle.render_hard(p, W, H, with_kappa=True)
+    rho = np.hypot(*(_pixel_points(W, H) - np.array(c)).T)
+    rho1 = np.sqrt(np.maximum(rho ** 2 - r1 ** 2, 0.0))
+    rho0 = np.sqrt(np.maximum(rho1 ** 2 - r0 ** 2, 0.0))
+    want = np.where(rho <= r1, 1.0, np.where(rho1 <= r0, rho / np.maximum(rho1, 1e-300),
+                                             rho / np.maximum(rho0, 1e-300)))
+    ok = got["margin"] > 1e-9
+    assert np.array_equal(got["idx"][ok], np.where(rho <= r1, 1, np.where(rho1 <= r0, 0, -1))[ok])
+    assert np.abs(got["kappa"][ok] / want[ok] - 1.0).max() < 1e-12
+    assert (want[ok & (rho1 > r0)] > 1.0).all()
+
+
+def test_chain_condition_against_svd_of_difference_jacobians():
+    """kappa on a small capsule program against a brute-force chain: trace
+    each pixel with the single-map routine, take each passed stroke's 2x2
+    Jacobian by central differences and its largest singular value by numpy's
+    SVD, and multiply.  Independent of the oracle's dual numbers and of its
+    closed-form 2x2 spectral norm."""
+    p = _tiny_program(6, 29, r_lo=0.04, r_hi=0.12)
+    W = H = 12
+    got = oracle.render_hard(p, W, H, with_kappa=True)
+    h = 1e-6
+    checked = 0
+    for q, x0 in enumerate(_pixel_points(W, H)):
+        if got["margin"][q] < 1e-6:
+            continue
+        x = x0[None, :].copy()
+        kap = 1.0
+        for j in range(p.n - 1, -1, -1):
+            st = tuple(float(v) for v in (p.cx[j], p.cy[j], p.theta[j], p.length[j], p.half_width[j]))
+            if seg_distance(x, st)[0] <= st[4]:
+                break
+            pts = x + np.array([[h, 0.0], [-h, 0.0], [0.0, h], [0.0, -h]])
+            y = oracle.psi_map(pts, st, oracle.MODE_CLAMP)
+            J = np.stack([(y[0] - y[1]) / (2 * h), (y[2] - y[3]) / (2 * h)], 1)
+            kap *= np.linalg.svd(J, compute_uv=False)[0]
+            x = oracle.psi_map(x, st, oracle.MODE_CLAMP)
+        assert abs(got["kappa"][q] / kap - 1.0) < 1e-6, q
+        checked += 1
+    assert checked > 0.9 * W * H
+    assert got["kappa"].max() > 1.5
+
+
+def test_chain_condition_of_the_inert_render_is_one():
+    p = _tiny_program(6, 31, r_lo=0.04, r_hi=0.12)
+    got = oracle.render_hard(p, 16, 16, with_kappa=True, inert=True)
+    assert np.array_equal(got["kappa"], np.ones(256))
+
+
 def test_soft_render_tends_to_hard():
     """As the relaxation width goes to zero, Eq. relax tends to the indicator
     and the soft render to the hard render away from deposit boundaries."""
@@ -764,3 +839,57 @@ def test_early_exit_changes_the_render_by_at_most_the_exit_transmittance():
         assert exited.sum() > 0.5 * W * H
         assert (d <= ex["T0"] + 1e-15).all()
         assert np.array_equal(ex["rgb"][~exited], full["rgb"][~exited])
+
+
+# --------------------------------------------------------------------------- operation counts (measurement)
+
+def test_operation_counts_by_hand():
+    """The counting scalar against counts taken by hand from the definitions
+    (FP32 add / subtract / multiply = 1, a division by a pixel value = 1 XU + 1,
+    sqrt / atan2 / sin / cos = 1 XU, exp = 1 XU + 1).  One pixel at
+    (0.4375, 0.4375) of an 8 x 8 canvas:
+      * inside a capsule beside its flank: frame 8 (two differences, two dot
+        products), distance 1 (the zero offset along the segment), margin 1;
+      * inside a drop, on its cap: frame 8, distance 4 + 1 XU, margin 1;
+      * outside a drop (right cap, passes on): the front 13 + 1 XU, then Eq.
+        back 41 + 9 XU: C 5, the root 4 + 2 XU, the arclength 4 + 1 XU, the two
+        perimeters 4, q 1 + 1 XU, v 3 + 1 XU, the new arclength 4 + 1 XU, the
+        point on the stadium 8 + 3 XU, back to the canvas 8;
+      * its soft step adds the coverage 3 + 2 XU and the compositing 11."""
+    def one(strokes):
+        a = np.asarray(strokes, float)
+        n = a.shape[0]
+        return inputs.Program(cx=a[:, 0], cy=a[:, 1], theta=a[:, 2], length=a[:, 3], half_width=a[:, 4],
+                              logits=np.zeros((n, 1)), palette=np.array([[0.2, 0.4, 0.6]]),
+                              background=np.ones(3), color_temp=1.0)
+    pix = np.array([27])
+    c = oracle.count_ops(one([(0.4375, 0.4375, 0.3, 0.2, 0.1)]), 8, 8, 0.0, 0.005, pix=pix)["hard"]
+    assert (c["fp32"], c["xu"], c["visited_steps"]) == (10, 0, 1)
+    c = oracle.count_ops(one([(0.30, 0.4375, 0.0, 0.0, 0.2)]), 8, 8, 0.0, 0.005, pix=pix)["hard"]
+    assert (c["fp32"], c["xu"]) == (13, 1)
+    c = oracle.count_ops(one([(0.20, 0.4375, 0.0, 0.0, 0.1)]), 8, 8, 0.0, 0.005, pix=pix)
+    assert (c["hard"]["fp32"], c["hard"]["xu"]) == (54, 10)
+    assert (c["soft"]["fp32"], c["soft"]["xu"]) == (68, 12)
+    # the adjoint's regeneration is Eq. fwd on the pulled-back point, its coverage the front + Eq. relax
+    parts = c["adjoint"]["parts"]
+    assert (parts["coverage"]["fp32"], parts["coverage"]["xu"]) == (16, 3)
+    # a reverse sweep costs a small multiple of the forward work it reverses
+    fwd = 13 + 3 + 41
+    assert 1.0 <= parts["reverse_sweep"]["fp32"] / fwd <= 4.0
+
+
+@pytest.mark.slow
+def test_frozen_operation_counts_are_reproducible():
+    """The counts the benchmark divides by are what oracle/count_ops.py gives
+    (integer tallies, so the sums are exact)."""
+    path = os.path.join(os.path.dirname(GOLDEN), "..", "profiles", "opcount_1024_2000.json")
+    frozen = json.load(open(path))
+    pix = inputs.sample_pixels(4711, 1024 * 1024, frozen["pixels"])
+    got = oracle.count_ops(inputs.operating_program(), 1024, 1024, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, pix=pix)
+    for part in ("soft", "adjoint"):
+        key = "soft_forward" if part == "soft" else "adjoint"
+        assert got[part]["fp32"] == frozen["capsule"][key]["fp32"]
+        assert got[part]["xu"] == frozen["capsule"][key]["xu"]
+    hard = oracle.count_ops(inputs.resolution_program(), 1024, 1024, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN,
+                            pix=pix)["hard"]
+    assert hard["fp32"] == frozen["capsule"]["hard_per_visited_step"]["fp32"]
