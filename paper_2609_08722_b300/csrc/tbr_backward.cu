@@ -281,7 +281,13 @@ __global__ void k_grad_sum(const float* __restrict__ partial, int G, int n8, con
 }
 
 // Per stroke: geometry gradients, and the colour chain rule
-// dc_i/dz_iq = p_iq (Pal_q - c_i) / tau_c for the logits.
+// dc_i/dz_iq = p_iq (Pal_q - c_i) / tau_c for the logits.  Pal_q - c_i is
+// formed as sum_q' p_iq' (Pal_q - Pal_q') (the weights sum to one): for the
+// dominant entry it is a small difference of two nearly equal colours, which
+// Pal_q - c_i would take from the rounding of c_i.  A drop (L = 0) without a
+// coupling profile has no direction, so its angle gradient is exactly zero
+// (the renders are invariant under theta there); the sums over pixels would
+// only leave rounding.  A coupled drop's profile turns with theta.
 __global__ void k_grad_out(EpilogueArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
@@ -289,18 +295,25 @@ __global__ void k_grad_out(EpilogueArgs a) {
                    a.status[ST_TIMEOUT] != 0ull;
   const float nan = __int_as_float(0x7fc00000);
   const float* g8 = a.grad8 + static_cast<size_t>(i) * 8;
+  const float* R = a.packed + static_cast<size_t>(i) * kRec;
   a.g_cx[i] = bad ? nan : g8[0];
   a.g_cy[i] = bad ? nan : g8[1];
-  a.g_th[i] = bad ? nan : g8[2];
+  const bool round_drop = R[F_L] == 0.0f && R[F_C1] == 0.0f && R[F_C1 + 1] == 0.0f && R[F_C1 + 2] == 0.0f;
+  a.g_th[i] = bad ? nan : (round_drop ? 0.0f : g8[2]);
   a.g_len[i] = bad ? nan : g8[3];
   a.g_r[i] = bad ? nan : g8[4];
-  const float* R = a.packed + static_cast<size_t>(i) * kRec;
-  const float c0 = R[F_CR], c1 = R[F_CG], c2 = R[F_CB];
+  const float* p = a.probs + static_cast<size_t>(i) * a.k;
   for (int q = 0; q < a.k; ++q) {
     const float* pal = a.palette + 3 * q;
-    const float d = fmaf(pal[0] - c0, g8[5], fmaf(pal[1] - c1, g8[6], (pal[2] - c2) * g8[7]));
-    a.g_logits[static_cast<size_t>(i) * a.k + q] =
-        bad ? nan : a.probs[static_cast<size_t>(i) * a.k + q] * d * a.inv_color_temp;
+    float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f;
+    for (int u = 0; u < a.k; ++u) {
+      const float* pu = a.palette + 3 * u;
+      d0 = fmaf(p[u], pal[0] - pu[0], d0);
+      d1 = fmaf(p[u], pal[1] - pu[1], d1);
+      d2 = fmaf(p[u], pal[2] - pu[2], d2);
+    }
+    const float d = fmaf(d0, g8[5], fmaf(d1, g8[6], d2 * g8[7]));
+    a.g_logits[static_cast<size_t>(i) * a.k + q] = bad ? nan : p[q] * d * a.inv_color_temp;
   }
 }
 
@@ -328,23 +341,35 @@ __global__ void k_grad_palette(EpilogueArgs a) {
 
 }  // namespace
 
+int device_sm_count() {
+  static PerDeviceInt cache;
+  return cache.get([](int dev) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    return sms;
+  });
+}
+
 int backward_grid(int W, int H, int inert) {
-  static int per_sm[2] = {-1, -1};
-  static int sms = 0;
-  if (per_sm[0] < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_backward2<kBwdCH, false>, kTileThreads, 0) !=
-            cudaSuccess || per_sm[0] < 1)
-      per_sm[0] = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_backward<kBwdCH, true>, kTileThreads, 0) !=
-            cudaSuccess || per_sm[1] < 1)
-      per_sm[1] = 1;
-  }
+  static PerDeviceInt pair_cache, one_cache;
+  const int per_sm = inert ? one_cache.get([](int) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward<kBwdCH, true>, kTileThreads, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    return b;
+  })
+                           : pair_cache.get([](int) {
+                               int b = 0;
+                               if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward2<kBwdCH, false>,
+                                                                                 kTileThreads, 0) != cudaSuccess ||
+                                   b < 1)
+                                 b = 1;
+                               return b;
+                             });
   const int tiles = inert ? ((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH)
                           : ((W + kPairTileW - 1) / kPairTileW) * ((H + kPairTileH - 1) / kPairTileH);
-  const int g0 = per_sm[inert ? 1 : 0] * sms;
+  const int g0 = per_sm * device_sm_count();
   const int waves = (tiles + g0 - 1) / g0;
   return (tiles + waves - 1) / waves;
 }

@@ -182,17 +182,16 @@ __global__ void __launch_bounds__(kTileThreads) k_backward_c(BwdArgs a) {
 }  // namespace
 
 int backward_grid_coupled(int W, int H) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backward_c<kBwdCCH>, kTileThreads, 0) !=
-            cudaSuccess || per_sm < 1)
-      per_sm = 1;
-  }
+  static PerDeviceInt cache;
+  const int per_sm = cache.get([](int) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward_c<kBwdCCH>, kTileThreads, 0) != cudaSuccess ||
+        b < 1)
+      b = 1;
+    return b;
+  });
   const int tiles = tile_count(W, H);
-  const int g0 = per_sm * (sms > 0 ? sms : 1);
+  const int g0 = per_sm * device_sm_count();
   const int waves = (tiles + g0 - 1) / g0;
   return (tiles + waves - 1) / waves;
 }

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "tbr.h"
 #include "tbr_poly.h"
 
@@ -244,6 +246,7 @@ struct Geo {
   float si, hi;       // signed frame coordinates of x_i
   float so, ho;       // signed frame coordinates of x_{i-1}
   float sp, sig;      // sigma' = dist(x_i), sigma = dist(x_{i-1})
+  float dsp;          // sigma' - sigma, in displacement form (exterior steps)
   float t, tn;        // folded arclength coordinates of x_i and x_{i-1}
   float ud, uh;       // at x_i: cap ? (sin phi, cos phi) : (0, 1)
   float phi;          // at x_i on a cap: angle from the flank normal
@@ -309,10 +312,12 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
     q.cb = q.cap_o ? q.uh : 1.0f;
     float dS, dH;
     if (q.floored) {                   // direct form, same ray
+      q.dsp = q.sp - q.sig;
       dS = q.sig * q.sb - as;
       dH = q.sig * q.cb - ah;
     } else {
       const float dsig = -div_a(Ag, kPiF * (q.sp + q.sig));
+      q.dsp = -dsig;
       dS = dsig * q.ud;
       dH = dsig * q.uh;
     }
@@ -350,6 +355,7 @@ __device__ __forceinline__ void psi_local(float s, float h, const StrokeF& g, Ge
   q.sig = div_a(C, g.L + sqrt_a(fmaf(kPiF, C, g.L2)));
   const float Q = fmaf(kPiF, q.sig, g.L);
   const float dsig = q.floored ? q.sig - q.sp : -div_a(Ag, fmaf(kPiF, q.sp + q.sig, g.twoL));
+  q.dsp = -dsig;
   q.tn = q.t * (Q * iQp);
   q.cap_o = q.tn > g.hl;
   float dS, dH;
@@ -414,6 +420,7 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
     const float B = fmaf(q.sig, kPiF * q.sig, Ag);
     q.sp = div_a(B, sqrt_a(kPiF * B));
     const float dsp = div_a(Ag, kPiF * (q.sig + q.sp));
+    q.dsp = dsp;
     q.t = q.sp * q.beta;
     q.cap_i = q.cap_o;
     q.phi = q.beta; q.ud = q.sb; q.uh = q.cb;
@@ -444,6 +451,7 @@ __device__ __forceinline__ void phi_local(float s, float h, const StrokeF& g, Ge
   const float B = fmaf(q.sig, fmaf(kPiF, q.sig, g.twoL), Ag);
   q.sp = div_a(B, g.L + sqrt_a(fmaf(kPiF, B, g.L2)));
   const float dsp = div_a(Ag, fmaf(kPiF, q.sig + q.sp, g.twoL));
+  q.dsp = dsp;
   const float Qp = fmaf(kPiF, q.sp, g.L);
   q.t = q.tn * (Qp * iQ);
   q.cap_i = q.t > g.hl;
@@ -571,6 +579,33 @@ __device__ __forceinline__ void add_frame_disp(float& xh, float& yh, float& xl, 
 //   z       the (clamped) coverage logit (r - sigma') / w
 // Outputs: gradient of lambda^x_{i-1} . psi_i + mu_i alpha_i with respect to
 // (cx, cy, theta, L, r).
+// The angle cotangent of one exterior step without the cancellation of its two
+// rotation halves.  In the folded frame, rotating the stroke by theta about m is
+// a rotation about the cap centre (L/2, 0) plus a shift of the cap centre by
+// L/2 along the normal.  On a cap the pull-back keeps the centred arclength, so
+// the first part only sees the stretch 1 - d beta/d phi = L (sigma - sigma') /
+// (Q' sigma) of the angle; the second part is (L/2) (ghn - g_ah) with g_ah the
+// full folded cotangent of |h| (coverage included, whose own angle term
+// -(L/2) cos phi cancels against it).  spm = sign(s) sign(h).
+__device__ __forceinline__ float theta_vjp_cap(float spm, float L, float hl, float dsp, float iQp, float gsn,
+                                               float ghn, float sb, float cb, float g_ah) {
+  const float k = -L * dsp * iQp;  // sigma (1 - d beta / d phi)
+  return spm * fmaf(k, fmaf(ghn, sb, -gsn * cb), hl * (ghn - g_ah));
+}
+// On a flank the map is (|s|, sigma') -> (|s| Q/Q', sigma) with d sigma/d sigma'
+// = Q'/Q; the rotation's share is |s|-weighted and proportional to sigma' -
+// sigma throughout: b1 = (sigma' - sigma) (L/Q' - pi^2 |s|^2 (Q + Q') / (Q Q'^2)),
+// b2 = -pi |s| (sigma' - sigma) (Q + Q') / (Q Q'); the coverage adds -|s| g_cov
+// (g_cov = its cotangent of sigma').
+__device__ __forceinline__ float theta_vjp_flank(float spm, float L, float as, float dsp, float Q, float Qp,
+                                                 float gsn, float ghn, float g_cov) {
+  const float iQ = rcp_a(Q), iQp = rcp_a(Qp);
+  const float QQ = (Q + Qp) * iQ * iQp;
+  const float b1 = dsp * fmaf(-kPiF * kPiF * as * as, QQ * iQp, L * iQp);
+  const float b2 = -kPiF * as * dsp * QQ;
+  return spm * (fmaf(gsn, b1, ghn * b2) - as * g_cov);
+}
+
 __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& lamx, float& lamy,
                                          float mua, float z, float& gcx, float& gcy, float& gth,
                                          float& gL, float& gr) {
@@ -636,7 +671,18 @@ __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& 
   const float nly = fmaf(GS, g.ey, GH * g.ex);
   gcx = lamx - nlx;
   gcy = lamy - nly;
-  gth = fmaf(q.so, lh, -q.ho * ls) + fmaf(GS, q.hi, -GH * q.si);
+  // theta turns the frame about m: the cotangent is lambda . J (x_{i-1} - m) -
+  // (D psi^T lambda) . J (x_i - m) plus the coverage's share.  Far from a short
+  // stroke the map is nearly radial and the two halves, each of size
+  // |lambda| |x - m|, cancel to a value of order L; on exterior steps that stay
+  // on a cap or on a flank the difference is formed directly instead, from
+  // sigma' - sigma and the offset L/2 of the cap centre (theta_vjp_*).
+  if (!q.floored && q.cap_i && q.cap_o)
+    gth = theta_vjp_cap(q.sgs * q.sgh, g.L, g.hl, q.dsp, Qp > 0.0f ? rcp_a(Qp) : 0.0f, gsn, ghn, q.sb, q.cb, g_ah);
+  else if (!q.floored && !q.cap_i && !q.cap_o)
+    gth = theta_vjp_flank(q.sgs * q.sgh, g.L, fabsf(q.si), q.dsp, Q, Qp, gsn, ghn, -mua * g.iw);
+  else
+    gth = fmaf(q.so, lh, -q.ho * ls) + fmaf(GS, q.hi, -GH * q.si);
   gL = g_L;
   gr = g_r;
   lamx = nlx;
@@ -783,6 +829,31 @@ struct BwdArgs {
   int coupled = 0;              // 1: the coupling variant (one pixel per thread, no repair)
 };
 constexpr int kRepairMax = 1024;  // largest repair list (sorted by one CTA)
+
+// A launch-shape value (SM count, resident CTAs per SM) cached per device
+// ordinal under a lock: several host threads may launch at once (the serving
+// worker beside a caller), and one process may drive devices that differ in
+// SM count.  compute(dev) runs once per device, with that device current.
+struct PerDeviceInt {
+  static constexpr int kMaxDevices = 64;
+  std::mutex mu;
+  int val[kMaxDevices] = {};
+  bool have[kMaxDevices] = {};
+  template <class F>
+  int get(F&& compute) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return compute(dev < 0 ? 0 : dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!have[dev]) {
+      val[dev] = compute(dev);
+      have[dev] = true;
+    }
+    return val[dev];
+  }
+};
+// Streaming multiprocessors of the current device (>= 1).
+int device_sm_count();
+
 int backward_grid(int W, int H, int inert);  // CTAs of the persistent backward grid
 int backward_grid_coupled(int W, int H);     // the same for the coupling variant's adjoint
 cudaError_t launch_backward_coupled(const BwdArgs& a, cudaStream_t st);

@@ -105,6 +105,7 @@ __device__ __forceinline__ void pair_records_fill(const float* __restrict__ S0, 
 struct Geo2 {
   f2 sgs, sgh, si, hi, so, ho, sp, sig, tn, ud, uh, phi, sb, cb, beta;
   f2 Q, Qp, iQ, iQp;
+  f2 dsp;  // sigma' - sigma (displacement form)
 };
 
 // x_i = Phi_i(x_{i-1}) for two pixels at frame points (s, h) of x_{i-1}, in the
@@ -126,6 +127,7 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
     const f2 B = fma2(q.sig, mul2(F2(kPiF), q.sig), Ar);
     q.sp = sqrt2(mul2(B, F2(1.0f / kPiF)));
     const f2 dsp = mul2(Ar, rcp2(mul2(F2(kPiF), add2(q.sig, q.sp))));
+    q.dsp = dsp;
     q.phi = q.beta; q.ud = q.sb; q.uh = q.cb;
     q.Q = mul2(F2(kPiF), q.sig);
     q.Qp = mul2(F2(kPiF), q.sp);
@@ -151,6 +153,7 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   const f2 B = fma2(q.sig, fma2(F2(kPiF), q.sig, P[P_2L]), Ar);
   q.sp = mul2(B, rcp2(add2(L, sqrt2(fma2(F2(kPiF), B, P[P_L2])))));
   const f2 dsp = mul2(Ar, rcp2(fma2(F2(kPiF), add2(q.sig, q.sp), P[P_2L])));
+  q.dsp = dsp;
   q.Q = fma2(F2(kPiF), q.sig, L);
   q.Qp = fma2(F2(kPiF), q.sp, L);
   q.iQ = rcp2(q.Q);
@@ -320,7 +323,22 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
   const f2 nly = fma2(GS, ey, mul2(GH, ex));
   gcx = sub2(lamx, nlx);
   gcy = sub2(lamy, nly);
-  gth = add2(sub2(mul2(q.so, lh), mul2(q.ho, ls)), sub2(mul2(GS, q.hi), mul2(GH, q.si)));
+  // theta: the rotation about m without the cancellation of its two halves
+  // (theta_vjp_cap / theta_vjp_flank).  A flank step has sin beta = 0; the
+  // flank form is evaluated only when some pixel of the converged lanes needs it.
+  const f2 spm = mul2(q.sgs, q.sgh);
+  const f2 kc = mul2(mul2(P[P_L], q.dsp), q.iQp);
+  f2 inner = fma2(mul2(kc, F2(-1.0f)), sub2(mul2(ghn, q.sb), mul2(gsn, q.cb)), mul2(P[P_HL], sub2(ghn, g_ah)));
+  const bool fx = q.sb.x == 0.0f, fy = q.sb.y == 0.0f;
+  if (__any_sync(__activemask(), fx || fy)) {
+    const f2 as = abs2(q.si);
+    const f2 QQ = mul2(add2(q.Q, q.Qp), mul2(q.iQ, q.iQp));
+    const f2 b1 = mul2(q.dsp, fma2(mul2(F2(-kPiF * kPiF), mul2(as, as)), mul2(QQ, q.iQp), mul2(P[P_L], q.iQp)));
+    const f2 b2 = mul2(mul2(as, F2(-kPiF)), mul2(q.dsp, QQ));
+    const f2 fl = fma2(as, mul2(mua, P[P_IW]), fma2(gsn, b1, mul2(ghn, b2)));
+    inner = sel2(fx, fy, fl, inner);
+  }
+  gth = mul2(spm, inner);
   gL = g_L;
   gr = g_r;
   lamx = nlx;

@@ -222,18 +222,14 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_serve(ServeArgs a) {
 }  // namespace
 
 int serve_grid() {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_serve, kTileThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
+  static PerDeviceInt cache;
+  const int per_sm = cache.get([](int) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_serve, kTileThreads, 0) != cudaSuccess || b < 1) b = 1;
     // leave one CTA per SM free so packing and edit kernels of new requests can run alongside
-    if (per_sm > 1) per_sm -= 1;
-  }
-  return per_sm * sms;
+    return b > 1 ? b - 1 : b;
+  });
+  return per_sm * device_sm_count();
 }
 
 cudaError_t launch_serve(const ServeArgs& a, cudaStream_t st) {

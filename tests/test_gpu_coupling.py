@@ -4,10 +4,12 @@ flow", Eq. coupling, Eq. profile) on the GPU against the FP64 oracle.
 Tolerances as for the capsule renderer: hard-render index bit-exact outside
 the band where the oracle's margin |sigma' - sigma_b(v)| < 1e-5 (a mismatch
 outside it only where the chain condition kappa * 6e-8 > 1e-5); soft render
-|R_gpu - R_oracle| <= 1e-4 per channel.  Replay-adjoint gradients: relative
-error per parameter group within max(1e-3, 2 x the oracle's own sensitivity),
-the sensitivity being how far the oracle's FP64 gradient moves when every
-stroke parameter is perturbed by one FP32 rounding (relative 6e-8).  At the
+|R_gpu - R_oracle| <= 1e-4 per channel.  Replay-adjoint gradients: the group
+norm ratio within 1e-3, and per element the bound of ``paritycheck.compare``
+(1e-3 relative with its floor, or within 4 x the element's own sensitivity:
+how far the oracle's FP64 gradient entry moves when every stroke parameter is
+perturbed by one FP32 rounding, relative 6e-8); a finite-difference test holds
+a well-conditioned case to 1e-3 per element.  At the
 sharp relaxation the coupled profile makes the gradient far more sensitive
 than the capsule map's (up to 4e-3 against 1.4e-5 on the 50-stroke program,
 most of it from coupled drops, whose v is the polar angle about their
@@ -21,6 +23,7 @@ import pytest
 import torch
 
 import oracle
+from paritycheck import check_hard, compare, oracle_sensitivity
 from paper_2609_08722_b300 import inputs, tbr
 
 pytestmark = pytest.mark.gpu
@@ -33,22 +36,6 @@ GROUPS = ["cx", "cy", "theta", "length", "half_width", "logits", "palette"]
 
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
-def grad_sensitivity(p, W, H, tau, tau_min, cot, og, pix=None, trials=2):
-    """Per group: the largest relative move of the oracle's gradient when every
-    stroke parameter is perturbed by one FP32 rounding."""
-    rng = np.random.default_rng(2025)
-    worst = {k: 0.0 for k in GROUPS}
-    for _ in range(trials):
-        q = p.copy()
-        for k in ("cx", "cy", "theta", "length", "half_width"):
-            v = getattr(q, k).astype(np.float64)
-            setattr(q, k, v * (1.0 + rng.uniform(-6e-8, 6e-8, v.shape)))
-        oq = oracle.soft_vjp(q, W, H, tau, tau_min, cot, pix=pix)
-        for k in GROUPS:
-            worst[k] = max(worst[k], rel(oq[k].ravel(), og[k].ravel()))
-    return worst
 
 
 def coupled(p, seed, **kw):
@@ -71,15 +58,9 @@ def hard_check(p, W, H, label):
     rgb, idx, st = tbr.render_hard(dp, W, H, stats=True)
     o = oracle.render_hard(p, W, H, with_kappa=True)
     idx = idx.cpu().numpy().ravel()
-    mism = idx != o["idx"]
-    band = o["margin"] < BAND
-    outside = mism & ~band
-    cond = o["kappa"] * 6e-8 > BAND
-    print(f"coupled hard {label}: band {band.sum()}, mismatches {mism.sum()} (outside band {outside.sum()}), "
-          f"stats {st}")
-    assert not (outside & ~cond).any()
-    assert mism.mean() < 0.01
-    ok = ~mism
+    c = check_hard(p, idx, o, W, H, f"coupled hard {label}, stats {st}")
+    assert c["mismatch"] < 0.01 * W * H
+    ok = idx == o["idx"]
     assert np.abs(rgb.cpu().numpy().reshape(-1, 3)[ok] - o["rgb"][ok]).max() < 1e-6
     return rgb, idx, o
 
@@ -122,10 +103,7 @@ def test_coupled_operating_point_sampled():
     _, idx, _ = tbr.render_hard(dp, W, H)
     pix = inputs.sample_pixels(36, W * H, 4000)
     oh = oracle.render_hard(p, W, H, pix=pix, with_kappa=True)
-    mism = idx.cpu().numpy().ravel()[pix] != oh["idx"]
-    outside = mism & (oh["margin"] >= BAND) & (oh["kappa"] * 6e-8 <= BAND)
-    print(f"coupled hard op: mismatches {mism.sum()} of {pix.size}, unexplained {outside.sum()}")
-    assert not outside.any()
+    check_hard(p, idx.cpu().numpy().ravel()[pix], oh, W, H, "coupled hard op", pix=pix)
 
 
 def test_zero_profile_is_the_capsule_render():
@@ -194,13 +172,15 @@ def test_backward_coupled(which, W, H, tau, tau_min):
     g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
     st = ctx.status()
     og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64))
-    errs = {k: rel(g[k].cpu().numpy().ravel(), og[k].ravel()) for k in GROUPS}
-    sens = grad_sensitivity(p, W, H, tau, tau_min, cot.astype(np.float64), og)
-    print(f"coupled adjoint {which} tau={tau}: " + ", ".join(f"{k} {e:.2e} (sens {sens[k]:.1e})"
-                                                           for k, e in errs.items())
-          + f"; records {st['records']}")
-    for k, e in errs.items():
-        assert e <= max(GRAD_TOL, 2.0 * sens[k]), k
+    sens = oracle_sensitivity(p, W, H, tau, tau_min, cot.astype(np.float64), og)
+    print(f"coupled adjoint {which} tau={tau}: records {st['records']}, oracle norm sensitivity "
+          + ", ".join(f"{k} {v:.1e}" for k, v in sens["norm"].items()))
+    # At the sharp relaxation a coupled drop's profile turns with its polar
+    # angle, which is undefined at the centre: on the 50-stroke program (half
+    # drops) up to a fifth of the entries move by more than 1e-3 under one FP32
+    # rounding of the inputs; those are held to 4 x that move instead.
+    compare(g, og, sens=sens, label=f"coupled adjoint {which} tau={tau}",
+            max_cond_frac=0.2 if (which == "small" and tau == 0.0) else 0.05)
     assert st["overflow_pixels"] == 0
     # the profile matters: the capsule map's gradients differ
     plain = p.copy()
@@ -222,11 +202,37 @@ def test_backward_coupled_operating_point_sampled():
     full[torch.from_numpy(pix).cuda()] = torch.from_numpy(cot).cuda()
     g = ctx.backward(full.view(H, W, 3))
     og = oracle.soft_vjp(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), pix=pix)
-    sens = grad_sensitivity(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), og, pix=pix)
-    for k in GROUPS:
-        e = rel(g[k].cpu().numpy().ravel(), og[k].ravel())
-        print(f"coupled adjoint op {k}: {e:.3e} (sens {sens[k]:.1e})")
-        assert e <= max(GRAD_TOL, 2.0 * sens[k]), k
+    sens = oracle_sensitivity(p, W, H, inputs.SHARP_TAU, inputs.SHARP_TAU_MIN, cot.astype(np.float64), og, pix=pix)
+    print("coupled adjoint op: oracle norm sensitivity " + ", ".join(f"{k} {v:.1e}" for k, v in sens["norm"].items()))
+    compare(g, og, sens=sens, label="coupled adjoint op")
+
+
+def test_backward_coupled_against_finite_differences():
+    """The coupled replay adjoint against FP64 central differences of the
+    oracle's soft render, on 12 seeded parameters of the 50-stroke coupled
+    program at tau = 0.3 (where the oracle's gradient is well conditioned)."""
+    p = small_coupled()
+    W = H = 64
+    tau, tau_min = 0.3, 0.01
+    dp = tbr.DeviceProgram.from_host(p)
+    _, ctx = tbr.render_soft(dp, W, H, tau, tau_min, record=True)
+    cot = inputs.make_cotangent(409, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    u = inputs.uniform(410, 24).reshape(12, 2)
+    params = [(int(a * p.n), int(b * (5 + p.k))) for a, b in u]
+    fd = oracle.fd_gradient(p, W, H, tau, tau_min, cot.astype(np.float64), params)
+    og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64))
+    names = ["cx", "cy", "theta", "length", "half_width"]
+    worst = 0.0
+    for (j, q), want in zip(params, fd):
+        grp = names[q] if q < 5 else "logits"
+        got = float(g[grp].cpu().numpy().reshape(p.n, -1)[j, 0 if q < 5 else q - 5])
+        floor = 1e-3 * float(np.abs(og[grp]).max())
+        e = abs(got - want) / max(abs(want), floor)
+        worst = max(worst, e)
+        print(f"stroke {j} param {q}: gpu {got:.6e} fd {want:.6e} ratio {e:.2e}")
+        assert e <= GRAD_TOL, (j, q)
+    print(f"coupled adjoint vs FD: worst {worst:.2e}")
 
 
 def test_coupled_context_is_not_reused_for_the_capsule_map():

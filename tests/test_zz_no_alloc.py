@@ -1,7 +1,9 @@
 """The allocation-free hard render (tbr_render_hard_noalloc), called through the
 C ABI, gives the same image and index map as tbr_render_hard, on two calls in a
 row with different programs (its fixed scratch array keeps the previous call's
-contents, so the second call checks that nothing stale leaks through).
+contents, so the second call checks that nothing stale leaks through), and
+takes no device memory while doing so (free device memory and the
+stream-ordered pool's counters are unchanged across each call).
 
 It is meant for callers that may not allocate device memory (a plugin inside a
 runtime that owns the device's memory, a real-time loop that must not wait on
@@ -35,6 +37,21 @@ def _coupled_small():
     return p
 
 
+def _device_memory():
+    """(free device bytes, default pool's bytes in use, default pool's bytes
+    reserved) on the current device, after a synchronize."""
+    torch.cuda.synchronize()
+    free = torch.cuda.mem_get_info()[0]
+    from cuda.bindings import runtime as rt
+    err, pool = rt.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+    assert err == rt.cudaError_t.cudaSuccess
+    err, used = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+    assert err == rt.cudaError_t.cudaSuccess
+    err, reserved = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrReservedMemCurrent)
+    assert err == rt.cudaError_t.cudaSuccess
+    return free, int(used), int(reserved)
+
+
 def _render_noalloc(dp, W, H, n_prefix=-1, snap=False):
     rgb = torch.full((H, W, 3), float("nan"), device="cuda")
     idx = torch.full((H, W), -7, device="cuda", dtype=torch.int32)
@@ -54,8 +71,16 @@ def test_noalloc_hard_render_matches_the_allocating_entry_point():
     for prog, W, H, n_prefix, snap in cases:
         dp = tbr.DeviceProgram.from_host(prog)
         ref_rgb, ref_idx, _ = tbr.render_hard(dp, W, H, n_prefix=n_prefix, snap=snap)
-        rgb, idx = _render_noalloc(dp, W, H, n_prefix, snap)
-        torch.cuda.synchronize()
+        rgb = torch.full((H, W, 3), float("nan"), device="cuda")
+        idx = torch.full((H, W), -7, device="cuda", dtype=torch.int32)
+        before = _device_memory()
+        s = dp.struct()
+        rc = _noalloc()(ctypes.byref(s), W, H, n_prefix, int(snap), ctypes.c_void_p(rgb.data_ptr()),
+                        ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        tbr.check(rc)
+        after = _device_memory()
+        # the call took no device memory: neither from the device nor from the stream-ordered pool
+        assert after == before, (before, after)
         assert torch.equal(idx, ref_idx)
         assert float((rgb - ref_rgb).abs().max()) <= 1e-6
 
