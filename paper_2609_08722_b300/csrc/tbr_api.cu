@@ -9,6 +9,7 @@
 #include <atomic>
 
 #include "tbr_host.h"
+#include "tbr_tile.cuh"
 
 namespace tbr {
 
@@ -94,7 +95,7 @@ cudaError_t ctx_allocate(tbr_ctx* c, int n, int k, int W, int H, int ck, int cap
   if (e == cudaSuccess && c->repair_cap > 0) e = dalloc(&c->repair_count, 1, st);
   if (e == cudaSuccess && c->repair_cap > 0)
     e = dalloc(&c->corr, static_cast<size_t>(c->repair_cap) * n * 8, st);
-  if (e == cudaSuccess && c->repair_cap > 0) e = dalloc(&c->repair_first, P, st);
+  if (e == cudaSuccess && c->repair_cap > 0) e = dalloc(&c->repair_first, P + pair_tile_count(W, H), st);
   c->bytes = static_cast<size_t>(n) * kRec * 4 + ST_COUNT * 8 + static_cast<size_t>(n) * k * 4 +
              static_cast<size_t>(k) * 12 + P * 24 + nck * P * 20 +
              (inert ? 0 : static_cast<size_t>(cap) * P * 20) + static_cast<size_t>(c->grid) * n * 32 +
@@ -151,6 +152,7 @@ cudaError_t ctx_backward(tbr_ctx* c, const float* dLdR, float* g_cx, float* g_cy
   ba.drift_tol = c->drift_tol;
   ba.repair_list = c->repair_list; ba.repair_count = c->repair_count; ba.repair_cap = c->repair_cap;
   ba.corr = c->corr; ba.repair_first = c->repair_first;
+  ba.tile_drift = c->repair_first ? c->repair_first + static_cast<size_t>(c->W) * c->H : nullptr;
   ba.coupled = c->coupled;
   cudaError_t e = launch_backward(ba, st);
   if (e != cudaSuccess) return e;

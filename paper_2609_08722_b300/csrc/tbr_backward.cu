@@ -94,11 +94,13 @@ __device__ __forceinline__ void load_pair(const BwdArgs& a, int px, int py0, boo
 
 // The same replay adjoint with two vertically adjacent pixels per thread
 // (32 x 16 tiles, packed FP32 pair arithmetic; tbr_pair.cuh).  Used for the
-// exterior-transport model; the inert-mark model keeps k_backward.  The QUEUE
-// instance runs only when the plain one counted checkpoint drift: it repeats
-// the same computation (rewriting identical slices) and queues each drifting
-// pixel for the FP64 repair; otherwise it returns at once.  Keeping the queue
-// out of the plain instance keeps its hot loop free of that code.
+// exterior-transport model; the inert-mark model keeps k_backward.  The plain
+// instance flags every tile in which a checkpoint drifted (a.tile_drift).  The
+// QUEUE instance runs only when drift was counted, and then only over the
+// flagged tiles: it repeats their computation (writing no slices) and queues
+// each drifting pixel for the FP64 repair; otherwise it returns at once.
+// Keeping the queue out of the plain instance keeps its hot loop free of that
+// code.
 template <int CH, bool QUEUE>
 __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
@@ -125,6 +127,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
   rv.repair_cap = a.repair_cap;
   rv.repair_first = a.repair_first;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    if (QUEUE && a.tile_drift[tile] == 0) continue;  // CTA-uniform
     int px, py0;
     pair_tile_pixel(tile, W, px, py0);
     bool valid[2];
@@ -132,9 +135,11 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
     PixelState st[2];
     float lC[2][3];
     load_pair(a, px, py0, skip, valid, off, st, lC);
+    const unsigned drift0 = drift;
     if (!backward_tile2<CH, QUEUE>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first,
                                    drift, status))
       break;
+    if (!QUEUE && a.tile_drift && __syncthreads_or(drift != drift0) && threadIdx.x == 0) a.tile_drift[tile] = 1;
     first = false;
   }
   if (!QUEUE) {
@@ -379,8 +384,10 @@ cudaError_t launch_backward(const BwdArgs& a, cudaStream_t st) {
   if (a.coupled) return launch_backward_coupled(a, st);
   const bool repair = !a.inert && a.repair_list && a.repair_cap > 0;
   if (repair) {
+    // repair_first holds the per-pixel queued flags, then the per-tile drift flags
     cudaError_t e = cudaMemsetAsync(a.repair_count, 0, sizeof(int), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(a.repair_first, 0, static_cast<size_t>(a.W) * a.H, st);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(a.repair_first, 0, static_cast<size_t>(a.W) * a.H + pair_tile_count(a.W, a.H), st);
     if (e != cudaSuccess) return e;
   }
   {

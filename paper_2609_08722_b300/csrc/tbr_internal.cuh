@@ -572,13 +572,6 @@ __device__ __forceinline__ void add_frame_disp(float& xh, float& yh, float& xl, 
   pos_add(yh, yl, fmaf(ds, g.ey, dh * g.ex));
 }
 
-// Vector-Jacobian product of one step (Eq. adjstep, Eq. adjparam), written out
-// by reverse-mode differentiation of psi_local in the stroke frame.
-//   lam     lambda^x_{i-1} (world), replaced by lambda^x_i
-//   mua     mu_i * d alpha / d z (0 where the clamp binds)
-//   z       the (clamped) coverage logit (r - sigma') / w
-// Outputs: gradient of lambda^x_{i-1} . psi_i + mu_i alpha_i with respect to
-// (cx, cy, theta, L, r).
 // The angle cotangent of one exterior step without the cancellation of its two
 // rotation halves.  In the folded frame, rotating the stroke by theta about m is
 // a rotation about the cap centre (L/2, 0) plus a shift of the cap centre by
@@ -586,11 +579,12 @@ __device__ __forceinline__ void add_frame_disp(float& xh, float& yh, float& xl, 
 // the first part only sees the stretch 1 - d beta/d phi = L (sigma - sigma') /
 // (Q' sigma) of the angle; the second part is (L/2) (ghn - g_ah) with g_ah the
 // full folded cotangent of |h| (coverage included, whose own angle term
-// -(L/2) cos phi cancels against it).  spm = sign(s) sign(h).
+// -(L/2) cos phi cancels against it), i.e. -(L/2) w_h with w the displacement
+// cotangent of step_vjp_ext.  spm = sign(s) sign(h).
 __device__ __forceinline__ float theta_vjp_cap(float spm, float L, float hl, float dsp, float iQp, float gsn,
-                                               float ghn, float sb, float cb, float g_ah) {
+                                               float ghn, float sb, float cb, float wh) {
   const float k = -L * dsp * iQp;  // sigma (1 - d beta / d phi)
-  return spm * fmaf(k, fmaf(ghn, sb, -gsn * cb), hl * (ghn - g_ah));
+  return spm * fmaf(k, fmaf(ghn, sb, -gsn * cb), -hl * wh);
 }
 // On a flank the map is (|s|, sigma') -> (|s| Q/Q', sigma) with d sigma/d sigma'
 // = Q'/Q; the rotation's share is |s|-weighted and proportional to sigma' -
@@ -606,12 +600,93 @@ __device__ __forceinline__ float theta_vjp_flank(float spm, float L, float as, f
   return spm * (fmaf(gsn, b1, ghn * b2) - as * g_cov);
 }
 
+// VJP of an exterior step that stays on a cap or on a flank, in displacement
+// form.  psi moves the folded point p = (|s|, |h|) to p + D(p), D small far
+// from the stroke; the step's cotangents are written through D alone:
+// lambda_{i-1} = lambda_i + R S w and d/dm = -R S w with w = (dD/dp)^T g + the
+// coverage's share (S the fold signs, R the frame), so none of them is the
+// difference of two quantities of size |lambda|.
+//   cap: p = c + sigma' u(phi), p + D = c + sigma u(beta), c = (L/2, 0),
+//        u(a) = (sin a, cos a), beta = phi + delta with
+//        delta = (sigma' - sigma) L (phi - pi/2) / (Q' sigma);
+//        dD/dsigma' = (pi (sigma'-sigma)/Q) u(beta) + (u(beta) - u(phi)) + sigma delta_sigma' u'(beta),
+//        dD/dphi    = -(sigma'-sigma) u'(beta) + sigma' (u'(beta) - u'(phi)) + sigma delta_phi u'(beta),
+//        delta_phi = (sigma'-sigma) L / (Q' sigma),
+//        delta_sigma' = -delta (pi/Q + pi/Q' + Q'/(Q sigma)),
+//        and dsigma'/dp = u(phi), dphi/dp = u'(phi) / sigma';
+//   flank: D = (-|s| pi (sigma'-sigma) / Q', -(sigma'-sigma)).
+// L and r enter through sigma (dsigma/dL = (sigma'-sigma-r)/Q, dsigma/dr =
+// -(L + pi r)/Q at fixed sigma'), through delta, and (L) through the cap
+// centre, whose shift moves p relative to c.  The angle uses theta_vjp_*.
+// Returns the 8 cotangents like step_vjp.  gsn, ghn: the folded cotangent of
+// the output point; gcv: the coverage's cotangent of sigma'.
+__device__ __forceinline__ void step_vjp_ext(const Geo& q, const StrokeF& g, float gsn, float ghn, float gcv,
+                                             float mua, float z, float& lamx, float& lamy, float& gcx,
+                                             float& gcy, float& gth, float& gL, float& gr) {
+  const float Q = fmaf(kPiF, q.sig, g.L), Qp = fmaf(kPiF, q.sp, g.L);
+  const float iQ = rcp_a(Q), iQp = rcp_a(Qp);
+  const float sgL = (q.dsp - g.r) * iQ;           // d sigma / dL
+  const float sgr = -fmaf(kPiF, g.r, g.L) * iQ;   // d sigma / dr
+  float ws, wh, gLl, grl;
+  if (q.cap_i) {
+    const float isg = rcp_a(q.sig), isp = rcp_a(q.sp);
+    const float room = q.phi - 0.5f * kPiF;        // phi - pi/2 <= 0
+    const float sdphi = q.dsp * g.L * iQp;         // sigma delta_phi
+    const float sdel = sdphi * room;               // sigma delta
+    const float sdsp = -sdel * fmaf(kPiF, iQ + iQp, Qp * iQ * isg);  // sigma delta_sigma'
+    const float pdQ = kPiF * q.dsp * iQ;
+    // dD/dsigma' and dD/dphi (u'(a) = (cos a, -sin a))
+    const float As0 = fmaf(pdQ, q.sb, fmaf(sdsp, q.cb, q.sb - q.ud));
+    const float As1 = fmaf(pdQ, q.cb, fmaf(-sdsp, q.sb, q.cb - q.uh));
+    const float Ap0 = fmaf(sdphi - q.dsp, q.cb, q.sp * (q.cb - q.uh));
+    const float Ap1 = fmaf(q.dsp - sdphi, q.sb, q.sp * (q.ud - q.sb));
+    const float g_sp = fmaf(gsn, As0, fmaf(ghn, As1, gcv));
+    const float g_ph = fmaf(gsn, Ap0, ghn * Ap1) * isp;
+    ws = fmaf(q.ud, g_sp, q.uh * g_ph);
+    wh = fmaf(q.uh, g_sp, -q.ud * g_ph);
+    // explicit L and r: D = sigma u(beta) - sigma' u(phi) through sigma and delta
+    const float sdL = room * iQp * (fmaf(-g.L, sgL, q.dsp) - q.dsp * g.L * fmaf(sgL, isg, iQp));
+    const float sdr = -room * g.L * sgr * q.sp * iQp * isg;
+    gLl = fmaf(gsn, fmaf(sgL, q.sb, sdL * q.cb), ghn * fmaf(sgL, q.cb, -sdL * q.sb)) - 0.5f * ws;
+    grl = fmaf(gsn, fmaf(sgr, q.sb, sdr * q.cb), ghn * fmaf(sgr, q.cb, -sdr * q.sb));
+    gth = theta_vjp_cap(q.sgs * q.sgh, g.L, g.hl, q.dsp, iQp, gsn, ghn, q.sb, q.cb, wh);
+  } else {
+    const float as = fabsf(q.si);
+    const float pdQp = kPiF * q.dsp * iQp;
+    ws = -gsn * pdQp;
+    wh = fmaf(gsn, as * kPiF * pdQp * (Q + Qp) * iQ * iQp, fmaf(ghn, kPiF * q.dsp * iQ, gcv));
+    gLl = fmaf(gsn, as * kPiF * fmaf(q.dsp, iQp, sgL) * iQp, ghn * sgL);
+    grl = fmaf(gsn, as * kPiF * sgr * iQp, ghn * sgr);
+    gth = theta_vjp_flank(q.sgs * q.sgh, g.L, as, q.dsp, Q, Qp, gsn, ghn, gcv);
+  }
+  const float GS = q.sgs * ws, GH = q.sgh * wh;
+  const float dlx = fmaf(GS, g.ex, -GH * g.ey);
+  const float dly = fmaf(GS, g.ey, GH * g.ex);
+  gcx = -dlx;
+  gcy = -dly;
+  gL = gLl;
+  gr = fmaf(mua, fmaf(-z, g.dlw, g.iw), grl);
+  lamx += dlx;
+  lamy += dly;
+}
+
+// Vector-Jacobian product of one step (Eq. adjstep, Eq. adjparam), written out
+// by reverse-mode differentiation of psi_local in the stroke frame.
+//   lam     lambda^x_{i-1} (world), replaced by lambda^x_i
+//   mua     mu_i * d alpha / d z (0 where the clamp binds)
+//   z       the (clamped) coverage logit (r - sigma') / w
+// Outputs: gradient of lambda^x_{i-1} . psi_i + mu_i alpha_i with respect to
+// (cx, cy, theta, L, r).
 __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& lamx, float& lamy,
                                          float mua, float z, float& gcx, float& gcy, float& gth,
                                          float& gL, float& gr) {
   const float ls = fmaf(lamx, g.ex, lamy * g.ey);   // lambda . e
   const float lh = fmaf(lamy, g.ex, -lamx * g.ey);  // lambda . e_perp
   const float gsn = q.sgs * ls, ghn = q.sgh * lh;
+  if (!q.floored && q.cap_i == q.cap_o) {  // exterior step on a cap or on a flank
+    step_vjp_ext(q, g, gsn, ghn, -mua * g.iw, mua, z, lamx, lamy, gcx, gcy, gth, gL, gr);
+    return;
+  }
   float g_tn, g_sig, g_hl = 0.0f, g_L = 0.0f, g_r = 0.0f, g_sp = 0.0f;
   if (!q.cap_o) {
     g_tn = gsn; g_sig = ghn;
@@ -672,17 +747,10 @@ __device__ __forceinline__ void step_vjp(const Geo& q, const StrokeF& g, float& 
   gcx = lamx - nlx;
   gcy = lamy - nly;
   // theta turns the frame about m: the cotangent is lambda . J (x_{i-1} - m) -
-  // (D psi^T lambda) . J (x_i - m) plus the coverage's share.  Far from a short
-  // stroke the map is nearly radial and the two halves, each of size
-  // |lambda| |x - m|, cancel to a value of order L; on exterior steps that stay
-  // on a cap or on a flank the difference is formed directly instead, from
-  // sigma' - sigma and the offset L/2 of the cap centre (theta_vjp_*).
-  if (!q.floored && q.cap_i && q.cap_o)
-    gth = theta_vjp_cap(q.sgs * q.sgh, g.L, g.hl, q.dsp, Qp > 0.0f ? rcp_a(Qp) : 0.0f, gsn, ghn, q.sb, q.cb, g_ah);
-  else if (!q.floored && !q.cap_i && !q.cap_o)
-    gth = theta_vjp_flank(q.sgs * q.sgh, g.L, fabsf(q.si), q.dsp, Q, Qp, gsn, ghn, -mua * g.iw);
-  else
-    gth = fmaf(q.so, lh, -q.ho * ls) + fmaf(GS, q.hi, -GH * q.si);
+  // (D psi^T lambda) . J (x_i - m) plus the coverage's share.
+  // floored steps and steps between a cap and a flank (near the stroke, no
+  // cancellation to avoid): the rotation about m as the difference of its halves
+  gth = fmaf(q.so, lh, -q.ho * ls) + fmaf(GS, q.hi, -GH * q.si);
   gL = g_L;
   gr = g_r;
   lamx = nlx;
@@ -826,6 +894,7 @@ struct BwdArgs {
   int repair_cap = 0;           // <= kRepairMax
   float* corr = nullptr;        // [repair_cap][n][8] gradient corrections
   unsigned char* repair_first = nullptr;  // [P] per-pixel "queued" flags, zeroed by launch_backward
+  unsigned char* tile_drift = nullptr;    // [pair tiles] drift seen in the tile (repair_first + P), zeroed too
   int coupled = 0;              // 1: the coupling variant (one pixel per thread, no repair)
 };
 constexpr int kRepairMax = 1024;  // largest repair list (sorted by one CTA)

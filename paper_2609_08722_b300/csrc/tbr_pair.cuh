@@ -105,7 +105,8 @@ __device__ __forceinline__ void pair_records_fill(const float* __restrict__ S0, 
 struct Geo2 {
   f2 sgs, sgh, si, hi, so, ho, sp, sig, tn, ud, uh, phi, sb, cb, beta;
   f2 Q, Qp, iQ, iQp;
-  f2 dsp;  // sigma' - sigma (displacement form)
+  f2 dsp;       // sigma' - sigma (displacement form)
+  f2 isg, isp;  // 1 / sigma, 1 / sigma'
 };
 
 // x_i = Phi_i(x_{i-1}) for two pixels at frame points (s, h) of x_{i-1}, in the
@@ -133,6 +134,8 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
     q.Qp = mul2(F2(kPiF), q.sp);
     q.iQ = rcp2_pos(q.Q);
     q.iQp = rcp2(q.Qp);
+    q.isg = is;
+    q.isp = mul2(F2(kPiF), q.iQp);
     ds = mul2(q.sgs, mul2(dsp, q.sb));
     dh = mul2(q.sgh, mul2(dsp, q.cb));
     q.si = add2(s, ds);
@@ -164,7 +167,9 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   // and with (sb, cb, beta) = (0, 1, 0) the cap formulas give dH = dsigma',
   // (ud, uh, phi) = (0, 1, 0); only dS needs the flank's own form.
   const f2 room = sub2(F2(0.5f * kPiF), q.beta);
-  f2 delta = mul2(mul2(mul2(dsp, L), room), mul2(q.iQ, rcp2(q.sp)));
+  q.isg = is;
+  q.isp = rcp2(q.sp);
+  f2 delta = mul2(mul2(mul2(dsp, L), room), mul2(q.iQ, q.isp));
   delta = sel2(capo_x, capo_y, min2(max2(delta, F2(0.0f)), room), F2(0.0f));
   const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
   const f2 cD = sub2(F2(1.0f), omc);
@@ -281,68 +286,73 @@ __device__ __forceinline__ void add_frame_disp2(f2& xl, f2& yl, const f2* __rest
   yl = add2(yl, fma2(ds, P[P_EY], mul2(dh, P[P_EX])));
 }
 
-// VJP of one regeneration step for two pixels: step_vjp with the flank
-// conventions folded in (no branch).  Regenerated samples are never floored.
+// VJP of one regeneration step for two pixels, in the displacement form of
+// step_vjp_ext (tbr_internal.cuh): cap-to-cap components use its cap branch,
+// flank-to-flank components its flank branch (evaluated only when a converged
+// lane has one; a flank step has sin beta = 0).  Regenerated samples are never
+// floored, and flank-to-cap steps take the scalar routines.
+__device__ __forceinline__ f2 neg2(f2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ P, f2& lamx, f2& lamy, f2 mua, f2 z,
                                           f2& gcx, f2& gcy, f2& gth, f2& gL, f2& gr) {
-  const f2 ex = P[P_EX], ey = P[P_EY];
+  const f2 ex = P[P_EX], ey = P[P_EY], L = P[P_L];
   const f2 ls = fma2(lamx, ex, mul2(lamy, ey));
   const f2 lh = sub2(mul2(lamy, ex), mul2(lamx, ey));
   const f2 gsn = mul2(q.sgs, ls), ghn = mul2(q.sgh, lh);
-  // x_{i-1}: cap point (sigma, beta) or flank point (tn, sigma)
-  f2 g_sig = fma2(gsn, q.sb, mul2(ghn, q.cb));
-  const f2 g_tn = sub2(mul2(gsn, q.cb), mul2(ghn, q.sb));
-  f2 g_hl = sub2(gsn, g_tn);
-  g_sig = sub2(g_sig, mul2(g_tn, q.beta));
-  // tn = t Q / Q': cotangents of t, Q and (minus) Q'
-  const f2 gtt = mul2(g_tn, q.tn);
-  const f2 g_t0 = mul2(mul2(g_tn, q.Q), q.iQp);
-  const f2 g_Q = mul2(gtt, q.iQ);
-  const f2 g_Qn = mul2(gtt, q.iQp);
-  f2 g_L = sub2(g_Q, g_Qn);
-  g_sig = fma2(F2(kPiF), g_Q, g_sig);
-  // sigma solves A_L(sigma) = C(sigma', r, L): d sigma/dC = 1/(2Q), d sigma/dL = -sigma/Q,
-  // dC/dsigma' = Q', dC/dr = -(pi r + L), dC/dL = 2(sigma' - r)
-  const f2 g_C2 = mul2(g_sig, q.iQ);  // twice the cotangent of C
-  g_L = sub2(g_L, mul2(g_C2, q.sig));
-  f2 g_sp = fma2(g_C2, q.Qp, mul2(F2(-kPiF), g_Qn));
-  f2 g_r = mul2(g_C2, P[P_NPR]);
-  g_L = fma2(g_C2, sub2(q.sp, P[P_R]), g_L);
-  // coverage alpha(z), z = (r - sigma') / w(r)
-  g_sp = sub2(g_sp, mul2(mua, P[P_IW]));
-  g_r = fma2(mua, sub2(P[P_IW], mul2(z, P[P_DLW])), g_r);
-  // t = L/2 + sigma' phi and sigma' = |(|s| - L/2, |h|)| on a cap; t = |s|, sigma' = |h| on the flank
-  g_hl = add2(g_hl, g_t0);
-  g_sp = fma2(g_t0, q.phi, g_sp);
-  const f2 g_d = fma2(g_sp, q.ud, mul2(g_t0, q.uh));
-  const f2 g_ah = sub2(mul2(g_sp, q.uh), mul2(g_t0, q.ud));
-  g_hl = sub2(g_hl, g_d);
-  g_L = fma2(F2(0.5f), g_hl, g_L);
-  const f2 GS = mul2(q.sgs, g_d), GH = mul2(q.sgh, g_ah);
-  const f2 nlx = sub2(mul2(GS, ex), mul2(GH, ey));
-  const f2 nly = fma2(GS, ey, mul2(GH, ex));
-  gcx = sub2(lamx, nlx);
-  gcy = sub2(lamy, nly);
-  // theta: the rotation about m without the cancellation of its two halves
-  // (theta_vjp_cap / theta_vjp_flank).  A flank step has sin beta = 0; the
-  // flank form is evaluated only when some pixel of the converged lanes needs it.
-  const f2 spm = mul2(q.sgs, q.sgh);
-  const f2 kc = mul2(mul2(P[P_L], q.dsp), q.iQp);
-  f2 inner = fma2(mul2(kc, F2(-1.0f)), sub2(mul2(ghn, q.sb), mul2(gsn, q.cb)), mul2(P[P_HL], sub2(ghn, g_ah)));
+  const f2 gcvn = mul2(mua, P[P_IW]);               // minus the coverage's cotangent of sigma'
+  // g . u(beta), g . u'(beta), g . u(phi), g . u'(phi)  (u(a) = (sin a, cos a), u' = (cos a, -sin a))
+  const f2 gu = fma2(gsn, q.sb, mul2(ghn, q.cb));
+  const f2 gup = sub2(mul2(gsn, q.cb), mul2(ghn, q.sb));
+  const f2 guf = fma2(gsn, q.ud, mul2(ghn, q.uh));
+  const f2 gufp = sub2(mul2(gsn, q.uh), mul2(ghn, q.ud));
+  const f2 sgL = mul2(sub2(q.dsp, P[P_R]), q.iQ);   // d sigma / dL
+  const f2 sgr = mul2(P[P_NPR], q.iQ);              // d sigma / dr
+  const f2 dspL = mul2(q.dsp, L);
+  const f2 sdphi = mul2(dspL, q.iQp);               // sigma delta_phi
+  const f2 room = sub2(q.phi, F2(0.5f * kPiF));
+  const f2 K = mul2(room, q.iQp);
+  // cap to cap: g . dD/dsigma' and g . dD/dphi
+  const f2 nsdsp = mul2(mul2(sdphi, room),
+                        fma2(F2(kPiF), add2(q.iQ, q.iQp), mul2(mul2(q.Qp, q.iQ), q.isg)));  // -sigma delta_sigma'
+  const f2 pdQ = mul2(mul2(F2(kPiF), q.dsp), q.iQ);
+  const f2 g_sp = sub2(fma2(pdQ, gu, sub2(gu, guf)), fma2(nsdsp, gup, gcvn));
+  const f2 g_ph = mul2(fma2(sub2(sdphi, q.dsp), gup, mul2(q.sp, sub2(gup, gufp))), q.isp);
+  f2 ws = fma2(q.ud, g_sp, mul2(q.uh, g_ph));
+  f2 wh = sub2(mul2(q.uh, g_sp), mul2(q.ud, g_ph));
+  // explicit L and r through sigma and delta
+  const f2 sdL = mul2(K, sub2(fma2(neg2(L), sgL, q.dsp), mul2(dspL, fma2(sgL, q.isg, q.iQp))));
+  const f2 nsdr = mul2(mul2(K, mul2(L, sgr)), mul2(q.sp, q.isg));  // -sigma delta_r
+  f2 gLm = fma2(F2(-0.5f), ws, fma2(sgL, gu, mul2(sdL, gup)));
+  f2 grm = sub2(mul2(sgr, gu), mul2(nsdr, gup));
+  f2 th = sub2(mul2(sdphi, gup), mul2(P[P_HL], wh));
   const bool fx = q.sb.x == 0.0f, fy = q.sb.y == 0.0f;
-  if (__any_sync(__activemask(), fx || fy)) {
+  if (__any_sync(__activemask(), fx || fy)) {  // flank to flank
     const f2 as = abs2(q.si);
+    const f2 pdQp = mul2(mul2(F2(kPiF), q.dsp), q.iQp);
     const f2 QQ = mul2(add2(q.Q, q.Qp), mul2(q.iQ, q.iQp));
-    const f2 b1 = mul2(q.dsp, fma2(mul2(F2(-kPiF * kPiF), mul2(as, as)), mul2(QQ, q.iQp), mul2(P[P_L], q.iQp)));
-    const f2 b2 = mul2(mul2(as, F2(-kPiF)), mul2(q.dsp, QQ));
-    const f2 fl = fma2(as, mul2(mua, P[P_IW]), fma2(gsn, b1, mul2(ghn, b2)));
-    inner = sel2(fx, fy, fl, inner);
+    const f2 pas = mul2(F2(kPiF), as);
+    const f2 wsf = mul2(neg2(gsn), pdQp);
+    const f2 whf = sub2(fma2(gsn, mul2(mul2(pas, pdQp), QQ), mul2(ghn, pdQ)), gcvn);
+    const f2 gLf = fma2(gsn, mul2(mul2(pas, fma2(q.dsp, q.iQp, sgL)), q.iQp), mul2(ghn, sgL));
+    const f2 grf = fma2(gsn, mul2(mul2(pas, sgr), q.iQp), mul2(ghn, sgr));
+    const f2 b1 = mul2(q.dsp, fma2(mul2(neg2(pas), pas), mul2(QQ, q.iQp), mul2(L, q.iQp)));
+    const f2 b2 = mul2(neg2(pas), mul2(q.dsp, QQ));
+    const f2 thf = fma2(as, gcvn, fma2(gsn, b1, mul2(ghn, b2)));
+    ws = sel2(fx, fy, wsf, ws);
+    wh = sel2(fx, fy, whf, wh);
+    gLm = sel2(fx, fy, gLf, gLm);
+    grm = sel2(fx, fy, grf, grm);
+    th = sel2(fx, fy, thf, th);
   }
-  gth = mul2(spm, inner);
-  gL = g_L;
-  gr = g_r;
-  lamx = nlx;
-  lamy = nly;
+  gth = mul2(mul2(q.sgs, q.sgh), th);
+  gL = gLm;
+  gr = fma2(mua, sub2(P[P_IW], mul2(z, P[P_DLW])), grm);
+  const f2 GS = mul2(q.sgs, ws), GH = mul2(q.sgh, wh);
+  const f2 dlx = sub2(mul2(GS, ex), mul2(GH, ey));
+  const f2 dly = fma2(GS, ey, mul2(GH, ex));
+  gcx = neg2(dlx);
+  gcy = neg2(dly);
+  lamx = add2(lamx, dlx);
+  lamy = add2(lamy, dly);
 }
 
 // Thread -> pixel pair of a 32 x 16 tile: column lane, rows 2 warp and 2 warp + 1.
@@ -698,7 +708,7 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
     __syncthreads();
     if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
     const int t = threadIdx.x;
-    if (t < cntc * 8) {
+    if (!QUEUE && t < cntc * 8) {  // the queueing pass only finds drifting pixels
       float sum = 0.0f;
 #pragma unroll
       for (int w = 0; w < kTileThreads / 32; ++w) sum += rb[w][t];
