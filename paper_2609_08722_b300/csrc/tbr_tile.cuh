@@ -419,6 +419,125 @@ __device__ bool hard_tile(ChunkRing<CH>& ring, const float* __restrict__ packed,
   return ok;
 }
 
+// Live-pixel state moved between threads by hard_tile_compact.
+struct HardLive {
+  float xh[kTileThreads], yh[kTileThreads], xl[kTileThreads], yl[kTileThreads];
+  int pix[kTileThreads];
+  int warp_base[kTileThreads / 32 + 1];
+};
+
+// hard_tile with CTA-wide compaction of the live pixels.  The chain of Eq.
+// chain stops at a different stroke for every pixel (a few hundred of 2000 on
+// average, all of them for background pixels), so a warp whose pixels mostly
+// finished would keep issuing for the few still alive.  After every chunk the
+// live pixels (position hi/lo and pixel index) are packed, in pixel order, into
+// the first threads of the CTA through shared memory; warps past the live count
+// then skip the chunk's strokes.  A pixel's colour and index are written when
+// it stops (or, for the background, after the last chunk).  Same arguments and
+// results as hard_tile; st is shared scratch.
+template <int CH, bool DROPS = false, bool COUPLED = false>
+__device__ bool hard_tile_compact(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, int tile, int W,
+                                  int H, const float bg[3], bool poison, float* __restrict__ out_rgb,
+                                  int* __restrict__ out_idx, HardLive& st, unsigned& band, unsigned& visited,
+                                  unsigned& background, unsigned long long* status) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int px, py;
+  tile_pixel(tile, W, px, py);
+  const bool valid = px < W && py < H;
+  int pix = valid ? py * W + px : -1;
+  bool alive = valid && !poison;
+  float xh = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
+  float yh = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
+  float xl = 0.0f, yl = 0.0f;
+  auto write = [&](int p, int hit) {
+    float c0 = bg[0], c1 = bg[1], c2 = bg[2];
+    if (hit >= 0) {
+      const float* R = packed + static_cast<size_t>(hit) * kRec;
+      c0 = R[F_CR]; c1 = R[F_CG]; c2 = R[F_CB];
+    }
+    out_rgb[3 * static_cast<size_t>(p) + 0] = c0;
+    out_rgb[3 * static_cast<size_t>(p) + 1] = c1;
+    out_rgb[3 * static_cast<size_t>(p) + 2] = c2;
+    if (out_idx) out_idx[p] = hit;
+  };
+  const int nch = (n + CH - 1) / CH;
+  auto chunk_src = [&](int q) { return packed + static_cast<size_t>(nch - 1 - q) * CH * kRec; };
+  auto chunk_cnt = [&](int q) { return min(CH, n - (nch - 1 - q) * CH); };
+  if (threadIdx.x == 0) {
+    if (nch > 0) ring.issue(0, chunk_src(0), chunk_cnt(0));
+    if (nch > 1) ring.issue(1, chunk_src(1), chunk_cnt(1));
+  }
+  bool ok = true;
+  int live = kTileThreads;  // threads [0, live) may hold a live pixel
+  for (int q = 0; q < nch; ++q) {
+    const int b = q & 1;
+    const bool got = ring.wait(b, status);
+    if (__syncthreads_or(!got)) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);
+      ok = false;
+      break;
+    }
+    const int base = (nch - 1 - q) * CH;
+    const int cnt = chunk_cnt(q);
+    const float* S0 = ring.data(b);
+    if (alive) {
+      for (int j = cnt - 1; j >= 0; --j) {
+        ++visited;
+        if (hard_step<DROPS, COUPLED>(xh, yh, xl, yl, S0 + j * kRec, band)) {
+          write(pix, base + j);
+          alive = false;
+          break;
+        }
+      }
+    }
+    // pack the live pixels into threads [0, live)
+    const unsigned m = __ballot_sync(0xffffffffu, alive);
+    if (lane == 0) st.warp_base[warp] = __popc(m);
+    __syncthreads();  // every thread is done with the chunk's records here
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int w = 0; w < kTileThreads / 32; ++w) {
+        const int c = st.warp_base[w];
+        st.warp_base[w] = acc;
+        acc += c;
+      }
+      st.warp_base[kTileThreads / 32] = acc;
+      if (acc > 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));
+    }
+    __syncthreads();
+    live = st.warp_base[kTileThreads / 32];
+    if (live == 0) {
+      if (q + 1 < nch) ring.wait(b ^ 1, status);  // drain the prefetched chunk
+      break;
+    }
+    if (alive) {
+      const int d = st.warp_base[warp] + __popc(m & ((1u << lane) - 1u));
+      st.xh[d] = xh; st.yh[d] = yh; st.xl[d] = xl; st.yl[d] = yl; st.pix[d] = pix;
+    }
+    __syncthreads();
+    alive = static_cast<int>(threadIdx.x) < live;
+    if (alive) {
+      const int t = threadIdx.x;
+      xh = st.xh[t]; yh = st.yh[t]; xl = st.xl[t]; yl = st.yl[t]; pix = st.pix[t];
+    }
+    __syncthreads();  // the state area is rewritten after the next chunk
+  }
+  if (alive && ok) {  // background: no footprint reached
+    write(pix, -1);
+    ++background;
+  }
+  if (poison || !ok) {  // values failed the checks, or a wait gave up: every pixel of the tile is NaN
+    __syncthreads();
+    if (valid) {
+      const size_t p = static_cast<size_t>(py) * W + px;
+      const float nan = __int_as_float(0x7fc00000);
+      out_rgb[3 * p + 0] = nan; out_rgb[3 * p + 1] = nan; out_rgb[3 * p + 2] = nan;
+      if (out_idx) out_idx[p] = -1;
+    }
+  }
+  return ok;
+}
+
 // d alpha path only (psi = id, inert-mark model): cotangent of sigma' pushed
 // back to (x, theta, L, r).
 __device__ __forceinline__ void inert_vjp(float s, float h, const StrokeF& g, float& sp_out, float& lamx,
