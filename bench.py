@@ -31,32 +31,43 @@ sys.path.insert(0, ROOT)
 N_STROKES, RES, PALETTE = 2000, 1024, 16
 CHECKPOINT_EVERY = 64
 
-# Algorithmic FP32 work per pixel-stroke (FP32 arithmetic instructions: add, mul
-# and fused multiply-add each count 1; transcendental / reciprocal operations are
-# counted separately), counted from the step formulas of the kernels at this
-# workload's measured branch mix (95% of steps on a capsule cap): forward =
-# frame + distance 9, coverage + compositing 11, radial root 7, tangential map
-# 7, back to world 6 (cap path); adjoint = Phi regeneration 31, coverage +
-# adjoint step 21, VJP of psi and alpha 61, reduce-scatter 9 (cap path).
-OPS_FWD = 40.6
-OPS_BWD = 120.8
-XU_FWD = 11.8
-XU_BWD = 15.7
-# Transfer renderer R_D, soft forward per pixel-stroke: capsule distance 9 +
-# coverage and compositing 11 + 16 drops x (centre 2, offset 4, rho^2 2,
-# sigma^2 1, step 3, update 2 = 14); XU: 16 x (sqrt + rcp) + 4.
-OPS_FWD_D = 9 + 11 + 16 * 14
-XU_FWD_D = 16 * 2 + 4
-# Coupling variant Phi_g, soft forward: the capsule forward plus the profile at
-# the point's v (angle 3, sine polynomial 6, cubic in w 3), the coupled C and
-# area 2, and the deposit boundary sigma_b 3; XU: sqrt and rcp of sigma_b.
-OPS_FWD_G = OPS_FWD + 17
-XU_FWD_G = XU_FWD + 2
-# FP32 lane peak: 148 SMs x 128 FP32 lanes x 2032 MHz (one op per lane per cycle);
-# XU (MUFU) peak: 16 results per clock per SM (4 per sub-partition).
+# Algorithmic work per unit, counted once from the FP64 oracle with a counting
+# scalar (oracle/count_ops.py writes the frozen file): FP32-pipe operations as
+# FLOPs (add, subtract, multiply = 1; the oracle writes no fused multiply-add)
+# and XU operations (sqrt, sin, cos, atan2, exp, log, reciprocal), per
+# pixel-stroke of the soft render and of the replay adjoint, and per visited
+# step of the hard render.
+OPCOUNT_PATH = os.path.join(ROOT, "profiles", "opcount_1024_2000.json")
+
+
+def load_opcounts():
+    with open(OPCOUNT_PATH) as f:
+        return json.load(f)
+
+
+# FP32 FLOP peak: 148 SMs x 128 FP32 lanes x 2 FLOP per fused multiply-add x
+# 2032 MHz; XU (MUFU) peak: 16 results per clock per SM (4 per sub-partition).
 SMS, LANES, SM_MAX_MHZ, XU_PER_SM = 148, 128, 2032.0, 16
-PEAK_GOPS = SMS * LANES * SM_MAX_MHZ * 1e-3
+PEAK_GFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e-3
 PEAK_XU_GOPS = SMS * XU_PER_SM * SM_MAX_MHZ * 1e-3
+PEAK_BASIS = "148 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2032 MHz (recipe unit counts and maximum clock)"
+XU_BASIS = "148 SMs x 16 MUFU results per clock x 2032 MHz"
+
+
+def alu_roofline(kernel, counts, units, ms):
+    """Roofline block of one ALU-bound kernel: the oracle's FLOPs and XU ops
+    per unit x units per launch / the launch's event-timed duration."""
+    f, x = counts["fp32"], counts["xu"]
+    ach = f * units / (ms * 1e-3) * 1e-9
+    xach = x * units / (ms * 1e-3) * 1e-9
+    return {"bound": "alu", "kernel": kernel, "achieved": ach, "peak": PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": ach / PEAK_GFLOPS, "ops_per_unit": f, "launch_ms": ms,
+            "xu": {"ops_per_unit": x, "achieved": xach, "peak": PEAK_XU_GOPS, "unit": "Gop/s",
+                   "frac": xach / PEAK_XU_GOPS, "peak_basis": XU_BASIS},
+            "combined_bound_frac": max(ach / PEAK_GFLOPS, xach / PEAK_XU_GOPS),
+            "peak_basis": PEAK_BASIS, "peak_kind": "derived (MEASURED_PEAKS has no FP32 figure)",
+            "ops_source": "profiles/opcount_1024_2000.json (FP64 oracle evaluated with a counting scalar)"}
+
 
 METRIC = "pixel·stroke evals/s fwd+adjoint @2000 strokes 1024²"
 
@@ -73,6 +84,8 @@ def parse_args():
     ap.add_argument("--fit-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hard", action="store_true", help="skip the hard-render resolution sweep")
+    ap.add_argument("--no-memory", action="store_true",
+                    help="skip the peak-memory comparison (checkpoint sweep and checkpointed AD)")
     ap.add_argument("--serve-requests", type=int, default=200,
                     help="requests of the serving stream (0 skips the serving measurement)")
     ap.add_argument("--res", type=int, default=RES, help="square resolution (profiling cases only)")
@@ -250,6 +263,83 @@ def oracle_compensate_ms(prog):
     return out
 
 
+# ---------------------------------------------------------------------------
+# peak device memory of the replay adjoint against checkpointed AD (Sec. 5.2)
+# ---------------------------------------------------------------------------
+def pool_used(high=True, reset=False):
+    """Bytes in use in the device's default stream-ordered pool, in which the
+    library allocates its contexts: the high-water mark (optionally reset to
+    the current use first), or the current use."""
+    import torch
+    from cuda.bindings import runtime as rt
+    err, pool = rt.cudaDeviceGetDefaultMemPool(torch.cuda.current_device())
+    if err != rt.cudaError_t.cudaSuccess:
+        return None
+    attr = rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemHigh if high else rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent
+    if reset:
+        from cuda.bindings import driver
+        rt.cudaMemPoolSetAttribute(pool, attr, driver.cuuint64_t(0))
+    err, v = rt.cudaMemPoolGetAttribute(pool, attr)
+    return int(v) if err == rt.cudaError_t.cudaSuccess else None
+
+
+def adjoint_memory(prog, target, W, H, tau, tau_min, sweep=(32, 64, 128, 256), ad_segment=20):
+    """Peak device memory and time of one loss + gradient step: the replay
+    adjoint at each checkpoint interval k (library pool high-water + torch
+    tensors), and autograd with a checkpoint every ``ad_segment`` strokes
+    (torch's peak).  Each step starts from freed memory."""
+    import torch
+
+    from paper_2609_08722_b300 import ad_baseline, tbr
+    out = {"replay": [], "stored_state_bytes": 12 * W * H * prog.n}
+    for k in sweep:
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        pool_base = pool_used(high=False)
+        pool_used(reset=True)
+        torch.cuda.reset_peak_memory_stats()
+        t_base = torch.cuda.memory_allocated()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rgb, ctx = tbr.render_soft(prog, W, H, tau, tau_min, record=True, checkpoint_every=k)
+        _, dL = tbr.loss_mse(rgb, target)
+        ctx.backward(dL)
+        e1.record()
+        torch.cuda.synchronize()
+        pool = pool_used()
+        pool = None if pool is None or pool_base is None else pool - pool_base
+        torch_peak = torch.cuda.max_memory_allocated() - t_base
+        st = ctx.status()
+        out["replay"].append({"checkpoint_every": k, "context_bytes": ctx.nbytes(), "pool_peak_bytes": pool,
+                              "torch_peak_bytes": torch_peak,
+                              "peak_bytes": (pool or 0) + torch_peak, "ms_first_call": e0.elapsed_time(e1),
+                              "max_records": st["max_records"]})
+        ctx.destroy()
+        del rgb, dL, ctx
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+    class _P:
+        pass
+    ap = _P()
+    for name in ("cx", "cy", "theta", "length", "half_width", "logits", "palette"):
+        setattr(ap, name, getattr(prog, name))
+    ap.background = torch.tensor(prog.background, dtype=torch.float32, device=target.device)
+    ap.color_temp = float(prog.color_temp)
+    torch.cuda.reset_peak_memory_stats()
+    t_base = torch.cuda.memory_allocated()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    loss, _ = ad_baseline.mse_step(ap, target, W, H, tau, tau_min, segment=ad_segment)
+    e1.record()
+    torch.cuda.synchronize()
+    out["checkpointed_ad"] = {"segment": ad_segment, "peak_bytes": torch.cuda.max_memory_allocated() - t_base,
+                              "ms": e0.elapsed_time(e1), "loss": float(loss),
+                              "impl": "PyTorch autograd, torch.utils.checkpoint every 20 strokes, FP32"}
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     """--impl reference: the oracle as the reference arm (rank 0 only)."""
     rank, world, _ = dist_env()
@@ -364,16 +454,15 @@ def run_native(args):
     memory = {"replay_context_bytes": ctx.nbytes(),
               "side_table_records_per_pixel": st["records"] / P,
               "checkpoint_every": CHECKPOINT_EVERY,
-              "stored_state_bytes": 12 * P * prog.n,
-              "checkpointed_ad_every_20_states_bytes": 12 * P * -(-prog.n // 20)}
+              "stored_state_bytes": 12 * P * prog.n}
 
     units = float(P) * prog.n
     step_ms_max, value = whole_job_rate(units, step_ms, world, device)
 
     # roofline of the dominant kernel (replay adjoint), timed with events on its stream
+    opc = load_opcounts()
     bl, bt = kernel_ms["backward"]
     bwd_ms = bt / max(bl, 1)
-    achieved = OPS_BWD * units / (bwd_ms * 1e-3) * 1e-9
     sl, stt = kernel_ms["soft"]
     soft_ms = stt / max(sl, 1)
     traffic = None
@@ -385,6 +474,9 @@ def run_native(args):
                 traffic = tr.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
+    roofline = alu_roofline("k_backward2 (replay adjoint)", opc["capsule"]["adjoint"], units, bwd_ms)
+    roofline["traffic"] = traffic
+    soft_roofline = alu_roofline("k_soft (soft forward + record)", opc["capsule"]["soft_forward"], units, soft_ms)
 
     # e2e through the public API with host buffers: upload program + target from
     # pinned memory, fwd + loss + adjoint, read back gradients and loss
@@ -483,10 +575,14 @@ def run_native(args):
                 torch.cuda.synchronize()
                 ts.append(hs.elapsed_time(he))
             hms = sum(ts) / len(ts)
+            rl = alu_roofline("k_hard", opc["capsule"]["hard_per_visited_step"], st_h["visited_steps"], hms)
             hard.append({"res": r, "ms": hms, "nominal_evals_per_s": r * r * hp.n / (hms * 1e-3),
                          "executed_evals_per_s": st_h["visited_steps"] / (hms * 1e-3),
                          "visited_steps_per_pixel": st_h["visited_steps"] / (r * r),
-                         "fp64_band_steps": st_h["band_steps"], "background_pixels": st_h["background_pixels"]})
+                         "fp64_band_steps": st_h["band_steps"], "background_pixels": st_h["background_pixels"],
+                         "roofline": {k: rl[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
+                                                         "combined_bound_frac")}
+                         | {"xu_frac": rl["xu"]["frac"], "unit_of_work": "visited step"}})
             del rgb_h, idx_h
 
     def timed(fn, reps=3):
@@ -509,13 +605,12 @@ def run_native(args):
         idx_d = torch.empty((H, W), dtype=torch.int32, device=device)
         soft_d = timed(lambda: tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb_d, transport="drops"))
         hard_d = timed(lambda: tbr.render_hard(prog, W, H, out_rgb=rgb_d, out_idx=idx_d, transport="drops"))
-        ach = OPS_FWD_D * units / (soft_d * 1e-3) * 1e-9
+        rl = alu_roofline("k_soft (R_D)", opc["drops"]["soft_forward"], units, soft_d)
         transfer = {"workload": "R_D (sixteen-drop transport) soft forward and hard render of the same program",
                     "soft_forward_ms": soft_d, "soft_evals_per_s": units / (soft_d * 1e-3),
                     "hard_ms": hard_d,
-                    "soft_roofline": {"ops_per_unit": OPS_FWD_D, "achieved": ach, "frac": ach / PEAK_GOPS,
-                                      "xu_ops_per_unit": XU_FWD_D,
-                                      "xu_frac": XU_FWD_D * units / (soft_d * 1e-3) * 1e-9 / PEAK_XU_GOPS}}
+                    "soft_roofline": {k: rl[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
+                                                         "combined_bound_frac")} | {"xu_frac": rl["xu"]["frac"]}}
         del rgb_d, idx_d
 
     # coupling variant Phi_g (seeded profiles) on the same program: soft forward
@@ -544,7 +639,9 @@ def run_native(args):
 
         step_g = timed(coupled_step)
         cctx.destroy()
-        ach = OPS_FWD_G * units / (soft_g * 1e-3) * 1e-9
+        rl = alu_roofline("k_soft (Phi_g)", opc["coupled"]["soft_forward"], units, soft_g)
+        both = {k: opc["coupled"]["soft_forward"][k] + opc["coupled"]["adjoint"][k] for k in ("fp32", "xu")}
+        rla = alu_roofline("Phi_g soft forward + replay adjoint step", both, units, step_g)
         coupling = {"workload": "Phi_g (profiles c_1 in [0, 0.4], |c_2| <= 0.15, |c_3| <= 0.1, seed 403) soft "
                                 "forward and hard render of the same program",
                     "soft_forward_ms": soft_g, "soft_evals_per_s": units / (soft_g * 1e-3),
@@ -552,9 +649,10 @@ def run_native(args):
                     "capsule_soft_forward_early_exit_ms": soft_x,
                     "fwd_adjoint_step_ms": step_g, "fwd_adjoint_evals_per_s": units / (step_g * 1e-3),
                     "early_exit": "forward-only capsule render stopping each pixel once T < 1e-12",
-                    "soft_roofline": {"ops_per_unit": OPS_FWD_G, "achieved": ach, "frac": ach / PEAK_GOPS,
-                                      "xu_ops_per_unit": XU_FWD_G,
-                                      "xu_frac": XU_FWD_G * units / (soft_g * 1e-3) * 1e-9 / PEAK_XU_GOPS}}
+                    "soft_roofline": {k: rl[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
+                                                         "combined_bound_frac")} | {"xu_frac": rl["xu"]["frac"]},
+                    "fwd_adjoint_step_roofline": {k: rla[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
+                                                                      "combined_bound_frac")}}
         del rgb_g, idx_g, dpg
 
     # one-pass closed-form compensation of the same program (anchor and endpoint
@@ -585,6 +683,9 @@ def run_native(args):
             comp["cpu_oracle_ms"] = oracle_compensate_ms(prog_h)
         cpu["forward_rates"] = oracle_forward_rates(prog_h, inputs.resolution_program())
 
+    if rank == 0 and not args.no_memory and args.res == RES and args.strokes == N_STROKES:
+        memory.update(adjoint_memory(prog, target, W, H, tau, tau_min))
+
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0 and args.res == RES and args.strokes == N_STROKES:
         from paper_2609_08722_b300 import serve_bench
@@ -607,15 +708,8 @@ def run_native(args):
                        "target": "hard render of a second seeded 2000-stroke program",
                        "l2": "flushed between timed steps (256 MB write); step working set > L2",
                        "parallelism": f"independent program per GPU x{world}"},
-            "roofline": {"bound": "alu", "kernel": "k_backward (replay adjoint)", "achieved": achieved,
-                         "peak": PEAK_GOPS, "unit": "Gop/s", "frac": achieved / PEAK_GOPS,
-                         "traffic": traffic, "ops_per_unit": OPS_BWD,
-                         "xu": {"ops_per_unit": XU_BWD, "achieved": XU_BWD * units / (bwd_ms * 1e-3) * 1e-9,
-                                "peak": PEAK_XU_GOPS, "frac": XU_BWD * units / (bwd_ms * 1e-3) * 1e-9 / PEAK_XU_GOPS,
-                                "peak_basis": "148 SMs x 16 MUFU results per clock x 2032 MHz"},
-                         "combined_bound_frac": max(OPS_BWD / PEAK_GOPS, XU_BWD / PEAK_XU_GOPS) * units * 1e-9
-                                                / (bwd_ms * 1e-3),
-                         "peak_basis": "148 SMs x 128 FP32 lanes x 2032 MHz (recipe unit counts and clock)"},
+            "roofline": roofline,
+            "soft_forward_roofline": soft_roofline,
             "kernel_ms": {"backward": bwd_ms, "soft_forward": soft_ms,
                           "other": step_ms - bwd_ms - soft_ms},
             "fit_step_ms": fit_ms,
