@@ -376,6 +376,7 @@ typedef struct {
   int32_t checkpoint_every;  /* soft requests: checkpoint interval (64) */
   int32_t record_capacity;   /* soft requests: side-table records per pixel (64) */
   int32_t idle_exit_us;      /* persistent kernel idle exit (2000 us) */
+  int32_t ready_wait_us;     /* longest device wait for a request's ready word (1000000 us), see tbr_request */
 } tbr_serve_config;
 
 enum {
@@ -402,6 +403,16 @@ typedef struct {
   int32_t edit_start;        /* first stroke affected / insertion index */
   int32_t insert_palette;    /* insert: palette entry of the new stroke (logits 6 * onehot) */
   float insert_stroke[5];    /* insert: cx, cy, theta, length, half_width */
+  /* Optional (NULL: none): a word in device or host-mapped memory that the
+   * request's producer sets to nonzero once the inputs (target) and the output
+   * buffers may be used, for producers outside the stream order of `stream`
+   * (another process, a host thread, a copy engine the caller drives).  Each of
+   * the request's work items waits for it on the device, at most
+   * ready_wait_us; if the wait runs out the request completes without
+   * rendering (a hard request leaves its outputs untouched, a soft request
+   * writes NaN loss and gradients) and tbr_serve_poll / tbr_serve_wait report
+   * TBR_ERR_TIMEOUT.  The server stays usable. */
+  const volatile int32_t* ready;
 } tbr_request;
 
 typedef struct {

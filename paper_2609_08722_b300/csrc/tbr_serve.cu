@@ -225,6 +225,8 @@ tbr_status admit(tbr_server* s, Request& q) {
   d.packed = q.packed; d.out_rgb = r.out_rgb; d.out_idx = soft ? nullptr : r.out_idx; d.target = r.target;
   d.partial = q.partial; d.loss_part = q.loss_part; d.probs = q.probs; d.palette = pg.palette;
   d.grad8 = q.grad8; d.out_grad = r.out_grad; d.out_loss = r.out_loss; d.status = q.status;
+  d.ready = reinterpret_cast<const volatile int*>(r.ready);
+  d.ready_wait_ns = static_cast<unsigned long long>(s->cfg.ready_wait_us) * 1000ull;
   e = cudaMemcpyAsync(s->ring_dev + (q.seq % kServeRing), &d, sizeof(ServeDesc), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q.staged, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventRecord(q.staged, st);
@@ -397,6 +399,7 @@ void tbr_serve_default_config(tbr_serve_config* c) {
   c->checkpoint_every = 64;
   c->record_capacity = 64;
   c->idle_exit_us = 2000;
+  c->ready_wait_us = 1000000;
 }
 
 tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** out) {
@@ -405,7 +408,7 @@ tbr_status tbr_serve_create(const tbr_serve_config* cfg, tbr_server** out) {
   tbr_serve_config c;
   if (cfg) c = *cfg; else tbr_serve_default_config(&c);
   if (c.max_inflight < 1 || c.max_inflight > kServeMaxSlots || c.max_strokes < 1 || c.checkpoint_every < 1 ||
-      c.record_capacity < 1 || c.idle_exit_us < 1)
+      c.record_capacity < 1 || c.idle_exit_us < 1 || c.ready_wait_us < 0)
     return fail(TBR_ERR_INVALID_ARG, "invalid serving configuration");
   tbr_server* s = new tbr_server();
   s->cfg = c;

@@ -32,6 +32,8 @@ struct ServeDesc {
   float* out_grad;         // soft: [5n + nk] (cx, cy, theta, length, half_width, logits)
   float* out_loss;         // soft: device scalar or NULL
   unsigned long long* status;  // [ST_COUNT]
+  const volatile int* ready;   // NULL, or the word each item waits for (nonzero = go)
+  unsigned long long ready_wait_ns;
 };
 
 // Control block in mapped pinned memory.

@@ -119,7 +119,37 @@ __global__ void __launch_bounds__(kTileThreads, 3) k_serve(ServeArgs a) {
     const ServeDesc& d = sd;
     const long long local = item - d.item_base;
     bool ok = true;
-    if (d.kind == kServeHard) {
+    // the request's ready word (if any): thread 0 waits for it, at most
+    // ready_wait_ns; a request that already timed out skips the wait and the work
+    if (threadIdx.x == 0) {
+      int go = 1;
+      if (d.ready) {
+        go = d.status[ST_TIMEOUT] == 0ull ? 1 : 0;
+        if (go && *d.ready == 0) {
+          const uint64_t t0 = global_timer_ns();
+          unsigned backoff = 64;
+          while (*d.ready == 0) {
+            if (global_timer_ns() - t0 > d.ready_wait_ns) {
+              atomicAdd(d.status + ST_TIMEOUT, 1ull);
+              go = 0;
+              break;
+            }
+            __nanosleep(backoff);
+            backoff = min(backoff * 2u, 4096u);
+          }
+        }
+        __threadfence();  // inputs written before the ready word are seen after it
+      }
+      s_last = go;
+    }
+    __syncthreads();
+    const bool run_item = s_last != 0;
+    __syncthreads();  // s_last is reused at completion
+    if (!run_item) {
+      // nothing of the item is computed; its status reports the timeout (a soft
+      // request's loss part is poisoned, so its loss and gradients come out NaN)
+      if (d.kind != kServeHard && threadIdx.x == 0) d.loss_part[local] = __longlong_as_double(0x7ff8000000000000ll);
+    } else if (d.kind == kServeHard) {
       const bool poison = d.status[ST_INVALID] != 0ull;
       unsigned band = 0, visited = 0;
       bool background = false;

@@ -537,7 +537,8 @@ REQ_HARD, REQ_SOFT_ADJOINT, REQ_RECOLOUR, REQ_REORDER, REQ_INSERT = 0, 1, 2, 3, 
 class TbrServeConfig(ctypes.Structure):
     _fields_ = [("memory_cap_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int32),
                 ("max_strokes", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("record_capacity", ctypes.c_int32), ("idle_exit_us", ctypes.c_int32)]
+                ("record_capacity", ctypes.c_int32), ("idle_exit_us", ctypes.c_int32),
+                ("ready_wait_us", ctypes.c_int32)]
 
 
 class TbrRequest(ctypes.Structure):
@@ -547,7 +548,7 @@ class TbrRequest(ctypes.Structure):
                 ("out_rgb", ctypes.c_void_p), ("out_idx", ctypes.c_void_p), ("out_loss", ctypes.c_void_p),
                 ("out_grad", ctypes.c_void_p), ("edit_a", ctypes.c_int32), ("edit_b", ctypes.c_int32),
                 ("edit_start", ctypes.c_int32), ("insert_palette", ctypes.c_int32),
-                ("insert_stroke", ctypes.c_float * 5)]
+                ("insert_stroke", ctypes.c_float * 5), ("ready", ctypes.c_void_p)]
 
 
 class TbrServeCounters(ctypes.Structure):
@@ -610,7 +611,10 @@ class Server:
 
     def submit(self, kind: int, program: int, W: int, H: int, out_rgb=None, out_idx=None, target=None,
                out_loss=None, out_grad=None, tau=0.0, tau_min=1.0, snap=False, edit_a=0, edit_b=0,
-               edit_start=0, insert_palette=0, insert_stroke=(0.5, 0.5, 0.0, 0.0, 0.05), stream=None) -> int:
+               edit_start=0, insert_palette=0, insert_stroke=(0.5, 0.5, 0.0, 0.0, 0.05), stream=None,
+               ready=None) -> int:
+        """ready: optional int32 tensor (device memory) whose first word the
+        request's work items wait to become nonzero (tbr_request.ready)."""
         r = TbrRequest()
         r.kind, r.program, r.W, r.H, r.n_prefix, r.snap = kind, program, W, H, -1, int(bool(snap))
         r.tau, r.tau_min = float(tau), float(tau_min)
@@ -618,11 +622,14 @@ class Server:
         r.out_loss, r.out_grad = _ptr(out_loss), _ptr(out_grad)
         r.edit_a, r.edit_b, r.edit_start, r.insert_palette = edit_a, edit_b, edit_start, insert_palette
         r.insert_stroke = (ctypes.c_float * 5)(*[float(v) for v in insert_stroke])
+        if ready is not None and ready.dtype != torch.int32:
+            raise TypeError("ready must be an int32 tensor")
+        r.ready = _ptr(ready)
         rid = ctypes.c_uint64()
         check(_serve_lib().tbr_serve_submit(ctypes.c_void_p(self.handle), ctypes.byref(r), ctypes.byref(rid),
                                             _stream(stream)))
         # keep the caller's buffers alive until the request is released
-        self._keep[int(rid.value)] = (target, out_rgb, out_idx, out_loss, out_grad)
+        self._keep[int(rid.value)] = (target, out_rgb, out_idx, out_loss, out_grad, ready)
         return int(rid.value)
 
     def poll(self, rid: int) -> tuple[bool, int]:

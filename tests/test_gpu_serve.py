@@ -35,6 +35,38 @@ def programs():
     return hs, [tbr.DeviceProgram.from_host(h) for h in hs]
 
 
+class MappedWord:
+    """One int32 in mapped pinned host memory (cudaHostAllocMapped): the host
+    writes it, kernels read it through its device address."""
+
+    def __init__(self):
+        from cuda.bindings import runtime as rt
+        self.rt = rt
+        err, self.host = rt.cudaHostAlloc(4, rt.cudaHostAllocMapped)
+        assert err == rt.cudaError_t.cudaSuccess
+        err, self.dev = rt.cudaHostGetDevicePointer(self.host, 0)
+        assert err == rt.cudaError_t.cudaSuccess
+        self.set(0)
+
+    def set(self, v):
+        import ctypes
+        ctypes.c_int32.from_address(int(self.host)).value = v
+
+    def device_view(self):
+        class _View:  # what Server.submit needs of a ready tensor
+            dtype = torch.int32
+
+            def __init__(self, ptr):
+                self._p = ptr
+
+            def data_ptr(self):
+                return self._p
+        return _View(int(self.dev))
+
+    def free(self):
+        self.rt.cudaFreeHost(self.host)
+
+
 def hard_request(server, pid, W, H):
     rgb = torch.full((H, W, 3), float("nan"), device="cuda")
     idx = torch.full((H, W), -7, dtype=torch.int32, device="cuda")
@@ -195,3 +227,53 @@ def test_kernel_relaunches_after_idle(server, programs):
     ref_rgb, ref_idx, _ = tbr.render_hard(ds[0], 64, 64)
     torch.cuda.synchronize()
     assert torch.equal(idx, ref_idx)
+
+
+def test_ready_word_wait_runs_out_and_the_server_stays_usable(programs):
+    """A request whose ready word is never set: every item's bounded device wait
+    gives up after ready_wait_us, the request completes with TBR_ERR_TIMEOUT and
+    leaves its outputs untouched, and the server goes on serving: a request
+    whose word is set later (before the limit) and one without a word render
+    the plain path's result.  No GPU fault or trap is involved: the wait is a
+    polled loop on the device clock that returns a status."""
+    hs, dps = programs
+    s = tbr.Server(tbr.default_serve_config(max_strokes=4096, ready_wait_us=3000))
+    try:
+        pid = s.load_program(dps[1])
+        W, H = 96, 64
+        never = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rgb0 = torch.full((H, W, 3), float("nan"), device="cuda")
+        idx0 = torch.full((H, W), -7, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        r0 = s.submit(tbr.REQ_HARD, pid, W, H, out_rgb=rgb0, out_idx=idx0, ready=never)
+        assert s.wait(r0) == tbr.TBR_ERR_TIMEOUT
+        assert torch.isnan(rgb0).all() and (idx0 == -7).all()
+        t = torch.full((H, W, 3), 0.5, device="cuda")
+        r0s = s.submit(tbr.REQ_SOFT_ADJOINT, pid, W, H, target=t, out_loss=torch.zeros(1, device="cuda"),
+                       out_grad=torch.zeros(5 * hs[1].n + hs[1].n * hs[1].k, device="cuda"), ready=never)
+        assert s.wait(r0s) == tbr.TBR_ERR_TIMEOUT
+        # set later by a host thread writing mapped pinned memory while the
+        # request waits (limit raised for it): the producer outside stream order
+        s2 = tbr.Server(tbr.default_serve_config(max_strokes=4096, ready_wait_us=2000000))
+        word = MappedWord()
+        try:
+            pid2 = s2.load_program(dps[1])
+            rgb = torch.full((H, W, 3), float("nan"), device="cuda")
+            idx = torch.full((H, W), -7, dtype=torch.int32, device="cuda")
+            torch.cuda.synchronize()
+            rid = s2.submit(tbr.REQ_HARD, pid2, W, H, out_rgb=rgb, out_idx=idx, ready=word.device_view())
+            time.sleep(0.05)
+            word.set(1)
+            assert s2.wait(rid) == tbr.TBR_OK
+            ref_rgb, ref_idx, _ = tbr.render_hard(dps[1], W, H)
+            assert torch.equal(idx, ref_idx) and torch.equal(rgb, ref_rgb)
+        finally:
+            s2.destroy()
+            word.free()
+        # the first server still serves
+        rid, rgb, idx = hard_request(s, pid, W, H)
+        assert s.wait(rid) == tbr.TBR_OK
+        ref_rgb, ref_idx, _ = tbr.render_hard(dps[1], W, H)
+        assert torch.equal(idx, ref_idx) and torch.equal(rgb, ref_rgb)
+    finally:
+        s.destroy()
