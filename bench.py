@@ -283,10 +283,11 @@ def pool_used(high=True, reset=False):
     return int(v) if err == rt.cudaError_t.cudaSuccess else None
 
 
-def adjoint_memory(prog, target, W, H, tau, tau_min, sweep=(32, 64, 128, 256), ad_segment=20):
+def adjoint_memory(prog, target, W, H, tau, tau_min, record_capacity, sweep=(32, 64, 128, 256), ad_segment=20):
     """Peak device memory and time of one loss + gradient step: the replay
     adjoint at each checkpoint interval k (library pool high-water + torch
-    tensors), and autograd with a checkpoint every ``ad_segment`` strokes
+    tensors) with the side table sized to ``record_capacity`` records per
+    pixel, and autograd with a checkpoint every ``ad_segment`` strokes
     (torch's peak).  Each step starts from freed memory."""
     import torch
 
@@ -301,7 +302,8 @@ def adjoint_memory(prog, target, W, H, tau, tau_min, sweep=(32, 64, 128, 256), a
         t_base = torch.cuda.memory_allocated()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        rgb, ctx = tbr.render_soft(prog, W, H, tau, tau_min, record=True, checkpoint_every=k)
+        rgb, ctx = tbr.render_soft(prog, W, H, tau, tau_min, record=True, checkpoint_every=k,
+                                   record_capacity=record_capacity)
         _, dL = tbr.loss_mse(rgb, target)
         ctx.backward(dL)
         e1.record()
@@ -310,7 +312,8 @@ def adjoint_memory(prog, target, W, H, tau, tau_min, sweep=(32, 64, 128, 256), a
         pool = None if pool is None or pool_base is None else pool - pool_base
         torch_peak = torch.cuda.max_memory_allocated() - t_base
         st = ctx.status()
-        out["replay"].append({"checkpoint_every": k, "context_bytes": ctx.nbytes(), "pool_peak_bytes": pool,
+        out["replay"].append({"checkpoint_every": k, "record_capacity": record_capacity,
+                              "context_bytes": ctx.nbytes(), "pool_peak_bytes": pool,
                               "torch_peak_bytes": torch_peak,
                               "peak_bytes": (pool or 0) + torch_peak, "ms_first_call": e0.elapsed_time(e1),
                               "max_records": st["max_records"]})
@@ -684,7 +687,8 @@ def run_native(args):
         cpu["forward_rates"] = oracle_forward_rates(prog_h, inputs.resolution_program())
 
     if rank == 0 and not args.no_memory and args.res == RES and args.strokes == N_STROKES:
-        memory.update(adjoint_memory(prog, target, W, H, tau, tau_min))
+        # side table sized to the program: the measured largest record count rounded up to 8
+        memory.update(adjoint_memory(prog, target, W, H, tau, tau_min, record_capacity=8 * (st["max_records"] // 8 + 1)))
 
     serve = None
     if rank == 0 and world == 1 and args.serve_requests > 0 and args.res == RES and args.strokes == N_STROKES:

@@ -136,8 +136,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
     float lC[2][3];
     load_pair(a, px, py0, skip, valid, off, st, lC);
     const unsigned drift0 = drift;
-    if (!backward_tile2<CH, QUEUE>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first,
-                                   drift, status))
+    // two strokes per loop iteration let the compiler overlap their independent work
+    if (!backward_tile2<CH, QUEUE, 2>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first,
+                                      drift, status))
       break;
     if (!QUEUE && a.tile_drift && __syncthreads_or(drift != drift0) && threadIdx.x == 0) a.tile_drift[tile] = 1;
     first = false;

@@ -653,7 +653,7 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
 // that segment, to rv.repair_list (off[c] is then the pixel index) for the
 // FP64 repair pass.  All threads of the CTA must call it.  Returns false if a
 // bounded wait gave up.
-template <int CH, bool QUEUE>
+template <int CH, bool QUEUE, int UNROLL = 1>
 __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, const bool (&valid)[2],
                                const PixelState (&st)[2], const float (&lC)[2][3], const float bg[3],
                                const RecordView& rv, const size_t (&off)[2], f2* __restrict__ pbuf,
@@ -687,6 +687,7 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
     pair_records_fill<false>(S0, cntc, pbuf, nullptr);
     __syncthreads();
     float (*rb)[CH * 8] = red[b];
+#pragma unroll UNROLL
     for (int j = 0; j < cntc; ++j) {
       const int i1 = q * CH + j + 1;
       float vv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};

@@ -19,7 +19,7 @@ namespace tbr {
 
 namespace {
 
-constexpr int kSoftCH = 64;
+constexpr int kSoftCH = 128;
 
 template <int CH, bool RECORD, bool INERT, bool DROPS, bool COUPLED, bool EXIT>
 __device__ __forceinline__ void soft_body(const SoftArgs& a) {

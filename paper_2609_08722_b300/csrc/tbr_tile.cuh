@@ -89,6 +89,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
     const int cntc = chunk_cnt(q);
     const float* S0 = ring.data(b);
     if (live) {
+#pragma unroll 4
       for (int j = cntc - 1; j >= 0; --j) {
         const int i1 = base + j + 1;  // the paper's 1-based stroke index
         if (RECORD && i1 == next_ck) {
@@ -189,9 +190,10 @@ __device__ __forceinline__ FrameF64 frame_f64(const float* __restrict__ S) {
 // Membership test and psi (Eq. back) recomputed in FP64 from the hi/lo
 // position, used where |sigma' - r| < kBand (|sigma' - sigma_b(v)| for the
 // coupling variant, whose membership is A_L(sigma') <= A_L(r) g(v), i.e. C <= 0).
-// Returns true if the point is inside.
+// Returns true if the point is inside.  Inlined: as a called function, the
+// register saves around the call ran on every step of the hard render's loop.
 template <bool COUPLED = false>
-static __device__ __noinline__ bool hard_step_f64(float& xh, float& yh, float& xl, float& yl,
+static __device__ __forceinline__ bool hard_step_f64(float& xh, float& yh, float& xl, float& yl,
                                            const float* __restrict__ S) {
   const FrameF64 f = frame_f64(S);
   const double mx = f.mx, my = f.my, ex = f.ex, ey = f.ey, hl = f.hl, r = f.r;
@@ -481,6 +483,7 @@ __device__ bool hard_tile_compact(ChunkRing<CH>& ring, const float* __restrict__
     const int cnt = chunk_cnt(q);
     const float* S0 = ring.data(b);
     if (alive) {
+#pragma unroll 4
       for (int j = cnt - 1; j >= 0; --j) {
         ++visited;
         if (hard_step<DROPS, COUPLED>(xh, yh, xl, yl, S0 + j * kRec, band)) {
