@@ -630,7 +630,7 @@ def run_native(args):
         soft_g = timed(lambda: tbr.render_soft(dpg, W, H, tau, tau_min, out_rgb=rgb_g))
         hard_g = timed(lambda: tbr.render_hard(dpg, W, H, out_rgb=rgb_g, out_idx=idx_g))
         # the coupled fwd + adjoint step (record, MSE seed, replay adjoint with
-        # dual-number local Jacobians) against the same target
+        # the hand-derived step VJP) against the same target
         _, cctx = tbr.render_soft(dpg, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
                                   out_rgb=rgb_g)
 

@@ -4,16 +4,15 @@
 //   x_i = Phi_g,i(x_{i-1}) in FP32 displacement form, or the side-table record
 //   where the forward's floor bound, or the position checkpoint;
 //   log T_i from the coverage of the deposit {u <= A_L(r) g(v)};
-//   the adjoint step with the local Jacobians of psi_g and of the coverage,
-//   taken by forward-mode dual numbers (tbr_dual.cuh) instead of the capsule
-//   kernels' hand-derived VJP.
+//   the adjoint step as the hand-derived reverse product of psi_g's
+//   displacement and of the coverage (tbr_coupled_vjp.cuh).
 // One pixel per thread on the persistent grid of 32x8 tiles, strokes streamed
 // first to last through the shared-memory ring; the 8 per-stroke gradient
 // values go through the same warp reduce-scatter and CTA slice as the other
 // adjoints, so the epilogue's fixed-order sum applies unchanged.
 #include <math.h>
 
-#include "tbr_dual.cuh"
+#include "tbr_coupled_vjp.cuh"
 #include "tbr_tile.cuh"
 
 namespace tbr {
@@ -99,24 +98,25 @@ __device__ bool backward_tile_coupled(ChunkRing<CH>& ring, const float* __restri
             xh = c.x; yh = c.y; xl = c.z; yl = c.w;
           }
         }
-        CoupledJac J;
-        coupled_jac(xh, yh, xl, yl, S, J);
-        if (at_ck) lt = rv.ck_lt[cko]; else lt += J.sp2;  // log T_i = log T_{i-1} - log(1 - alpha_i)
-        const float T = ex2_a(lt);
-        const float mu = T * (lCc - lT);
-        const float Ta = T * J.alpha;
+        // Eq. adjstep / Eq. adjparam: G = d/d(x, theta, L, r) of lambda^x . disp + mu alpha,
+        // mu = T_i (lC . c - lambda^T); log T_i = log T_{i-1} - log(1 - alpha_i)
+        float G[5], alpha, oma, T = 0.0f;
+        coupled_vjp(xh, yh, xl, yl, S,
+                    [&](float, float, float sp2, float& sx, float& sy, float& smu) {
+                      if (at_ck) lt = rv.ck_lt[cko]; else lt += sp2;
+                      T = ex2_a(lt);
+                      sx = lx;
+                      sy = ly;
+                      smu = T * (lCc - lT);
+                    },
+                    G, alpha, oma);
+        const float Ta = T * alpha;
         v5 = lC0 * Ta; v6 = lC1 * Ta; v7 = lC2 * Ta;
-        // Eq. adjparam: psi_g and alpha depend on x_i - m, so d/dm = -d/dx
-        v0 = -fmaf(mu, J.da[0], fmaf(lx, J.dd[0][0], ly * J.dd[1][0]));
-        v1 = -fmaf(mu, J.da[1], fmaf(lx, J.dd[0][1], ly * J.dd[1][1]));
-        v2 = fmaf(mu, J.da[2], fmaf(lx, J.dd[0][2], ly * J.dd[1][2]));
-        v3 = fmaf(mu, J.da[3], fmaf(lx, J.dd[0][3], ly * J.dd[1][3]));
-        v4 = fmaf(mu, J.da[4], fmaf(lx, J.dd[0][4], ly * J.dd[1][4]));
-        // Eq. adjstep: lambda^x_i = (I + D disp)^T lambda^x_{i-1} + mu d alpha / dx
-        const float nlx = lx + fmaf(mu, J.da[0], fmaf(lx, J.dd[0][0], ly * J.dd[1][0]));
-        const float nly = ly + fmaf(mu, J.da[1], fmaf(lx, J.dd[0][1], ly * J.dd[1][1]));
-        lx = nlx; ly = nly;
-        lT = fmaf(J.oma, lT, J.alpha * lCc);
+        // psi_g and alpha depend on x_i - m, so d/dm = -d/dx
+        v0 = -G[0]; v1 = -G[1]; v2 = G[2]; v3 = G[3]; v4 = G[4];
+        lx += G[0];
+        ly += G[1];
+        lT = fmaf(oma, lT, alpha * lCc);
       }
       const float vv[8] = {v0, v1, v2, v3, v4, v5, v6, v7};
       const float r = warp_reduce8(vv);

@@ -161,8 +161,9 @@ def test_coupled_program_is_rejected_where_unsupported():
 @pytest.mark.parametrize("which,W,H,tau,tau_min", [("small", 128, 128, 0.0, 1 / 200), ("small", 96, 96, 0.3, 0.01),
                                                    ("long", 75, 61, 0.0, 1 / 200)])
 def test_backward_coupled(which, W, H, tau, tau_min):
-    """The replay adjoint of the coupled soft render (Phi_g regeneration, local
-    Jacobians by dual numbers) against the oracle's stored-state adjoint."""
+    """The replay adjoint of the coupled soft render (Phi_g regeneration, the
+    hand-derived step VJP) against the oracle's stored-state adjoint (whose
+    local Jacobians come from dual numbers)."""
     p = small_coupled() if which == "small" else long_coupled()
     dp = tbr.DeviceProgram.from_host(p)
     rgb, ctx = tbr.render_soft(dp, W, H, tau, tau_min, record=True)
