@@ -20,10 +20,11 @@ constexpr int kServeCH = 32;
 
 __device__ __forceinline__ long long ld_volatile_ll(const volatile long long* p) { return *p; }
 
-// Three CTAs per SM (the register cap this implies costs the paired adjoint a
-// few spills); the host leaves one CTA slot per SM to the packing and edit
-// kernels of newly admitted requests.
-__global__ void __launch_bounds__(kTileThreads, 3) k_serve(ServeArgs a) {
+// Two CTAs per SM: the paired adjoint keeps its 128 registers without spills
+// (at three CTAs per SM its spills cost the soft requests more than the third
+// CTA gains the hard ones).  The host leaves eight CTA slots of the machine to
+// the packing, edit and epilogue kernels of other requests.
+__global__ void __launch_bounds__(kTileThreads, 2) k_serve(ServeArgs a) {
   __shared__ __align__(128) float sbuf[2 * kServeCH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
   __shared__ float red[2][kTileThreads / 32][kServeCH * 8];
@@ -256,10 +257,11 @@ int serve_grid() {
   const int per_sm = cache.get([](int) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_serve, kTileThreads, 0) != cudaSuccess || b < 1) b = 1;
-    // leave one CTA per SM free so packing and edit kernels of new requests can run alongside
-    return b > 1 ? b - 1 : b;
+    return b;
   });
-  return per_sm * device_sm_count();
+  // leave a few CTA slots free so packing, edit and epilogue kernels of other requests can run alongside
+  const int g = per_sm * device_sm_count();
+  return g > 16 ? g - 8 : g;
 }
 
 cudaError_t launch_serve(const ServeArgs& a, cudaStream_t st) {
