@@ -65,33 +65,6 @@ __global__ void __launch_bounds__(kTileThreads, 4) k_backward(BwdArgs a) {
   if (lane == 0 && dsum) atomicAdd(status + ST_DRIFT, static_cast<unsigned long long>(dsum));
 }
 
-// The pixel pair (px, py0), (px, py0 + 1) as k_backward2 starts it: validity,
-// record offsets, the forward's s_0 and the cotangent.  An invalid pixel keeps
-// a finite position and a zero cotangent.
-__device__ __forceinline__ void load_pair(const BwdArgs& a, int px, int py0, bool skip, bool (&valid)[2],
-                                          size_t (&off)[2], PixelState (&st)[2], float (&lC)[2][3]) {
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int py = py0 + c;
-    valid[c] = px < a.W && py < a.H && !skip;
-    off[c] = valid[c] ? static_cast<size_t>(py) * a.W + px : 0;
-    st[c] = PixelState{(static_cast<float>(px) + 0.5f) / static_cast<float>(a.W),
-                       (static_cast<float>(py) + 0.5f) / static_cast<float>(a.H), 0.0f, 0.0f, 0.0f, 0,
-                       0.0f, 0.0f, 0.0f};
-    lC[c][0] = lC[c][1] = lC[c][2] = 0.0f;
-    if (valid[c]) {
-      const float4 s0 = a.s0[off[c]];
-      const float2 s0b = a.s0b[off[c]];
-      st[c].xh = s0.x; st[c].yh = s0.y; st[c].xl = s0.z; st[c].yl = s0.w;
-      st[c].lt = s0b.x;
-      st[c].cnt = __float_as_int(s0b.y);
-      lC[c][0] = a.dLdR[3 * off[c] + 0];
-      lC[c][1] = a.dLdR[3 * off[c] + 1];
-      lC[c][2] = a.dLdR[3 * off[c] + 2];
-    }
-  }
-}
-
 // The same replay adjoint with two vertically adjacent pixels per thread
 // (32 x 16 tiles, packed FP32 pair arithmetic; tbr_pair.cuh).  Used for the
 // exterior-transport model; the inert-mark model keeps k_backward.  The plain

@@ -9,6 +9,7 @@
 // the rare flank-to-cap regeneration take the scalar routines per pixel.
 #pragma once
 
+#include "tbr_coupled_vjp.cuh"
 #include "tbr_tile.cuh"
 
 namespace tbr {
@@ -569,6 +570,33 @@ __device__ __forceinline__ void pair_state_init(PairState& ps, const bool (&vali
   }
 }
 
+// The pixel pair (px, py0), (px, py0 + 1) as k_backward2 starts it: validity,
+// record offsets, the forward's s_0 and the cotangent.  An invalid pixel keeps
+// a finite position and a zero cotangent.
+__device__ __forceinline__ void load_pair(const BwdArgs& a, int px, int py0, bool skip, bool (&valid)[2],
+                                          size_t (&off)[2], PixelState (&st)[2], float (&lC)[2][3]) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const int py = py0 + c;
+    valid[c] = px < a.W && py < a.H && !skip;
+    off[c] = valid[c] ? static_cast<size_t>(py) * a.W + px : 0;
+    st[c] = PixelState{(static_cast<float>(px) + 0.5f) / static_cast<float>(a.W),
+                       (static_cast<float>(py) + 0.5f) / static_cast<float>(a.H), 0.0f, 0.0f, 0.0f, 0,
+                       0.0f, 0.0f, 0.0f};
+    lC[c][0] = lC[c][1] = lC[c][2] = 0.0f;
+    if (valid[c]) {
+      const float4 s0 = a.s0[off[c]];
+      const float2 s0b = a.s0b[off[c]];
+      st[c].xh = s0.x; st[c].yh = s0.y; st[c].xl = s0.z; st[c].yl = s0.w;
+      st[c].lt = s0b.x;
+      st[c].cnt = __float_as_int(s0b.y);
+      lC[c][0] = a.dLdR[3 * off[c] + 0];
+      lC[c][1] = a.dLdR[3 * off[c] + 1];
+      lC[c][2] = a.dLdR[3 * off[c] + 2];
+    }
+  }
+}
+
 // Stroke i1 of the paired replay adjoint (S: packed record, P: pair record;
 // at_ck / cko: checkpoint stroke and its record offset).  Writes each pixel's 8
 // gradient values to g[c][.].  At a checkpoint, counts in drift the pixels
@@ -644,6 +672,396 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
   }
 }
 
+// ---------------------------------------------------------------------------
+// The paired replay adjoint of the coupling variant Phi_g (Eq. coupling, Eq.
+// profile).  Its pair extension record holds the floor constants and the
+// profile cubic of each staged stroke.
+// ---------------------------------------------------------------------------
+enum : int { XG_KA = 0, XG_FL2 = 1, XG_G0 = 2, XG_G1 = 3, XG_G2 = 4, XG_G3 = 5, kPairExtG = 6 };
+
+// All threads: fill the coupling extension of the cnt strokes staged at S0.
+__device__ __forceinline__ void pair_ext_g_fill(const float* __restrict__ S0, int cnt, f2* __restrict__ gext) {
+  for (int e = threadIdx.x; e < cnt * kPairExtG; e += kTileThreads) {
+    const int j = e / kPairExtG, k = e - j * kPairExtG;
+    gext[e] = F2(S0[j * kRec + (k < 2 ? F_KA + k : F_G0 + k - 2)]);
+  }
+}
+
+// g - 1 at the angle 4 pi v, for two pixels (as profile_gm1).
+__device__ __forceinline__ f2 profile_gm1_2(f2 ang, const f2* __restrict__ X) {
+  const f2 a = sub2(min2(max2(ang, F2(0.0f)), F2(kPiF)), F2(0.5f * kPiF));
+  const f2 w = neg2(sin_pi2_2(a));
+  return fma2(w, fma2(w, fma2(w, X[XG_G3], X[XG_G2]), X[XG_G1]), X[XG_G0]);
+}
+
+// x_i = Phi_g,i(x_{i-1}) for two pixels at frame points (s, h) of x_{i-1}, in
+// the displacement form of phi_local<true>: the normal step adds A_L(r) g(v),
+// v the centred arclength of the point's own leaf (on a drop, beta / (2 pi)).
+// Returns the mask of the pixels whose step goes from the flank onto a cap;
+// their outputs are not valid and the caller recomputes them with phi_local.
+__device__ __forceinline__ int phi_pair_g(f2 s, f2 h, const f2* __restrict__ P, const f2* __restrict__ X, f2& ds,
+                                          f2& dh) {
+  const f2 L = P[P_L], Ar = P[P_AR];
+  const f2 sgs = sgn2(s), sgh = sgn2(h);
+  const f2 as = abs2(s), ah = abs2(h);
+  if (L.x == 0.0f) {  // drop: radial (warp-uniform branch)
+    const f2 x2 = fma2(as, as, mul2(ah, ah));
+    const f2 is = rsqrt2(max2(x2, F2(kTiny)));  // 1 / sigma
+    const f2 sig = mul2(x2, is);
+    const f2 sb = mul2(as, is);
+    const f2 cb = sel2(x2.x > 0.0f, x2.y > 0.0f, mul2(ah, is), F2(1.0f));
+    const f2 beta = atan2_pos2(as, ah);
+    const f2 Ag = fma2(Ar, profile_gm1_2(add2(beta, beta), X), Ar);
+    const f2 sp = sqrt2(mul2(fma2(sig, mul2(F2(kPiF), sig), Ag), F2(1.0f / kPiF)));
+    const f2 dsp = mul2(Ag, rcp2(mul2(F2(kPiF), add2(sig, sp))));
+    ds = mul2(sgs, mul2(dsp, sb));
+    dh = mul2(sgh, mul2(dsp, cb));
+    return 0;
+  }
+  const f2 hl = P[P_HL];
+  const f2 d = sub2(as, hl);
+  const bool co_x = d.x > 0.0f, co_y = d.y > 0.0f;
+  const f2 dp = max2(d, F2(0.0f));
+  const f2 x2 = fma2(dp, dp, mul2(ah, ah));
+  const f2 is = rsqrt2(max2(x2, F2(kTiny)));  // 1 / sigma
+  const f2 sig = mul2(x2, is);
+  const f2 sb = mul2(dp, is);
+  const f2 cb = sel2(co_x, co_y, mul2(ah, is), F2(1.0f));
+  const f2 beta = atan2_pos2(dp, ah);
+  const f2 tn = fma2(sig, beta, min2(as, hl));
+  const f2 iQ = rcp2(fma2(F2(kPiF), sig, L));
+  const f2 Ag = fma2(Ar, profile_gm1_2(mul2(F2(2.0f * kPiF), mul2(tn, iQ)), X), Ar);  // 4 pi v = 2 pi t / Q
+  const f2 B = fma2(sig, fma2(F2(kPiF), sig, P[P_2L]), Ag);
+  const f2 sp = mul2(B, rcp2(add2(L, sqrt2(fma2(F2(kPiF), B, P[P_L2])))));
+  const f2 dsp = mul2(Ag, rcp2(fma2(F2(kPiF), add2(sig, sp), P[P_2L])));
+  const f2 t = mul2(tn, mul2(fma2(F2(kPiF), sp, L), iQ));
+  const bool ci_x = t.x > hl.x, ci_y = t.y > hl.y;
+  // cap to cap: rotation by delta, clamped to the cap; on the flank delta = 0
+  // and (sb, cb) = (0, 1), so the cap's dH is the flank's dsigma'
+  const f2 room = sub2(F2(0.5f * kPiF), beta);
+  f2 delta = mul2(mul2(mul2(dsp, L), room), mul2(iQ, rcp2(sp)));
+  delta = sel2(co_x, co_y, min2(max2(delta, F2(0.0f)), room), F2(0.0f));
+  const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
+  const f2 dSc = fma2(dsp, sb, mul2(sp, sub2(mul2(cb, sD), mul2(sb, omc))));
+  const f2 dH = sub2(mul2(dsp, cb), mul2(sp, fma2(sb, sD, mul2(cb, omc))));
+  const f2 dSf = mul2(mul2(tn, F2(kPiF)), mul2(dsp, iQ));  // flank to flank
+  ds = mul2(sgs, sel2(co_x, co_y, dSc, dSf));
+  dh = mul2(sgh, dH);
+  return ((!co_x && ci_x) ? 1 : 0) | ((!co_y && ci_y) ? 2 : 0);
+}
+
+// Pair form of coupled_vjp (tbr_coupled_vjp.cuh) at the hi/lo positions x_i of
+// two pixels: the same primal and reverse pass, written branch-free for the
+// cap-to-cap rotation and the flank (on the flank (ud, uh, phi) = (0, 1, 0)
+// clamps delta to 0, so the rotation's formulas give dH, and the flank's own dS
+// terms are added under a warp vote).  Returns the mask of pixels in the direct
+// form (floored, or cap to flank); their G, alpha and oma are not valid and the
+// caller recomputes them with coupled_vjp.  seed(alpha, oma, sp2, lx, ly, mu)
+// as in coupled_vjp, for both pixels.
+template <class Seed>
+__device__ __forceinline__ int coupled_vjp2(f2 Xh, f2 Yh, f2 Xl, f2 Yl, const f2* __restrict__ P,
+                                            const f2* __restrict__ X, Seed&& seed, f2 (&G)[5], f2& alpha, f2& oma) {
+  const f2 ex = P[P_EX], ey = P[P_EY], L = P[P_L], r = P[P_R], hl = P[P_HL], Ar = P[P_AR], kA = X[XG_KA];
+  const f2 dxw = add2(sub2(Xh, P[P_MX]), Xl), dyw = add2(sub2(Yh, P[P_MY]), Yl);
+  const f2 s = fma2(dxw, ex, mul2(dyw, ey)), h = sub2(mul2(dyw, ex), mul2(dxw, ey));
+  const f2 sgs = sgn2(s), sgh = sgn2(h);
+  const f2 as = abs2(s), ah = abs2(h);
+  // ---- primal
+  const f2 d = sub2(as, hl);
+  const bool ci_x = d.x > 0.0f, ci_y = d.y > 0.0f;
+  const f2 dp = max2(d, F2(0.0f));
+  const f2 x2 = fma2(dp, dp, mul2(ah, ah));
+  const f2 inv = rsqrt2(max2(x2, F2(kTiny)));  // 1 / sigma'
+  const f2 sp = mul2(x2, inv);
+  const f2 ud = mul2(dp, inv);
+  const f2 uh = sel2(ci_x, ci_y, mul2(ah, inv), F2(1.0f));
+  const f2 phi = atan2_pos2(dp, ah);
+  const f2 t = fma2(sp, phi, min2(as, hl));
+  const f2 iQp = rcp2(fma2(F2(kPiF), sp, L));
+  const f2 am = fma2(F2(2.0f * kPiF), mul2(t, iQp), F2(-0.5f * kPiF));  // 4 pi v - pi/2
+  const f2 w = neg2(sin_pi2_2(am));
+  const f2 gm1 = fma2(w, fma2(w, fma2(w, X[XG_G3], X[XG_G2]), X[XG_G1]), X[XG_G0]);
+  const f2 Ag = fma2(Ar, gm1, Ar);
+  const f2 kAs = fma2(F2(kPiF), sp, kA);
+  const f2 spr = sub2(sp, r);
+  const f2 C = fma2(spr, kAs, neg2(mul2(Ar, gm1)));
+  const bool fl_x = C.x < X[XG_FL2].x, fl_y = C.y < X[XG_FL2].y;
+  const f2 rin = fma2(F2(kPiF), C, P[P_L2]);
+  const f2 iroot = rsqrt2(max2(rin, F2(kTiny)));
+  const f2 iden1 = rcp2(fma2(rin, iroot, L));
+  const f2 sig = mul2(C, iden1);
+  const f2 Q = fma2(F2(kPiF), sig, L);
+  const f2 tn = mul2(t, mul2(Q, iQp));
+  const bool co_x = tn.x > hl.x, co_y = tn.y > hl.y;
+  const int mask = ((fl_x || (ci_x && !co_x)) ? 1 : 0) | ((fl_y || (ci_y && !co_y)) ? 2 : 0);
+  const f2 iden2 = rcp2(fma2(F2(kPiF), add2(sp, sig), P[P_2L]));
+  const f2 dsig = neg2(mul2(Ag, iden2));
+  const f2 isig = rcp2(sig);
+  const f2 Pm = sub2(phi, F2(0.5f * kPiF));
+  const f2 k0 = mul2(Pm, mul2(iQp, isig));
+  const f2 delta0 = neg2(mul2(mul2(dsig, L), k0));
+  const bool c1x = delta0.x < -phi.x, c1y = delta0.y < -phi.y;
+  f2 delta = sel2(c1x, c1y, neg2(phi), delta0);
+  const bool c2x = delta.x > 0.0f, c2y = delta.y > 0.0f;
+  delta = sel2(c2x, c2y, F2(0.0f), delta);
+  const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
+  const f2 cD = sub2(F2(1.0f), omc);
+  const f2 sigsD = mul2(sig, sD), sigomc = mul2(sig, omc);
+  const f2 pQ = mul2(F2(kPiF), iQp);
+  const f2 dS = sel2(ci_x, ci_y, fma2(dsig, ud, sub2(mul2(uh, sigsD), mul2(ud, sigomc))), mul2(mul2(as, pQ), dsig));
+  const f2 dH = sub2(mul2(dsig, uh), fma2(ud, sigsD, mul2(uh, sigomc)));
+  // coverage from the deposit boundary sigma_b(v)
+  const f2 cin = fma2(F2(kPiF), Ag, P[P_L2]);
+  const f2 iR2 = rsqrt2(max2(cin, F2(kTiny)));
+  const f2 iD2 = rcp2(fma2(cin, iR2, L));
+  const f2 rb = mul2(Ag, iD2);
+  const f2 iw = P[P_IW];
+  const f2 z = mul2(sub2(rb, sp), iw);
+  const bool clx = z.x > kZMax, cly = z.y > kZMax;
+  const f2 ez = ex22(mul2(min2(z, F2(kZMax)), F2(kLog2e)));
+  const f2 opl = add2(F2(1.0f), ez);
+  oma = rcp2(opl);
+  alpha = mul2(ez, oma);
+  f2 lx, ly, mu;
+  seed(alpha, oma, lg22(opl), lx, ly, mu);
+
+  // ---- reverse
+  const f2 ls = fma2(lx, ex, mul2(ly, ey)), lh = sub2(mul2(ly, ex), mul2(lx, ey));
+  const f2 b_dS = mul2(sgs, ls), b_dH = mul2(sgh, lh);
+  const f2 b_z = sel2(clx, cly, F2(0.0f), mul2(mu, mul2(alpha, oma)));
+  const f2 b_rb = mul2(b_z, iw);
+  f2 b_sp = neg2(b_rb);
+  f2 b_r = neg2(mul2(mul2(b_z, z), P[P_DLW]));
+  const f2 b_D2 = neg2(mul2(mul2(b_rb, rb), iD2));
+  const f2 b_cin = mul2(mul2(b_D2, F2(0.5f)), iR2);
+  f2 b_Ag = fma2(F2(kPiF), b_cin, mul2(b_rb, iD2));
+  f2 b_L = fma2(P[P_2L], b_cin, b_D2);
+  // cap-to-cap rotation (the flank's terms follow)
+  f2 b_dsig = fma2(b_dS, ud, mul2(b_dH, uh));
+  f2 b_sig = sub2(mul2(b_dS, sub2(mul2(uh, sD), mul2(ud, omc))), mul2(b_dH, fma2(ud, sD, mul2(uh, omc))));
+  const f2 dso = sub2(dsig, sigomc);
+  const f2 b_ud = sub2(mul2(b_dS, dso), mul2(b_dH, sigsD));
+  const f2 b_uh = fma2(b_dS, sigsD, mul2(b_dH, dso));
+  const f2 b_sD = mul2(sig, sub2(mul2(b_dS, uh), mul2(b_dH, ud)));
+  const f2 b_omc = neg2(mul2(sig, fma2(b_dS, ud, mul2(b_dH, uh))));
+  const f2 b_delta = fma2(b_sD, cD, mul2(b_omc, sD));
+  // delta free, clamped at -phi, or clamped at 0
+  const f2 bdf = sel2(!c1x && !c2x, !c1y && !c2y, b_delta, F2(0.0f));
+  f2 b_phi = sel2(c1x && !c2x, c1y && !c2y, neg2(b_delta), F2(0.0f));
+  const f2 kd = neg2(mul2(bdf, mul2(dsig, L)));
+  b_dsig = fma2(neg2(mul2(bdf, L)), k0, b_dsig);
+  b_L = fma2(neg2(mul2(bdf, dsig)), k0, b_L);
+  b_phi = fma2(kd, mul2(iQp, isig), b_phi);
+  f2 b_iQp = mul2(kd, mul2(Pm, isig));
+  b_sig = fma2(neg2(mul2(bdf, delta)), isig, b_sig);
+  f2 b_as = F2(0.0f);
+  if (__any_sync(__activemask(), !ci_x || !ci_y)) {
+    // flank to flank: dS = pi |s| dsig / Q' (dH = dsig is the rotation's on the flank)
+    const f2 fq = sel2(ci_x, ci_y, F2(0.0f), mul2(b_dS, pQ));
+    b_dsig = fma2(fq, as, b_dsig);
+    b_as = mul2(fq, dsig);
+    b_iQp = fma2(sel2(ci_x, ci_y, F2(0.0f), mul2(b_dS, F2(kPiF))), mul2(as, dsig), b_iQp);
+  }
+  // dsig = -Ag / (pi (sp + sig) + 2L)
+  const f2 b_den2 = neg2(mul2(mul2(b_dsig, dsig), iden2));
+  b_Ag = fma2(neg2(b_dsig), iden2, b_Ag);
+  b_sp = fma2(F2(kPiF), b_den2, b_sp);
+  b_sig = fma2(F2(kPiF), b_den2, b_sig);
+  b_L = fma2(F2(2.0f), b_den2, b_L);
+  // sig = C / (L + sqrt(pi C + L^2))
+  const f2 b_den1 = neg2(mul2(mul2(b_sig, sig), iden1));
+  const f2 b_rin = mul2(mul2(b_den1, F2(0.5f)), iroot);
+  const f2 b_C = fma2(F2(kPiF), b_rin, mul2(b_sig, iden1));
+  b_L = fma2(P[P_2L], b_rin, add2(b_L, b_den1));
+  // C = (sp - r)(2L + pi (r + sp)) - A_L(r) (g - 1); Ag = A_L(r) (1 + (g - 1))
+  b_sp = fma2(b_C, fma2(F2(kPiF), spr, kAs), b_sp);
+  b_r = fma2(neg2(b_C), kAs, b_r);
+  f2 b_kA = mul2(b_C, spr);
+  const f2 bAC = sub2(b_Ag, b_C);
+  const f2 b_Ar = fma2(gm1, bAC, b_Ag);
+  const f2 b_gm1 = mul2(Ar, bAC);
+  // the cubic in w = cos 4 pi v = -sin(am)
+  const f2 b_w = mul2(b_gm1, fma2(w, fma2(mul2(F2(3.0f), X[XG_G3]), w, mul2(F2(2.0f), X[XG_G2])), X[XG_G1]));
+  const f2 b_ang = neg2(mul2(mul2(b_w, F2(2.0f * kPiF)), sub2(F2(1.0f), omc_pi2_2(am))));
+  const f2 b_t = mul2(b_ang, iQp);
+  b_iQp = fma2(b_ang, t, b_iQp);
+  const f2 b_Qp = neg2(mul2(mul2(b_iQp, iQp), iQp));
+  b_L = add2(b_L, b_Qp);
+  b_sp = fma2(F2(kPiF), b_Qp, b_sp);
+  // t = sp phi + min(|s|, L/2); on a cap u = (d, |h|) / sp, phi = atan2(d, |h|)
+  b_sp = fma2(b_t, phi, b_sp);
+  b_phi = fma2(b_t, sp, b_phi);
+  const f2 ub = fma2(ud, b_ud, mul2(uh, b_uh));
+  const f2 bdd = sel2(ci_x, ci_y, fma2(fma2(b_phi, uh, fma2(neg2(ud), ub, b_ud)), inv, mul2(b_sp, ud)), F2(0.0f));
+  const f2 b_ah = fma2(fma2(neg2(b_phi), ud, fma2(neg2(uh), ub, b_uh)), inv, mul2(b_sp, uh));
+  b_as = add2(b_as, add2(bdd, sel2(ci_x, ci_y, F2(0.0f), b_t)));
+  b_L = fma2(F2(0.5f), sel2(ci_x, ci_y, sub2(b_t, bdd), F2(0.0f)), b_L);
+  // A_L(r) = (2L + pi r) r
+  b_kA = fma2(b_Ar, r, b_kA);
+  b_r = fma2(b_Ar, kA, b_r);
+  b_L = fma2(F2(2.0f), b_kA, b_L);
+  b_r = fma2(F2(kPiF), b_kA, b_r);
+  // frame, and the rotation of the displacement back to world
+  const f2 g_s = mul2(sgs, b_as), g_h = mul2(sgh, b_ah);
+  const f2 dsw = mul2(sgs, dS), dhw = mul2(sgh, dH);
+  const f2 ddx = sub2(mul2(dsw, ex), mul2(dhw, ey)), ddy = fma2(dsw, ey, mul2(dhw, ex));
+  G[0] = sub2(mul2(g_s, ex), mul2(g_h, ey));
+  G[1] = fma2(g_s, ey, mul2(g_h, ex));
+  G[2] = add2(sub2(mul2(g_s, h), mul2(g_h, s)), sub2(mul2(ly, ddx), mul2(lx, ddy)));
+  G[3] = b_L;
+  G[4] = b_r;
+  return mask;
+}
+
+// One stroke of the Phi_g replay adjoint for one pixel in scalar arithmetic:
+// x_i from the side table (pop), from Phi_g,i followed by a reset to the
+// checkpoint (at_ck), or from Phi_g,i; log2 T_i from the checkpoint or Eq. rT;
+// then the step VJP (coupled_vjp), whose 8 gradient values are written to v.
+// Returns true if, at a checkpoint of a valid pixel, the regenerated position
+// differed from the stored one by more than drift_tol.
+__device__ __forceinline__ bool coupled_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S, float lC0,
+                                               float lC1, float lC2, bool pop, bool at_ck, bool valid, float4 rp,
+                                               float4 ckp, float ck_lt, float drift_tol, float (&v)[8]) {
+  bool drifted = false;
+  if (pop) {
+    // x_i was within the floor's reach: read it back (Lemma "Support of the replay record")
+    a.xh = rp.x; a.yh = rp.y; a.xl = rp.z; a.yl = rp.w;
+  } else {
+    Geo gq;
+    float s, h, ds, dh;
+    to_frame(a.xh, a.yh, a.xl, a.yl, g, s, h);
+    phi_local<true>(s, h, g, gq, ds, dh, *reinterpret_cast<const float4*>(S + F_G0));
+    add_frame_disp(a.xh, a.yh, a.xl, a.yl, g, ds, dh);
+    if (at_ck && valid) {  // measure the drift against the stored position, then reset to it
+      drifted = fabsf((a.xh - ckp.x) + (a.xl - ckp.z)) > drift_tol ||
+                fabsf((a.yh - ckp.y) + (a.yl - ckp.w)) > drift_tol;
+      a.xh = ckp.x; a.yh = ckp.y; a.xl = ckp.z; a.yl = ckp.w;
+    }
+  }
+  const float lCc = fmaf(lC0, S[F_CR], fmaf(lC1, S[F_CG], lC2 * S[F_CB]));
+  float G[5], alpha, oma, T = 0.0f;
+  coupled_vjp(a.xh, a.yh, a.xl, a.yl, S,
+              [&](float, float, float sp2, float& sx, float& sy, float& smu) {
+                if (at_ck) a.lt = ck_lt; else a.lt += sp2;
+                T = ex2_a(a.lt);
+                sx = a.lx;
+                sy = a.ly;
+                smu = T * (lCc - a.lT);
+              },
+              G, alpha, oma);
+  const float Ta = T * alpha;
+  v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;
+  // psi_g and alpha depend on x_i - m, so d/dm = -d/dx
+  v[0] = -G[0]; v[1] = -G[1]; v[2] = G[2]; v[3] = G[3]; v[4] = G[4];
+  a.lx += G[0];
+  a.ly += G[1];
+  a.lT = fmaf(oma, a.lT, alpha * lCc);
+  return drifted;
+}
+
+// Stroke i1 of the paired replay adjoint under Phi_g (X: the coupling
+// extension record), as pair_stroke: pops, checkpoints and flank-to-cap
+// regeneration take coupled_stroke per pixel, and a pixel whose step VJP is in
+// the direct form takes coupled_vjp from the same x_i.
+__device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __restrict__ S, const f2* __restrict__ P,
+                                              const f2* __restrict__ X, int i1, bool at_ck, size_t cko,
+                                              const RecordView& rv, const bool (&valid)[2], const size_t (&off)[2],
+                                              float (&g)[2][8], unsigned& drift) {
+  const bool pop0 = i1 == ps.nri[0], pop1 = i1 == ps.nri[1];
+  bool scalar = at_ck || pop0 || pop1;
+  if (!scalar) {
+    // x_i = Phi_g,i(x_{i-1}) (Eq. rpos), both pixels at once
+    f2 s, h, ds, dh;
+    to_frame2(ps.Xh, ps.Yh, ps.Xl, ps.Yl, P, s, h);
+    scalar = phi_pair_g(s, h, P, X, ds, dh) != 0;  // flank to cap: redo this stroke per pixel
+    if (!scalar) {  // hi/lo two-sum every step, as pos_add: no rounding of lo builds up between renormalisations
+      const f2 ddx = sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY]));
+      const f2 ddy = fma2(ds, P[P_EY], mul2(dh, P[P_EX]));
+      const f2 sx = add2(ps.Xh, ddx), sy = add2(ps.Yh, ddy);
+      ps.Xl = add2(ps.Xl, sub2(ddx, sub2(sx, ps.Xh)));
+      ps.Yl = add2(ps.Yl, sub2(ddy, sub2(sy, ps.Yh)));
+      ps.Xh = sx;
+      ps.Yh = sy;
+    }
+  }
+  if (scalar) {
+    const StrokeF sg = load_stroke(S);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const bool pop = c == 0 ? pop0 : pop1;
+      float4 rp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (pop) {
+        rp = rv.rec[static_cast<size_t>(ps.rc[c] - 1) * rv.stride + off[c]];
+        --ps.rc[c];
+        ps.nri[c] = ps.rc[c] > 0 ? rv.rec_i[static_cast<size_t>(ps.rc[c] - 1) * rv.stride + off[c]] : -1;
+      }
+      float4 ckp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      float ckl = 0.0f;
+      if (at_ck && valid[c]) {
+        ckp = rv.ckpt[cko + off[c]];
+        ckl = rv.ck_lt[cko + off[c]];
+      }
+      PixAdj a{comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), comp(ps.LT, c), comp(ps.LTT, c),
+               comp(ps.LX, c), comp(ps.LY, c)};
+      if (coupled_stroke(a, sg, S, comp(ps.LC0, c), comp(ps.LC1, c), comp(ps.LC2, c), pop, at_ck, valid[c], rp,
+                         ckp, ckl, rv.drift_tol, g[c]))
+        ++drift;
+      put(ps.Xh, c, a.xh); put(ps.Yh, c, a.yh); put(ps.Xl, c, a.xl); put(ps.Yl, c, a.yl);
+      put(ps.LT, c, a.lt); put(ps.LTT, c, a.lT); put(ps.LX, c, a.lx); put(ps.LY, c, a.ly);
+    }
+    return;
+  }
+  const f2 lCc = fma2(ps.LC0, P[P_CR], fma2(ps.LC1, P[P_CG], mul2(ps.LC2, P[P_CB])));
+  f2 nLT, T, G[5], alpha, oma;
+  const int vm = coupled_vjp2(ps.Xh, ps.Yh, ps.Xl, ps.Yl, P, X,
+                              [&](f2, f2, f2 sp2, f2& sx, f2& sy, f2& smu) {
+                                nLT = add2(ps.LT, sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
+                                T = ex22(nLT);
+                                sx = ps.LX;
+                                sy = ps.LY;
+                                smu = mul2(T, sub2(lCc, ps.LTT));
+                              },
+                              G, alpha, oma);
+  const f2 Ta = mul2(T, alpha);
+  f2 nLTT = fma2(oma, ps.LTT, mul2(alpha, lCc));
+  f2 nLX = add2(ps.LX, G[0]), nLY = add2(ps.LY, G[1]);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    g[c][0] = -comp(G[0], c); g[c][1] = -comp(G[1], c); g[c][2] = comp(G[2], c); g[c][3] = comp(G[3], c);
+    g[c][4] = comp(G[4], c);
+    g[c][5] = comp(ps.LC0, c) * comp(Ta, c); g[c][6] = comp(ps.LC1, c) * comp(Ta, c);
+    g[c][7] = comp(ps.LC2, c) * comp(Ta, c);
+  }
+  if (vm) {  // the direct form (floored, or cap to flank) in scalar arithmetic from the same x_i
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (!(vm & (1 << c))) continue;
+      float lt = comp(ps.LT, c), Tc = 0.0f, Gs[5], al, om;
+      const float lTo = comp(ps.LTT, c), lxo = comp(ps.LX, c), lyo = comp(ps.LY, c), lCcc = comp(lCc, c);
+      coupled_vjp(comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), S,
+                  [&](float, float, float sp2, float& sx, float& sy, float& smu) {
+                    lt += sp2;
+                    Tc = ex2_a(lt);
+                    sx = lxo;
+                    sy = lyo;
+                    smu = Tc * (lCcc - lTo);
+                  },
+                  Gs, al, om);
+      put(nLT, c, lt);
+      put(nLTT, c, fmaf(om, lTo, al * lCcc));
+      put(nLX, c, lxo + Gs[0]);
+      put(nLY, c, lyo + Gs[1]);
+      const float Tac = Tc * al;
+      g[c][0] = -Gs[0]; g[c][1] = -Gs[1]; g[c][2] = Gs[2]; g[c][3] = Gs[3]; g[c][4] = Gs[4];
+      g[c][5] = comp(ps.LC0, c) * Tac; g[c][6] = comp(ps.LC1, c) * Tac; g[c][7] = comp(ps.LC2, c) * Tac;
+    }
+  }
+  ps.LT = nLT;
+  ps.LTT = nLTT;
+  ps.LX = nLX;
+  ps.LY = nLY;
+}
+
 // Replay adjoint (Sec. 5.2) of a 32 x 16 tile, two pixels per thread, over
 // strokes 1 .. n; otherwise as backward_tile.  st[c], lC[c][.], valid[c] and
 // off[c] (the pixel's element offset in the replay record) describe pixel c of
@@ -651,14 +1069,16 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
 // cotangent.  pbuf is shared [CH][kPairRec] float2.  With QUEUE, a pixel whose
 // checkpoint drift first exceeds rv.drift_tol is appended, with the start of
 // that segment, to rv.repair_list (off[c] is then the pixel index) for the
-// FP64 repair pass.  All threads of the CTA must call it.  Returns false if a
-// bounded wait gave up.
-template <int CH, bool QUEUE, int UNROLL = 1>
+// FP64 repair pass.  With COUPLED, the strokes follow the coupling variant
+// Phi_g (pair_stroke_g; gext is shared [CH][kPairExtG] float2).  All threads
+// of the CTA must call it.  Returns false if a bounded wait gave up.
+template <int CH, bool QUEUE, int UNROLL = 1, bool COUPLED = false>
 __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, const bool (&valid)[2],
                                const PixelState (&st)[2], const float (&lC)[2][3], const float bg[3],
                                const RecordView& rv, const size_t (&off)[2], f2* __restrict__ pbuf,
                                float (*red)[kTileThreads / 32][CH * 8], float* __restrict__ slice, bool first,
-                               unsigned& drift, unsigned long long* status) {
+                               unsigned& drift, unsigned long long* status, f2* __restrict__ gext = nullptr) {
+  static_assert(!(COUPLED && QUEUE), "the coupling variant's adjoint has no FP64 repair");
   static_assert(CH * 8 == kTileThreads, "one partial per thread per chunk");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ck = rv.ck;
@@ -685,6 +1105,7 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
     const int cntc = chunk_cnt(q);
     const float* S0 = ring.data(b);
     pair_records_fill<false>(S0, cntc, pbuf, nullptr);
+    if (COUPLED) pair_ext_g_fill(S0, cntc, gext);
     __syncthreads();
     float (*rb)[CH * 8] = red[b];
 #pragma unroll UNROLL
@@ -699,7 +1120,11 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
       }
       if (any) {
         float g[2][8];
-        pair_stroke<QUEUE>(ps, S0 + j * kRec, pbuf + j * kPairRec, i1, at_ck, cko, rv, valid, off, g, drift);
+        if constexpr (COUPLED)
+          pair_stroke_g(ps, S0 + j * kRec, pbuf + j * kPairRec, gext + j * kPairExtG, i1, at_ck, cko, rv, valid,
+                        off, g, drift);
+        else
+          pair_stroke<QUEUE>(ps, S0 + j * kRec, pbuf + j * kPairRec, i1, at_ck, cko, rv, valid, off, g, drift);
 #pragma unroll
         for (int k = 0; k < 8; ++k) vv[k] = g[0][k] + g[1][k];
       }
