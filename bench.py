@@ -52,6 +52,12 @@ PEAK_GFLOPS = SMS * LANES * 2 * SM_MAX_MHZ * 1e-3
 PEAK_XU_GOPS = SMS * XU_PER_SM * SM_MAX_MHZ * 1e-3
 PEAK_BASIS = "148 SMs x 128 FP32 lanes x 2 FLOP (FMA) x 2032 MHz (recipe unit counts and maximum clock)"
 XU_BASIS = "148 SMs x 16 MUFU results per clock x 2032 MHz"
+# The same FP32 work against the lane-instruction rate (one operation per lane
+# per clock, 148 x 128 x 2032 MHz): the fraction of FP32 issue slots the
+# oracle's unfused operations would fill.  A kernel that fuses a multiply and
+# an add into one FFMA can exceed 1 on this basis; the FLOP basis above is the
+# conservative one and is the one reported as frac.
+PEAK_LANE_GOPS = SMS * LANES * SM_MAX_MHZ * 1e-3
 
 
 def alu_roofline(kernel, counts, units, ms):
@@ -65,6 +71,7 @@ def alu_roofline(kernel, counts, units, ms):
             "xu": {"ops_per_unit": x, "achieved": xach, "peak": PEAK_XU_GOPS, "unit": "Gop/s",
                    "frac": xach / PEAK_XU_GOPS, "peak_basis": XU_BASIS},
             "combined_bound_frac": max(ach / PEAK_GFLOPS, xach / PEAK_XU_GOPS),
+            "lane_frac": ach / PEAK_LANE_GOPS,
             "peak_basis": PEAK_BASIS, "peak_kind": "derived (MEASURED_PEAKS has no FP32 figure)",
             "ops_source": "profiles/opcount_1024_2000.json (FP64 oracle evaluated with a counting scalar)"}
 
