@@ -97,6 +97,8 @@ def parse_args():
                     help="requests of the serving stream (0 skips the serving measurement)")
     ap.add_argument("--res", type=int, default=RES, help="square resolution (profiling cases only)")
     ap.add_argument("--strokes", type=int, default=N_STROKES, help="stroke count (profiling cases only)")
+    ap.add_argument("--coupling", action="store_true",
+                    help="profiling cases only: time the coupling variant Phi_g (seeded profiles) as the main step")
     return ap.parse_args()
 
 
@@ -408,6 +410,8 @@ def run_native(args):
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
 
     prog_h, targ_h = rank_programs(rank, args.strokes)
+    if args.coupling:
+        prog_h.coupling = inputs.make_coupling(403, prog_h.n)
     prog = tbr.DeviceProgram.from_host(prog_h, device)
     targ = tbr.DeviceProgram.from_host(targ_h, device)
     W = H = args.res
@@ -484,9 +488,11 @@ def run_native(args):
                 traffic = tr.get("bytes_per_launch")
         except (OSError, ValueError):
             traffic = None
-    roofline = alu_roofline("k_backward2 (replay adjoint)", opc["capsule"]["adjoint"], units, bwd_ms)
-    roofline["traffic"] = traffic
-    soft_roofline = alu_roofline("k_soft (soft forward + record)", opc["capsule"]["soft_forward"], units, soft_ms)
+    fam = "coupled" if args.coupling else "capsule"
+    roofline = alu_roofline("k_backward_c2 (Phi_g replay adjoint)" if args.coupling else "k_backward2 (replay adjoint)",
+                            opc[fam]["adjoint"], units, bwd_ms)
+    roofline["traffic"] = None if args.coupling else traffic
+    soft_roofline = alu_roofline("k_soft (soft forward + record)", opc[fam]["soft_forward"], units, soft_ms)
 
     # e2e through the public API with host buffers: upload program + target from
     # pinned memory, fwd + loss + adjoint, read back gradients and loss
@@ -713,7 +719,8 @@ def run_native(args):
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded programs, no dataset)",
-            "config": {"workload": f"soft forward + replay adjoint, {prog.n} capsule strokes at {W}x{H}",
+            "config": {"workload": f"soft forward + replay adjoint, {prog.n} "
+                                   f"{'Phi_g (coupling seed 403)' if args.coupling else 'capsule'} strokes at {W}x{H}",
                        "strokes": prog.n, "resolution": [W, H], "palette": PALETTE, "tau": tau,
                        "tau_min": tau_min, "checkpoint_every": CHECKPOINT_EVERY,
                        "target": "hard render of a second seeded 2000-stroke program",

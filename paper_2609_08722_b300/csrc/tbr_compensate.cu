@@ -11,8 +11,9 @@
 // The N (N - 1) / 2 point transforms run as a wavefront on one CTA: step
 // j = N-1 .. 0 first finalises stroke j (its points have passed every later
 // stroke), then every thread applies psi_j to the points of its strokes i < j.
-// One barrier per step; positions are hi/lo float pairs; points and the
-// compensated geometry live in global memory (L1-resident for one CTA).
+// One barrier per step; positions are hi/lo float pairs.  Up to 4096 strokes
+// the points stay in registers (k_compensate_reg); longer programs keep them,
+// and the compensated geometry, in global memory (k_compensate).
 #include <math.h>
 
 #include "tbr_host.h"
@@ -33,16 +34,22 @@ struct CompArgs {
   unsigned long long* status;
 };
 
-// psi_j with the ideal interior extension at a hi/lo point (hard-render map):
-// returns true if the point lies in K_j (then clamped onto the segment, or left
-// in place when skip), else moves it by the exterior map.
-__device__ __forceinline__ bool comp_step(float4& p, const float* __restrict__ G, bool skip) {
+// The compensated geometry of one stroke as the steps read it (m, e, L/2, r and
+// the constants derived from them, formed once per stroke).
+__device__ __forceinline__ StrokeF comp_geometry(const float* __restrict__ G) {
   StrokeF g;
   g.mx = G[0]; g.my = G[1]; g.ex = G[2]; g.ey = G[3]; g.hl = G[4]; g.r = G[5];
   g.L = 2.0f * g.hl; g.twoL = 2.0f * g.L; g.L2 = g.L * g.L;
   g.kA = fmaf(kPiF, g.r, g.twoL);
   g.Ar = g.kA * g.r;
   g.fl2 = 0.0f; g.iw = 0.0f; g.dlw = 0.0f;
+  return g;
+}
+
+// psi_j with the ideal interior extension at a hi/lo point (hard-render map):
+// returns true if the point lies in K_j (then clamped onto the segment, or left
+// in place when skip), else moves it by the exterior map.
+__device__ __forceinline__ bool comp_step(float4& p, const StrokeF& g, bool skip) {
   float s, h;
   to_frame(p.x, p.y, p.z, p.w, g, s, h);
   const float as = fabsf(s), ah = fabsf(h), d = as - g.hl;
@@ -77,6 +84,40 @@ __device__ __forceinline__ float2 seg_end(const float* __restrict__ R, int c) {
            : make_float2(__fsub_rn(R[F_MX], hx), __fsub_rn(R[F_MY], hy));
 }
 
+// Stroke j has passed every later stroke: its compensated geometry is the given
+// one moved by the displacement of its start (and end), p[c] its pre-imaged
+// points.  A stroke no step moved keeps its parameters bit for bit.  Writes the
+// outputs and the geometry G = (m, e, L/2, r) the steps read.
+__device__ __forceinline__ void comp_finalize(const CompArgs& a, int j, const float4 (&p)[2], float* G) {
+  const float* R = a.packed + static_cast<size_t>(j) * kRec;
+  const int npt = a.endpoint ? 2 : 1;
+  float2 dsp[2];
+  for (int c = 0; c < npt; ++c) {
+    const float2 q = seg_end(R, c);
+    dsp[c] = make_float2((p[c].x - q.x) + p[c].z, (p[c].y - q.y) + p[c].w);
+  }
+  float mx, my, ex = R[F_EX], ey = R[F_EY], hl = R[F_HL], th = R[F_TH];
+  if (a.endpoint) {
+    mx = R[F_MX] + 0.5f * (dsp[0].x + dsp[1].x);
+    my = R[F_MY] + 0.5f * (dsp[0].y + dsp[1].y);
+    const float gx = dsp[1].x - dsp[0].x, gy = dsp[1].y - dsp[0].y;
+    if (gx != 0.0f || gy != 0.0f) {
+      const float dx = fmaf(2.0f * hl, ex, gx), dy = fmaf(2.0f * hl, ey, gy);
+      const float Ln = sqrtf(fmaf(dx, dx, dy * dy));
+      if (Ln > 0.0f) {
+        ex = dx / Ln; ey = dy / Ln;
+        th = atan2f(dy, dx);
+      }
+      hl = 0.5f * Ln;
+    }
+  } else {
+    mx = R[F_MX] + dsp[0].x;
+    my = R[F_MY] + dsp[0].y;
+  }
+  G[0] = mx; G[1] = my; G[2] = ex; G[3] = ey; G[4] = hl; G[5] = R[F_R];
+  a.cx[j] = mx; a.cy[j] = my; a.th[j] = th; a.len[j] = a.endpoint ? 2.0f * hl : R[F_L];
+}
+
 __global__ void __launch_bounds__(kCompThreads) k_compensate(CompArgs a) {
   const int n = a.n, npt = a.endpoint ? 2 : 1;
   // the points start at the given segment's start (and end)
@@ -91,46 +132,17 @@ __global__ void __launch_bounds__(kCompThreads) k_compensate(CompArgs a) {
   __syncthreads();
   for (int j = n - 1; j >= 0; --j) {
     if ((j % kCompThreads) == static_cast<int>(threadIdx.x)) {
-      // stroke j has passed every later stroke: its compensated geometry is the
-      // given one moved by the displacement of its start (and end); a stroke no
-      // step moved keeps its parameters bit for bit
-      const float* R = a.packed + static_cast<size_t>(j) * kRec;
-      float2 dsp[2];
-      for (int c = 0; c < npt; ++c) {
-        const float4 p = a.pts[2 * j + c];
-        const float2 q = seg_end(R, c);
-        dsp[c] = make_float2((p.x - q.x) + p.z, (p.y - q.y) + p.w);
-      }
-      float mx, my, ex = R[F_EX], ey = R[F_EY], hl = R[F_HL], th = R[F_TH];
-      if (a.endpoint) {
-        mx = R[F_MX] + 0.5f * (dsp[0].x + dsp[1].x);
-        my = R[F_MY] + 0.5f * (dsp[0].y + dsp[1].y);
-        const float gx = dsp[1].x - dsp[0].x, gy = dsp[1].y - dsp[0].y;
-        if (gx != 0.0f || gy != 0.0f) {
-          const float dx = fmaf(2.0f * hl, ex, gx), dy = fmaf(2.0f * hl, ey, gy);
-          const float Ln = sqrtf(fmaf(dx, dx, dy * dy));
-          if (Ln > 0.0f) {
-            ex = dx / Ln; ey = dy / Ln;
-            th = atan2f(dy, dx);
-          }
-          hl = 0.5f * Ln;
-        }
-      } else {
-        mx = R[F_MX] + dsp[0].x;
-        my = R[F_MY] + dsp[0].y;
-      }
-      float* G = a.geo + static_cast<size_t>(j) * 6;
-      G[0] = mx; G[1] = my; G[2] = ex; G[3] = ey; G[4] = hl; G[5] = R[F_R];
-      a.cx[j] = mx; a.cy[j] = my; a.th[j] = th; a.len[j] = a.endpoint ? 2.0f * hl : R[F_L];
+      float4 p[2] = {a.pts[2 * j], a.pts[2 * j + 1]};
+      comp_finalize(a, j, p, a.geo + static_cast<size_t>(j) * 6);
     }
     __syncthreads();
     if (j == 0) break;
-    const float* G = a.geo + static_cast<size_t>(j) * 6;
+    const StrokeF g = comp_geometry(a.geo + static_cast<size_t>(j) * 6);
     for (int i = threadIdx.x; i < j; i += blockDim.x) {
       bool blk = false;
       for (int c = 0; c < npt; ++c) {
         float4 p = a.pts[2 * i + c];
-        blk |= comp_step(p, G, a.skip != 0);
+        blk |= comp_step(p, g, a.skip != 0);
         a.pts[2 * i + c] = p;
       }
       if (blk) a.blocked[i] = 1;
@@ -143,6 +155,69 @@ __global__ void __launch_bounds__(kCompThreads) k_compensate(CompArgs a) {
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.status + ST_RECORDS, static_cast<unsigned long long>(cnt));
 }
+
+// The same wavefront with every point in registers: thread t owns strokes
+// t + m kCompThreads (m < K), so for n <= K kCompThreads no point leaves its
+// thread.  Stroke j's owner applies psi_{j+1} to point j and finalises stroke j
+// at once, without waiting for the other points; the geometry goes through a
+// double-buffered shared slot, so one barrier per step orders it before every
+// thread applies psi_j.  The arithmetic is k_compensate's, operation for
+// operation.
+template <int K>
+__global__ void __launch_bounds__(kCompThreads) k_compensate_reg(CompArgs a) {
+  __shared__ float sgeo[2][6];
+  const int n = a.n, npt = a.endpoint ? 2 : 1, t = threadIdx.x;
+  const bool skip = a.skip != 0;
+  float4 P[K][2];
+  unsigned blk = 0;
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const int i = t + m * kCompThreads;
+    const float* R = a.packed + static_cast<size_t>(i < n ? i : 0) * kRec;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const float2 q = seg_end(R, c);
+      P[m][c] = make_float4(q.x, q.y, 0.0f, 0.0f);
+    }
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const int b = j & 1;
+    if ((j % kCompThreads) == t) {
+      const int mj = j / kCompThreads;
+#pragma unroll
+      for (int m = 0; m < K; ++m)
+        if (m == mj) comp_finalize(a, j, P[m], sgeo[b]);
+    }
+    __syncthreads();
+    if (j == 0) break;
+    const StrokeF g = comp_geometry(sgeo[b]);
+    // points nearest the front first: the owner of stroke j - 1 finalises it next
+#pragma unroll
+    for (int m = K - 1; m >= 0; --m) {
+      const int i = t + m * kCompThreads;
+      if (i < j) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+          if (c < npt && comp_step(P[m][c], g, skip)) blk |= 1u << m;
+      }
+    }
+  }
+  unsigned cnt = 0;
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const int i = t + m * kCompThreads;
+    if (i < n) {
+      const unsigned f = (blk >> m) & 1u;
+      a.blocked[i] = static_cast<int>(f);
+      cnt += f;
+    }
+  }
+  // blocked count (fixed order: per thread, then one atomic per warp)
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(a.status + ST_RECORDS, static_cast<unsigned long long>(cnt));
+}
+
+constexpr int kCompRegPts = 4;  // strokes per thread held in registers
 
 }  // namespace
 
@@ -181,7 +256,8 @@ tbr_status tbr_compensate(const tbr_program* prog, int32_t endpoint, int32_t ski
     CompArgs a{packed, n, endpoint ? 1 : 0, skip_blocked ? 1 : 0, pts, geo, out_cx, out_cy, out_theta,
                out_length, out_blocked, status};
     KernelTimer kt(TBR_K_COMPENSATE, st);
-    k_compensate<<<1, kCompThreads, 0, st>>>(a);
+    if (n <= kCompRegPts * kCompThreads) k_compensate_reg<kCompRegPts><<<1, kCompThreads, 0, st>>>(a);
+    else k_compensate<<<1, kCompThreads, 0, st>>>(a);
     e = cudaGetLastError();
   }
   unsigned long long host[ST_COUNT] = {0};

@@ -4,7 +4,8 @@ on the GPU against the FP64 oracle.
 - Anchor and endpoint variants, clamped and skipped blocked steps, at 40
   strokes: the compensated segment ends agree with the oracle's within 1e-6.
 - At 2000 and 2500 strokes (two and three thread strides of the one-CTA
-  wavefront, a ragged last one) the chain is ill-conditioned wherever points
+  wavefront, a ragged last one; points in registers) and at 4500 strokes
+  (points in global memory) the chain is ill-conditioned wherever points
   are clamped onto later segments: perturbing the FP32 inputs by one rounding
   (relative 6e-8) moves the oracle's own FP64 result by up to 2e-5 (operating
   program, anchor) and 5e-3 (dense 2500-stroke program, endpoints).  Each
@@ -121,6 +122,15 @@ def test_three_strides_sparse(endpoint, skip):
     blocked), well conditioned: 2e-5 absolute."""
     p = inputs.make_program(2500, seed=79, palette_seed=78, k=8, r_lo=0.001, r_hi=0.004, len_max=0.05)
     compare(p, endpoint, skip, flag_slack=2, tol=2e-5)
+
+
+@pytest.mark.parametrize("endpoint", [False, True])
+def test_past_the_register_limit_sparse(endpoint):
+    """4500 sparse strokes: more than the 4096 whose points the wavefront holds
+    in registers, so the points live in global memory (the same arithmetic);
+    2e-5 absolute as the other sparse program."""
+    p = inputs.make_program(4500, seed=83, palette_seed=78, k=8, r_lo=0.001, r_hi=0.004, len_max=0.05)
+    compare(p, endpoint, False, flag_slack=2, tol=2e-5)
 
 
 def _prog(cx, cy, th, L, r):
