@@ -597,7 +597,7 @@ def run_native(args):
                          "visited_steps_per_pixel": st_h["visited_steps"] / (r * r),
                          "fp64_band_steps": st_h["band_steps"], "background_pixels": st_h["background_pixels"],
                          "roofline": {k: rl[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
-                                                         "combined_bound_frac")}
+                                                         "combined_bound_frac", "lane_frac")}
                          | {"xu_frac": rl["xu"]["frac"], "unit_of_work": "visited step"}})
             del rgb_h, idx_h
 
@@ -626,7 +626,7 @@ def run_native(args):
                     "soft_forward_ms": soft_d, "soft_evals_per_s": units / (soft_d * 1e-3),
                     "hard_ms": hard_d,
                     "soft_roofline": {k: rl[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
-                                                         "combined_bound_frac")} | {"xu_frac": rl["xu"]["frac"]}}
+                                                         "combined_bound_frac", "lane_frac")} | {"xu_frac": rl["xu"]["frac"]}}
         del rgb_d, idx_d
 
     # coupling variant Phi_g (seeded profiles) on the same program: soft forward
@@ -666,9 +666,9 @@ def run_native(args):
                     "fwd_adjoint_step_ms": step_g, "fwd_adjoint_evals_per_s": units / (step_g * 1e-3),
                     "early_exit": "forward-only capsule render stopping each pixel once T < 1e-12",
                     "soft_roofline": {k: rl[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
-                                                         "combined_bound_frac")} | {"xu_frac": rl["xu"]["frac"]},
+                                                         "combined_bound_frac", "lane_frac")} | {"xu_frac": rl["xu"]["frac"]},
                     "fwd_adjoint_step_roofline": {k: rla[k] for k in ("achieved", "unit", "frac", "ops_per_unit",
-                                                                      "combined_bound_frac")}}
+                                                                      "combined_bound_frac", "lane_frac")}}
         del rgb_g, idx_g, dpg
 
     # one-pass closed-form compensation of the same program (anchor and endpoint
