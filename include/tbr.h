@@ -476,6 +476,24 @@ TBR_API tbr_status tbr_profile_enable(int32_t on);
 TBR_API tbr_status tbr_profile_read(int32_t kernel, tbr_kernel_time* out);
 TBR_API void tbr_profile_reset(void);
 
+/* ------------------------------------------------------------------------
+ * Arithmetic peaks, measured (the denominators of the ALU roofline; no file
+ * the driver writes gives an FP32 or MUFU rate).  Runs one warm-up and one
+ * timed launch of a chain microbenchmark on every SM (4 CTAs of 256 threads
+ * per SM, 8 independent chains per thread, iters iterations) on `stream` and
+ * synchronises it.  *rate is in operations per second: FLOPs for the FMA kinds
+ * (a fused multiply-add counts 2, per lane), results for the MUFU kinds;
+ * *elapsed_ms (nullable) is the timed launch's duration.  TBR_ERR_INVALID_ARG
+ * for an unknown kind, iters <= 0 or a NULL rate.
+ * ------------------------------------------------------------------------ */
+enum {
+  TBR_PEAK_FFMA2 = 0,  /* packed FP32 fused multiply-add (FFMA2) */
+  TBR_PEAK_FFMA = 1,   /* scalar FP32 fused multiply-add */
+  TBR_PEAK_EX2 = 2,    /* MUFU ex2.approx */
+  TBR_PEAK_RCP = 3     /* MUFU rcp.approx */
+};
+TBR_API tbr_status tbr_measure_peak(int32_t kind, int32_t iters, double* rate, double* elapsed_ms, void* stream);
+
 /* Thread-local description of the last error (never NULL). */
 TBR_API const char* tbr_last_error(void);
 

@@ -32,7 +32,7 @@ EXPORTED = ["tbr_render_hard", "tbr_render_hard_transport", "tbr_render_hard_noa
             "tbr_fit_destroy", "tbr_serve_default_config", "tbr_serve_create", "tbr_serve_load_program",
             "tbr_serve_submit", "tbr_serve_poll", "tbr_serve_wait", "tbr_serve_request_times",
             "tbr_serve_release", "tbr_serve_stats", "tbr_serve_destroy", "tbr_profile_enable", "tbr_profile_read", "tbr_profile_reset",
-            "tbr_last_error", "tbr_version"]
+            "tbr_measure_peak", "tbr_last_error", "tbr_version"]
 
 
 class TbrError(RuntimeError):
@@ -364,6 +364,9 @@ def _fit_lib():
         L.tbr_profile_read.argtypes = [ctypes.c_int32, ctypes.POINTER(TbrKernelTime)]
         L.tbr_profile_reset.argtypes = []
         L.tbr_profile_reset.restype = None
+        L.tbr_measure_peak.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), P]
+        L.tbr_measure_peak.restype = ctypes.c_int
         L._fit_typed = True
     return L
 
@@ -456,6 +459,19 @@ def profile_read(kernel: str) -> tuple[int, float]:
     t = TbrKernelTime()
     check(_fit_lib().tbr_profile_read(KERNELS[kernel], ctypes.byref(t)))
     return int(t.launches), float(t.total_ms)
+
+
+PEAK_KINDS = {"ffma2": 0, "ffma": 1, "ex2": 2, "rcp": 3}
+
+
+def measure_peak(kind: str, iters: int = 200000, stream=None) -> tuple[float, float]:
+    """tbr_measure_peak: (operations per second, timed launch ms) of one chain
+    microbenchmark on every SM -- FLOPs for "ffma2" / "ffma" (a fused
+    multiply-add counts 2 per lane), MUFU results for "ex2" / "rcp"."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    check(_fit_lib().tbr_measure_peak(PEAK_KINDS[kind], int(iters), ctypes.byref(rate), ctypes.byref(ms),
+                                      _stream(stream)))
+    return float(rate.value), float(ms.value)
 
 
 # ---------------------------------------------------------------------------

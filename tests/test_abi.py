@@ -52,3 +52,7 @@ def test_invalid_arguments_fail_on_the_host():
     assert lib.tbr_render_backward(None, None, None, None, None, None, None, None, None, None) == \
         tbr.TBR_ERR_INVALID_ARG
     assert lib.tbr_loss_mse(None, None, 4, None, None, None) == tbr.TBR_ERR_INVALID_ARG
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    tbr._fit_lib()
+    assert lib.tbr_measure_peak(7, 10, ctypes.byref(rate), ctypes.byref(ms), None) == tbr.TBR_ERR_INVALID_ARG
+    assert lib.tbr_measure_peak(0, 0, ctypes.byref(rate), None, None) == tbr.TBR_ERR_INVALID_ARG
