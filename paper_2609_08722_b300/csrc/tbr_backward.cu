@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward2(BwdArgs a) {
     load_pair(a, px, py0, skip, valid, off, st, lC);
     const unsigned drift0 = drift;
     // two strokes per loop iteration let the compiler overlap their independent work
-    if (!backward_tile2<CH, QUEUE, 2>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice, first,
-                                      drift, status))
+    if (!backward_tile2<CH, QUEUE, 2, false, true>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red,
+                                                   slice, first, drift, status))
       break;
     if (!QUEUE && a.tile_drift && __syncthreads_or(drift != drift0) && threadIdx.x == 0) a.tile_drift[tile] = 1;
     first = false;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(64) k_repair(BwdArgs a) {
     const float4 rp = pop ? rv.rec[static_cast<size_t>(ps.rc[ct] - 1) * P + off[ct]] : make_float4(0, 0, 0, 0);
     float g[2][8];
     unsigned drift = 0;
-    pair_stroke<false>(ps, S, Pr, i1, at_ck, cko, rv, valid, off, g, drift);
+    pair_stroke<false>(ps, S, Pr, i1, at_ck, cko, (i1 & (kRenorm - 1)) == 0, rv, valid, off, g, drift);
     float* o = out + static_cast<size_t>(i1 - 1) * 8;
     if (active) {
       float4 ckp = make_float4(0.0f, 0.0f, 0.0f, 0.0f);

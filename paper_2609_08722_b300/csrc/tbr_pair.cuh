@@ -598,13 +598,14 @@ __device__ __forceinline__ void load_pair(const BwdArgs& a, int px, int py0, boo
 }
 
 // Stroke i1 of the paired replay adjoint (S: packed record, P: pair record;
-// at_ck / cko: checkpoint stroke and its record offset).  Writes each pixel's 8
-// gradient values to g[c][.].  At a checkpoint, counts in drift the pixels
-// whose regenerated position drifted past rv.drift_tol and, with QUEUE, queues
-// a pixel's first drifting segment on rv.repair_list.
+// at_ck / cko: checkpoint stroke and its record offset; renorm: i1 is a
+// multiple of kRenorm, after which a regenerated position is renormalised).
+// Writes each pixel's 8 gradient values to g[c][.].  At a checkpoint, counts
+// in drift the pixels whose regenerated position drifted past rv.drift_tol
+// and, with QUEUE, queues a pixel's first drifting segment on rv.repair_list.
 template <bool QUEUE>
 __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restrict__ S, const f2* __restrict__ P,
-                                            int i1, bool at_ck, size_t cko, const RecordView& rv,
+                                            int i1, bool at_ck, size_t cko, bool renorm, const RecordView& rv,
                                             const bool (&valid)[2], const size_t (&off)[2], float (&g)[2][8],
                                             unsigned& drift) {
   const bool pop0 = i1 == ps.nri[0], pop1 = i1 == ps.nri[1];
@@ -651,7 +652,7 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
     }
   } else {
     add_frame_disp2(ps.Xl, ps.Yl, P, ds, dh);
-    if ((i1 & (kRenorm - 1)) == 0) {
+    if (renorm) {
       pos_renorm2(ps.Xh, ps.Xl);
       pos_renorm2(ps.Yh, ps.Yl);
     }
@@ -1070,9 +1071,13 @@ __device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __rest
 // checkpoint drift first exceeds rv.drift_tol is appended, with the start of
 // that segment, to rv.repair_list (off[c] is then the pixel index) for the
 // FP64 repair pass.  With COUPLED, the strokes follow the coupling variant
-// Phi_g (pair_stroke_g; gext is shared [CH][kPairExtG] float2).  All threads
-// of the CTA must call it.  Returns false if a bounded wait gave up.
-template <int CH, bool QUEUE, int UNROLL = 1, bool COUPLED = false>
+// Phi_g (pair_stroke_g; gext is shared [CH][kPairExtG] float2).  With BLOCKED
+// and a checkpoint interval that is a multiple of kRenorm, the strokes run in
+// aligned blocks whose inner strokes skip the checkpoint and renormalisation
+// tests (a second copy of the loop: it costs registers, so only the standalone
+// capsule adjoint takes it).  All threads of the CTA must call it.  Returns
+// false if a bounded wait gave up.
+template <int CH, bool QUEUE, int UNROLL = 1, bool COUPLED = false, bool BLOCKED = false>
 __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, const bool (&valid)[2],
                                const PixelState (&st)[2], const float (&lC)[2][3], const float bg[3],
                                const RecordView& rv, const size_t (&off)[2], f2* __restrict__ pbuf,
@@ -1086,6 +1091,7 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
   PairState ps;
   pair_state_init(ps, valid, st, lC, bg, rv, off);
   int next_ck = (ck < n) ? ck : 0;
+  const bool ck_aligned = BLOCKED && (ck & (kRenorm - 1)) == 0 && (CH & (kRenorm - 1)) == 0;
   const int nch = (n + CH - 1) / CH;
   auto chunk_src = [&](int q) { return packed + static_cast<size_t>(q) * CH * kRec; };
   auto chunk_cnt = [&](int q) { return min(CH, n - q * CH); };
@@ -1108,11 +1114,10 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
     if (COUPLED) pair_ext_g_fill(S0, cntc, gext);
     __syncthreads();
     float (*rb)[CH * 8] = red[b];
-#pragma unroll UNROLL
-    for (int j = 0; j < cntc; ++j) {
+    // one stroke: regeneration, adjoint step, VJP, and the warp reduce-scatter of its 8 values
+    auto stroke = [&](int j, bool at_ck, bool renorm) {
       const int i1 = q * CH + j + 1;
       float vv[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-      const bool at_ck = (i1 == next_ck);  // CTA-uniform
       size_t cko = 0;
       if (at_ck) {
         next_ck = (next_ck + ck < n) ? next_ck + ck : 0;
@@ -1124,12 +1129,31 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
           pair_stroke_g(ps, S0 + j * kRec, pbuf + j * kPairRec, gext + j * kPairExtG, i1, at_ck, cko, rv, valid,
                         off, g, drift);
         else
-          pair_stroke<QUEUE>(ps, S0 + j * kRec, pbuf + j * kPairRec, i1, at_ck, cko, rv, valid, off, g, drift);
+          pair_stroke<QUEUE>(ps, S0 + j * kRec, pbuf + j * kPairRec, i1, at_ck, cko, renorm, rv, valid, off, g,
+                             drift);
 #pragma unroll
         for (int k = 0; k < 8; ++k) vv[k] = g[0][k] + g[1][k];
       }
       const float r = warp_reduce8(vv);
       if ((lane & 3) == 0) rb[warp][j * 8 + ((lane >> 2) & 7)] = r;
+    };
+    if (BLOCKED && ck_aligned) {
+      // blocks of kRenorm strokes aligned to the stroke index (q CH is a multiple
+      // of kRenorm): only a block's last stroke can be a checkpoint or a
+      // renormalisation point, so the others run without either test
+      for (int j0 = 0; j0 < cntc; j0 += kRenorm) {
+        const int jl = min(j0 + kRenorm, cntc) - 1;
+#pragma unroll UNROLL
+        for (int j = j0; j < jl; ++j) stroke(j, false, false);
+        const int il = q * CH + jl + 1;
+        stroke(jl, il == next_ck, (il & (kRenorm - 1)) == 0);  // (next_ck is CTA-uniform)
+      }
+    } else {
+#pragma unroll UNROLL
+      for (int j = 0; j < cntc; ++j) {
+        const int i1 = q * CH + j + 1;
+        stroke(j, i1 == next_ck, (i1 & (kRenorm - 1)) == 0);
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0 && q + 2 < nch) ring.issue(b, chunk_src(q + 2), chunk_cnt(q + 2));

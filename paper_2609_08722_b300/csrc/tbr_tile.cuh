@@ -89,15 +89,9 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
     const int cntc = chunk_cnt(q);
     const float* S0 = ring.data(b);
     if (live) {
-#pragma unroll 4
-      for (int j = cntc - 1; j >= 0; --j) {
+      // one stroke (j: index in the chunk); true once the pixel took its early exit
+      auto stroke = [&](int j) -> bool {
         const int i1 = base + j + 1;  // the paper's 1-based stroke index
-        if (RECORD && i1 == next_ck) {
-          const size_t o = static_cast<size_t>(i1 / ck - 1) * rv.stride + rv.off;
-          rv.ckpt[o] = make_float4(st.xh, st.yh, st.xl, st.yl);
-          rv.ck_lt[o] = st.lt;
-          next_ck -= ck;
-        }
         const float* S = S0 + j * kRec;
         const StrokeF g = load_stroke(S);
         float sp, rb = g.r, ds = 0.0f, dh = 0.0f, ddx = 0.0f, ddy = 0.0f;
@@ -143,7 +137,7 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
         st.lt -= cv.sp2;
         if (EXIT && st.lt < exit_lt) {
           live = false;
-          break;
+          return true;
         }
         if (DROPS) {
           st.cnt += drops_step(st.xh, st.yh, st.xl, st.yl, g);
@@ -158,11 +152,47 @@ __device__ bool soft_forward_tile(ChunkRing<CH>& ring, const float* __restrict__
           }
           st.xl += ddx;
           st.yl += ddy;
-          if ((i1 & (kRenorm - 1)) == 1) {
-            pos_renorm(st.xh, st.xl);
-            pos_renorm(st.yh, st.yl);
+        }
+        return false;
+      };
+      auto checkpoint = [&](int i1) {
+        const size_t o = static_cast<size_t>(i1 / ck - 1) * rv.stride + rv.off;
+        rv.ckpt[o] = make_float4(st.xh, st.yh, st.xl, st.yl);
+        rv.ck_lt[o] = st.lt;
+        next_ck -= ck;
+      };
+      // Blocks of kRenorm strokes aligned to the stroke index (base is a multiple
+      // of kRenorm): the position is renormalised after each block's last stroke
+      // (index = 1 mod kRenorm), and with a checkpoint interval that is a multiple
+      // of kRenorm a checkpoint can only fall before a block's first stroke, so
+      // neither test runs per stroke.
+      const bool ck_aligned = (ck & (kRenorm - 1)) == 0;
+      for (int hi = cntc - 1; hi >= 0;) {
+        const int lo = hi & ~(kRenorm - 1);
+        bool stop = false;
+        if (!RECORD || ck_aligned) {
+          if (RECORD && base + hi + 1 == next_ck) checkpoint(base + hi + 1);
+#pragma unroll 4
+          for (int j = hi; j >= lo; --j)
+            if (stroke(j)) {
+              stop = true;
+              break;
+            }
+        } else {
+          for (int j = hi; j >= lo; --j) {
+            if (base + j + 1 == next_ck) checkpoint(base + j + 1);
+            if (stroke(j)) {
+              stop = true;
+              break;
+            }
           }
         }
+        if (stop) break;
+        if (!DROPS && !INERT) {
+          pos_renorm(st.xh, st.xl);
+          pos_renorm(st.yh, st.yl);
+        }
+        hi = lo - 1;
       }
     }
     if (!EXIT) {
