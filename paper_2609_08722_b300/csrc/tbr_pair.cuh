@@ -403,19 +403,9 @@ __device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict_
     pair_records_fill<true>(S0, cntc, pbuf, pext);
     __syncthreads();
     if (any) {
-      for (int j = cntc - 1; j >= 0; --j) {
+      // one stroke (j: index in the chunk)
+      auto stroke = [&](int j) {
         const int i1 = base + j + 1;  // the paper's 1-based stroke index
-        if (RECORD && i1 == next_ck) {
-          const size_t o = static_cast<size_t>(i1 / ck - 1) * rv.stride;
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            if (valid[c]) {
-              rv.ckpt[o + off[c]] = make_float4(comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c));
-              rv.ck_lt[o + off[c]] = comp(LT, c);
-            }
-          }
-          next_ck -= ck;
-        }
         const f2* P = pbuf + j * kPairRec;
         const f2* X = pext + j * kPairExt;
         const f2 dx = add2(sub2(Xh, P[P_MX]), Xl), dy = add2(sub2(Yh, P[P_MY]), Yl);
@@ -472,10 +462,34 @@ __device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict_
         LT = sub2(LT, cv.sp2);  // log2 T_{i-1} = log2 T_i + log2(1 - alpha_i)
         Xl = add2(Xl, ddx);
         Yl = add2(Yl, ddy);
-        if ((i1 & (kRenorm - 1)) == 1) {
-          pos_renorm2(Xh, Xl);
-          pos_renorm2(Yh, Yl);
+      };
+      auto checkpoint = [&](int i1) {
+        const size_t o = static_cast<size_t>(i1 / ck - 1) * rv.stride;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (valid[c]) {
+            rv.ckpt[o + off[c]] = make_float4(comp(Xh, c), comp(Yh, c), comp(Xl, c), comp(Yl, c));
+            rv.ck_lt[o + off[c]] = comp(LT, c);
+          }
         }
+        next_ck -= ck;
+      };
+      // blocks of kRenorm strokes aligned to the stroke index, as soft_forward_tile
+      const bool ck_aligned = (ck & (kRenorm - 1)) == 0;
+      for (int hi = cntc - 1; hi >= 0;) {
+        const int lo = hi & ~(kRenorm - 1);
+        if (!RECORD || ck_aligned) {
+          if (RECORD && base + hi + 1 == next_ck) checkpoint(base + hi + 1);
+          for (int j = hi; j >= lo; --j) stroke(j);
+        } else {
+          for (int j = hi; j >= lo; --j) {
+            if (base + j + 1 == next_ck) checkpoint(base + j + 1);
+            stroke(j);
+          }
+        }
+        pos_renorm2(Xh, Xl);
+        pos_renorm2(Yh, Yl);
+        hi = lo - 1;
       }
     }
     __syncthreads();

@@ -20,10 +20,12 @@ constexpr int kServeCH = 32;
 
 __device__ __forceinline__ long long ld_volatile_ll(const volatile long long* p) { return *p; }
 
-// Two CTAs per SM: the paired adjoint keeps its 128 registers without spills
-// (at three CTAs per SM its spills cost the soft requests more than the third
-// CTA gains the hard ones).  The host leaves eight CTA slots of the machine to
-// the packing, edit and epilogue kernels of other requests.
+// Two CTAs per SM at 128 registers (at three CTAs per SM the paired adjoint's
+// spills cost the soft requests more than the third CTA gains the hard ones).
+// The soft items run the blocked stroke loops of the standalone kernels (the
+// adjoint also two strokes per iteration); their second loop copies cost a few
+// spilled registers and still win.  The host leaves eight CTA slots of the
+// machine to the packing, edit and epilogue kernels of other requests.
 __global__ void __launch_bounds__(kTileThreads, 2) k_serve(ServeArgs a) {
   __shared__ __align__(128) float sbuf[2 * kServeCH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
@@ -206,8 +208,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_serve(ServeArgs a) {
           lC[c][0] = d.seed_scale * e0; lC[c][1] = d.seed_scale * e1; lC[c][2] = d.seed_scale * e2;
           if (st[c].cnt > d.cap) ++ovf;
         }
-        if (!backward_tile2<kServeCH, false>(ring, d.packed, d.n, valid, st, lC, d.bg, rv, off, pbuf, red, slice, first,
-                                      drift, d.status)) {
+        if (!backward_tile2<kServeCH, false, 2, false, true>(ring, d.packed, d.n, valid, st, lC, d.bg, rv, off, pbuf,
+                                                             red, slice, first, drift, d.status)) {
           ok = false;
           break;
         }
