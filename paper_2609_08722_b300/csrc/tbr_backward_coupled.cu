@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_backward_c2(BwdArgs a) {
     PixelState st[2];
     float lC[2][3];
     load_pair(a, px, py0, skip, valid, off, st, lC);
-    if (!backward_tile2<CH, false, 1, true>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red, slice,
-                                            first, drift, status, gext))
+    if (!backward_tile2<CH, false, 1, true, true>(ring, a.packed, n, valid, st, lC, a.bg, rv, off, pbuf, red,
+                                                  slice, first, drift, status, gext))
       break;
     first = false;
   }

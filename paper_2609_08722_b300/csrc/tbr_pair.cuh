@@ -1088,9 +1088,9 @@ __device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __rest
 // Phi_g (pair_stroke_g; gext is shared [CH][kPairExtG] float2).  With BLOCKED
 // and a checkpoint interval that is a multiple of kRenorm, the strokes run in
 // aligned blocks whose inner strokes skip the checkpoint and renormalisation
-// tests (a second copy of the loop: it costs registers, so only the standalone
-// capsule adjoint takes it).  All threads of the CTA must call it.  Returns
-// false if a bounded wait gave up.
+// tests (a second copy of the loop; it costs registers, but measured faster in
+// every adjoint that uses this tile).  All threads of the CTA must call it.
+// Returns false if a bounded wait gave up.
 template <int CH, bool QUEUE, int UNROLL = 1, bool COUPLED = false, bool BLOCKED = false>
 __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ packed, int n, const bool (&valid)[2],
                                const PixelState (&st)[2], const float (&lC)[2][3], const float bg[3],
