@@ -124,6 +124,8 @@ def parse_args():
                     help="requests of the serving stream (0 skips the serving measurement)")
     ap.add_argument("--res", type=int, default=RES, help="square resolution (profiling cases only)")
     ap.add_argument("--strokes", type=int, default=N_STROKES, help="stroke count (profiling cases only)")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="profiling cases only: skip the peak microbenchmark (the roofline then uses the derived peaks)")
     ap.add_argument("--coupling", action="store_true",
                     help="profiling cases only: time the coupling variant Phi_g (seeded profiles) as the main step")
     return ap.parse_args()
@@ -437,7 +439,8 @@ def run_native(args):
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if world == 1 else local
 
     try:
-        measure_peaks()
+        if not args.no_peaks:
+            measure_peaks()
     except tbr.TbrError as e:
         print(f"bench: peak measurement failed ({e}); the roofline uses the derived peaks", file=sys.stderr)
     prog_h, targ_h = rank_programs(rank, args.strokes)
