@@ -22,6 +22,8 @@ __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 // a - b as one FFMA2: b * (-1) + a
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// a * b - c as one FFMA2 with the addend negated (a single rounding)
+__device__ __forceinline__ f2 fms2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, make_float2(-c.x, -c.y)); }
 __device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ f2 sgn2(f2 a) { return make_float2(sgn1(a.x), sgn1(a.y)); }
 __device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
@@ -174,13 +176,13 @@ __device__ __forceinline__ int phi_pair(f2 s, f2 h, const f2* __restrict__ P, Ge
   delta = sel2(capo_x, capo_y, min2(max2(delta, F2(0.0f)), room), F2(0.0f));
   const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
   const f2 cD = sub2(F2(1.0f), omc);
-  const f2 dSc = fma2(dsp, q.sb, mul2(q.sp, sub2(mul2(q.cb, sD), mul2(q.sb, omc))));
-  const f2 dH = sub2(mul2(dsp, q.cb), mul2(q.sp, fma2(q.sb, sD, mul2(q.cb, omc))));
+  const f2 dSc = fma2(dsp, q.sb, mul2(q.sp, fms2(q.cb, sD, mul2(q.sb, omc))));
+  const f2 dH = fms2(dsp, q.cb, mul2(q.sp, fma2(q.sb, sD, mul2(q.cb, omc))));
   // flank to flank: translation along the flank
   const f2 dSf = mul2(mul2(q.tn, F2(kPiF)), mul2(dsp, q.iQ));
   const f2 dS = sel2(capo_x, capo_y, dSc, dSf);
   q.ud = fma2(q.sb, cD, mul2(q.cb, sD));
-  q.uh = sub2(mul2(q.cb, cD), mul2(q.sb, sD));
+  q.uh = fms2(q.cb, cD, mul2(q.sb, sD));
   q.phi = add2(q.beta, delta);
   ds = mul2(q.sgs, dS);
   dh = mul2(q.sgh, dH);
@@ -221,7 +223,7 @@ __device__ __forceinline__ int psi_pair(f2 s, f2 h, const f2* __restrict__ P, co
   f2 delta = mul2(mul2(mul2(nds, L), sub2(phi, F2(0.5f * kPiF))), mul2(iQp, rcp2(sig)));
   delta = sel2(ci_x, ci_y, min2(max2(delta, mul2(phi, F2(-1.0f))), F2(0.0f)), F2(0.0f));
   const f2 sD = sin_pi2_2(delta), omc = omc_pi2_2(delta);
-  const f2 dSc = sub2(mul2(sig, sub2(mul2(uh, sD), mul2(ud, omc))), mul2(nds, ud));
+  const f2 dSc = fms2(sig, fms2(uh, sD, mul2(ud, omc)), mul2(nds, ud));
   const f2 dH = mul2(F2(-1.0f), fma2(sig, fma2(ud, sD, mul2(uh, omc)), mul2(nds, uh)));
   // flank to flank: tangential step |s| pi (sigma - sigma') / Q'
   const f2 dSf = mul2(mul2(as, F2(-kPiF)), mul2(nds, iQp));
@@ -283,7 +285,7 @@ __device__ __forceinline__ void pos_renorm2(f2& hi, f2& lo) {
 }
 // Adds a frame displacement to the lo parts of two hi/lo positions.
 __device__ __forceinline__ void add_frame_disp2(f2& xl, f2& yl, const f2* __restrict__ P, f2 ds, f2 dh) {
-  xl = add2(xl, sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY])));
+  xl = add2(xl, fms2(ds, P[P_EX], mul2(dh, P[P_EY])));
   yl = add2(yl, fma2(ds, P[P_EY], mul2(dh, P[P_EX])));
 }
 
@@ -297,14 +299,14 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
                                           f2& gcx, f2& gcy, f2& gth, f2& gL, f2& gr) {
   const f2 ex = P[P_EX], ey = P[P_EY], L = P[P_L];
   const f2 ls = fma2(lamx, ex, mul2(lamy, ey));
-  const f2 lh = sub2(mul2(lamy, ex), mul2(lamx, ey));
+  const f2 lh = fms2(lamy, ex, mul2(lamx, ey));
   const f2 gsn = mul2(q.sgs, ls), ghn = mul2(q.sgh, lh);
   const f2 gcvn = mul2(mua, P[P_IW]);               // minus the coverage's cotangent of sigma'
   // g . u(beta), g . u'(beta), g . u(phi), g . u'(phi)  (u(a) = (sin a, cos a), u' = (cos a, -sin a))
   const f2 gu = fma2(gsn, q.sb, mul2(ghn, q.cb));
-  const f2 gup = sub2(mul2(gsn, q.cb), mul2(ghn, q.sb));
+  const f2 gup = fms2(gsn, q.cb, mul2(ghn, q.sb));
   const f2 guf = fma2(gsn, q.ud, mul2(ghn, q.uh));
-  const f2 gufp = sub2(mul2(gsn, q.uh), mul2(ghn, q.ud));
+  const f2 gufp = fms2(gsn, q.uh, mul2(ghn, q.ud));
   const f2 sgL = mul2(sub2(q.dsp, P[P_R]), q.iQ);   // d sigma / dL
   const f2 sgr = mul2(P[P_NPR], q.iQ);              // d sigma / dr
   const f2 dspL = mul2(q.dsp, L);
@@ -318,13 +320,13 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
   const f2 g_sp = sub2(fma2(pdQ, gu, sub2(gu, guf)), fma2(nsdsp, gup, gcvn));
   const f2 g_ph = mul2(fma2(sub2(sdphi, q.dsp), gup, mul2(q.sp, sub2(gup, gufp))), q.isp);
   f2 ws = fma2(q.ud, g_sp, mul2(q.uh, g_ph));
-  f2 wh = sub2(mul2(q.uh, g_sp), mul2(q.ud, g_ph));
+  f2 wh = fms2(q.uh, g_sp, mul2(q.ud, g_ph));
   // explicit L and r through sigma and delta
   const f2 sdL = mul2(K, sub2(fma2(neg2(L), sgL, q.dsp), mul2(dspL, fma2(sgL, q.isg, q.iQp))));
   const f2 nsdr = mul2(mul2(K, mul2(L, sgr)), mul2(q.sp, q.isg));  // -sigma delta_r
   f2 gLm = fma2(F2(-0.5f), ws, fma2(sgL, gu, mul2(sdL, gup)));
-  f2 grm = sub2(mul2(sgr, gu), mul2(nsdr, gup));
-  f2 th = sub2(mul2(sdphi, gup), mul2(P[P_HL], wh));
+  f2 grm = fms2(sgr, gu, mul2(nsdr, gup));
+  f2 th = fms2(sdphi, gup, mul2(P[P_HL], wh));
   const bool fx = q.sb.x == 0.0f, fy = q.sb.y == 0.0f;
   if (__any_sync(__activemask(), fx || fy)) {  // flank to flank
     const f2 as = abs2(q.si);
@@ -348,7 +350,7 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
   gL = gLm;
   gr = fma2(mua, sub2(P[P_IW], mul2(z, P[P_DLW])), grm);
   const f2 GS = mul2(q.sgs, ws), GH = mul2(q.sgh, wh);
-  const f2 dlx = sub2(mul2(GS, ex), mul2(GH, ey));
+  const f2 dlx = fms2(GS, ex, mul2(GH, ey));
   const f2 dly = fma2(GS, ey, mul2(GH, ex));
   gcx = neg2(dlx);
   gcy = neg2(dly);
@@ -416,10 +418,10 @@ __device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict_
           fix = drop_pair(dx, dy, P, X, sp, ddx, ddy);
         } else {
           const f2 s = fma2(dx, P[P_EX], mul2(dy, P[P_EY]));
-          const f2 h = sub2(mul2(dy, P[P_EX]), mul2(dx, P[P_EY]));
+          const f2 h = fms2(dy, P[P_EX], mul2(dx, P[P_EY]));
           f2 ds, dh;
           fix = psi_pair(s, h, P, X, sp, ds, dh);
-          ddx = sub2(mul2(ds, P[P_EX]), mul2(dh, P[P_EY]));
+          ddx = fms2(ds, P[P_EX], mul2(dh, P[P_EY]));
           ddy = fma2(ds, P[P_EY], mul2(dh, P[P_EX]));
         }
         if (fix) {  // floored or cap to flank: scalar step per pixel
