@@ -24,6 +24,8 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c
 __device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 // a * b - c as one FFMA2 with the addend negated (a single rounding)
 __device__ __forceinline__ f2 fms2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, make_float2(-c.x, -c.y)); }
+// c - a * b as one FFMA2 with a negated factor
+__device__ __forceinline__ f2 fnma2(f2 a, f2 b, f2 c) { return __ffma2_rn(make_float2(-a.x, -a.y), b, c); }
 __device__ __forceinline__ f2 abs2(f2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ f2 sgn2(f2 a) { return make_float2(sgn1(a.x), sgn1(a.y)); }
 __device__ __forceinline__ f2 max2(f2 a, f2 b) { return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y)); }
@@ -285,8 +287,8 @@ __device__ __forceinline__ void pos_renorm2(f2& hi, f2& lo) {
 }
 // Adds a frame displacement to the lo parts of two hi/lo positions.
 __device__ __forceinline__ void add_frame_disp2(f2& xl, f2& yl, const f2* __restrict__ P, f2 ds, f2 dh) {
-  xl = add2(xl, fms2(ds, P[P_EX], mul2(dh, P[P_EY])));
-  yl = add2(yl, fma2(ds, P[P_EY], mul2(dh, P[P_EX])));
+  xl = fma2(ds, P[P_EX], fnma2(dh, P[P_EY], xl));
+  yl = fma2(ds, P[P_EY], fma2(dh, P[P_EX], yl));
 }
 
 // VJP of one regeneration step for two pixels, in the displacement form of
@@ -322,7 +324,7 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
   f2 ws = fma2(q.ud, g_sp, mul2(q.uh, g_ph));
   f2 wh = fms2(q.uh, g_sp, mul2(q.ud, g_ph));
   // explicit L and r through sigma and delta
-  const f2 sdL = mul2(K, sub2(fma2(neg2(L), sgL, q.dsp), mul2(dspL, fma2(sgL, q.isg, q.iQp))));
+  const f2 sdL = mul2(K, fnma2(dspL, fma2(sgL, q.isg, q.iQp), fma2(neg2(L), sgL, q.dsp)));
   const f2 nsdr = mul2(mul2(K, mul2(L, sgr)), mul2(q.sp, q.isg));  // -sigma delta_r
   f2 gLm = fma2(F2(-0.5f), ws, fma2(sgL, gu, mul2(sdL, gup)));
   f2 grm = fms2(sgr, gu, mul2(nsdr, gup));
@@ -348,14 +350,13 @@ __device__ __forceinline__ void step_vjp2(const Geo2& q, const f2* __restrict__ 
   }
   gth = mul2(mul2(q.sgs, q.sgh), th);
   gL = gLm;
-  gr = fma2(mua, sub2(P[P_IW], mul2(z, P[P_DLW])), grm);
+  gr = fma2(mua, fnma2(z, P[P_DLW], P[P_IW]), grm);
   const f2 GS = mul2(q.sgs, ws), GH = mul2(q.sgh, wh);
-  const f2 dlx = fms2(GS, ex, mul2(GH, ey));
-  const f2 dly = fma2(GS, ey, mul2(GH, ex));
-  gcx = neg2(dlx);
-  gcy = neg2(dly);
-  lamx = add2(lamx, dlx);
-  lamy = add2(lamy, dly);
+  // the centre's cotangent -dlambda, formed directly (the negations fold into the FFMA2 / FMUL2 operands)
+  gcx = fms2(GH, ey, mul2(GS, ex));
+  gcy = fnma2(GS, ey, mul2(neg2(GH), ex));
+  lamx = sub2(lamx, gcx);
+  lamy = sub2(lamy, gcy);
 }
 
 // Thread -> pixel pair of a 32 x 16 tile: column lane, rows 2 warp and 2 warp + 1.
