@@ -20,8 +20,8 @@ __device__ __forceinline__ f2 F2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ f2 add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ f2 mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
-// a - b as one FFMA2: b * (-1) + a
-__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// a - b as one FADD2 with the second operand negated (the same rounding as a - b)
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 // a * b - c as one FFMA2 with the addend negated (a single rounding)
 __device__ __forceinline__ f2 fms2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, make_float2(-c.x, -c.y)); }
 // c - a * b as one FFMA2 with a negated factor
