@@ -8,9 +8,12 @@
 // When recording: a sample the floor touched pushes (x_i, i) onto the pixel's
 // side table (Lemma "Support of the replay record"), every k-th stroke stores
 // (x_i, log2 T_i), and s_0 = (x_0, log2 T_0, record count) closes the pixel.
-// The recording forward of the capsule map runs two pixels per thread
-// (k_soft2: 32x16 tiles, soft_forward_tile2, the pair arithmetic of the adjoint
-// and of the serving kernel); the other instances keep one pixel per thread.
+// The capsule map's recording forward runs two pixels per thread (k_soft2:
+// 32x16 tiles, soft_forward_tile2, the pair arithmetic of the adjoint and of the
+// serving kernel); the forward-only instances keep one pixel per thread, so that
+// a render with the early exit and one without share their arithmetic (a
+// paired forward-only render measured 5.54 vs 5.94 ms), as do the inert, R_D and
+// Phi_g instances.
 // (The paired form first measured slower, 7.34 vs 6.96 ms; after the blocked
 // stroke loop and the FFMA2 folds it is 5.99 vs 6.16 ms at 1024^2 x 2000.)
 #include <math.h>
@@ -74,9 +77,10 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
 }
 
 
-// The recording forward of the capsule map with two pixels per thread (32 x 16
-// tiles, soft_forward_tile2, as the serving kernel runs it).
-template <int CH>
+// The soft forward of the capsule map with two pixels per thread (32 x 16
+// tiles, soft_forward_tile2, as the serving kernel runs it); RECORD: with the
+// replay record.
+template <int CH, bool RECORD>
 __global__ void __launch_bounds__(kTileThreads) k_soft2(SoftArgs a) {
   __shared__ __align__(128) float sbuf[2 * CH * kRec];
   __shared__ __align__(8) uint64_t sbar[2];
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(kTileThreads) k_soft2(SoftArgs a) {
   }
   RecordView rv{a.rec, a.rec_i, a.ckpt, a.ck_lt, P, 0, a.cap, a.ck_every};
   PixelState st[2];
-  const bool ok = soft_forward_tile2<CH, true>(ring, a.packed, a.n, valid, x0, y0, rv, off, pbuf, pext, st, status);
+  const bool ok = soft_forward_tile2<CH, RECORD>(ring, a.packed, a.n, valid, x0, y0, rv, off, pbuf, pext, st, status);
   unsigned c_tot = 0, c_max = 0, c_ovf = 0;
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -116,11 +120,14 @@ __global__ void __launch_bounds__(kTileThreads) k_soft2(SoftArgs a) {
     a.out_rgb[3 * p + 0] = o0;
     a.out_rgb[3 * p + 1] = o1;
     a.out_rgb[3 * p + 2] = o2;
-    a.s0[p] = make_float4(st[c].xh, st[c].yh, st[c].xl, st[c].yl);
-    a.s0b[p] = make_float2(st[c].lt, __int_as_float(st[c].cnt));
-    const unsigned cc = static_cast<unsigned>(st[c].cnt);
-    c_tot += cc; c_max = max(c_max, cc); c_ovf += cc > static_cast<unsigned>(a.cap) ? 1u : 0u;
+    if (RECORD) {
+      a.s0[p] = make_float4(st[c].xh, st[c].yh, st[c].xl, st[c].yl);
+      a.s0b[p] = make_float2(st[c].lt, __int_as_float(st[c].cnt));
+      const unsigned cc = static_cast<unsigned>(st[c].cnt);
+      c_tot += cc; c_max = max(c_max, cc); c_ovf += cc > static_cast<unsigned>(a.cap) ? 1u : 0u;
+    }
   }
+  if (!RECORD) return;
   const unsigned tot = __reduce_add_sync(0xffffffffu, c_tot);
   const unsigned mx = __reduce_max_sync(0xffffffffu, c_max);
   const unsigned ovf = __reduce_add_sync(0xffffffffu, c_ovf);
@@ -150,7 +157,7 @@ cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
   } else if (rec && a.inert) {
     k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
   } else if (rec) {
-    k_soft2<kSoftCH><<<pair_tile_count(a.W, a.H), kTileThreads, 0, st>>>(a);
+    k_soft2<kSoftCH, true><<<pair_tile_count(a.W, a.H), kTileThreads, 0, st>>>(a);
   } else if (a.inert) {
     if (ex) k_soft<kSoftCH, false, true, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
     else k_soft<kSoftCH, false, true><<<tiles, kTileThreads, 0, st>>>(a);
