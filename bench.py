@@ -526,7 +526,9 @@ def run_native(args):
     roofline = alu_roofline("k_backward_c2 (Phi_g replay adjoint)" if args.coupling else "k_backward2 (replay adjoint)",
                             opc[fam]["adjoint"], units, bwd_ms)
     roofline["traffic"] = None if args.coupling else traffic
-    soft_roofline = alu_roofline("k_soft2 (soft forward + record, two pixels per thread)", opc[fam]["soft_forward"], units, soft_ms)
+    soft_name = ("k_soft (Phi_g soft forward + record)" if args.coupling
+                 else "k_soft2 (soft forward + record, two pixels per thread)")
+    soft_roofline = alu_roofline(soft_name, opc[fam]["soft_forward"], units, soft_ms)
 
     # e2e through the public API with host buffers: upload program + target from
     # pinned memory, fwd + loss + adjoint, read back gradients and loss
