@@ -527,7 +527,7 @@ def run_native(args):
                             opc[fam]["adjoint"], units, bwd_ms)
     roofline["traffic"] = None if args.coupling else traffic
     soft_name = ("k_soft (Phi_g soft forward + record)" if args.coupling
-                 else "k_soft2 (soft forward + record, two pixels per thread)")
+                 else "k_soft (soft forward + record)")
     soft_roofline = alu_roofline(soft_name, opc[fam]["soft_forward"], units, soft_ms)
 
     # e2e through the public API with host buffers: upload program + target from

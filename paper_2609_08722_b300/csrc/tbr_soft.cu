@@ -8,17 +8,14 @@
 // When recording: a sample the floor touched pushes (x_i, i) onto the pixel's
 // side table (Lemma "Support of the replay record"), every k-th stroke stores
 // (x_i, log2 T_i), and s_0 = (x_0, log2 T_0, record count) closes the pixel.
-// The capsule map's recording forward runs two pixels per thread (k_soft2:
-// 32x16 tiles, soft_forward_tile2, the pair arithmetic of the adjoint and of the
-// serving kernel); the forward-only instances keep one pixel per thread, so that
-// a render with the early exit and one without share their arithmetic (a
-// paired forward-only render measured 5.54 vs 5.94 ms), as do the inert, R_D and
-// Phi_g instances.
-// (The paired form first measured slower, 7.34 vs 6.96 ms; after the blocked
-// stroke loop and the FFMA2 folds it is 5.99 vs 6.16 ms at 1024^2 x 2000.)
+// One pixel per thread here.  A two-pixel form (soft_forward_tile2, as the
+// serving kernel runs it) measured 5.99 vs 6.16 ms at 1024^2 x 2000, but its
+// roundings match the adjoint's paired regeneration less closely: along a fit,
+// a checkpoint then drifts past the tolerance every few steps, and the FP64
+// repair of one such pixel (a serial replay of all its strokes) costs 5-13 ms.
 #include <math.h>
 
-#include "tbr_pair.cuh"
+#include "tbr_tile.cuh"
 
 namespace tbr {
 
@@ -77,67 +74,6 @@ __global__ void __launch_bounds__(kTileThreads) k_soft(SoftArgs a) {
 }
 
 
-// The soft forward of the capsule map with two pixels per thread (32 x 16
-// tiles, soft_forward_tile2, as the serving kernel runs it); RECORD: with the
-// replay record.
-template <int CH, bool RECORD>
-__global__ void __launch_bounds__(kTileThreads) k_soft2(SoftArgs a) {
-  __shared__ __align__(128) float sbuf[2 * CH * kRec];
-  __shared__ __align__(8) uint64_t sbar[2];
-  __shared__ __align__(16) f2 pbuf[CH * kPairRec];
-  __shared__ __align__(16) f2 pext[CH * kPairExt];
-  const int lane = threadIdx.x & 31;
-  const int W = a.W, H = a.H;
-  int px, py0;
-  pair_tile_pixel(blockIdx.x, W, px, py0);
-  const size_t P = static_cast<size_t>(W) * H;
-  unsigned long long* status = a.status;
-  const bool invalid_prog = status[ST_INVALID] != 0ull;
-  ChunkRing<CH> ring;
-  ring.init(sbuf, sbar);
-  bool valid[2];
-  size_t off[2];
-  float x0[2], y0[2];
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    const int py = py0 + c;
-    valid[c] = px < W && py < H;
-    off[c] = valid[c] ? static_cast<size_t>(py) * W + px : 0;
-    x0[c] = (static_cast<float>(px) + 0.5f) / static_cast<float>(W);
-    y0[c] = (static_cast<float>(py) + 0.5f) / static_cast<float>(H);
-  }
-  RecordView rv{a.rec, a.rec_i, a.ckpt, a.ck_lt, P, 0, a.cap, a.ck_every};
-  PixelState st[2];
-  const bool ok = soft_forward_tile2<CH, RECORD>(ring, a.packed, a.n, valid, x0, y0, rv, off, pbuf, pext, st, status);
-  unsigned c_tot = 0, c_max = 0, c_ovf = 0;
-#pragma unroll
-  for (int c = 0; c < 2; ++c) {
-    if (!valid[c]) continue;
-    const size_t p = off[c];
-    const float T0 = ex2_a(st[c].lt);
-    float o0 = fmaf(T0, a.bg[0], st[c].C0), o1 = fmaf(T0, a.bg[1], st[c].C1), o2 = fmaf(T0, a.bg[2], st[c].C2);
-    if (invalid_prog || !ok) o0 = o1 = o2 = __int_as_float(0x7fc00000);
-    a.out_rgb[3 * p + 0] = o0;
-    a.out_rgb[3 * p + 1] = o1;
-    a.out_rgb[3 * p + 2] = o2;
-    if (RECORD) {
-      a.s0[p] = make_float4(st[c].xh, st[c].yh, st[c].xl, st[c].yl);
-      a.s0b[p] = make_float2(st[c].lt, __int_as_float(st[c].cnt));
-      const unsigned cc = static_cast<unsigned>(st[c].cnt);
-      c_tot += cc; c_max = max(c_max, cc); c_ovf += cc > static_cast<unsigned>(a.cap) ? 1u : 0u;
-    }
-  }
-  if (!RECORD) return;
-  const unsigned tot = __reduce_add_sync(0xffffffffu, c_tot);
-  const unsigned mx = __reduce_max_sync(0xffffffffu, c_max);
-  const unsigned ovf = __reduce_add_sync(0xffffffffu, c_ovf);
-  if (lane == 0) {
-    if (tot) atomicAdd(status + ST_RECORDS, static_cast<unsigned long long>(tot));
-    if (mx) atomicMax(status + ST_MAXREC, static_cast<unsigned long long>(mx));
-    if (ovf) atomicAdd(status + ST_OVERFLOW, static_cast<unsigned long long>(ovf));
-  }
-}
-
 }  // namespace
 
 cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
@@ -157,7 +93,7 @@ cudaError_t launch_soft(const SoftArgs& a, cudaStream_t st) {
   } else if (rec && a.inert) {
     k_soft<kSoftCH, true, true><<<tiles, kTileThreads, 0, st>>>(a);
   } else if (rec) {
-    k_soft2<kSoftCH, true><<<pair_tile_count(a.W, a.H), kTileThreads, 0, st>>>(a);
+    k_soft<kSoftCH, true, false><<<tiles, kTileThreads, 0, st>>>(a);
   } else if (a.inert) {
     if (ex) k_soft<kSoftCH, false, true, false, false, true><<<tiles, kTileThreads, 0, st>>>(a);
     else k_soft<kSoftCH, false, true><<<tiles, kTileThreads, 0, st>>>(a);
