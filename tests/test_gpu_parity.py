@@ -123,6 +123,67 @@ def test_soft_ragged(small, W, H):
     compare(g, og, sens=sens, label=f"ragged {W}x{H}")
 
 
+@pytest.mark.parametrize("n", [0, 1])
+def test_soft_and_adjoint_of_empty_and_single_stroke_programs(small, n):
+    """No strokes: the soft render is the background, the stroke gradients are
+    empty and the palette's is zero, through the recording render with its
+    adjoint and through the loss-fused call.  One stroke: both against the
+    oracle (a single chunk holding one stroke, no checkpoint)."""
+    p, _ = small
+    q = p.prefix(n)
+    dq = tbr.DeviceProgram.from_host(q)
+    W, H = 37, 21
+    rgb, ctx = tbr.render_soft(dq, W, H, 0.0, 1 / 200, record=True)
+    o = oracle.render_soft(q, W, H, 0.0, 1 / 200)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= (1e-7 if n == 0 else SOFT_TOL)
+    cot = inputs.make_cotangent(22, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(q, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    target = torch.from_numpy(inputs.make_cotangent(23, W * H)).reshape(H, W, 3).cuda()
+    loss, gf, _, _ = tbr.soft_adjoint_mse(dq, target, 0.0, 1 / 200)
+    if n == 0:
+        for k in GROUPS[:-1]:
+            assert g[k].numel() == 0 and gf[k].numel() == 0
+        assert torch.count_nonzero(g["palette"]).item() == 0 and torch.count_nonzero(gf["palette"]).item() == 0
+        bg = torch.tensor(np.asarray(q.background, dtype=np.float32), device="cuda")
+        want = float(((bg.double() - target.double()) ** 2).mean())
+        assert abs(float(loss.item()) - want) <= 1e-6 * max(1.0, want)
+    else:
+        sens = oracle_sensitivity(q, W, H, 0.0, 1 / 200, cot.astype(np.float64), og)
+        compare(g, og, sens=sens, label="one stroke")
+        for k in GROUPS:
+            assert torch.isfinite(gf[k]).all()
+
+
+@pytest.mark.parametrize("W,H,ck,trials", [(58, 46, 32, 3), (58, 46, 48, 3), (29, 23, 64, 20)])
+def test_soft_and_adjoint_of_a_long_program(W, H, ck, trials):
+    """10000 strokes (five times the operating program) on ragged canvases:
+    313 chunks through the stroke ring, up to 312 checkpoints (48 is not a
+    multiple of the renormalisation block, so the stroke loops take their
+    per-stroke checkpoint test), up to 27 side-table records per pixel.
+    On the 29x23 canvas most strokes are smaller than a pixel, so one edge
+    sample sets each of their entries; entries near the floor of the relative
+    bound then move by up to 3e-3 of themselves under one FP32 rounding of the
+    inputs, and three perturbation trials underestimate that move by about
+    half, so that case samples twenty."""
+    p = inputs.make_program(10000, seed=131, palette_seed=231, k=16, r_lo=0.003, r_hi=0.03)
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True, checkpoint_every=ck)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    err = np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"])
+    print(f"long program soft max {err.max():.3e}")
+    assert err.max() <= SOFT_TOL
+    st = ctx.status()
+    recs = o["nrec"].mean()
+    print(f"records/px gpu {st['records'] / (W * H):.2f} oracle {recs:.2f}, max {st['max_records']} / {o['nrec'].max()}")
+    assert abs(st["records"] / (W * H) - recs) < 0.05 * recs + 0.5
+    cot = inputs.make_cotangent(24, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    sens = oracle_sensitivity(p, W, H, 0.0, 1 / 200, cot.astype(np.float64), og, trials=trials)
+    compare(g, og, sens=sens, label=f"10000 strokes, {W}x{H}, k = {ck}")
+
+
 @pytest.mark.parametrize("W,H", [(75, 61), (64, 33)])
 def test_backward_long_strokes(W, H):
     """No drops and strokes up to 0.8 long: most samples sit beside a flank,
