@@ -128,6 +128,10 @@ def parse_args():
                     help="profiling cases only: skip the peak microbenchmark (the roofline then uses the derived peaks)")
     ap.add_argument("--coupling", action="store_true",
                     help="profiling cases only: time the coupling variant Phi_g (seeded profiles) as the main step")
+    ap.add_argument("--profile-case", choices=["rd-soft", "compensation"], default=None,
+                    help="profiling cases only: run one workload alone (the R_D soft forward at --res / --strokes, or "
+                         "the anchor compensation of the --strokes program), --warmup + --steps launches, and print "
+                         "its event times instead of the bench line")
     return ap.parse_args()
 
 
@@ -426,6 +430,37 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
+def run_profile_case(args, prog, W, H, tau, tau_min, device):
+    """One workload other than the step, alone, so that a counter capture of
+    its kernel has few launches before it: W untimed and K event-timed calls."""
+    import torch
+
+    from paper_2609_08722_b300 import tbr
+
+    if args.profile_case == "rd-soft":
+        rgb = torch.empty((H, W, 3), device=device)
+
+        def fn():
+            tbr.render_soft(prog, W, H, tau, tau_min, out_rgb=rgb, transport="drops")
+        what = f"R_D soft forward, {prog.n} strokes at {W}x{H}"
+    else:
+        def fn():
+            tbr.compensate(prog, endpoint=False)
+        what = f"anchor compensation of the {prog.n}-stroke program"
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    print(json.dumps({"profile_case": args.profile_case, "workload": what, "ms": ts}), flush=True)
+
+
 def run_native(args):
     import numpy as np
     import torch
@@ -452,6 +487,10 @@ def run_native(args):
     P = W * H
     target, _, _ = tbr.render_hard(targ, W, H, with_idx=False)
     tau, tau_min = inputs.SHARP_TAU, inputs.SHARP_TAU_MIN
+    if args.profile_case:
+        if rank == 0:
+            run_profile_case(args, prog, W, H, tau, tau_min, device)
+        return
 
     rgb = torch.empty((H, W, 3), device=device)
     _, ctx = tbr.render_soft(prog, W, H, tau, tau_min, record=True, checkpoint_every=CHECKPOINT_EVERY,
