@@ -632,9 +632,17 @@ def run_native(args):
         ee.record()
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks(es.elapsed_time(ee) / args.steps, world, device)
+        # the kernels are deterministic, so the gradients the last e2e step read back
+        # must equal, bit for bit, those of a step on the device-resident inputs
+        _, g_dev = step()
+        torch.cuda.synchronize()
+        same = all(torch.equal(host_out[k], g_dev[k].cpu()) for k in out_names)
+        if not same:
+            print("bench: e2e gradients differ from the device-resident step", file=sys.stderr)
         e2e = {"value": sum_over_ranks(units, world, device) / (e2e_ms * 1e-3), "unit": "evals/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
-               "pipelined": "step k + 1 uploads on a copy stream while step k computes (two input buffers)"}
+               "pipelined": "step k + 1 uploads on a copy stream while step k computes (two input buffers)",
+               "gradients_match_device_step": bool(same)}
 
     # loss-fused forward + adjoint (tbr_render_soft_adjoint_mse): the same kernels behind one call
     fused = None
