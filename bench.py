@@ -821,6 +821,17 @@ def run_native(args):
     # the sort and the repair, which return at once when no checkpoint drifted),
     # epilogue (3)
     kernels_per_step = 1 + 1 + 2 + 1 + 3 + 3
+    # the paper's own timings of this workload on its GPU (Table "adjoint" and the
+    # paragraph "Fitting performance"): another machine, so they stand beside this
+    # run's figures as context; vs_baseline stays null
+    paper = None
+    if args.res == RES and args.strokes == N_STROKES and not args.coupling:
+        k64 = next((r for r in (memory or {}).get("replay", []) if r.get("checkpoint_every") == 64), None)
+        paper = {"machine": "one RTX PRO 4000 (24 GB), FP32, fused Triton adjoint",
+                 "backward_step_s": 0.52, "backward_peak_gb": 1.72, "optimisation_step_s": 0.55,
+                 "this_run": {"backward_s": bwd_ms * 1e-3, "fwd_adjoint_step_s": step_ms_max * 1e-3,
+                              "fit_step_s": fit_ms * 1e-3 if fit_ms else None,
+                              "replay_peak_gb_k64": k64["peak_bytes"] / 1e9 if k64 else None}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
@@ -852,6 +863,7 @@ def run_native(args):
             "gpu_launches": kernels_per_step * args.steps,
             "records_per_pixel": st["records"] / P, "max_records": st["max_records"],
             "drift_resets": st["drift_resets"], "wall_s": wall,
+            "paper_context": paper,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
