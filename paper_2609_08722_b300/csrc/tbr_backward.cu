@@ -180,13 +180,13 @@ __global__ void __launch_bounds__(64) k_repair(BwdArgs a) {
                 const_cast<float*>(a.ck_lt), P, 0, a.cap, ck};
   rv.drift_tol = a.drift_tol;
   PairState ps;
-  pair_state_init(ps, valid, st, lC, a.bg, rv, off);
+  pair_state_init(ps, valid, st, lC, rv, off);
   PixAdj ra{};
   double x64 = 0.0, y64 = 0.0;
   bool active = false;
   auto start = [&]() {
     ra = PixAdj{comp(ps.Xh, ct), comp(ps.Yh, ct), comp(ps.Xl, ct), comp(ps.Yl, ct), comp(ps.LT, ct),
-                comp(ps.LTT, ct), comp(ps.LX, ct), comp(ps.LY, ct)};
+                comp(ps.LD, ct), comp(ps.LX, ct), comp(ps.LY, ct)};
     x64 = static_cast<double>(ra.xh) + static_cast<double>(ra.xl);
     y64 = static_cast<double>(ra.yh) + static_cast<double>(ra.yl);
     active = true;
@@ -199,6 +199,9 @@ __global__ void __launch_bounds__(64) k_repair(BwdArgs a) {
     const float* S = a.packed + static_cast<size_t>(i1 - 1) * kRec;
 #pragma unroll
     for (int k = 0; k < kPairRec; ++k) Pr[k] = F2(S[k]);
+    // the colour step c_i - c_{i-1}, as the adjoint's pair records hold it (pair_records_fill)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) Pr[P_CR + c] = F2(S[F_CR + c] - (i1 > 1 ? S[F_CR + c - kRec] : a.bg[c]));
     const bool at_ck = (i1 == next_ck);
     size_t cko = 0;
     if (at_ck) {
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(64) k_repair(BwdArgs a) {
       ra.xh = static_cast<float>(x64); ra.xl = static_cast<float>(x64 - static_cast<double>(ra.xh));
       ra.yh = static_cast<float>(y64); ra.yl = static_cast<float>(y64 - static_cast<double>(ra.yh));
       float v[8];
-      scalar_stroke(ra, load_stroke(S), S, lC[ct][0], lC[ct][1], lC[ct][2], pop, at_ck, true, rp, ckp, ckl,
+      scalar_stroke(ra, load_stroke(S), Pr, lC[ct][0], lC[ct][1], lC[ct][2], pop, at_ck, true, rp, ckp, ckl,
                     a.drift_tol, v);
       if (pop) {
         x64 = static_cast<double>(rp.x) + static_cast<double>(rp.z);

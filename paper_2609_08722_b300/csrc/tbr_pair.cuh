@@ -92,12 +92,20 @@ enum : int {
 static_assert(P_CB == kPairRec - 1 && X_FL2 == kPairExt - 1, "pair record = packed floats 0..17");
 
 // All threads: fill the pair records of the cnt strokes staged at S0 (and, with
-// EXT, the forward's extension).  The caller synchronises before use.
-template <bool EXT>
+// EXT, the forward's extension).  With DCOL (the adjoint) the colour fields
+// hold the colour step c_i - c_{i-1} instead of c_i, (pc0, pc1, pc2) being the
+// colour of the stroke before the chunk's first (the background c_0 before
+// stroke 1).  The caller synchronises before use.
+template <bool EXT, bool DCOL = false>
 __device__ __forceinline__ void pair_records_fill(const float* __restrict__ S0, int cnt, f2* __restrict__ pbuf,
-                                                  f2* __restrict__ pext) {
-  for (int e = threadIdx.x; e < cnt * kPairRec; e += kTileThreads)
-    pbuf[e] = F2(S0[(e / kPairRec) * kRec + (e % kPairRec)]);
+                                                  f2* __restrict__ pext, float pc0 = 0.0f, float pc1 = 0.0f,
+                                                  float pc2 = 0.0f) {
+  for (int e = threadIdx.x; e < cnt * kPairRec; e += kTileThreads) {
+    const int j = e / kPairRec, f = e % kPairRec;
+    float v = S0[j * kRec + f];
+    if (DCOL && f >= P_CR) v -= j > 0 ? S0[(j - 1) * kRec + f] : (f == P_CR ? pc0 : (f == P_CG ? pc1 : pc2));
+    pbuf[e] = F2(v);
+  }
   if (EXT) {
     for (int e = threadIdx.x; e < cnt * kPairExt; e += kTileThreads)
       pext[e] = F2(S0[(e / kPairExt) * kRec + kPairRec + (e % kPairExt)]);
@@ -509,7 +517,7 @@ __device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict_
 struct PixAdj {
   float xh, yh, xl, yl;  // x_{i-1} (hi/lo), replaced by x_i
   float lt;              // log2 T_{i-1}, replaced by log2 T_i
-  float lT;              // lambda^T
+  float lD;              // lambda^C . c_i - lambda^T_i (0 before stroke 1)
   float lx, ly;          // lambda^x
 };
 
@@ -517,9 +525,11 @@ struct PixAdj {
 // backward_tile: x_i from the side table (pop), from Phi_i followed by a reset
 // to the checkpoint (at_ck), or from Phi_i; log2 T_i from the checkpoint or
 // Eq. rT; then the adjoint step and the VJP, whose 8 gradient values are
-// written to v.  Returns true if, at a checkpoint of a valid pixel, the
-// regenerated position differed from the stored one by more than drift_tol.
-__device__ __forceinline__ bool scalar_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S, float lC0,
+// written to v.  P is the stroke's pair record (its colour fields hold the
+// colour step c_i - c_{i-1}, pair_records_fill).  Returns true if, at a
+// checkpoint of a valid pixel, the regenerated position differed from the
+// stored one by more than drift_tol.
+__device__ __forceinline__ bool scalar_stroke(PixAdj& a, const StrokeF& g, const f2* __restrict__ P, float lC0,
                                               float lC1, float lC2, bool pop, bool at_ck, bool valid, float4 rp,
                                               float4 ckp, float ck_lt, float drift_tol, float (&v)[8]) {
   Geo gq;
@@ -550,12 +560,13 @@ __device__ __forceinline__ bool scalar_stroke(PixAdj& a, const StrokeF& g, const
   const Cover cv = coverage(gq.sp, g);
   if (at_ck) a.lt = ck_lt; else a.lt += cv.sp2;
   const float T = ex2_a(a.lt);
-  const float lCc = fmaf(lC0, S[F_CR], fmaf(lC1, S[F_CG], lC2 * S[F_CB]));
-  const float mu = T * (lCc - a.lT);
+  // lambda^C . c_i - lambda^T_{i-1}, carried as a difference (see pair_stroke)
+  const float E = a.lD + fmaf(lC0, P[P_CR].x, fmaf(lC1, P[P_CG].x, lC2 * P[P_CB].x));
+  const float mu = T * E;
   const float Ta = T * cv.alpha;
   v[5] = lC0 * Ta; v[6] = lC1 * Ta; v[7] = lC2 * Ta;
   step_vjp(gq, g, a.lx, a.ly, mu * cv.dadz, cv.z, v[0], v[1], v[2], v[3], v[4]);
-  a.lT = fmaf(cv.oma, a.lT, cv.alpha * lCc);
+  a.lD = cv.oma * E;
   return drifted;
 }
 
@@ -563,22 +574,22 @@ __device__ __forceinline__ bool scalar_stroke(PixAdj& a, const StrokeF& g, const
 struct PairState {
   f2 Xh, Yh, Xl, Yl;  // x_{i-1}, hi/lo
   f2 LT;              // log2 T_{i-1}
-  f2 LTT, LX, LY;     // lambda^T, lambda^x
+  f2 LD, LX, LY;      // lambda^C . c_{i-1} - lambda^T_{i-1} (see pair_stroke), lambda^x
   f2 LC0, LC1, LC2;   // lambda^C_0 (constant)
   int rc[2], nri[2];  // side-table records left; stroke index of the top one (-1: none)
 };
 
 // Initial pair state from the forward's s_0 and the cotangent (Eq. adjstep
-// initial values: lambda^T_0 = lambda^C_0 . c_0, lambda^x_0 = 0).
+// initial values: lambda^T_0 = lambda^C_0 . c_0, so LD = 0; lambda^x_0 = 0).
 __device__ __forceinline__ void pair_state_init(PairState& ps, const bool (&valid)[2], const PixelState (&st)[2],
-                                                const float (&lC)[2][3], const float bg[3], const RecordView& rv,
+                                                const float (&lC)[2][3], const RecordView& rv,
                                                 const size_t (&off)[2]) {
   ps.Xh = make_float2(st[0].xh, st[1].xh); ps.Yh = make_float2(st[0].yh, st[1].yh);
   ps.Xl = make_float2(st[0].xl, st[1].xl); ps.Yl = make_float2(st[0].yl, st[1].yl);
   ps.LT = make_float2(st[0].lt, st[1].lt);
   ps.LC0 = make_float2(lC[0][0], lC[1][0]); ps.LC1 = make_float2(lC[0][1], lC[1][1]);
   ps.LC2 = make_float2(lC[0][2], lC[1][2]);
-  ps.LTT = fma2(ps.LC0, F2(bg[0]), fma2(ps.LC1, F2(bg[1]), mul2(ps.LC2, F2(bg[2]))));
+  ps.LD = F2(0.0f);
   ps.LX = F2(0.0f); ps.LY = F2(0.0f);
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -652,9 +663,9 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
         ckp = rv.ckpt[cko + off[c]];
         ckl = rv.ck_lt[cko + off[c]];
       }
-      PixAdj a{comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), comp(ps.LT, c), comp(ps.LTT, c),
+      PixAdj a{comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), comp(ps.LT, c), comp(ps.LD, c),
                comp(ps.LX, c), comp(ps.LY, c)};
-      if (scalar_stroke(a, sg, S, comp(ps.LC0, c), comp(ps.LC1, c), comp(ps.LC2, c), pop, at_ck, valid[c], rp,
+      if (scalar_stroke(a, sg, P, comp(ps.LC0, c), comp(ps.LC1, c), comp(ps.LC2, c), pop, at_ck, valid[c], rp,
                         ckp, ckl, rv.drift_tol, g[c])) {
         ++drift;
         // first drift of this pixel: queue the segment (i1 - ck, i1] for the FP64 repair
@@ -665,7 +676,7 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
         }
       }
       put(ps.Xh, c, a.xh); put(ps.Yh, c, a.yh); put(ps.Xl, c, a.xl); put(ps.Yl, c, a.yl);
-      put(ps.LT, c, a.lt); put(ps.LTT, c, a.lT); put(ps.LX, c, a.lx); put(ps.LY, c, a.ly);
+      put(ps.LT, c, a.lt); put(ps.LD, c, a.lD); put(ps.LX, c, a.lx); put(ps.LY, c, a.ly);
     }
   } else {
     add_frame_disp2(ps.Xl, ps.Yl, P, ds, dh);
@@ -676,13 +687,21 @@ __device__ __forceinline__ void pair_stroke(PairState& ps, const float* __restri
     const Cover2 cv = coverage2(gq.sp, P);
     ps.LT = add2(ps.LT, cv.sp2);  // log T_i = log T_{i-1} - log(1 - alpha_i)
     const f2 T = ex22(ps.LT);
-    const f2 lCc = fma2(ps.LC0, P[P_CR], fma2(ps.LC1, P[P_CG], mul2(ps.LC2, P[P_CB])));
-    const f2 mu = mul2(T, sub2(lCc, ps.LTT));
+    // mu = T_i (lambda^C . c_i - lambda^T_{i-1}).  lambda^T tracks the colour
+    // composited behind stroke i, which for strokes coloured like those behind
+    // them differs from c_i only by (c_i - c_0) times the transmittance behind;
+    // as a difference of two such numbers it would keep only eps / (that
+    // transmittance) of its relative precision.  So the difference itself is
+    // carried: LD_i = lambda^C . c_i - lambda^T_i = (1 - alpha_i) E_i, with
+    // E_i = LD_{i-1} + lambda^C . (c_i - c_{i-1}) and LD_0 = 0 (lambda^T_0 =
+    // lambda^C . c_0); the pair record holds the colour step.
+    const f2 E = add2(ps.LD, fma2(ps.LC0, P[P_CR], fma2(ps.LC1, P[P_CG], mul2(ps.LC2, P[P_CB]))));
+    const f2 mu = mul2(T, E);
     const f2 Ta = mul2(T, cv.alpha);
     const f2 c5 = mul2(ps.LC0, Ta), c6 = mul2(ps.LC1, Ta), c7 = mul2(ps.LC2, Ta);
     f2 gcx, gcy, gth, gL, gr;
     step_vjp2(gq, P, ps.LX, ps.LY, mul2(mu, cv.dadz), cv.z, gcx, gcy, gth, gL, gr);
-    ps.LTT = fma2(cv.oma, ps.LTT, mul2(cv.alpha, lCc));
+    ps.LD = mul2(cv.oma, E);
     g[0][0] = gcx.x; g[0][1] = gcy.x; g[0][2] = gth.x; g[0][3] = gL.x; g[0][4] = gr.x;
     g[0][5] = c5.x; g[0][6] = c6.x; g[0][7] = c7.x;
     g[1][0] = gcx.y; g[1][1] = gcy.y; g[1][2] = gth.y; g[1][3] = gL.y; g[1][4] = gr.y;
@@ -937,9 +956,10 @@ __device__ __forceinline__ int coupled_vjp2(f2 Xh, f2 Yh, f2 Xl, f2 Yl, const f2
 // then the step VJP (coupled_vjp), whose 8 gradient values are written to v.
 // Returns true if, at a checkpoint of a valid pixel, the regenerated position
 // differed from the stored one by more than drift_tol.
-__device__ __forceinline__ bool coupled_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S, float lC0,
-                                               float lC1, float lC2, bool pop, bool at_ck, bool valid, float4 rp,
-                                               float4 ckp, float ck_lt, float drift_tol, float (&v)[8]) {
+__device__ __forceinline__ bool coupled_stroke(PixAdj& a, const StrokeF& g, const float* __restrict__ S,
+                                               const f2* __restrict__ P, float lC0, float lC1, float lC2, bool pop,
+                                               bool at_ck, bool valid, float4 rp, float4 ckp, float ck_lt,
+                                               float drift_tol, float (&v)[8]) {
   bool drifted = false;
   if (pop) {
     // x_i was within the floor's reach: read it back (Lemma "Support of the replay record")
@@ -956,7 +976,7 @@ __device__ __forceinline__ bool coupled_stroke(PixAdj& a, const StrokeF& g, cons
       a.xh = ckp.x; a.yh = ckp.y; a.xl = ckp.z; a.yl = ckp.w;
     }
   }
-  const float lCc = fmaf(lC0, S[F_CR], fmaf(lC1, S[F_CG], lC2 * S[F_CB]));
+  const float E = a.lD + fmaf(lC0, P[P_CR].x, fmaf(lC1, P[P_CG].x, lC2 * P[P_CB].x));  // as scalar_stroke
   float G[5], alpha, oma, T = 0.0f;
   coupled_vjp(a.xh, a.yh, a.xl, a.yl, S,
               [&](float, float, float sp2, float& sx, float& sy, float& smu) {
@@ -964,7 +984,7 @@ __device__ __forceinline__ bool coupled_stroke(PixAdj& a, const StrokeF& g, cons
                 T = ex2_a(a.lt);
                 sx = a.lx;
                 sy = a.ly;
-                smu = T * (lCc - a.lT);
+                smu = T * E;
               },
               G, alpha, oma);
   const float Ta = T * alpha;
@@ -973,7 +993,7 @@ __device__ __forceinline__ bool coupled_stroke(PixAdj& a, const StrokeF& g, cons
   v[0] = -G[0]; v[1] = -G[1]; v[2] = G[2]; v[3] = G[3]; v[4] = G[4];
   a.lx += G[0];
   a.ly += G[1];
-  a.lT = fmaf(oma, a.lT, alpha * lCc);
+  a.lD = oma * E;
   return drifted;
 }
 
@@ -1019,17 +1039,17 @@ __device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __rest
         ckp = rv.ckpt[cko + off[c]];
         ckl = rv.ck_lt[cko + off[c]];
       }
-      PixAdj a{comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), comp(ps.LT, c), comp(ps.LTT, c),
+      PixAdj a{comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), comp(ps.LT, c), comp(ps.LD, c),
                comp(ps.LX, c), comp(ps.LY, c)};
-      if (coupled_stroke(a, sg, S, comp(ps.LC0, c), comp(ps.LC1, c), comp(ps.LC2, c), pop, at_ck, valid[c], rp,
+      if (coupled_stroke(a, sg, S, P, comp(ps.LC0, c), comp(ps.LC1, c), comp(ps.LC2, c), pop, at_ck, valid[c], rp,
                          ckp, ckl, rv.drift_tol, g[c]))
         ++drift;
       put(ps.Xh, c, a.xh); put(ps.Yh, c, a.yh); put(ps.Xl, c, a.xl); put(ps.Yl, c, a.yl);
-      put(ps.LT, c, a.lt); put(ps.LTT, c, a.lT); put(ps.LX, c, a.lx); put(ps.LY, c, a.ly);
+      put(ps.LT, c, a.lt); put(ps.LD, c, a.lD); put(ps.LX, c, a.lx); put(ps.LY, c, a.ly);
     }
     return;
   }
-  const f2 lCc = fma2(ps.LC0, P[P_CR], fma2(ps.LC1, P[P_CG], mul2(ps.LC2, P[P_CB])));
+  const f2 E = add2(ps.LD, fma2(ps.LC0, P[P_CR], fma2(ps.LC1, P[P_CG], mul2(ps.LC2, P[P_CB]))));  // as pair_stroke
   f2 nLT, T, G[5], alpha, oma;
   const int vm = coupled_vjp2(ps.Xh, ps.Yh, ps.Xl, ps.Yl, P, X,
                               [&](f2, f2, f2 sp2, f2& sx, f2& sy, f2& smu) {
@@ -1037,11 +1057,11 @@ __device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __rest
                                 T = ex22(nLT);
                                 sx = ps.LX;
                                 sy = ps.LY;
-                                smu = mul2(T, sub2(lCc, ps.LTT));
+                                smu = mul2(T, E);
                               },
                               G, alpha, oma);
   const f2 Ta = mul2(T, alpha);
-  f2 nLTT = fma2(oma, ps.LTT, mul2(alpha, lCc));
+  f2 nLD = mul2(oma, E);
   f2 nLX = add2(ps.LX, G[0]), nLY = add2(ps.LY, G[1]);
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -1055,18 +1075,18 @@ __device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __rest
     for (int c = 0; c < 2; ++c) {
       if (!(vm & (1 << c))) continue;
       float lt = comp(ps.LT, c), Tc = 0.0f, Gs[5], al, om;
-      const float lTo = comp(ps.LTT, c), lxo = comp(ps.LX, c), lyo = comp(ps.LY, c), lCcc = comp(lCc, c);
+      const float Ec = comp(E, c), lxo = comp(ps.LX, c), lyo = comp(ps.LY, c);
       coupled_vjp(comp(ps.Xh, c), comp(ps.Yh, c), comp(ps.Xl, c), comp(ps.Yl, c), S,
                   [&](float, float, float sp2, float& sx, float& sy, float& smu) {
                     lt += sp2;
                     Tc = ex2_a(lt);
                     sx = lxo;
                     sy = lyo;
-                    smu = Tc * (lCcc - lTo);
+                    smu = Tc * Ec;
                   },
                   Gs, al, om);
       put(nLT, c, lt);
-      put(nLTT, c, fmaf(om, lTo, al * lCcc));
+      put(nLD, c, om * Ec);
       put(nLX, c, lxo + Gs[0]);
       put(nLY, c, lyo + Gs[1]);
       const float Tac = Tc * al;
@@ -1075,7 +1095,7 @@ __device__ __forceinline__ void pair_stroke_g(PairState& ps, const float* __rest
     }
   }
   ps.LT = nLT;
-  ps.LTT = nLTT;
+  ps.LD = nLD;
   ps.LX = nLX;
   ps.LY = nLY;
 }
@@ -1106,7 +1126,7 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
   const int ck = rv.ck;
   const bool any = valid[0] || valid[1];
   PairState ps;
-  pair_state_init(ps, valid, st, lC, bg, rv, off);
+  pair_state_init(ps, valid, st, lC, rv, off);
   int next_ck = (ck < n) ? ck : 0;
   const bool ck_aligned = BLOCKED && (ck & (kRenorm - 1)) == 0 && (CH & (kRenorm - 1)) == 0;
   const int nch = (n + CH - 1) / CH;
@@ -1127,7 +1147,11 @@ __device__ bool backward_tile2(ChunkRing<CH>& ring, const float* __restrict__ pa
     }
     const int cntc = chunk_cnt(q);
     const float* S0 = ring.data(b);
-    pair_records_fill<false>(S0, cntc, pbuf, nullptr);
+    {  // colour of the stroke before the chunk (the background before stroke 1)
+      const float* pc = q > 0 ? packed + (static_cast<size_t>(q) * CH - 1) * kRec + F_CR : nullptr;
+      pair_records_fill<false, true>(S0, cntc, pbuf, nullptr, pc ? pc[0] : bg[0], pc ? pc[1] : bg[1],
+                                     pc ? pc[2] : bg[2]);
+    }
     if (COUPLED) pair_ext_g_fill(S0, cntc, gext);
     __syncthreads();
     float (*rb)[CH * 8] = red[b];

@@ -618,7 +618,10 @@ __device__ bool backward_tile(ChunkRing<CH>& ring, const float* __restrict__ pac
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ck = rv.ck;
   float xh = st.xh, yh = st.yh, xl = st.xl, yl = st.yl, lt = st.lt;
-  float lT = fmaf(lC0, bg[0], fmaf(lC1, bg[1], lC2 * bg[2]));
+  // lambda^C . c_i - lambda^T_i, carried as a difference (pair_stroke, tbr_pair.cuh):
+  // E_i = lD + lambda^C . (c_i - c_{i-1}), mu = T_i E_i, lD <- (1 - alpha_i) E_i
+  float lD = 0.0f;
+  float pcR = bg[0], pcG = bg[1], pcB = bg[2];  // c_{i-1} (c_0: the background)
   float lx = 0.0f, ly = 0.0f;
   int rc = min(st.cnt, rv.cap), nri = -1;
   float4 rpos = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -650,17 +653,19 @@ __device__ bool backward_tile(ChunkRing<CH>& ring, const float* __restrict__ pac
     for (int j = 0; j < cntc; ++j) {
       const int i1 = q * CH + j + 1;
       float v0 = 0.0f, v1 = 0.0f, v2 = 0.0f, v3 = 0.0f, v4 = 0.0f, v5 = 0.0f, v6 = 0.0f, v7 = 0.0f;
+      const float cR = S0[j * kRec + F_CR], cG = S0[j * kRec + F_CG], cB = S0[j * kRec + F_CB];
+      const float dR = cR - pcR, dG = cG - pcG, dB = cB - pcB;
+      pcR = cR; pcG = cG; pcB = cB;
       if (valid) {
         const float* S = S0 + j * kRec;
         const StrokeF g = load_stroke(S);
-        const float cR = S[F_CR], cG = S[F_CG], cB = S[F_CB];
         const bool at_ck = (i1 == next_ck);
         size_t cko = 0;
         if (at_ck) {
           next_ck = (next_ck + ck < n) ? next_ck + ck : 0;
           cko = static_cast<size_t>(i1 / ck - 1) * rv.stride + rv.off;
         }
-        const float lCc = fmaf(lC0, cR, fmaf(lC1, cG, lC2 * cB));
+        const float E = lD + fmaf(lC0, dR, fmaf(lC1, dG, lC2 * dB));
         if (INERT) {
           float s, h, sp;
           to_frame(xh, yh, xl, yl, g, s, h);
@@ -669,11 +674,11 @@ __device__ bool backward_tile(ChunkRing<CH>& ring, const float* __restrict__ pac
           const Cover cv = coverage(sp, g);
           if (at_ck) lt = rv.ck_lt[cko]; else lt += cv.sp2;
           const float T = ex2_a(lt);
-          const float mu = T * (lCc - lT);
+          const float mu = T * E;
           const float Ta = T * cv.alpha;
           v5 = lC0 * Ta; v6 = lC1 * Ta; v7 = lC2 * Ta;
           inert_vjp(s, h, g, sp, lx, ly, mu * cv.dadz, cv.z, true, v0, v1, v2, v3, v4);
-          lT = fmaf(cv.oma, lT, cv.alpha * lCc);
+          lD = cv.oma * E;
         } else {
           Geo gq;
           float s, h, ds, dh;
@@ -708,11 +713,11 @@ __device__ bool backward_tile(ChunkRing<CH>& ring, const float* __restrict__ pac
           const Cover cv = coverage(gq.sp, g);
           if (at_ck) lt = rv.ck_lt[cko]; else lt += cv.sp2;  // log T_i = log T_{i-1} - log(1 - alpha_i)
           const float T = ex2_a(lt);
-          const float mu = T * (lCc - lT);
+          const float mu = T * E;
           const float Ta = T * cv.alpha;
           v5 = lC0 * Ta; v6 = lC1 * Ta; v7 = lC2 * Ta;
           step_vjp(gq, g, lx, ly, mu * cv.dadz, cv.z, v0, v1, v2, v3, v4);
-          lT = fmaf(cv.oma, lT, cv.alpha * lCc);
+          lD = cv.oma * E;
         }
       }
       const float vv[8] = {v0, v1, v2, v3, v4, v5, v6, v7};
