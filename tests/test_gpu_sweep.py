@@ -24,6 +24,9 @@ Per case:
 
 The Phi_g cases keep the coupled tests' 20% share for entries passing by the
 allowance (coupled drops turn their profile with the polar angle).
+
+A second sweep draws 150 programs for the transfer renderer R_D (sixteen-drop
+transport, forward only): hard indices by ``check_hard``, soft render to 1e-4.
 """
 import numpy as np
 import pytest
@@ -37,6 +40,8 @@ pytestmark = pytest.mark.gpu
 
 SEED = 11
 CASES = 120
+SEED_RD = 21
+CASES_RD = 150
 
 
 def draw_cases(seed, count):
@@ -85,3 +90,38 @@ def test_sweep(case):
     og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64), inert=inert)
     sens = oracle_sensitivity(p, W, H, tau, tau_min, cot.astype(np.float64), og, inert=inert)
     compare(g, og, sens=sens, label=label, max_cond_frac=0.2 if c["coupled"] else 0.05, norm_sens=True)
+
+
+def draw_cases_rd(seed, count):
+    """The R_D sweep's configurations, in draw order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        c = {"W": int(rng.choice([1, 7, 33, 64, 77, 130])), "H": int(rng.choice([1, 9, 45, 100])),
+             "n": int(rng.choice([0, 1, 17, 64, 200, 600]))}
+        c["r_lo"] = float(rng.choice([0.005, 0.01, 0.02]))
+        c["r_hi"] = c["r_lo"] * float(rng.choice([2, 4, 8]))
+        c["len_max"] = float(rng.choice([0.0, 0.1, 0.3, 0.8]))
+        c["p_drop"] = float(rng.choice([0.0, 0.5, 1.0]))
+        c["tau"] = float(rng.choice([0.0, 0.1, 0.3]))
+        c["tau_min"] = float(rng.choice([1 / 200, 1 / 50]))
+        c["k"] = int(rng.choice([1, 4, 16]))
+        c["seed"] = int(rng.integers(1000, 10 ** 6))
+        out.append(c)
+    return out
+
+
+@pytest.mark.parametrize("case", range(CASES_RD))
+def test_sweep_transfer_renderer(case):
+    c = draw_cases_rd(SEED_RD, CASES_RD)[case]
+    W, H = c["W"], c["H"]
+    label = f"R_D sweep {case}: " + ", ".join(f"{k}={v}" for k, v in c.items())
+    p = inputs.make_program(c["n"], seed=c["seed"], palette_seed=c["seed"] + 1, k=c["k"], r_lo=c["r_lo"],
+                            r_hi=c["r_hi"], len_max=c["len_max"], p_drop=c["p_drop"])
+    dp = tbr.DeviceProgram.from_host(p)
+    _, idx, _ = tbr.render_hard(dp, W, H, transport="drops")
+    check_hard(p, idx.cpu().numpy(), oracle.render_hard(p, W, H, with_kappa=True, transport="drops"), W, H, label,
+               transport="drops")
+    rgb, _ = tbr.render_soft(dp, W, H, c["tau"], c["tau_min"], transport="drops")
+    o = oracle.render_soft(p, W, H, c["tau"], c["tau_min"], transport="drops")
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= 1e-4, label
