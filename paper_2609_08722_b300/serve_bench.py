@@ -166,9 +166,12 @@ class _Bench:
         return lat, time.perf_counter() - t0
 
 
-def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, cap_bytes: int = 80 << 30):
+def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, cap_bytes: int = 80 << 30,
+        sweep=(0.3, 0.5, 0.9, 1.2)):
     """Returns a dict with capacity, and p50/p99 latency of both arms at
-    ``rho`` x the server's measured capacity."""
+    ``rho`` x the server's measured capacity; ``rate_sweep`` repeats the
+    Poisson run of both arms at each further load in ``sweep`` (the same
+    seeded draws, gaps scaled by 1 / load)."""
     b = _Bench(n_prog, seed)
     stream = make_stream(n_req, n_prog, seed + 1)
     server = tbr.Server(tbr.default_serve_config(memory_cap_bytes=cap_bytes, max_strokes=8192))
@@ -183,16 +186,28 @@ def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, c
         print(f"serve_bench: capacity run {wall_cap:.1f} s", file=sys.stderr, flush=True)
         capacity = len(stream) / wall_cap
         # Poisson arrivals at rho x capacity
-        gaps = -np.log(1.0 - inputs.uniform(seed + 2, len(stream))) / (rho * capacity)
-        arrivals = np.cumsum(gaps) - gaps[0]
-        lat_s, wall_s = b.run_server(stream, arrivals.tolist(), server, pids)
+        unit = -np.log(1.0 - inputs.uniform(seed + 2, len(stream))) / capacity
+
+        def schedule(load):
+            gaps = unit / load
+            return (np.cumsum(gaps) - gaps[0]).tolist()
+
+        arrivals = schedule(rho)
+        lat_s, wall_s = b.run_server(stream, arrivals, server, pids)
         queue_s = float(np.mean(b.queue_ms))
         st = server.stats()
+        swept = {}
+        for load in sweep:
+            lat, wall = b.run_server(stream, schedule(load), server, pids)
+            swept[load] = {"server": _arm(lat, wall, len(stream))}
     finally:
         server.destroy()
     print(f"serve_bench: poisson run {wall_s:.1f} s", file=sys.stderr, flush=True)
     b.run_per_launch(make_stream(10, n_prog, seed + 7), [0.0] * 10)
-    lat_p, wall_p = b.run_per_launch(stream, arrivals.tolist())
+    lat_p, wall_p = b.run_per_launch(stream, arrivals)
+    for load in sweep:
+        lat, wall = b.run_per_launch(stream, schedule(load))
+        swept[load]["per_launch"] = _arm(lat, wall, len(stream))
     print(f"serve_bench: per-launch poisson run {wall_p:.1f} s", file=sys.stderr, flush=True)
     lat_pc, wall_pc = b.run_per_launch(stream, [0.0] * len(stream))
     p50s, p99s, means = _percentiles(lat_s)
@@ -206,7 +221,13 @@ def run(n_req: int = 200, n_prog: int = 64, rho: float = 0.7, seed: int = 501, c
                    "persistent_ctas": st["persistent_ctas"]},
         "per_launch": {"capacity_req_per_s": len(stream) / wall_pc, "p50_ms": p50p, "p99_ms": p99p,
                        "mean_ms": meanp, "throughput_req_per_s": len(stream) / wall_p},
+        "rate_sweep": [{"rho": load, "arrival_rate_per_s": load * capacity, **swept[load]} for load in sweep],
     }
+
+
+def _arm(lat, wall, count):
+    p50, p99, mean = _percentiles(lat)
+    return {"p50_ms": p50, "p99_ms": p99, "mean_ms": mean, "throughput_req_per_s": count / wall}
 
 
 if __name__ == "__main__":
