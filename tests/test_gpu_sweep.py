@@ -27,6 +27,10 @@ allowance (coupled drops turn their profile with the polar angle).
 
 A second sweep draws 150 programs for the transfer renderer R_D (sixteen-drop
 transport, forward only): hard indices by ``check_hard``, soft render to 1e-4.
+A third draws 120 hard renders on large canvases (150 .. 1024 pixels a side,
+1 .. 3000 strokes, counts on and off the 64-stroke chunk boundary, prefixes,
+snapped colours, Phi_g), compared on 3000 sampled pixels each: the live-pixel
+compaction and the FP64 band at sizes the small sweep does not reach.
 """
 import numpy as np
 import pytest
@@ -42,6 +46,8 @@ SEED = 11
 CASES = 120
 SEED_RD = 21
 CASES_RD = 150
+SEED_HARD = 31
+CASES_HARD = 120
 
 
 def draw_cases(seed, count):
@@ -125,3 +131,42 @@ def test_sweep_transfer_renderer(case):
     rgb, _ = tbr.render_soft(dp, W, H, c["tau"], c["tau_min"], transport="drops")
     o = oracle.render_soft(p, W, H, c["tau"], c["tau_min"], transport="drops")
     assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= 1e-4, label
+
+
+def draw_cases_hard(seed, count):
+    """The large-canvas hard sweep's configurations, in draw order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        c = {"W": int(rng.choice([200, 256, 333, 512, 700, 1024])), "H": int(rng.choice([150, 256, 300, 512, 1024])),
+             "n": int(rng.choice([1, 63, 64, 65, 500, 1000, 2000, 3000]))}
+        c["r_lo"] = float(rng.choice([0.002, 0.003, 0.01]))
+        c["r_hi"] = c["r_lo"] * float(rng.choice([4, 10, 16]))
+        c["len_max"] = float(rng.choice([0.0, 0.2, 0.5]))
+        c["p_drop"] = float(rng.choice([0.0, 0.5, 1.0]))
+        c["k"] = int(rng.choice([4, 16]))
+        c["prefix"] = int(rng.choice([-1, -1, c["n"] // 2]))
+        c["snap"] = bool(rng.random() < 0.2)
+        c["coupled"] = bool(rng.random() < 0.2)
+        c["seed"] = int(rng.integers(1000, 10 ** 6))
+        out.append(c)
+    return out
+
+
+@pytest.mark.parametrize("case", range(CASES_HARD))
+def test_sweep_hard_large_canvas(case):
+    c = draw_cases_hard(SEED_HARD, CASES_HARD)[case]
+    W, H, prefix, snap = c["W"], c["H"], c["prefix"], c["snap"]
+    label = f"hard sweep {case}: " + ", ".join(f"{k}={v}" for k, v in c.items())
+    p = inputs.make_program(c["n"], seed=c["seed"], palette_seed=c["seed"] + 1, k=c["k"], r_lo=c["r_lo"],
+                            r_hi=c["r_hi"], len_max=c["len_max"], p_drop=c["p_drop"])
+    if c["coupled"]:
+        p.coupling = inputs.make_coupling(c["seed"] + 2, c["n"])
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, idx, _ = tbr.render_hard(dp, W, H, n_prefix=prefix, snap=snap)
+    pix = inputs.sample_pixels(c["seed"] + 5, W * H, 3000)
+    o = oracle.render_hard(p, W, H, n_prefix=prefix, snap=snap, with_kappa=True, pix=pix)
+    gi = idx.cpu().numpy().ravel()[pix]
+    check_hard(p, gi, o, W, H, label, pix=pix, n_prefix=prefix, snap=snap)
+    same = gi == o["idx"]
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3)[pix][same] - o["rgb"][same]).max(initial=0.0) < 1e-6, label
