@@ -31,6 +31,15 @@ A third draws 120 hard renders on large canvases (150 .. 1024 pixels a side,
 1 .. 3000 strokes, counts on and off the 64-stroke chunk boundary, prefixes,
 snapped colours, Phi_g), compared on 3000 sampled pixels each: the live-pixel
 compaction and the FP64 band at sizes the small sweep does not reach.
+A fourth draws 40 one-pass compensations (1 .. 5000 strokes, anchor and
+endpoint variants) held to ``test_gpu_compensate.compare``: blocked flags
+within a small slack, each stroke's ends within 1e-6 + 50 x the oracle's own
+move under one FP32 rounding of the inputs.  Draws of the variant that skips
+blocked steps are skipped here.  Skipping makes the result jump where a
+point sits on a later footprint's boundary to FP32 precision, so a sampled
+move does not bound it: on three of 80 such draws the oracle's own result for
+the worst stroke jumped by 4e-3 .. 1.3e-2 in 20 trials, as far as the GPU's
+differed, while 3 trials had shown none.
 """
 import numpy as np
 import pytest
@@ -48,6 +57,8 @@ SEED_RD = 21
 CASES_RD = 150
 SEED_HARD = 31
 CASES_HARD = 120
+SEED_COMP = 41
+CASES_COMP = 40
 
 
 def draw_cases(seed, count):
@@ -170,3 +181,32 @@ def test_sweep_hard_large_canvas(case):
     check_hard(p, gi, o, W, H, label, pix=pix, n_prefix=prefix, snap=snap)
     same = gi == o["idx"]
     assert np.abs(rgb.cpu().numpy().reshape(-1, 3)[pix][same] - o["rgb"][same]).max(initial=0.0) < 1e-6, label
+
+
+def draw_cases_comp(seed, count):
+    """The compensation sweep's configurations, in draw order."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        c = {"n": int(rng.choice([1, 2, 17, 100, 700, 1024, 1025, 3000, 4097, 5000]))}
+        c["r_lo"] = float(rng.choice([0.002, 0.005, 0.01]))
+        c["r_hi"] = c["r_lo"] * float(rng.choice([2, 5, 10]))
+        c["len_max"] = float(rng.choice([0.0, 0.1, 0.3]))
+        c["p_drop"] = float(rng.choice([0.0, 0.5, 1.0]))
+        c["endpoint"] = bool(rng.random() < 0.5)
+        c["skip"] = bool(rng.random() < 0.3)
+        c["seed"] = int(rng.integers(1000, 10 ** 6))
+        out.append(c)
+    return out
+
+
+@pytest.mark.parametrize("case", range(CASES_COMP))
+def test_sweep_compensation(case):
+    from test_gpu_compensate import compare as compare_compensation
+
+    c = draw_cases_comp(SEED_COMP, CASES_COMP)[case]
+    if c["skip"]:
+        pytest.skip("the variant that skips blocked steps is discontinuous at footprint boundaries")
+    p = inputs.make_program(c["n"], seed=c["seed"], palette_seed=c["seed"] + 1, k=4, r_lo=c["r_lo"],
+                            r_hi=c["r_hi"], len_max=c["len_max"], p_drop=c["p_drop"])
+    compare_compensation(p, c["endpoint"], False, flag_slack=max(2, c["n"] // 200), sens_bound=True)
