@@ -184,6 +184,32 @@ def test_soft_and_adjoint_of_a_long_program(W, H, ck, trials):
     compare(g, og, sens=sens, label=f"10000 strokes, {W}x{H}, k = {ck}")
 
 
+@pytest.mark.parametrize("R,n", [(4096, 500), (8192, 100)])
+def test_soft_and_adjoint_at_the_largest_sizes(R, n):
+    """16.7M and 67.1M pixels: the side table, checkpoints and slices hold up to
+    1.1e9 elements (24 GB at 8192^2), so every pixel-indexed offset must be
+    formed in 64 bits.  Soft colours and the adjoint (cotangent on 2048
+    sampled pixels) against the oracle on those pixels."""
+    p = inputs.make_program(n, seed=141, palette_seed=241, k=16, r_lo=0.003, r_hi=0.05)
+    dp = tbr.DeviceProgram.from_host(p)
+    rgb, ctx = tbr.render_soft(dp, R, R, 0.0, 1 / 200, record=True, record_capacity=16)
+    pix = inputs.sample_pixels(43, R * R, 2048)
+    o = oracle.render_soft(p, R, R, 0.0, 1 / 200, pix=pix)
+    err = np.abs(rgb.view(-1, 3)[torch.from_numpy(pix).cuda()].cpu().numpy() - o["rgb"])
+    print(f"{R}^2 soft max {err.max():.3e}")
+    assert err.max() <= SOFT_TOL
+    del rgb
+    cot = inputs.make_cotangent(44, pix.size)
+    full = torch.zeros((R * R, 3), device="cuda")
+    full[torch.from_numpy(pix).cuda()] = torch.from_numpy(cot).cuda()
+    g = ctx.backward(full.view(R, R, 3))
+    assert ctx.status()["overflow_pixels"] == 0
+    og = oracle.soft_vjp(p, R, R, 0.0, 1 / 200, cot.astype(np.float64), pix=pix)
+    sens = oracle_sensitivity(p, R, R, 0.0, 1 / 200, cot.astype(np.float64), og, pix=pix)
+    compare(g, og, sens=sens, label=f"{R}^2, {n} strokes (2048 sampled pixels)")
+    ctx.destroy()
+
+
 @pytest.mark.parametrize("W,H", [(75, 61), (64, 33)])
 def test_backward_long_strokes(W, H):
     """No drops and strokes up to 0.8 long: most samples sit beside a flank,
