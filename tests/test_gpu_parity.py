@@ -210,6 +210,24 @@ def test_soft_and_adjoint_at_the_largest_sizes(R, n):
     ctx.destroy()
 
 
+@pytest.mark.parametrize("k", [64, 256])
+def test_large_palettes(k):
+    """Palettes of 64 and 256 colours: the softmax colour of the pack, the
+    logits chain rule of the epilogue (sum over the palette per stroke) and the
+    palette gradient, against the oracle."""
+    p = inputs.make_program(80, seed=151, palette_seed=251, k=k, r_lo=0.01, r_hi=0.08)
+    dp = tbr.DeviceProgram.from_host(p)
+    W, H = 70, 45
+    rgb, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    cot = inputs.make_cotangent(45, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    sens = oracle_sensitivity(p, W, H, 0.0, 1 / 200, cot.astype(np.float64), og)
+    compare(g, og, sens=sens, label=f"palette of {k}")
+
+
 @pytest.mark.parametrize("W,H", [(75, 61), (64, 33)])
 def test_backward_long_strokes(W, H):
     """No drops and strokes up to 0.8 long: most samples sit beside a flank,
