@@ -543,7 +543,10 @@ T soft_coverage(const T& margin, const T& r, double tau, double tau_min) {
   T w = tau * r;
   if (value(w) < tau_min) w = T(tau_min);
   T z = -margin / w;
-  T a = 1.0 / (1.0 + exp(-z));
+  // sigmoid(z); far outside a deposit (z < -700) e^-z would overflow and its
+  // derivative turn into inf / inf, so there the same value is written as
+  // e^z / (1 + e^z)
+  T a = value(z) < -700.0 ? exp(z) / (1.0 + exp(z)) : 1.0 / (1.0 + exp(-z));
   if (value(a) > kAlphaMax) a = T(kAlphaMax);
   return a;
 }

@@ -439,6 +439,26 @@ def test_stored_state_adjoint_matches_finite_differences(inert):
     assert np.abs(got - fd).max() < 1e-6 * scale
 
 
+def test_far_stroke_keeps_the_adjoint_finite():
+    """A stroke far off the canvas at the sharp relaxation (w = 1/200): its
+    logit is about -720, where e^-z overflows FP64.  Its coverage is 0 to the
+    precision of the arithmetic, and the adjoint (Eq. relax in its
+    overflow-free form) must stay finite and match central differences: the
+    far stroke still transports every pixel."""
+    p = _tiny_program(5, 41, r_lo=0.08, r_hi=0.2)
+    p.cx[2] = 3.0
+    p.cy[2] = -2.0
+    W = H = 10
+    cot = inputs.make_cotangent(9, W * H).astype(np.float64)
+    g = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot)
+    for k in ("cx", "cy", "theta", "length", "half_width", "logits"):
+        assert np.isfinite(np.asarray(g[k])).all(), k
+    params = [(j, q) for j in range(p.n) for q in range(5)]
+    fd = oracle.fd_gradient(p, W, H, 0.0, 1 / 200, cot, params, h_geo=1e-6)
+    got = np.array([g[oracle._FIELD[q]][j] for (j, q) in params])
+    assert np.abs(got - fd).max() < 1e-5 * np.abs(fd).max()
+
+
 def test_stored_state_adjoint_matches_forward_mode():
     """The reverse recurrence against exact forward-mode differentiation of the
     whole soft render (the paper prints 5.4e-15 against autograd)."""
