@@ -228,6 +228,44 @@ def test_large_palettes(k):
     compare(g, og, sens=sens, label=f"palette of {k}")
 
 
+def extreme_program():
+    """60 strokes, with: one swallowing a third of the canvas (r = 0.3, L =
+    0.4), one thinner than a pixel (r = 1e-4), one centred far off the canvas
+    at (3, -2) (logits near -720 at the sharp relaxation), one longer than the
+    canvas (L = 2), angles of +-37 rad, and one centred on a corner."""
+    p = inputs.make_program(60, seed=161, palette_seed=261, k=8, r_lo=0.01, r_hi=0.06)
+    p.half_width[5] = 0.3
+    p.length[5] = 0.4
+    p.half_width[12] = 1e-4
+    p.length[12] = 0.05
+    p.cx[20] = 3.0
+    p.cy[20] = -2.0
+    p.length[25] = 2.0
+    p.half_width[25] = 0.02
+    p.theta[30] = 37.0
+    p.theta[31] = -37.0
+    p.cx[50] = 0.0
+    p.cy[50] = 0.0
+    return p
+
+
+@pytest.mark.parametrize("tau,tau_min", [(0.0, 1 / 200), (0.3, 1 / 50)])
+def test_extreme_geometry(tau, tau_min):
+    p = extreme_program()
+    dp = tbr.DeviceProgram.from_host(p)
+    W, H = 96, 80
+    _, idx, _ = tbr.render_hard(dp, W, H)
+    check_hard(p, idx.cpu().numpy(), oracle.render_hard(p, W, H, with_kappa=True), W, H, "extreme hard")
+    rgb, ctx = tbr.render_soft(dp, W, H, tau, tau_min, record=True)
+    o = oracle.render_soft(p, W, H, tau, tau_min)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    cot = inputs.make_cotangent(46, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, tau, tau_min, cot.astype(np.float64))
+    sens = oracle_sensitivity(p, W, H, tau, tau_min, cot.astype(np.float64), og)
+    compare(g, og, sens=sens, label=f"extreme geometry tau={tau}")
+
+
 @pytest.mark.parametrize("W,H", [(75, 61), (64, 33)])
 def test_backward_long_strokes(W, H):
     """No drops and strokes up to 0.8 long: most samples sit beside a flank,
