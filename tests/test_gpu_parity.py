@@ -266,6 +266,32 @@ def test_extreme_geometry(tau, tau_min):
     compare(g, og, sens=sens, label=f"extreme geometry tau={tau}")
 
 
+@pytest.mark.parametrize("color_temp,background,palette_shift", [
+    (0.05, (0.0, 0.0, 0.0), 0.0),     # the end of the fit's schedule: nearly one-hot colours, black ground
+    (20.0, (0.2, 0.5, 0.9), 0.0),     # nearly uniform mixtures on a coloured ground
+    (1.0, (1.0, 1.0, 1.0), 0.7),      # palette values above 1 and below 0 (no clamp in the method)
+])
+def test_colour_extremes(color_temp, background, palette_shift):
+    """The colour chain of Eq. state and the softmax colours under extreme
+    temperatures, backgrounds and palettes: the soft render, the adjoint's
+    colour and transmittance terms, and the logits and palette gradients."""
+    p = inputs.make_program(60, seed=171, palette_seed=271, k=8, r_lo=0.01, r_hi=0.08)
+    p.color_temp = color_temp
+    p.background = np.asarray(background, dtype=np.float32)
+    if palette_shift:
+        p.palette = (p.palette * 2.0 - palette_shift).astype(np.float32)
+    dp = tbr.DeviceProgram.from_host(p)
+    W, H = 80, 60
+    rgb, ctx = tbr.render_soft(dp, W, H, 0.0, 1 / 200, record=True)
+    o = oracle.render_soft(p, W, H, 0.0, 1 / 200)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    cot = inputs.make_cotangent(47, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(p, W, H, 0.0, 1 / 200, cot.astype(np.float64))
+    sens = oracle_sensitivity(p, W, H, 0.0, 1 / 200, cot.astype(np.float64), og)
+    compare(g, og, sens=sens, label=f"colours tau_c={color_temp} bg={background} shift={palette_shift}")
+
+
 @pytest.mark.parametrize("W,H", [(75, 61), (64, 33)])
 def test_backward_long_strokes(W, H):
     """No drops and strokes up to 0.8 long: most samples sit beside a flank,
