@@ -266,6 +266,35 @@ def test_extreme_geometry(tau, tau_min):
     compare(g, og, sens=sens, label=f"extreme geometry tau={tau}")
 
 
+@pytest.mark.parametrize("tau,tau_min", [(0.0, 1 / 200), (0.3, 1 / 50)])
+def test_extreme_geometry_transfer_and_coupling(tau, tau_min):
+    """The same extreme program through the transfer renderer R_D (hard and
+    soft) and under the coupling variant Phi_g (hard, soft and adjoint; its
+    entries keep the coupled tests' 20% share by the sensitivity allowance)."""
+    W, H = 96, 80
+    p = extreme_program()
+    dp = tbr.DeviceProgram.from_host(p)
+    _, idx, _ = tbr.render_hard(dp, W, H, transport="drops")
+    check_hard(p, idx.cpu().numpy(), oracle.render_hard(p, W, H, with_kappa=True, transport="drops"), W, H,
+               "extreme R_D hard", transport="drops")
+    rgb, _ = tbr.render_soft(dp, W, H, tau, tau_min, transport="drops")
+    o = oracle.render_soft(p, W, H, tau, tau_min, transport="drops")
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    q = extreme_program()
+    q.coupling = inputs.make_coupling(403, q.n)
+    dq = tbr.DeviceProgram.from_host(q)
+    _, idx, _ = tbr.render_hard(dq, W, H)
+    check_hard(q, idx.cpu().numpy(), oracle.render_hard(q, W, H, with_kappa=True), W, H, "extreme Phi_g hard")
+    rgb, ctx = tbr.render_soft(dq, W, H, tau, tau_min, record=True)
+    o = oracle.render_soft(q, W, H, tau, tau_min)
+    assert np.abs(rgb.cpu().numpy().reshape(-1, 3) - o["rgb"]).max() <= SOFT_TOL
+    cot = inputs.make_cotangent(48, W * H)
+    g = ctx.backward(torch.from_numpy(cot).reshape(H, W, 3).cuda())
+    og = oracle.soft_vjp(q, W, H, tau, tau_min, cot.astype(np.float64))
+    sens = oracle_sensitivity(q, W, H, tau, tau_min, cot.astype(np.float64), og)
+    compare(g, og, sens=sens, label=f"extreme Phi_g tau={tau}", max_cond_frac=0.2)
+
+
 @pytest.mark.parametrize("color_temp,background,palette_shift", [
     (0.05, (0.0, 0.0, 0.0), 0.0),     # the end of the fit's schedule: nearly one-hot colours, black ground
     (20.0, (0.2, 0.5, 0.9), 0.0),     # nearly uniform mixtures on a coloured ground
