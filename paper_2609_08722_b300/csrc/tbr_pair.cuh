@@ -517,7 +517,7 @@ __device__ bool soft_forward_tile2(ChunkRing<CH>& ring, const float* __restrict_
 struct PixAdj {
   float xh, yh, xl, yl;  // x_{i-1} (hi/lo), replaced by x_i
   float lt;              // log2 T_{i-1}, replaced by log2 T_i
-  float lD;              // lambda^C . c_i - lambda^T_i (0 before stroke 1)
+  float lD;              // lambda^C . c_{i-1} - lambda^T_{i-1} (0 before stroke 1), replaced by its value at i
   float lx, ly;          // lambda^x
 };
 
