@@ -277,3 +277,66 @@ def test_ready_word_wait_runs_out_and_the_server_stays_usable(programs):
         assert torch.equal(idx, ref_idx) and torch.equal(rgb, ref_rgb)
     finally:
         s.destroy()
+
+
+def test_random_mix_matches_alone_and_the_plain_path():
+    """80 random requests over 12 random programs (1 .. 4000 strokes; 1 .. 333
+    pixels a side), submitted at once: hard and recolour requests equal the
+    plain entry point bit for bit, and every soft request, resubmitted alone,
+    reproduces its in-mix colours, loss and gradients bit for bit (the mix
+    never reorders a request's own arithmetic)."""
+    rng = np.random.default_rng(5)
+    s = tbr.Server(tbr.default_serve_config(max_strokes=4096))
+    try:
+        hosts, devs, pids = [], [], []
+        for j in range(12):
+            n = int(rng.choice([1, 50, 300, 1000, 4000]))
+            r_lo = float(rng.choice([0.003, 0.01]))
+            h = inputs.make_program(n, seed=7600 + j, palette_seed=78, k=int(rng.choice([4, 16])), r_lo=r_lo,
+                                    r_hi=r_lo * 8)
+            d = tbr.DeviceProgram.from_host(h)
+            hosts.append(h)
+            devs.append(d)
+            pids.append(s.load_program(d))
+        reqs = []
+        for _ in range(80):
+            j = int(rng.integers(0, 12))
+            W, H = int(rng.choice([1, 17, 64, 130, 256, 333])), int(rng.choice([1, 9, 64, 100, 256]))
+            u = rng.random()
+            if u < 0.6:
+                rid, rgb, idx = hard_request(s, pids[j], W, H)
+                reqs.append(("hard", j, W, H, rid, (rgb, idx)))
+            elif u < 0.9:
+                target, _, _ = tbr.render_hard(devs[(j + 1) % 12], W, H)
+                rid, rgb, loss, grad = soft_request(s, pids[j], devs[j].n, devs[j].k, target)
+                reqs.append(("soft", j, W, H, rid, (rgb, loss, grad, target)))
+            else:
+                a, b, start = 0, hosts[j].k - 1, hosts[j].n // 2
+                rgb = torch.empty((H, W, 3), device="cuda")
+                idx = torch.empty((H, W), dtype=torch.int32, device="cuda")
+                rid = s.submit(tbr.REQ_RECOLOUR, pids[j], W, H, out_rgb=rgb, out_idx=idx, edit_a=a, edit_b=b,
+                               edit_start=start)
+                reqs.append(("recolour", j, W, H, rid, (rgb, idx, a, b, start)))
+        for kind, j, W, H, rid, out in reqs:
+            assert s.wait(rid) == tbr.TBR_OK
+        torch.cuda.synchronize()
+        for kind, j, W, H, rid, out in reqs:
+            if kind == "hard":
+                ref_rgb, ref_idx, _ = tbr.render_hard(devs[j], W, H)
+                assert torch.equal(out[1], ref_idx) and torch.equal(out[0], ref_rgb), (kind, j, W, H)
+            elif kind == "recolour":
+                rgb, idx, a, b, start = out
+                e = hosts[j].copy()
+                lg = e.logits.copy()
+                lg[start:, [a, b]] = lg[start:, [b, a]]
+                e.logits = np.ascontiguousarray(lg)
+                ref_rgb, ref_idx, _ = tbr.render_hard(tbr.DeviceProgram.from_host(e), W, H)
+                assert torch.equal(idx, ref_idx) and torch.equal(rgb, ref_rgb), (kind, j, W, H)
+            else:
+                rgb, loss, grad, target = out
+                rid2, rgb2, loss2, grad2 = soft_request(s, pids[j], devs[j].n, devs[j].k, target)
+                assert s.wait(rid2) == tbr.TBR_OK
+                torch.cuda.synchronize()
+                assert torch.equal(rgb, rgb2) and torch.equal(loss, loss2) and torch.equal(grad, grad2), (kind, j, W, H)
+    finally:
+        s.destroy()
